@@ -1,0 +1,583 @@
+"""Plain, slow FP64 CPU oracle of the scattered-wave-function (SWF) Dirac method.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this module.  The product path (the CUDA library and its Python
+binding) never imports it, and this module imports nothing from the product package.
+
+It restates, in numpy float64/complex128 and in the paper's order, what the GPU path computes
+(G. Torgrimsson, "Solving the Dirac equation on a GPU for strong-field processes in
+multidimensional background fields"):
+
+* Sec. II, Eqs. 2-9: dressed Dirac equation (i D-slash - 1) psi = 0 with D_mu = d_mu + i A_mu,
+  split psi = psi_back + psi_scat (Eq. 4), inhomogeneous equation
+  (i D-slash - 1) psi_scat = A-slash psi_back (Eq. 6) with psi_scat(t_out) = 0 (Eq. 7),
+  pair number N(m, n) (Eq. 8) and the inner product (Eq. 9).
+* Sec. II.A: pseudo-spectral spatial derivative (Eq. 10) and a Dormand-Prince 5(4) march from
+  t_out back to t_in, here at a fixed step.
+* Sec. III, Eqs. 11-12: the paper's example fields.
+* Sec. IV, Eqs. 13-36: Breit-Wheeler amplitude M = M_ss + M_bs + M_sb, finite-time part by an
+  integrand appended to the ODE state (Eqs. 33-35) and the analytic past part (Eqs. 24-27) built
+  with the energy projectors of Eq. 23.
+* App. A.5, Eqs. A44-A45: spinor basis u_s(p), v_s(p), R_s;  App. A.6, Eq. A58: photon
+  polarisation basis.
+
+Conventions (the readings are listed in the design doc):
+* metric (+,-,-,-); A_mu covariant; Dirac representation of the gamma matrices;
+  alpha^k = gamma^0 gamma^k, beta = gamma^0.
+* Hamiltonian form of Eq. 6:  d psi_s/dt = -i [ H0 psi_s + V (psi_s + psi_b) ],
+  H0 = alpha.kappa + beta applied per Fourier mode e^{i kappa.x}, V = A_0 + alpha^k A_k.
+* Arrays are (4, nx, ny, nz) complex128 (the paper's (g, n_x, n_y, n_z) layout).  An axis with
+  n = 1 is trivial: the field does not depend on it, its cell width is 1 (the delta function of
+  that direction is stripped) and the marched wave carries a fixed momentum K along it
+  (K = p for an electron wave U, K = -q for a positron wave V).
+* Grid: x_j = -L/2 + j L/n, Fourier modes kappa = 2 pi fftfreq(n, L/n) (Nyquist negative).
+* Discrete Fourier transform with the continuum normalisation
+  psi~(kappa) = dx^d sum_x psi(x) e^{-i kappa.x}.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field as dc_field
+from fractions import Fraction
+
+import numpy as np
+
+# --------------------------------------------------------------------------------------------
+# Dirac algebra (Sec. II; Dirac representation)
+# --------------------------------------------------------------------------------------------
+SIGMA = (
+    np.array([[0, 1], [1, 0]], dtype=complex),
+    np.array([[0, -1j], [1j, 0]], dtype=complex),
+    np.array([[1, 0], [0, -1]], dtype=complex),
+)
+_Z2 = np.zeros((2, 2), dtype=complex)
+GAMMA0 = np.diag([1, 1, -1, -1]).astype(complex)
+GAMMA = (GAMMA0,) + tuple(np.block([[_Z2, s], [-s, _Z2]]) for s in SIGMA)
+ALPHA = tuple(GAMMA0 @ GAMMA[k] for k in (1, 2, 3))
+BETA = GAMMA0
+ETA = np.diag([1.0, -1.0, -1.0, -1.0])
+ID4 = np.eye(4, dtype=complex)
+
+
+def energy(p) -> float:
+    """On-shell energy p_0 = sqrt(1 + |p|^2) (units c = hbar = m = 1, Sec. I)."""
+    p = np.asarray(p, dtype=float)
+    return float(np.sqrt(1.0 + p @ p))
+
+
+def pslash(p) -> np.ndarray:
+    """p-slash = gamma^mu p_mu = gamma^0 p_0 - gamma^k p^k for the on-shell momentum p."""
+    p = np.asarray(p, dtype=float)
+    return GAMMA0 * energy(p) - sum(GAMMA[k + 1] * p[k] for k in range(3))
+
+
+# R_s of Eq. A45: gamma^0 gamma^1 R_s = R_s, i gamma^2 gamma^3 R_s = s R_s, R_r^+ R_s = delta_rs.
+R_SPIN = {
+    +1: np.array([1, 1, 1, 1], dtype=complex) / 2.0,
+    -1: np.array([1, -1, -1, 1], dtype=complex) / 2.0,
+}
+
+
+def _spinor_norm(p) -> float:
+    # sqrt(2 p_0 (p_0 + p_1)) of Eq. A44 with the covariant p_1 = -p^x.
+    return float(np.sqrt(2.0 * energy(p) * (energy(p) - float(p[0]))))
+
+
+def u_spinor(p, s: int) -> np.ndarray:
+    """Electron spinor u_s(p) = (1 + p-slash) R_s / sqrt(2 p_0 (p_0 + p_1))  (Eq. A44)."""
+    return (ID4 + pslash(p)) @ R_SPIN[s] / _spinor_norm(p)
+
+
+def v_spinor(p, s: int) -> np.ndarray:
+    """Positron spinor v_s(p) = (1 - p-slash) R_s / sqrt(2 p_0 (p_0 + p_1))  (Eq. A44)."""
+    return (ID4 - pslash(p)) @ R_SPIN[s] / _spinor_norm(p)
+
+
+def h0_matrix(kappa) -> np.ndarray:
+    """Free Dirac Hamiltonian alpha.kappa + beta for the mode e^{i kappa.x} (Eq. 10 applied)."""
+    kappa = np.asarray(kappa, dtype=float)
+    return sum(ALPHA[k] * kappa[k] for k in range(3)) + BETA
+
+
+def energy_projector(kappa, sign: int) -> np.ndarray:
+    """Projector onto the energy-sign eigenspace of H0(kappa): (1 + sign H0/E)/2.
+
+    sign = +1 picks the part evolving as e^{-iEt}, sign = -1 the part evolving as e^{+iEt}.
+    In the paper's labelling (Eq. 23, modes e^{i Q_j x^j} = e^{-i Q.x}) this is Lambda_{-sign}.
+    """
+    return 0.5 * (ID4 + sign * h0_matrix(kappa) / energy(kappa))
+
+
+def polarisation_basis(e_dir, k):
+    """(eps_perp, eps_par) of Eq. A58 for the field direction e and photon momentum k."""
+    e_dir = np.asarray(e_dir, dtype=float)
+    k = np.asarray(k, dtype=float)
+    perp = np.cross(e_dir, k)
+    perp = perp / np.linalg.norm(perp)
+    par = np.cross(perp, k)
+    par = par / np.linalg.norm(par)
+    return perp, par
+
+
+# --------------------------------------------------------------------------------------------
+# Grid (Sec. II.A)
+# --------------------------------------------------------------------------------------------
+@dataclass
+class Grid:
+    """Periodic box with n[a] points on [-L/2, L/2) per axis; n[a] = 1 marks a trivial axis."""
+
+    n: tuple
+    L: tuple
+
+    def __post_init__(self):
+        self.n = tuple(int(v) for v in self.n)
+        self.L = tuple(float(v) for v in self.L)
+        assert len(self.n) == 3 and len(self.L) == 3
+        self.dx = tuple(self.L[a] / self.n[a] if self.n[a] > 1 else 1.0 for a in range(3))
+        self.x = tuple(
+            (-self.L[a] / 2.0 + np.arange(self.n[a]) * self.dx[a]) if self.n[a] > 1 else np.zeros(1)
+            for a in range(3)
+        )
+        self.kappa = tuple(
+            (2.0 * np.pi * np.fft.fftfreq(self.n[a], self.dx[a])) if self.n[a] > 1 else np.zeros(1)
+            for a in range(3)
+        )
+        self.cell = float(np.prod(self.dx))
+        self.volume = float(np.prod([self.L[a] for a in range(3) if self.n[a] > 1]))
+
+    def coords(self):
+        return np.meshgrid(*self.x, indexing="ij")
+
+    def modes(self, K=(0.0, 0.0, 0.0)):
+        """Mode wave vectors on the grid; trivial axes carry the fixed momentum K."""
+        ks = [self.kappa[a] + (K[a] if self.n[a] == 1 else 0.0) for a in range(3)]
+        return np.meshgrid(*ks, indexing="ij")
+
+
+# --------------------------------------------------------------------------------------------
+# Background fields (Sec. III Eqs. 11-12, and the analytic workloads of the benchmarks)
+# --------------------------------------------------------------------------------------------
+@dataclass
+class Field:
+    """Analytic gauge potential A_mu(t, x) (covariant components).
+
+    kind = "zero":          A = 0.
+    kind = "sauter_gauss":  prm (E, omega, lam): A_1 = (E/omega) sech^2(omega t) exp(-r^2/lam^2),
+                            r^2 over the non-trivial axes (lam = inf gives a field of t alone).
+    kind = "pulse_gauss":   prm (a0, omega0, tau, w, wy): A_1 = a0 sin(omega0 (t - y))
+                            exp(-(t - y)^2/tau^2 - x^2/w^2) [times exp(-y^2/wy^2) when wy > 0].
+    kind = "single_e":      prm (E0, omega, kx, ky, kz): Eq. 11,
+                            A_0 = -(E0/kx) sin(kx x) exp(-(omega t)^2 - (kx x)^2 - (ky y)^2 - (kz z)^2).
+    kind = "double_e":      prm (E0, omega, kx, ky, kz, Dx): Eq. 12, A_0^one(x + Dx) + A_0^one(x - Dx).
+    """
+
+    kind: str
+    prm: tuple = ()
+
+
+def gauge_potential(fld: Field, t: float, X, Y, Z):
+    """Return (A_0, A_1, A_2, A_3) on the coordinate arrays at time t."""
+    zero = np.zeros(np.broadcast(X, Y, Z).shape)
+    if fld.kind == "zero":
+        return zero, zero, zero, zero
+    if fld.kind == "sauter_gauss":
+        E, om, lam = fld.prm[:3]
+        r2 = X * X + Y * Y + Z * Z
+        a1 = (E / om) / np.cosh(om * t) ** 2 * np.exp(-r2 / lam**2)
+        return zero, a1 + zero, zero, zero
+    if fld.kind == "pulse_gauss":
+        a0, om0, tau, w = fld.prm[:4]
+        wy = fld.prm[4] if len(fld.prm) > 4 else 0.0
+        u = t - Y
+        a1 = a0 * np.sin(om0 * u) * np.exp(-(u * u) / tau**2 - (X * X) / w**2)
+        if wy > 0:
+            a1 = a1 * np.exp(-(Y * Y) / wy**2)
+        return zero, a1 + zero, zero, zero
+    if fld.kind in ("single_e", "double_e"):
+        E0, om, kx, ky, kz = fld.prm[:5]
+
+        def one(xs):
+            return -(E0 / kx) * np.sin(kx * xs) * np.exp(
+                -(om * t) ** 2 - (kx * xs) ** 2 - (ky * Y) ** 2 - (kz * Z) ** 2
+            )
+
+        if fld.kind == "single_e":
+            a0 = one(X)
+        else:
+            dxs = fld.prm[5]
+            a0 = one(X + dxs) + one(X - dxs)
+        return a0 + zero, zero, zero, zero
+    raise ValueError(f"unknown field kind {fld.kind!r}")
+
+
+# --------------------------------------------------------------------------------------------
+# Plane-wave backgrounds (Sec. II, Eqs. 3-5)
+# --------------------------------------------------------------------------------------------
+@dataclass
+class Background:
+    """psi_back of Eq. 5: kind "U" -> u_s(p) e^{-i(p_0 t - p.x)}, kind "V" -> v_s(p) e^{+i(p_0 t - p.x)}."""
+
+    kind: str
+    p: tuple
+    s: int
+
+    def spinor(self):
+        return u_spinor(self.p, self.s) if self.kind == "U" else v_spinor(self.p, self.s)
+
+    def offset(self):
+        """Momentum carried along trivial axes: +p for U (mode e^{ipx}), -p for V (mode e^{-ipx})."""
+        p = np.asarray(self.p, dtype=float)
+        return tuple(p) if self.kind == "U" else tuple(-p)
+
+    def values(self, grid: Grid, t: float):
+        X, Y, Z = grid.coords()
+        p = np.asarray(self.p, dtype=float)
+        # trivial axes sit at x = 0: their plane-wave factor is carried by the mode offset
+        px = [p[a] if grid.n[a] > 1 else 0.0 for a in range(3)]
+        phase = energy(self.p) * t - (px[0] * X + px[1] * Y + px[2] * Z)
+        sign = -1.0 if self.kind == "U" else 1.0
+        return self.spinor()[:, None, None, None] * np.exp(1j * sign * phase)[None]
+
+
+# --------------------------------------------------------------------------------------------
+# Right-hand side of Eq. 6 with the spectral derivative of Eq. 10
+# --------------------------------------------------------------------------------------------
+def h0_field(grid: Grid, K=(0.0, 0.0, 0.0)):
+    """H0(kappa) on every grid mode, shape (4, 4, nx, ny, nz)."""
+    KX, KY, KZ = grid.modes(K)
+    return (
+        ALPHA[0][:, :, None, None, None] * KX[None, None]
+        + ALPHA[1][:, :, None, None, None] * KY[None, None]
+        + ALPHA[2][:, :, None, None, None] * KZ[None, None]
+        + BETA[:, :, None, None, None]
+    )
+
+
+def apply_h0(psi, h0):
+    """H0 psi by FFT -> (alpha.kappa + beta) -> inverse FFT (Eq. 10)."""
+    spec = np.fft.fftn(psi, axes=(1, 2, 3))
+    spec = np.einsum("ab...,b...->a...", h0, spec)
+    return np.fft.ifftn(spec, axes=(1, 2, 3))
+
+
+def apply_v(fld: Field, grid: Grid, t: float, phi):
+    """V(t, x) phi with V = A_0 + alpha^k A_k (A covariant)."""
+    X, Y, Z = grid.coords()
+    a = gauge_potential(fld, t, X, Y, Z)
+    out = a[0][None] * phi
+    for k in range(3):
+        if np.any(a[k + 1] != 0.0):
+            out = out + np.einsum("ab,b...->a...", ALPHA[k], a[k + 1][None] * phi)
+    return out
+
+
+def rhs(fld: Field, grid: Grid, bg: Background, h0, t: float, psi_s):
+    """d psi_s/dt = -i [ H0 psi_s + V (psi_s + psi_b) ]  (Eq. 6 in Hamiltonian form)."""
+    return -1j * (apply_h0(psi_s, h0) + apply_v(fld, grid, t, psi_s + bg.values(grid, t)))
+
+
+# --------------------------------------------------------------------------------------------
+# Dormand-Prince 5(4) at a fixed step (Sec. II.A; Dormand & Prince 1980 tableau)
+# --------------------------------------------------------------------------------------------
+_F = Fraction
+DP_C = [_F(0), _F(1, 5), _F(3, 10), _F(4, 5), _F(8, 9), _F(1), _F(1)]
+DP_A = [
+    [],
+    [_F(1, 5)],
+    [_F(3, 40), _F(9, 40)],
+    [_F(44, 45), _F(-56, 15), _F(32, 9)],
+    [_F(19372, 6561), _F(-25360, 2187), _F(64448, 6561), _F(-212, 729)],
+    [_F(9017, 3168), _F(-355, 33), _F(46732, 5247), _F(49, 176), _F(-5103, 18656)],
+    [_F(35, 384), _F(0), _F(500, 1113), _F(125, 192), _F(-2187, 6784), _F(11, 84)],
+]
+DP_B = [_F(35, 384), _F(0), _F(500, 1113), _F(125, 192), _F(-2187, 6784), _F(11, 84), _F(0)]
+DP_BSTAR = [_F(5179, 57600), _F(0), _F(7571, 16695), _F(393, 640), _F(-92097, 339200),
+            _F(187, 2100), _F(1, 40)]
+
+
+def dopri5_march(f, y0, t_out: float, t_in: float, n_steps: int, stage_hook=None):
+    """Fixed-step Dormand-Prince from t_out down to t_in (h < 0), first-same-as-last.
+
+    ``f(t, y)`` is the right-hand side.  ``stage_hook(t_i, Y_i)`` (optional) returns the
+    derivative of an appended quadrature variable at each stage, integrated with the same
+    weights b_i (Eq. 35's Y = (psi, M) form).  Returns (y(t_in), appended integral).
+    """
+    h = (t_in - t_out) / n_steps
+    c = [float(v) for v in DP_C]
+    a = [[float(v) for v in row] for row in DP_A]
+    b = [float(v) for v in DP_B]
+    y = y0.copy()
+    t = t_out
+    k = [f(t, y)] + [None] * 6
+    g = [stage_hook(t, y) if stage_hook else 0.0] + [0.0] * 6
+    acc = 0.0
+    for n in range(n_steps):
+        t = t_out + n * h
+        for i in range(1, 7):
+            yi = y.copy()
+            for j in range(i):
+                if a[i][j] != 0.0:
+                    yi = yi + (h * a[i][j]) * k[j]
+            k[i] = f(t + c[i] * h, yi)
+            if stage_hook is not None:
+                g[i] = stage_hook(t + c[i] * h, yi)
+            if i == 6:
+                y_next = yi  # the 5th-order solution equals the last stage value (a_7j = b_j)
+        if stage_hook is not None:
+            acc = acc + h * sum(b[j] * g[j] for j in range(7))
+        y = y_next
+        k[0] = k[6]
+        g[0] = g[6]
+    return y, acc
+
+
+def march_scattered(fld: Field, grid: Grid, bg: Background, t_in, t_out, n_steps):
+    """psi_scat(t_in) for psi_scat(t_out) = 0 (Eq. 7), marched backward through Eq. 6."""
+    h0 = h0_field(grid, bg.offset())
+    y0 = np.zeros((4,) + grid.n, dtype=complex)
+    y, _ = dopri5_march(lambda t, y: rhs(fld, grid, bg, h0, t, y), y0, t_out, t_in, n_steps)
+    return y
+
+
+# --------------------------------------------------------------------------------------------
+# Overlaps at t_in (Eqs. 8-9) and the Schwinger pair number
+# --------------------------------------------------------------------------------------------
+def inner(psi, phi, grid: Grid):
+    """(psi|phi) = integral d^dx psi^+ phi on the grid (Eq. 9)."""
+    return grid.cell * np.sum(np.conj(psi) * phi)
+
+
+def transform_on_grid(psi, grid: Grid):
+    """psi~(kappa) = dx^d sum_x psi(x) e^{-i kappa.x} on every grid mode (library FFT)."""
+    spec = np.fft.fftn(psi, axes=(1, 2, 3)) * grid.cell
+    KX, KY, KZ = np.meshgrid(*grid.kappa, indexing="ij")
+    # the grid starts at x = -L/2 instead of 0
+    shift = np.exp(1j * (KX * grid.x[0][0] + KY * grid.x[1][0] + KZ * grid.x[2][0]))
+    return spec * np.conj(shift)[None]
+
+
+def transform_at(psi, grid: Grid, kappa):
+    """psi~(kappa) at one arbitrary wave vector by the direct sum (off-grid momenta)."""
+    X, Y, Z = grid.coords()
+    kappa = np.asarray(kappa, dtype=float)
+    kk = [kappa[a] if grid.n[a] > 1 else 0.0 for a in range(3)]
+    ph = np.exp(-1j * (kk[0] * X + kk[1] * Y + kk[2] * Z))
+    return grid.cell * np.sum(psi * ph[None], axis=(1, 2, 3))
+
+
+def c_spectrum(psi_u, grid: Grid, t_in: float, K=(0.0, 0.0, 0.0)):
+    """C(m, (r, q)) = (U_scat^out(m) | V_back(r, q)) at t_in for every grid positron.
+
+    The positron with momentum q occupies the grid mode kappa = -q, so the entry at mode
+    index j belongs to q = -kappa_j.  Shape (2, nx, ny, nz); r = +1 first.
+    """
+    spec = transform_on_grid(psi_u, grid)
+    KX, KY, KZ = grid.modes(K)
+    out = np.zeros((2,) + grid.n, dtype=complex)
+    for idx in np.ndindex(*grid.n):
+        q = -np.array([KX[idx], KY[idx], KZ[idx]])
+        for ir, r in enumerate((+1, -1)):
+            v = v_spinor(q, r)
+            out[(ir,) + idx] = np.exp(1j * energy(q) * t_in) * (np.conj(spec[(slice(None),) + idx]) @ v)
+    return out
+
+
+def overlap_u_scat_v_back(psi_u, grid, t_in, q, r):
+    """(U_scat | V_back(r, q)) at t_in for any q (direct transform at kappa = -q)."""
+    spec = transform_at(psi_u, grid, -np.asarray(q, dtype=float))
+    return np.exp(1j * energy(q) * t_in) * (np.conj(spec) @ v_spinor(q, r))
+
+
+def overlap_u_back_v_scat(psi_v, grid, t_in, p, s):
+    """A(m, n) = (U_back(s, p) | V_scat) at t_in for any p (direct transform at kappa = p)."""
+    spec = transform_at(psi_v, grid, np.asarray(p, dtype=float))
+    return np.exp(1j * energy(p) * t_in) * (np.conj(u_spinor(p, s)) @ spec)
+
+
+def pair_number(psi_u, psi_v, grid: Grid, t_in, p, s, q, r, K_u=(0, 0, 0), K_v=(0, 0, 0)):
+    """Both lines of Eq. 8 for electron m = (s, p), positron n = (r, q).
+
+    Line 1: A + B, A = (U_back m | V_scat n), B = sum_i (U_scat m | U_back i)(U_back i | V_scat n).
+    Line 2: C + D, C = (U_scat m | V_back n), D = sum_i (U_scat m | V_back i)(V_back i | V_scat n).
+    The sum over i = (s', Q) runs over both spins and every grid mode with the weight L^{-d}
+    (a resolution of the identity on the grid).  Returns dict with A, B, C, D and both |.|^2.
+    """
+    su = transform_on_grid(psi_u, grid)
+    sv = transform_on_grid(psi_v, grid)
+    KXu, KYu, KZu = grid.modes(K_u)
+    KXv, KYv, KZv = grid.modes(K_v)
+    A = overlap_u_back_v_scat(psi_v, grid, t_in, p, s)
+    C = overlap_u_scat_v_back(psi_u, grid, t_in, q, r)
+    B = 0.0 + 0.0j
+    D = 0.0 + 0.0j
+    for idx in np.ndindex(*grid.n):
+        sl = (slice(None),) + idx
+        Q = np.array([KXu[idx], KYu[idx], KZu[idx]])   # U_back(s', Q) lives in mode Q
+        for sp in (+1, -1):
+            u = u_spinor(Q, sp)
+            e = energy(Q)
+            uu = np.exp(-1j * e * t_in) * (np.conj(su[sl]) @ u)     # (U_scat | U_back i)
+            uv = np.exp(1j * e * t_in) * (np.conj(u) @ sv[sl])      # (U_back i | V_scat)
+            B += uu * uv
+        Qv = -np.array([KXv[idx], KYv[idx], KZv[idx]])  # V_back(s', Q) lives in mode -Q
+        for sp in (+1, -1):
+            v = v_spinor(Qv, sp)
+            e = energy(Qv)
+            cu = np.exp(1j * e * t_in) * (np.conj(su[sl]) @ v)      # (U_scat | V_back i)
+            wv = np.exp(-1j * e * t_in) * (np.conj(v) @ sv[sl])     # (V_back i | V_scat)
+            D += cu * wv
+    B /= grid.volume
+    D /= grid.volume
+    return {"A": A, "B": B, "C": C, "D": D,
+            "N_line1": abs(A + B) ** 2, "N_line2": abs(C + D) ** 2}
+
+
+# --------------------------------------------------------------------------------------------
+# Nonlinear Breit-Wheeler (Sec. IV)
+# --------------------------------------------------------------------------------------------
+@dataclass
+class Photon:
+    """Plane-wave photon e^{-ikx} with polarisation eps_mu = (0, eps) (Eq. 13)."""
+
+    k: tuple
+    eps: tuple
+
+    def k0(self):
+        return float(np.linalg.norm(self.k))
+
+    def alpha_eps(self):
+        # gamma^0 eps-slash = gamma^0 gamma^k eps_k = alpha . eps
+        return sum(ALPHA[a] * self.eps[a] for a in range(3))
+
+
+def bw_integrand(grid, photon, bg_u, bg_v, t, psi_u, psi_v):
+    """dM_{a,b}/dt of Eq. 33's integrand: dx^d sum_x U_a^+ (alpha.eps) V_b e^{-ikx}.
+
+    Returns the three terms (ss, bs, sb) as a complex array of length 3.
+    """
+    X, Y, Z = grid.coords()
+    k = np.asarray(photon.k, dtype=float)
+    kk = [k[a] if grid.n[a] > 1 else 0.0 for a in range(3)]
+    ph = np.exp(-1j * photon.k0() * t + 1j * (kk[0] * X + kk[1] * Y + kk[2] * Z))
+    ae = photon.alpha_eps()
+    ub = bg_u.values(grid, t)
+    vb = bg_v.values(grid, t)
+
+    def term(uu, vv):
+        return grid.cell * np.sum(np.einsum("a...,ab,b...->...", np.conj(uu), ae, vv) * ph)
+
+    return np.array([term(psi_u, psi_v), term(ub, psi_v), term(psi_u, vb)])
+
+
+def bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps):
+    """March (U_scat, V_scat) together with M appended (Eqs. 33-35).
+
+    The appended variable obeys dM/dt = M-dot(t), M(t_out) = 0, so the finite-time part of
+    Eq. 17 is M_finite = integral_{t_in}^{t_out} M-dot dt = -M(t_in).
+    Returns (U_scat(t_in), V_scat(t_in), M_finite[3]).
+    """
+    h0u = h0_field(grid, bg_u.offset())
+    h0v = h0_field(grid, bg_v.offset())
+    shape = (4,) + grid.n
+
+    def f(t, y):
+        return np.stack([rhs(fld, grid, bg_u, h0u, t, y[0]), rhs(fld, grid, bg_v, h0v, t, y[1])])
+
+    def g(t, y):
+        return bw_integrand(grid, photon, bg_u, bg_v, t, y[0], y[1])
+
+    y0 = np.zeros((2,) + shape, dtype=complex)
+    y, m = dopri5_march(f, y0, t_out, t_in, n_steps, stage_hook=g)
+    return y[0], y[1], -m
+
+
+def bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in):
+    """Analytic t < t_in parts of Eqs. 25-27 with the energy projectors of Eq. 23.
+
+    For t < t_in every grid mode of U_scat, V_scat evolves freely, psi~(t, kappa) =
+    sum_sigma P_sigma(kappa) psi~(t_in, kappa) e^{-i sigma E (t - t_in)}, and the time integral
+    from -infinity to t_in of e^{i Omega (t - t_in)} is 1/(i Omega).  The photon momentum k must
+    be a grid mode (the V mode is the U mode minus k).  Returns (ss, bs, sb).
+    """
+    k = np.asarray(photon.k, dtype=float)
+    k0 = photon.k0()
+    ae = photon.alpha_eps()
+    Ku = bg_u.offset()
+    Kv = bg_v.offset()
+    su = transform_on_grid(psi_u, grid)
+    sv = transform_on_grid(psi_v, grid)
+    KXu, KYu, KZu = grid.modes(Ku)
+    KXv, KYv, KZv = grid.modes(Kv)
+    # integer mode shift of k along the non-trivial axes
+    shift = []
+    for a in range(3):
+        if grid.n[a] > 1:
+            m = k[a] * grid.L[a] / (2.0 * np.pi)
+            assert abs(m - round(m)) < 1e-9, "photon momentum must be a grid mode"
+            shift.append(int(round(m)))
+        else:
+            shift.append(0)
+    ss = 0.0 + 0.0j
+    for idx in np.ndindex(*grid.n):
+        jdx = tuple((idx[a] - shift[a]) % grid.n[a] for a in range(3))  # mode kappa - k
+        ku = np.array([KXu[idx], KYu[idx], KZu[idx]])
+        kv = np.array([KXv[jdx], KYv[jdx], KZv[jdx]])
+        eu, ev = energy(ku), energy(kv)
+        uu = su[(slice(None),) + idx]
+        vv = sv[(slice(None),) + jdx]
+        for sg in (+1, -1):
+            pu = energy_projector(ku, sg) @ uu
+            for sgp in (+1, -1):
+                pv = energy_projector(kv, sgp) @ vv
+                om = sg * eu - sgp * ev - k0
+                ss += (np.conj(pu) @ ae @ pv) / (1j * om)
+    ss = ss * np.exp(-1j * k0 * t_in) / grid.volume
+    # back, scat: U_back = u(p) e^{-i p0 t} in mode p, so V_scat is needed at mode p - k
+    p = np.asarray(bg_u.p, dtype=float)
+    u = bg_u.spinor()
+    kv = p - k
+    vv = transform_at(psi_v, grid, kv)
+    bs = 0.0 + 0.0j
+    for sgp in (+1, -1):
+        pv = energy_projector(kv, sgp) @ vv
+        om = energy(p) - sgp * energy(kv) - k0
+        bs += (np.conj(u) @ ae @ pv) / (1j * om)
+    bs = bs * np.exp(1j * energy(p) * t_in) * np.exp(-1j * k0 * t_in)
+    # scat, back: V_back = v(q) e^{+i q0 t} in mode -q, so U_scat is needed at mode k - q
+    q = np.asarray(bg_v.p, dtype=float)
+    v = bg_v.spinor()
+    ku = k - q
+    uu = transform_at(psi_u, grid, ku)
+    sb = 0.0 + 0.0j
+    for sg in (+1, -1):
+        pu = energy_projector(ku, sg) @ uu
+        om = sg * energy(ku) + energy(q) - k0
+        sb += (np.conj(pu) @ ae @ v) / (1j * om)
+    sb = sb * np.exp(1j * energy(q) * t_in) * np.exp(-1j * k0 * t_in)
+    return np.array([ss, bs, sb])
+
+
+def bw_amplitude(fld, grid, p, s, q, r, photon, t_in, t_out, n_steps):
+    """M = M_ss + M_bs + M_sb (Eq. 13), each the sum of its finite (Eq. 17) and past part."""
+    bg_u = Background("U", tuple(p), s)
+    bg_v = Background("V", tuple(q), r)
+    psi_u, psi_v, m_fin = bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps)
+    m_past = bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in)
+    return {"finite": m_fin, "past": m_past, "terms": m_fin + m_past,
+            "M": complex(np.sum(m_fin + m_past)), "psi_u": psi_u, "psi_v": psi_v}
+
+
+# --------------------------------------------------------------------------------------------
+# Convenience drivers used by tests and by the CPU baseline
+# --------------------------------------------------------------------------------------------
+@dataclass
+class SchwingerResult:
+    psi_u: np.ndarray
+    spectrum: np.ndarray = dc_field(default=None)
+
+
+def schwinger_spectrum(fld, grid, p, s, t_in, t_out, n_steps):
+    """One electron march and its C-spectrum |C(m, (r, q))|^2 over all grid positrons."""
+    bg = Background("U", tuple(p), s)
+    psi = march_scattered(fld, grid, bg, t_in, t_out, n_steps)
+    C = c_spectrum(psi, grid, t_in, bg.offset())
+    return psi, C
