@@ -1,0 +1,276 @@
+"""Benchmark of the SWF hot path on GB300.
+
+One step = one solve of the batched (2+1)D Schwinger workload through the C ABI: 128 instances
+(8 x 8 electron momenta in [-1, 1]^2, both spins, E drawn per instance) on a 256^2 grid, box 40,
+1000 fixed Dormand-Prince steps from t = 20 back to t = -20 in complex64, then the FP64
+C-spectrum |C(m, (r, q))|^2 over every grid positron (2 * 256^2 probabilities per instance).
+
+Metric: spinor site-updates per second (one grid point of one instance advanced one full step);
+the pair probabilities per second are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank solves its own copy of the batch (weak scaling, no collective
+on the data path); value = all ranks' site-updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spinor site-updates/s & pair probabilities/s per GB300 at rel.err <=1e-4 vs FP64"
+UNIT = "site-updates/s"
+WORKLOAD = "schwinger_batched: (2+1)D Schwinger, 256x256 grid, box 40, 128 instances, 1000 DP5 steps, c64 march + FP64 C-spectrum"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline arm)
+def oracle_sample(n_rk_steps=40):
+    """Times the FP64 oracle on one instance of the workload for a bounded number of steps
+    plus its C-spectrum, and scales to the metric's unit."""
+    import numpy as np
+    from oracle import swf_oracle as O
+    from paper_2512_16889_gb300 import workloads as W
+    from tests import oracle_adapter as OA
+
+    d = W.schwinger_batched()[0]
+    g, f, bg = OA.grid(d), OA.field(d), OA.background(d, 0)
+    h = (d["t_in"] - d["t_out"]) / d["n_steps"]
+    t0 = time.perf_counter()
+    psi = O.march_scattered(f, g, bg, d["t_out"] + n_rk_steps * h, d["t_out"], n_rk_steps)
+    t_march = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.c_spectrum(psi, g, d["t_in"])
+    t_proj = time.perf_counter() - t0
+    N = int(np.prod(d["n"]))
+    su_per_s = N * n_rk_steps / t_march
+    t_full = t_march * d["n_steps"] / n_rk_steps + t_proj
+    return {"value": su_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 of 128 instances, {n_rk_steps} of {d['n_steps']} steps + its C-spectrum "
+                      f"({t_march + t_proj:.1f} s), numpy FP64, single-threaded FFTs",
+            "probabilities_per_s": 2 * N / t_full}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    times = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        base = oracle_sample(n_rk_steps=10)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": base["sample"]},
+            "cpu_baseline": {"value": base["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" == r[5 + i] or r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2512_16889_gb300 import build, swf
+    from paper_2512_16889_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ds = W.schwinger_batched()
+    insts = [swf.from_workload(d) for d in ds]
+    arr = swf.instance_array(insts)
+    prec = swf.C64
+    n_inst = len(ds)
+    site_updates = sum(int(np.prod(d["n"])) * d["n_steps"] for d in ds)
+    probs = sum(2 * int(np.prod(d["n"])) for d in ds)
+    ctx = swf.Context(local)
+    stream = torch.cuda.current_stream()
+    res_dev = torch.empty(n_inst * swf.C.sizeof(swf.Result), dtype=torch.uint8, device="cuda")
+    spec_dev = torch.empty(probs, dtype=torch.float64, device="cuda")
+
+    def step():
+        ctx.solve_dev(None, res_dev, spec_dev, swf.SCHWINGER, prec, stream=stream, arr=arr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_read()  # clear counters
+    ctx.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ctx.profile_enable(False)
+    prof, launches = ctx.profile_read()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * site_updates * args.steps / (ms_max / 1e3)
+
+    # end to end through the host-pointer API (copies of inputs and outputs included)
+    e2e_steps = max(1, min(args.steps, 2))
+    ctx.solve(insts, swf.SCHWINGER, prec)  # warm the host path once
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.solve(insts, swf.SCHWINGER, prec)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_value = world * site_updates / float(tt.item())
+
+    # roofline of the march kernels (algorithmic 14 S bytes per site-update, S = 32 B in c64)
+    hbm, peak_kind = peaks()
+    march = {k: v for k, v in prof.items() if k in ("k_first", "k_mid", "k_last", "k_fused")}
+    march_ms = sum(v[0] for v in march.values()) / args.steps
+    march_launches = sum(v[1] for v in march.values())
+    dominant = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
+    S = 32.0
+    alg_bytes = 14.0 * S * site_updates
+    achieved = alg_bytes / (march_ms / 1e3) / 1e9 if march_ms > 0 else None
+    roof = {"bound": "hbm", "kernel": "+".join(sorted(march)) + " (the march, per solve)",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if achieved else None, "traffic": None,
+            "peak_kind": peak_kind + " (burst copy)", "launches_per_step": march_launches / args.steps,
+            "algorithmic_bytes_per_step": alg_bytes}
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": "256x256", "instances": n_inst, "n_steps": 1000,
+                           "precision": "complex64 march, FP64 projections",
+                           "l2": "inputs larger than L2 (2.3 GB working set per GPU)"},
+                "probabilities_per_s": world * probs * args.steps / (ms_max / 1e3),
+                "roofline": roof, "kernels": kernels, "dominant_kernel": dominant,
+                "gpu_launches": int(launches),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_inst * swf.C.sizeof(swf.Instance),
+                        "d2h_bytes_per_step": n_inst * swf.C.sizeof(swf.Result) + probs * 8},
+                "clocks": clk}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample()
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * swf.h -- C ABI of the GB300 (sm_103a) scattered-wave-function (SWF) Dirac solver.
+ *
+ * The method (G. Torgrimsson, "Solving the Dirac equation on a GPU for strong-field processes
+ * in multidimensional background fields"):
+ *   Sec. II, Eq. 6:  (i D-slash - 1) psi_scat = A-slash psi_back, D_mu = d_mu + i A_mu (Eq. 2),
+ *                    psi_scat(t_out) = 0 (Eq. 7), marched back to t_in.
+ *   Sec. II.A:       spatial derivatives by FFT (Eq. 10); Dormand-Prince 5(4) in time.
+ *   Sec. II, Eq. 8:  pair number N(m, n) from overlaps (Eq. 9) at t_in.
+ *   Sec. IV:         Breit-Wheeler amplitude M = M_ss + M_bs + M_sb (Eqs. 13-14), finite-time
+ *                    part accumulated during the march (Eqs. 17, 33-35), past part at t_in
+ *                    (Eqs. 24-27) with the energy projectors of Eq. 23.
+ *
+ * Conventions shared by every entry point:
+ *   - units c = hbar = m = 1; metric (+,-,-,-); A_mu covariant; Dirac representation.
+ *   - Hamiltonian form of Eq. 6:  d psi_s/dt = -i [ H0 psi_s + V (psi_s + psi_b) ],
+ *     H0 = alpha.kappa + beta per Fourier mode e^{i kappa.x}, V = A_0 + alpha^k A_k.
+ *   - spinors u_s(p) = (1 + p-slash) R_s / sqrt(2 p0 (p0 - p^x)), v_s(p) = (1 - p-slash) R_s / ...
+ *     with R_+ = (1,1,1,1)/2, R_- = (1,-1,-1,1)/2 (Eqs. A44-A45); spin s = +1 or -1.
+ *   - grid: n[a] points on [-L[a]/2, L[a]/2) per axis a = x, y, z; mode kappa_j =
+ *     2 pi j'/L with j' = j for j < (n+1)/2 and j - n otherwise.  n[a] = 1 marks a trivial axis:
+ *     the field does not depend on it, its delta function is stripped, and the marched wave
+ *     carries its background's momentum along it.
+ *   - a spinor field on the grid is stored planar per component, x fastest:
+ *     element (c, z, y, x) at index ((c*nz + z)*ny + y)*nx + x, complex (re, im) interleaved,
+ *     complex64 (8 B) or complex128 (16 B) per the precision.
+ *
+ * Ownership and errors: the caller owns every pointer it passes; the library owns its
+ * workspace inside swf_ctx.  Every entry point returns a status, never aborts or traps, leaves
+ * outputs untouched on a validation error, and records a message for swf_last_error().
+ * Device-pointer entry points ("_dev") are asynchronous on the given stream (NULL = the
+ * context's stream); the host-pointer entry point solve_swf is synchronous.
+ */
+#ifndef SWF_H
+#define SWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SWF_OK = 0,
+  SWF_EINVAL = 1,       /* invalid argument (message says which) */
+  SWF_ENOMEM = 2,       /* device allocation failed or exceeds the context's workspace limit */
+  SWF_ECUDA = 3,        /* a CUDA runtime call failed */
+  SWF_ENUMERIC = 4,     /* a non-finite value appeared in the march */
+  SWF_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+  SWF_EUNSUPPORTED = 6  /* valid request outside what this build implements */
+} swf_status;
+
+typedef enum { SWF_SCHWINGER = 0, SWF_BREIT_WHEELER = 1 } swf_process;
+
+/* March precision.  SWF_C128: complex128 march and FP64 everywhere.  SWF_C64: complex64
+ * march with FP32 accumulation; phases of the plane waves are formed in FP64 and rounded once;
+ * the projections at t_in (FFT and spinor overlaps) run in FP64. */
+typedef enum { SWF_C128 = 0, SWF_C64 = 1 } swf_precision;
+
+/* Background field kinds; prm[] holds the parameters in the order listed. */
+typedef enum {
+  SWF_FIELD_ZERO = 0,          /* A = 0 */
+  SWF_FIELD_SAUTER_GAUSS = 1,  /* {E, omega, lambda}: A_1 = (E/omega) sech^2(omega t) exp(-r^2/lambda^2),
+                                  r over the non-trivial axes; lambda <= 0 means no spatial envelope */
+  SWF_FIELD_PULSE_GAUSS = 2,   /* {a0, omega0, tau, w, wy}: A_1 = a0 sin(omega0 (t - y))
+                                  exp(-(t-y)^2/tau^2 - x^2/w^2) [* exp(-y^2/wy^2) if wy > 0] */
+  SWF_FIELD_SINGLE_E = 3,      /* {E0, omega, kx, ky, kz}: Eq. 11, A_0 = -(E0/kx) sin(kx x)
+                                  exp(-(omega t)^2 - (kx x)^2 - (ky y)^2 - (kz z)^2) */
+  SWF_FIELD_DOUBLE_E = 4       /* {E0, omega, kx, ky, kz, Dx}: Eq. 12, A_0^one(x+Dx) + A_0^one(x-Dx) */
+} swf_field_kind;
+
+typedef struct {
+  int32_t kind;     /* swf_field_kind */
+  int32_t reserved;
+  double prm[8];
+} swf_field;
+
+typedef struct {
+  int32_t n[3];     /* points per axis (1 = trivial axis); each n > 1 must factor into 2, 3, 5 and be <= 512 */
+  int32_t n_steps;  /* fixed Dormand-Prince steps from t_out down to t_in */
+  double L[3];      /* box lengths (ignored on trivial axes) */
+  double t_in, t_out;
+} swf_grid;
+
+/* One problem instance.  Schwinger: an electron m = (s, p) (one U march) and optionally a
+ * positron n = (r, q) (one V march when SWF_WANT_FULL_N).  Breit-Wheeler: electron (s, p),
+ * positron (r, q) and photon (k, eps); U and V are marched together. */
+typedef struct {
+  swf_field field;
+  swf_grid grid;
+  double p[3]; int32_t s;
+  int32_t r;   double q[3];
+  double k[3]; double eps[3];  /* photon momentum (a grid mode) and polarisation eps_mu = (0, eps) */
+  int32_t flags;               /* SWF_WANT_* */
+  int32_t reserved;
+} swf_instance;
+
+#define SWF_WANT_SPECTRUM 1  /* Schwinger: |C(m,(r,q))|^2 for every grid positron q */
+#define SWF_WANT_FULL_N   2  /* Schwinger: march V too and return both lines of Eq. 8 */
+
+/* Per-instance scalar results (complex values as (re, im) pairs).
+ * Schwinger: amp = {C(m,n), D(m,n), A(m,n), B(m,n)} for the listed positron n = (r, q);
+ *            prob = {|C + D|^2, |A + B|^2} (without SWF_WANT_FULL_N: {|C|^2, 0}, D = A = B = 0).
+ * Breit-Wheeler: amp = {M_ss, M_bs, M_sb, M}, prob = {|M|^2, 0}.
+ * diag = {||psi_U(t_in)||^2, ||psi_V(t_in)||^2} (grid inner product, Eq. 9). */
+typedef struct {
+  double amp[8];
+  double prob[2];
+  double diag[2];
+} swf_result;
+
+typedef struct swf_ctx swf_ctx;
+
+/* Create a context on CUDA device `device` with its own stream.  Returns SWF_ECUDA if the
+ * device is absent.  *ctx is NULL on failure. */
+swf_status swf_create(swf_ctx** ctx, int device);
+
+/* Release the context and all its device memory.  NULL is accepted. */
+swf_status swf_destroy(swf_ctx* ctx);
+
+/* Thread-local message for the last non-OK status of this thread ("" if none). */
+const char* swf_last_error(void);
+
+/* Highest-level call: solve n_inst instances (host descriptors) and write host outputs.
+ * results:  n_inst swf_result (required).
+ * spectrum: optional (NULL = not wanted); for Schwinger instances with SWF_WANT_SPECTRUM,
+ *           |C(m,(r,q))|^2 for r = +1, -1 and every grid mode j, laid out per instance as
+ *           [2][nz][ny][nx] doubles, instances back to back in input order (instances without
+ *           the flag take no room).  The positron at mode index j has q = -kappa_j.
+ * Synchronous: returns after the results are in host memory. */
+swf_status solve_swf(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf_process process,
+                     swf_precision prec, swf_result* results, double* spectrum);
+
+/* Same as solve_swf with device output buffers (results: n_inst swf_result in device memory;
+ * spectrum as above, in device memory), asynchronous on `stream`. */
+swf_status solve_swf_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf_process process,
+                         swf_precision prec, swf_result* results_dev, double* spectrum_dev,
+                         void* stream);
+
+/* Lower-level: march n_inst instances' electron (bg = 0, background u_s(p) e^{-ipx}) or
+ * positron (bg = 1, background v_r(q) e^{+iqx}) scattered wave from psi_s(t_out) = 0 to t_in
+ * (Eqs. 6-7) and write psi_s(t_in) to psi_out_dev: per instance 4*nx*ny*nz complex values in
+ * the march precision, instances back to back.  All instances must share the grid. */
+swf_status swf_march_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst, int bg,
+                         swf_precision prec, void* psi_out_dev, void* stream);
+
+/* Lower-level: one evaluation of the right-hand side of Eq. 6,
+ * out = -i [ H0 psi + V(t) (psi + psi_b(t)) ], for one instance and background bg (0 = U,
+ * 1 = V), psi and out in the march precision and the layout above (device memory, may not
+ * alias).  Uses a workspace of one spinor field held by the context. */
+swf_status swf_rhs_dev(swf_ctx* ctx, const swf_instance* inst, int bg, swf_precision prec,
+                       double t, const void* psi_dev, void* out_dev, void* stream);
+
+/* Lower-level: the C-spectrum of Eq. 8's line 2 first term for n_inst electron waves at t_in:
+ * C(m,(r,q)) = (U_scat(m) | V_back(r,q)) for every grid mode, in FP64.  psi_dev as written by
+ * swf_march_dev (march precision); c_out_dev receives complex128 [inst][2][nz][ny][nx],
+ * prob_out_dev (optional) the |C|^2 doubles in the same layout. */
+swf_status swf_spectrum_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst,
+                            swf_precision prec, const void* psi_dev, double* c_out_dev,
+                            double* prob_out_dev, void* stream);
+
+/* Kernel timing hook (tracing).  When enabled, the context records a CUDA event pair on the
+ * launching stream around every kernel it launches and accumulates the elapsed time per kernel
+ * family.  swf_profile_read synchronises the context's events and returns up to max_entries
+ * families: names (max_entries * 32 chars, NUL-terminated), total milliseconds and launch counts;
+ * it then clears the accumulators.  *total_launches (optional) receives every kernel launched by
+ * the context since the previous read, timed or not. */
+swf_status swf_profile_enable(swf_ctx* ctx, int on);
+swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* total_ms,
+                            long long* launches, int* n_entries, long long* total_launches);
+
+/* Caps the context's device workspace (bytes; 0 = no cap).  Requests that need more return
+ * SWF_ENOMEM before touching the device. */
+swf_status swf_set_workspace_limit(swf_ctx* ctx, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWF_H */

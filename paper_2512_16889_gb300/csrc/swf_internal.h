@@ -1,0 +1,156 @@
+// Internal declarations shared by the SWF library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/swf.h"
+#include "swf_common.cuh"
+
+namespace swf {
+
+// One marched 4-spinor field: the background plane wave and the gauge field it sees.
+struct FieldDesc {
+  int kind;        // swf_field_kind
+  int acomp;       // index mu of the one non-zero A_mu (-1 for the zero field)
+  double prm[8];
+  double w[8];     // background spinor u_s(p) or v_r(q): (re, im) x 4
+  double e0;       // background energy p0 (or q0)
+  double tsign;    // time phase exp(i tsign e0 t): -1 for U, +1 for V
+  double K[3];     // momentum carried along trivial axes
+  double pmom[3];  // spatial phase exp(i pmom.x): p for U, -q for V
+};
+
+// Grid of one group of instances (all instances of a launch share it).
+struct GridDesc {
+  int n[3];
+  double L[3];
+  int N;        // n0 n1 n2
+  double dx[3]; // cell widths (1 on trivial axes)
+  double x0[3]; // first coordinate (-L/2, or 0 on trivial axes)
+};
+
+GridDesc make_grid(const swf_grid& g);
+
+// Spinors of Eq. A44 in the Dirac representation, FP64, host and device:
+// u_s(p) = (1 + p-slash) R_s / sqrt(2 p0 (p0 - p^x)), v_s(p) = (1 - p-slash) R_s / (same),
+// with p-slash = [[p0, -sigma.p], [sigma.p, -p0]], R_+ = (1,1,1,1)/2, R_- = (1,-1,-1,1)/2.
+// out = (re, im) of the four components.
+__host__ __device__ inline void spinor_uv(const double p[3], int s, bool is_v, double out[8]) {
+  const double p0 = sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  const double nrm = 1.0 / sqrt(2.0 * p0 * (p0 - p[0]));
+  const double ru0 = 0.5, ru1 = s > 0 ? 0.5 : -0.5;  // upper half of R_s
+  const double rl0 = s > 0 ? 0.5 : -0.5, rl1 = 0.5;  // lower half of R_s
+  // sigma.p applied to a real 2-vector (a, b): (pz a + px b - i py b, px a - pz b + i py a)
+  const double spl_re0 = p[2] * rl0 + p[0] * rl1, spl_im0 = -p[1] * rl1;
+  const double spl_re1 = p[0] * rl0 - p[2] * rl1, spl_im1 = p[1] * rl0;
+  const double spu_re0 = p[2] * ru0 + p[0] * ru1, spu_im0 = -p[1] * ru1;
+  const double spu_re1 = p[0] * ru0 - p[2] * ru1, spu_im1 = p[1] * ru0;
+  const double sg = is_v ? -1.0 : 1.0;  // u: 1 + p-slash, v: 1 - p-slash
+  // upper = (1 + sg p0) R_u - sg sigma.p R_l ; lower = sg sigma.p R_u + (1 - sg p0) R_l
+  out[0] = ((1.0 + sg * p0) * ru0 - sg * spl_re0) * nrm;
+  out[1] = (-sg * spl_im0) * nrm;
+  out[2] = ((1.0 + sg * p0) * ru1 - sg * spl_re1) * nrm;
+  out[3] = (-sg * spl_im1) * nrm;
+  out[4] = (sg * spu_re0 + (1.0 - sg * p0) * rl0) * nrm;
+  out[5] = (sg * spu_im0) * nrm;
+  out[6] = (sg * spu_re1 + (1.0 - sg * p0) * rl1) * nrm;
+  out[7] = (sg * spu_im1) * nrm;
+}
+__host__ __device__ inline double energy3(const double p[3]) { return sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]); }
+__host__ __device__ inline double mode_kappa(int j, int n, double L) {
+  if (n <= 1) return 0.0;
+  int jp = (j < (n + 1) / 2) ? j : j - n;
+  return 6.283185307179586476925286766559 * (double)jp / L;
+}
+
+FieldDesc make_field_desc(const swf_instance& in, int bg);
+
+// Builds the radix plan (radices 4, 2, 3, 5) of a length; false if n has another factor.
+bool make_radix_plan(int n, RadixPlan* pl);
+
+// Device workspace: a growable pool of named buffers owned by the context.
+struct Workspace {
+  std::map<std::string, std::pair<void*, size_t>> bufs;
+  size_t total = 0;
+  size_t limit = 0;  // 0 = no cap
+};
+
+struct TwiddleCache {
+  std::map<std::pair<int, int>, void*> tables;  // (n, is_double) -> device table
+};
+
+}  // namespace swf
+
+namespace swf {
+// Per-context kernel timing: event pairs recorded around launches, reduced on read.
+struct Profiler {
+  bool on = false;
+  long long launches = 0;                                 // every launch, timed or not
+  std::vector<cudaEvent_t> pool;                          // reusable events
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> marks;              // (family, first event index)
+  std::vector<std::string> families;
+  std::map<std::string, std::pair<double, long long>> acc;  // family -> (ms, launches)
+};
+}  // namespace swf
+
+struct swf_ctx {
+  int device;
+  cudaStream_t stream;
+  swf::Workspace ws;
+  swf::TwiddleCache tw;
+  swf::Profiler prof;
+};
+
+namespace swf {
+
+void set_error(const std::string& msg);
+
+// Kernel timing: call prof_begin before a launch and prof_end after it (same stream).
+int prof_begin(swf_ctx* ctx, const char* family, cudaStream_t st);
+void prof_end(swf_ctx* ctx, int mark, cudaStream_t st);
+struct ProfScope {
+  swf_ctx* ctx;
+  int mark;
+  cudaStream_t st;
+  ProfScope(swf_ctx* c, const char* fam, cudaStream_t s) : ctx(c), mark(prof_begin(c, fam, s)), st(s) {}
+  ~ProfScope() { prof_end(ctx, mark, st); }
+};
+swf_status cuda_status(cudaError_t e, const char* what);
+
+// Returns a device buffer of at least `bytes` under `name` (grows, never shrinks).
+swf_status ws_get(swf_ctx* ctx, const std::string& name, size_t bytes, void** ptr);
+// Device table exp(-2 pi i m/n), m < n, in float2 (is_double = 0) or double2.
+swf_status twiddles(swf_ctx* ctx, int n, int is_double, const void** ptr);
+
+// ---- march (swf_march.cu)
+// March n_f fields (all on grid g) from psi(t_out) = 0 to t_in; psi_out receives psi(t_in)
+// in the march precision [F][4][N].  fd_host: n_f descriptors.
+swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
+                        int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
+                        cudaStream_t st);
+swf_status rhs_eval(swf_ctx* ctx, const GridDesc& g, const FieldDesc& fd, swf_precision prec,
+                    double t, const void* psi, void* out, cudaStream_t st);
+
+// ---- projections (swf_project.cu)
+// psi [F][4][N] (march precision) -> FP64 transform on every grid mode, with the continuum
+// normalisation dx^d and the grid-origin phase: spec [F][4][N] double2.
+swf_status transform_fields(swf_ctx* ctx, const GridDesc& g, int n_f, swf_precision prec,
+                            const void* psi, double2* spec, cudaStream_t st);
+// C-spectrum from electron-wave transforms: c_out [F][2][N] double2, prob [F][2][N].
+swf_status c_spectrum(swf_ctx* ctx, const GridDesc& g, int n_f, const FieldDesc* fd_host,
+                      double t_in, const double2* spec, double2* c_out, double* prob,
+                      cudaStream_t st);
+// Direct FP64 transform of each field at one wave vector per field: out [F][4] double2.
+swf_status transform_at(swf_ctx* ctx, const GridDesc& g, int n_f, swf_precision prec,
+                        const void* psi, const double* kappa_host /* [F][3] */, double2* out,
+                        cudaStream_t st);
+// ||psi_f||^2 (grid inner product) per field: out [F].
+swf_status field_norms(swf_ctx* ctx, const GridDesc& g, int n_f, swf_precision prec,
+                       const void* psi, double* out, cudaStream_t st);
+
+}  // namespace swf

@@ -1,0 +1,552 @@
+// Time march of the scattered wave (Sec. II, Eq. 6; Sec. II.A) on the GPU.
+//
+// Right-hand side, per field f and stage value Y:
+//     k = -i [ H0 Y + V(t, x) (Y + psi_b(t, x)) ]
+// with H0 applied per Fourier mode (Eq. 10).  One evaluation is a chain of line passes over
+// the planar state [f][4][z][y][x]:
+//   first pass (x lines):  Y = y + h sum_j a_ij k_j (stage combine, Dormand-Prince), the local
+//                          term Z = -i V (Y + psi_b) stashed in the output slot, forward x-FFT;
+//   middle passes (y, z):  forward FFT along the axis; on the last axis -i H0(kappa)/N and the
+//                          inverse FFT;
+//   last pass (x lines):   inverse x-FFT and k = (that) + Z.
+// Gauge field and background are analytic and evaluated on the fly from per-field 1D tables
+// (every field kind is a product of a time factor and one factor per axis).
+#include <cstdio>
+#include <cstring>
+
+#include "swf_internal.h"
+
+namespace swf {
+
+// ---------------------------------------------------------------- Dormand-Prince 5(4) tableau
+// Dormand & Prince (1980); first-same-as-last: the 7th stage value is the new state.
+static const double DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+
+template <typename R>
+struct StageArgs {
+  cpx<R>* y;
+  const cpx<R>* kin[6];
+  double coef[6];
+  int nterm;
+  int write_y;
+  cpx<R>* kout;
+  cpx<R>* T;
+  const FieldDesc* fd;
+  const R* greal;       // per field: gx[nx] gy[ny] gz[nz]
+  const cpx<R>* gcplx;  // per field: ex[nx] ey[ny] ez[nz] w[4]
+  const cpx<R>* tw[3];
+  RadixPlan plan[3];
+  GridDesc g;
+  int nrows;            // ny * nz
+  double t;
+};
+
+// ---------------------------------------------------------------- field and background
+__device__ __forceinline__ double field_time_factor(const FieldDesc& F, double t, double y) {
+  switch (F.kind) {
+    case SWF_FIELD_SAUTER_GAUSS: {
+      const double c = cosh(F.prm[1] * t);
+      return (F.prm[0] / F.prm[1]) / (c * c);
+    }
+    case SWF_FIELD_PULSE_GAUSS: {
+      const double u = t - y;
+      return F.prm[0] * sin(F.prm[1] * u) * exp(-u * u / (F.prm[2] * F.prm[2]));
+    }
+    case SWF_FIELD_SINGLE_E:
+    case SWF_FIELD_DOUBLE_E: {
+      const double a = F.prm[1] * t;
+      return exp(-a * a);
+    }
+    default:
+      return 0.0;
+  }
+}
+
+__device__ __forceinline__ double single_e_x(const FieldDesc& F, double x) {
+  const double kx = F.prm[2];
+  return -(F.prm[0] / kx) * sin(kx * x) * exp(-(kx * x) * (kx * x));
+}
+
+__device__ double axis_factor(const FieldDesc& F, int axis, double xc) {
+  switch (F.kind) {
+    case SWF_FIELD_SAUTER_GAUSS: {
+      const double lam = F.prm[2];
+      return lam > 0.0 ? exp(-xc * xc / (lam * lam)) : 1.0;
+    }
+    case SWF_FIELD_PULSE_GAUSS:
+      if (axis == 0) return exp(-xc * xc / (F.prm[3] * F.prm[3]));
+      if (axis == 1) return F.prm[4] > 0.0 ? exp(-xc * xc / (F.prm[4] * F.prm[4])) : 1.0;
+      return 1.0;
+    case SWF_FIELD_SINGLE_E:
+    case SWF_FIELD_DOUBLE_E: {
+      if (axis == 0) {
+        if (F.kind == SWF_FIELD_SINGLE_E) return single_e_x(F, xc);
+        return single_e_x(F, xc + F.prm[5]) + single_e_x(F, xc - F.prm[5]);
+      }
+      const double k = F.prm[2 + axis];
+      return exp(-(k * xc) * (k * xc));
+    }
+    default:
+      return 0.0;
+  }
+}
+
+// Per-field tables, computed in FP64 and rounded once to the march precision.
+template <typename R>
+__global__ void k_tables(const FieldDesc* fd, GridDesc g, R* greal, cpx<R>* gcplx) {
+  const int f = blockIdx.y;
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  const FieldDesc& F = fd[f];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt + 4; i += gridDim.x * blockDim.x) {
+    if (i < nt) {
+      int axis = 0, j = i;
+      while (j >= g.n[axis]) { j -= g.n[axis]; ++axis; }
+      const double xc = g.n[axis] > 1 ? g.x0[axis] + j * g.dx[axis] : 0.0;
+      greal[(size_t)f * nt + i] = (R)axis_factor(F, axis, xc);
+      double sn, cs;
+      sincos(F.pmom[axis] * xc, &sn, &cs);
+      gcplx[(size_t)f * (nt + 4) + i] = mk<R>((R)cs, (R)sn);
+    } else {
+      const int c = i - nt;
+      gcplx[(size_t)f * (nt + 4) + i] = mk<R>((R)F.w[2 * c], (R)F.w[2 * c + 1]);
+    }
+  }
+}
+
+// V phi for the one non-zero covariant component A_mu = a (V = A_0 + alpha^k A_k).
+template <typename R>
+__device__ __forceinline__ void apply_v(int acomp, R a, const cpx<R>* p, cpx<R>* o) {
+  switch (acomp) {
+    case 0:
+      o[0] = a * p[0]; o[1] = a * p[1]; o[2] = a * p[2]; o[3] = a * p[3];
+      break;
+    case 1:  // alpha^x
+      o[0] = a * p[3]; o[1] = a * p[2]; o[2] = a * p[1]; o[3] = a * p[0];
+      break;
+    case 2:  // alpha^y
+      o[0] = a * mul_mi(p[3]); o[1] = a * mul_i(p[2]); o[2] = a * mul_mi(p[1]); o[3] = a * mul_i(p[0]);
+      break;
+    case 3:  // alpha^z
+      o[0] = a * p[2]; o[1] = (R)(-1) * (a * p[3]); o[2] = a * p[0]; o[3] = (R)(-1) * (a * p[1]);
+      break;
+    default:
+      o[0] = o[1] = o[2] = o[3] = mk<R>(0, 0);
+  }
+}
+
+// v <- -i s (alpha.kappa + beta) v  (Dirac representation, sigma.kappa blocks).
+template <typename R>
+__device__ __forceinline__ void h0_mi(cpx<R>* v, R kx, R ky, R kz, R s) {
+  const cpx<R> a = v[0], b = v[1], c = v[2], d = v[3];
+  // sigma.k (u0, u1) = (kz u0 + (kx - i ky) u1, (kx + i ky) u0 - kz u1)
+  const cpx<R> sl0 = kz * c + kx * d + ky * mul_mi(d);
+  const cpx<R> sl1 = kx * c + ky * mul_i(c) - kz * d;
+  const cpx<R> su0 = kz * a + kx * b + ky * mul_mi(b);
+  const cpx<R> su1 = kx * a + ky * mul_i(a) - kz * b;
+  v[0] = s * mul_mi(a + sl0);
+  v[1] = s * mul_mi(b + sl1);
+  v[2] = s * mul_mi(su0 - c);
+  v[3] = s * mul_mi(su1 - d);
+}
+
+__device__ __forceinline__ double kappa_of(int j, int n, double L, double K) {
+  return n > 1 ? mode_kappa(j, n, L) : K;
+}
+
+// ---------------------------------------------------------------- pass kernels
+template <typename R, int MAXE>
+__global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+  __shared__ double s_ft[64];
+  __shared__ cpx<R> s_tf;
+  const int f = blockIdx.y;
+  const int row0 = blockIdx.x * rows;
+  const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
+  const int N = A.g.N;
+  const size_t fo = (size_t)f * 4 * N;
+  const FieldDesc* F = A.fd + f;
+  for (int j = threadIdx.x; j < rows; j += blockDim.x) {
+    const int iy = (row0 + j) % ny;
+    const double yc = ny > 1 ? A.g.x0[1] + iy * A.g.dx[1] : 0.0;
+    s_ft[j] = field_time_factor(*F, A.t, yc);
+  }
+  if (threadIdx.x == 0) {
+    double sn, cs;
+    sincos(F->tsign * F->e0 * A.t, &sn, &cs);
+    s_tf = mk<R>((R)cs, (R)sn);
+  }
+  const int per = rows * nx;
+  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
+    const int c = e / per;
+    const int rem = e - c * per;
+    const int j = rem / nx;
+    const int x = rem - j * nx;
+    const int row = row0 + j;
+    cpx<R> v = mk<R>(0, 0);
+    if (row < A.nrows) {
+      const size_t gi = fo + (size_t)c * N + (size_t)row * nx + x;
+      v = A.y[gi];
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        if (q < A.nterm) v = v + (R)A.coef[q] * A.kin[q][gi];
+      if (A.write_y) A.y[gi] = v;
+    }
+    buf[(c * rows + j) * ld + x] = v;
+  }
+  __syncthreads();
+  const int nt = nx + ny + nz;
+  const R* gx = A.greal + (size_t)f * nt;
+  const R* gy = gx + nx;
+  const R* gz = gy + ny;
+  const cpx<R>* ex = A.gcplx + (size_t)f * (nt + 4);
+  const cpx<R>* ey = ex + nx;
+  const cpx<R>* ez = ey + ny;
+  const cpx<R>* wsp = ez + nz;
+  for (int e = threadIdx.x; e < per; e += blockDim.x) {
+    const int j = e / nx, x = e - j * nx;
+    const int row = row0 + j;
+    if (row >= A.nrows) continue;
+    const int iy = row % ny, iz = row / ny;
+    const R a = (R)s_ft[j] * gx[x] * gy[iy] * gz[iz];
+    const cpx<R> ph = s_tf * ex[x] * ey[iy] * ez[iz];
+    cpx<R> phi[4], vz[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) phi[c] = buf[(c * rows + j) * ld + x] + wsp[c] * ph;
+    apply_v<R>(F->acomp, a, phi, vz);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) A.kout[fo + (size_t)c * N + (size_t)row * nx + x] = mul_mi(vz[c]);
+  }
+  fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], false, A.tw[0]);
+  if (!only_x) {
+    for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
+      const int c = e / per;
+      const int rem = e - c * per;
+      const int j = rem / nx;
+      const int x = rem - j * nx;
+      const int row = row0 + j;
+      if (row < A.nrows) A.T[fo + (size_t)c * N + (size_t)row * nx + x] = buf[(c * rows + j) * ld + x];
+    }
+    return;
+  }
+  // one non-trivial axis: the whole derivative in this block
+  const R sc = (R)(1.0 / (double)N);
+  const R ky = (R)F->K[1], kz = (R)F->K[2];
+  for (int e = threadIdx.x; e < per; e += blockDim.x) {
+    const int j = e / nx, x = e - j * nx;
+    cpx<R> v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = buf[(c * rows + j) * ld + x];
+    h0_mi<R>(v, (R)kappa_of(x, nx, A.g.L[0], F->K[0]), ky, kz, sc);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) buf[(c * rows + j) * ld + x] = v[c];
+  }
+  __syncthreads();
+  fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], true, A.tw[0]);
+  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
+    const int c = e / per;
+    const int rem = e - c * per;
+    const int j = rem / nx;
+    const int x = rem - j * nx;
+    const int row = row0 + j;
+    if (row < A.nrows) {
+      const size_t gi = fo + (size_t)c * N + (size_t)row * nx + x;
+      A.kout[gi] = A.kout[gi] + buf[(c * rows + j) * ld + x];
+    }
+  }
+}
+
+template <typename R, int MAXE>
+__global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int TX, int ld, int do_fwd,
+                                             int do_h0, int do_inv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+  const int f = blockIdx.y;
+  const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
+  const int N = A.g.N;
+  const int na = A.g.n[axis];
+  const int ntx = (nx + TX - 1) / TX;
+  const int xt = blockIdx.x % ntx;
+  const int o = blockIdx.x / ntx;  // z index (axis 1) or y index (axis 2)
+  const size_t base = axis == 1 ? (size_t)o * nx * ny : (size_t)o * nx;
+  const size_t stride = axis == 1 ? (size_t)nx : (size_t)nx * ny;
+  const size_t fo = (size_t)f * 4 * N;
+  const int per = TX * na;
+  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
+    const int c = e / per;
+    const int rem = e - c * per;
+    const int m = rem / TX;
+    const int t = rem - m * TX;
+    const int x = xt * TX + t;
+    buf[(c * TX + t) * ld + m] = x < nx ? A.T[fo + (size_t)c * N + base + m * stride + x] : mk<R>(0, 0);
+  }
+  __syncthreads();
+  if (do_fwd) fft_lines<R, MAXE>(buf, ld, 4 * TX, A.plan[axis], false, A.tw[axis]);
+  if (do_h0) {
+    const FieldDesc* F = A.fd + f;
+    const R sc = (R)(1.0 / (double)N);
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int t = e / na, m = e - t * na;
+      const int x = xt * TX + t;
+      if (x >= nx) continue;
+      const int iy = axis == 1 ? m : o;
+      const int iz = axis == 2 ? m : o;
+      cpx<R> v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = buf[(c * TX + t) * ld + m];
+      h0_mi<R>(v, (R)kappa_of(x, nx, A.g.L[0], F->K[0]), (R)kappa_of(iy, ny, A.g.L[1], F->K[1]),
+               (R)kappa_of(iz, nz, A.g.L[2], F->K[2]), sc);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) buf[(c * TX + t) * ld + m] = v[c];
+    }
+    __syncthreads();
+  }
+  if (do_inv) fft_lines<R, MAXE>(buf, ld, 4 * TX, A.plan[axis], true, A.tw[axis]);
+  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
+    const int c = e / per;
+    const int rem = e - c * per;
+    const int m = rem / TX;
+    const int t = rem - m * TX;
+    const int x = xt * TX + t;
+    if (x < nx) A.T[fo + (size_t)c * N + base + m * stride + x] = buf[(c * TX + t) * ld + m];
+  }
+}
+
+template <typename R, int MAXE>
+__global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+  const int f = blockIdx.y;
+  const int row0 = blockIdx.x * rows;
+  const int nx = A.g.n[0];
+  const int N = A.g.N;
+  const size_t fo = (size_t)f * 4 * N;
+  const int per = rows * nx;
+  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
+    const int c = e / per;
+    const int rem = e - c * per;
+    const int j = rem / nx;
+    const int x = rem - j * nx;
+    const int row = row0 + j;
+    buf[(c * rows + j) * ld + x] =
+        row < A.nrows ? A.T[fo + (size_t)c * N + (size_t)row * nx + x] : mk<R>(0, 0);
+  }
+  __syncthreads();
+  fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], true, A.tw[0]);
+  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
+    const int c = e / per;
+    const int rem = e - c * per;
+    const int j = rem / nx;
+    const int x = rem - j * nx;
+    const int row = row0 + j;
+    if (row < A.nrows) {
+      const size_t gi = fo + (size_t)c * N + (size_t)row * nx + x;
+      A.kout[gi] = A.kout[gi] + buf[(c * rows + j) * ld + x];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+template <typename R> struct Prec;
+template <> struct Prec<float> { static constexpr int MAXE = 36; static constexpr int is_double = 0; };
+template <> struct Prec<double> { static constexpr int MAXE = 20; static constexpr int is_double = 1; };
+
+static const int kThreads = 256;
+
+template <typename R>
+static int elem_cap() { return kThreads * (Prec<R>::MAXE - 4); }
+
+template <typename R>
+static swf_status set_smem_attrs() {
+  static bool done = false;
+  if (done) return SWF_OK;
+  const int bytes = elem_cap<R>() * (int)sizeof(cpx<R>);
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_first<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_first)");
+  e = cudaFuncSetAttribute(k_mid<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_mid)");
+  e = cudaFuncSetAttribute(k_last<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last)");
+  done = true;
+  return SWF_OK;
+}
+
+// Launches one right-hand-side evaluation for F fields.
+template <typename R>
+static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaStream_t st) {
+  constexpr int MAXE = Prec<R>::MAXE;
+  const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
+  const int cap = elem_cap<R>();
+  int rows = cap / (4 * nx);
+  if (rows > 64) rows = 64;
+  if (rows > A.nrows) rows = A.nrows;
+  if (rows < 1) return SWF_EUNSUPPORTED;
+  const int ld = nx;
+  const bool only_x = (ny == 1 && nz == 1);
+  size_t smem = (size_t)4 * rows * ld * sizeof(cpx<R>);
+  dim3 grid_rows((A.nrows + rows - 1) / rows, F);
+  {
+    ProfScope ps(ctx, "k_first", st);
+    k_first<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, ld, only_x ? 1 : 0);
+  }
+  if (only_x) return SWF_OK;
+  int axes[2], na = 0;
+  if (ny > 1) axes[na++] = 1;
+  if (nz > 1) axes[na++] = 2;
+  auto mid = [&](int axis, int fwd, int h0, int inv) {
+    const int n_a = A.g.n[axis];
+    int TX = cap / (4 * n_a);
+    if (TX > 16) TX = 16;
+    if (TX > nx) TX = nx;
+    if (TX < 1) TX = 1;
+    const int ntx = (nx + TX - 1) / TX;
+    const int other = axis == 1 ? nz : ny;
+    dim3 grid(ntx * other, F);
+    size_t sm = (size_t)4 * TX * n_a * sizeof(cpx<R>);
+    ProfScope ps(ctx, "k_mid", st);
+    k_mid<R, MAXE><<<grid, kThreads, sm, st>>>(A, axis, TX, n_a, fwd, h0, inv);
+  };
+  if (na == 1) {
+    mid(axes[0], 1, 1, 1);
+  } else {
+    mid(1, 1, 0, 0);
+    mid(2, 1, 1, 1);
+    mid(1, 0, 0, 1);
+  }
+  {
+    ProfScope ps(ctx, "k_last", st);
+    k_last<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, ld);
+  }
+  return SWF_OK;
+}
+
+template <typename R>
+static swf_status prepare_args(swf_ctx* ctx, const GridDesc& g, int F, const FieldDesc* fd_host,
+                               StageArgs<R>* A, const char* tag, cudaStream_t st) {
+  swf_status s = set_smem_attrs<R>();
+  if (s != SWF_OK) return s;
+  std::memset(A, 0, sizeof(*A));
+  A->g = g;
+  A->nrows = g.n[1] * g.n[2];
+  for (int a = 0; a < 3; ++a) {
+    if (!make_radix_plan(g.n[a], &A->plan[a])) {
+      set_error("grid size must factor into 2, 3 and 5");
+      return SWF_EINVAL;
+    }
+    const void* tw = nullptr;
+    s = twiddles(ctx, g.n[a], Prec<R>::is_double, &tw);
+    if (s != SWF_OK) return s;
+    A->tw[a] = reinterpret_cast<const cpx<R>*>(tw);
+  }
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  void *pfd = nullptr, *pgr = nullptr, *pgc = nullptr;
+  std::string t(tag);
+  if ((s = ws_get(ctx, t + ".fd", sizeof(FieldDesc) * F, &pfd)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, t + ".greal", sizeof(R) * F * nt, &pgr)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, t + ".gcplx", sizeof(cpx<R>) * F * (nt + 4), &pgc)) != SWF_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(pfd, fd_host, sizeof(FieldDesc) * F, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload field descriptors");
+  A->fd = (const FieldDesc*)pfd;
+  A->greal = (const R*)pgr;
+  A->gcplx = (const cpx<R>*)pgc;
+  dim3 tg((nt + 4 + 127) / 128, F);
+  ProfScope ps(ctx, "k_tables", st);
+  k_tables<R><<<tg, 128, 0, st>>>(A->fd, g, (R*)pgr, (cpx<R>*)pgc);
+  return SWF_OK;
+}
+
+template <typename R>
+static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
+                             int F, const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
+  StageArgs<R> A;
+  swf_status s = prepare_args<R>(ctx, g, F, fd_host, &A, "march", st);
+  if (s != SWF_OK) return s;
+  const size_t state = (size_t)F * 4 * g.N * sizeof(cpx<R>);
+  void *py = nullptr, *pT = nullptr, *pk[7];
+  if ((s = ws_get(ctx, "march.y", state, &py)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.T", state, &pT)) != SWF_OK) return s;
+  for (int i = 0; i < 7; ++i) {
+    char nm[32];
+    std::snprintf(nm, sizeof nm, "march.k%d", i);
+    if ((s = ws_get(ctx, nm, state, &pk[i])) != SWF_OK) return s;
+  }
+  cudaError_t e = cudaMemsetAsync(py, 0, state, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset state");
+  A.y = (cpx<R>*)py;
+  A.T = (cpx<R>*)pT;
+  int slot[7] = {0, 1, 2, 3, 4, 5, 6};
+  const double h = (t_in - t_out) / n_steps;
+  // k_1 = f(t_out, 0)
+  A.nterm = 0;
+  A.write_y = 0;
+  A.kout = (cpx<R>*)pk[slot[0]];
+  A.t = t_out;
+  if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  for (int n = 0; n < n_steps; ++n) {
+    const double tn = t_out + n * h;
+    for (int i = 1; i < 7; ++i) {
+      int nt = 0;
+      for (int j = 0; j < i; ++j) {
+        if (DP_A[i][j] == 0.0) continue;
+        A.kin[nt] = (const cpx<R>*)pk[slot[j]];
+        A.coef[nt] = h * DP_A[i][j];
+        ++nt;
+      }
+      A.nterm = nt;
+      A.write_y = (i == 6);
+      A.kout = (cpx<R>*)pk[slot[i]];
+      A.t = tn + DP_C[i] * h;
+      if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+    }
+    std::swap(slot[0], slot[6]);
+  }
+  e = cudaMemcpyAsync(psi_out, py, state, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "copy psi(t_in)");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "march kernels");
+  return SWF_OK;
+}
+
+swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
+                        int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
+                        cudaStream_t st) {
+  if (prec == SWF_C64) return march_impl<float>(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
+  return march_impl<double>(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
+}
+
+template <typename R>
+static swf_status rhs_impl(swf_ctx* ctx, const GridDesc& g, const FieldDesc& fd, double t,
+                           const void* psi, void* out, cudaStream_t st) {
+  StageArgs<R> A;
+  swf_status s = prepare_args<R>(ctx, g, 1, &fd, &A, "rhs", st);
+  if (s != SWF_OK) return s;
+  void* pT = nullptr;
+  if ((s = ws_get(ctx, "rhs.T", (size_t)4 * g.N * sizeof(cpx<R>), &pT)) != SWF_OK) return s;
+  A.y = const_cast<cpx<R>*>((const cpx<R>*)psi);  // read only: write_y = 0
+  A.T = (cpx<R>*)pT;
+  A.kout = (cpx<R>*)out;
+  A.nterm = 0;
+  A.write_y = 0;
+  A.t = t;
+  if ((s = launch_eval<R>(ctx, A, 1, st)) != SWF_OK) return s;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "rhs kernels");
+  return SWF_OK;
+}
+
+swf_status rhs_eval(swf_ctx* ctx, const GridDesc& g, const FieldDesc& fd, swf_precision prec,
+                    double t, const void* psi, void* out, cudaStream_t st) {
+  if (prec == SWF_C64) return rhs_impl<float>(ctx, g, fd, t, psi, out, st);
+  return rhs_impl<double>(ctx, g, fd, t, psi, out, st);
+}
+
+}  // namespace swf

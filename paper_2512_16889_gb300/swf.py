@@ -1,0 +1,212 @@
+"""Python binding of the C ABI in ``include/swf.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``libswf.so``; this module only mirrors the
+C structures with ctypes and passes host pointers or torch device pointers through.  There is
+no CPU fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswf.so")
+
+SWF_OK, SWF_EINVAL, SWF_ENOMEM, SWF_ECUDA, SWF_ENUMERIC, SWF_ETIMEOUT, SWF_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["SWF_OK", "SWF_EINVAL", "SWF_ENOMEM", "SWF_ECUDA", "SWF_ENUMERIC", "SWF_ETIMEOUT",
+                "SWF_EUNSUPPORTED"]
+SCHWINGER, BREIT_WHEELER = 0, 1
+C128, C64 = 0, 1
+FIELD_ZERO, FIELD_SAUTER_GAUSS, FIELD_PULSE_GAUSS, FIELD_SINGLE_E, FIELD_DOUBLE_E = range(5)
+WANT_SPECTRUM, WANT_FULL_N = 1, 2
+
+
+class Field(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("prm", C.c_double * 8)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("n_steps", C.c_int32), ("L", C.c_double * 3),
+                ("t_in", C.c_double), ("t_out", C.c_double)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("field", Field), ("grid", Grid),
+                ("p", C.c_double * 3), ("s", C.c_int32),
+                ("r", C.c_int32), ("q", C.c_double * 3),
+                ("k", C.c_double * 3), ("eps", C.c_double * 3),
+                ("flags", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("amp", C.c_double * 8), ("prob", C.c_double * 2), ("diag", C.c_double * 2)]
+
+
+EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_march_dev",
+           "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
+           "swf_profile_read"]
+
+
+class SwfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libswf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2512_16889_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, ip, dp = C.c_void_p, C.c_int, C.c_double
+    inst_p, res_p, dbl_p = C.POINTER(Instance), C.POINTER(Result), C.POINTER(C.c_double)
+    lib.swf_create.argtypes = [C.POINTER(vp), ip]
+    lib.swf_destroy.argtypes = [vp]
+    lib.swf_last_error.restype = C.c_char_p
+    lib.solve_swf.argtypes = [vp, ip, inst_p, ip, ip, res_p, dbl_p]
+    lib.solve_swf_dev.argtypes = [vp, ip, inst_p, ip, ip, vp, vp, vp]
+    lib.swf_march_dev.argtypes = [vp, ip, inst_p, ip, ip, vp, vp]
+    lib.swf_rhs_dev.argtypes = [vp, inst_p, ip, ip, dp, vp, vp, vp]
+    lib.swf_spectrum_dev.argtypes = [vp, ip, inst_p, ip, vp, vp, vp, vp]
+    lib.swf_set_workspace_limit.argtypes = [vp, C.c_size_t]
+    lib.swf_profile_enable.argtypes = [vp, ip]
+    lib.swf_profile_read.argtypes = [vp, ip, C.c_char_p, dbl_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_longlong)]
+    for name in EXPORTS:
+        if name != "swf_last_error":
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != SWF_OK:
+        raise SwfError(status, _lib.swf_last_error().decode())
+
+
+def make_instance(field_kind, prm, n, L, t_in, t_out, n_steps, p=(0, 0, 0), s=1, q=(0, 0, 0), r=1,
+                  k=(0, 0, 0), eps=(0, 0, 0), flags=0) -> Instance:
+    inst = Instance()
+    inst.field.kind = field_kind
+    for i, v in enumerate(prm):
+        inst.field.prm[i] = float(v)
+    for a in range(3):
+        inst.grid.n[a] = int(n[a])
+        inst.grid.L[a] = float(L[a])
+        inst.p[a], inst.q[a], inst.k[a], inst.eps[a] = float(p[a]), float(q[a]), float(k[a]), float(eps[a])
+    inst.grid.n_steps = int(n_steps)
+    inst.grid.t_in, inst.grid.t_out = float(t_in), float(t_out)
+    inst.s, inst.r, inst.flags = int(s), int(r), int(flags)
+    return inst
+
+
+def instance_array(instances):
+    arr = (Instance * len(instances))()
+    for i, x in enumerate(instances):
+        arr[i] = x
+    return arr
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Context:
+    """A solver context on one CUDA device (owns workspace and a stream)."""
+
+    def __init__(self, device: int = 0):
+        load_library()
+        self._h = C.c_void_p()
+        _check(_lib.swf_create(C.byref(self._h), int(device)))
+
+    def close(self):
+        if self._h:
+            _lib.swf_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_workspace_limit(self, nbytes: int):
+        _check(_lib.swf_set_workspace_limit(self._h, int(nbytes)))
+
+    def profile_enable(self, on=True):
+        _check(_lib.swf_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, max_entries=32):
+        """{family: (total_ms, launches)} since the last read, and the total launch count."""
+        names = C.create_string_buffer(32 * max_entries)
+        ms = (C.c_double * max_entries)()
+        cnt = (C.c_longlong * max_entries)()
+        n = C.c_int()
+        total = C.c_longlong()
+        _check(_lib.swf_profile_read(self._h, max_entries, names, ms, cnt, C.byref(n), C.byref(total)))
+        out = {}
+        for i in range(n.value):
+            nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
+            out[nm] = (ms[i], cnt[i])
+        return out, total.value
+
+    # -- highest level, host buffers
+    def solve(self, instances, process=SCHWINGER, prec=C64):
+        arr = instance_array(instances)
+        res = (Result * len(instances))()
+        nspec = sum(2 * x.grid.n[0] * x.grid.n[1] * x.grid.n[2] for x in instances
+                    if process == SCHWINGER and (x.flags & WANT_SPECTRUM))
+        spec = np.zeros(max(nspec, 1), dtype=np.float64)
+        _check(_lib.solve_swf(self._h, len(instances), arr, process, prec, res,
+                              spec.ctypes.data_as(C.POINTER(C.c_double))))
+        return res, spec[:nspec]
+
+    # -- device buffers (torch tensors), asynchronous on `stream`
+    def solve_dev(self, instances, results_dev, spectrum_dev=None, process=SCHWINGER, prec=C64, stream=None,
+                  arr=None):
+        arr = arr if arr is not None else instance_array(instances)
+        _check(_lib.solve_swf_dev(self._h, len(arr), arr, process, prec, C.c_void_p(results_dev.data_ptr()),
+                                  C.c_void_p(spectrum_dev.data_ptr()) if spectrum_dev is not None else None,
+                                  _stream_ptr(stream)))
+
+    def march_dev(self, instances, psi_out, bg=0, prec=C64, stream=None):
+        arr = instance_array(instances)
+        _check(_lib.swf_march_dev(self._h, len(instances), arr, bg, prec, C.c_void_p(psi_out.data_ptr()),
+                                  _stream_ptr(stream)))
+
+    def rhs_dev(self, instance, t, psi, out, bg=0, prec=C64, stream=None):
+        arr = instance_array([instance])
+        _check(_lib.swf_rhs_dev(self._h, arr, bg, prec, float(t), C.c_void_p(psi.data_ptr()),
+                                C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+
+    def spectrum_dev(self, instances, psi, c_out=None, prob_out=None, prec=C64, stream=None):
+        arr = instance_array(instances)
+        _check(_lib.swf_spectrum_dev(self._h, len(instances), arr, prec, C.c_void_p(psi.data_ptr()),
+                                     C.c_void_p(c_out.data_ptr()) if c_out is not None else None,
+                                     C.c_void_p(prob_out.data_ptr()) if prob_out is not None else None,
+                                     _stream_ptr(stream)))
+
+
+FIELD_CODES = {"zero": FIELD_ZERO, "sauter_gauss": FIELD_SAUTER_GAUSS, "pulse_gauss": FIELD_PULSE_GAUSS,
+               "single_e": FIELD_SINGLE_E, "double_e": FIELD_DOUBLE_E}
+FLAG_CODES = {"spectrum": WANT_SPECTRUM, "full_n": WANT_FULL_N}
+
+
+def from_workload(d) -> Instance:
+    """Marshal one workload dict (see ``workloads``) into the C instance struct."""
+    kind, prm = d["field"]
+    flags = 0
+    for f in d.get("flags", ()):
+        flags |= FLAG_CODES[f]
+    return make_instance(FIELD_CODES[kind], prm, d["n"], d["L"], d["t_in"], d["t_out"], d["n_steps"],
+                         p=d["p"], s=d["s"], q=d["q"], r=d["r"], k=d["k"], eps=d["eps"], flags=flags)

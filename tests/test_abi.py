@@ -1,0 +1,81 @@
+"""The C ABI library builds, loads and exports every declared symbol; the ctypes mirrors match
+the C struct layouts; host-side validation and error reporting work without a GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_16889_gb300 import build, swf
+    build.build()
+    return swf.load_library()
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(INCLUDE)):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(INCLUDE, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:swf_status|const char\s*\*)\s*(\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "solve_swf" in names and "swf_create" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_c(lib):
+    from paper_2512_16889_gb300 import swf
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "swf.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(swf_field), sizeof(swf_grid), sizeof(swf_instance), sizeof(swf_result));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(swf_instance, grid), offsetof(swf_instance, p),
+         offsetof(swf_instance, q), offsetof(swf_instance, eps), offsetof(swf_instance, flags));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", INCLUDE, c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    sizes = [int(v) for v in out[:4]]
+    offs = [int(v) for v in out[4:]]
+    assert sizes == [C.sizeof(swf.Field), C.sizeof(swf.Grid), C.sizeof(swf.Instance), C.sizeof(swf.Result)]
+    assert offs == [swf.Instance.grid.offset, swf.Instance.p.offset, swf.Instance.q.offset,
+                    swf.Instance.eps.offset, swf.Instance.flags.offset]
+
+
+def test_errors_without_device(lib):
+    from paper_2512_16889_gb300 import swf
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-device path")
+    h = C.c_void_p()
+    st = lib.swf_create(C.byref(h), 0)
+    assert st == swf.SWF_ECUDA and not h
+    assert b"not available" in lib.swf_last_error()
+    # a NULL context is rejected by validation before any CUDA call
+    arr = swf.instance_array([swf.make_instance(1, (0.3, 0.5, 5.0), (8, 8, 1), (4, 4, 1), -1, 1, 2)])
+    res = (swf.Result * 1)()
+    assert lib.solve_swf(None, 1, arr, 0, 1, res, None) == swf.SWF_EINVAL
+    assert b"ctx is NULL" in lib.swf_last_error()
+    assert lib.swf_destroy(None) == swf.SWF_OK

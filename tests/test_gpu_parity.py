@@ -1,0 +1,207 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (derived in the design doc):
+* complex128 path: same scheme and steps as the oracle, only the summation order differs ->
+  1e-10 relative (state: max|diff| / max|ref|; scalars: |diff| / |ref|).
+* complex64 march: single-precision rounding accumulated over the march -> 1e-4 relative on
+  |C|^2 for modes above a floor of 1e-6 of the spectrum maximum, 2e-5 relative on the state.
+"""
+import numpy as np
+import pytest
+
+from oracle import swf_oracle as O
+from paper_2512_16889_gb300 import workloads as W
+from tests import oracle_adapter as OA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2512_16889_gb300 import build, swf
+    build.build()
+    ctx = swf.Context(0)
+    yield torch, swf, ctx
+    ctx.close()
+
+
+def to_complex(t):
+    a = t.cpu().numpy()
+    return a.view(np.complex128) if a.dtype == np.float64 else a.view(np.complex64).astype(np.complex128)
+
+
+def rel_state(got, ref):
+    return np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+
+
+RHS_CASES = [
+    dict(field=("sauter_gauss", (0.8, 0.6, 2.5)), n=(32, 24, 1), L=(16.0, 12.0, 1.0), p=(0.3, -0.2, 0.0), s=1),
+    dict(field=("single_e", (0.6, 0.5, 0.3, 0.3, 0.0)), n=(36, 20, 1), L=(24.0, 14.0, 1.0), p=(0.1, 0.2, 0.0), s=-1),
+    dict(field=("double_e", (0.5, 0.4, 0.3, 0.2, 0.0, 3.0)), n=(40, 30, 1), L=(30.0, 20.0, 1.0), p=(-0.3, 0.2, 0.0), s=1),
+    dict(field=("pulse_gauss", (1.0, 0.5, 4.0, 3.0, 0.0)), n=(48, 20, 1), L=(20.0, 18.0, 1.0), p=(0.4, -1.0, 0.0), s=1),
+    dict(field=("sauter_gauss", (0.7, 0.5, 2.0)), n=(12, 10, 8), L=(8.0, 7.0, 6.0), p=(0.2, 0.1, -0.3), s=-1),
+    dict(field=("single_e", (0.4, 0.5, 0.25, 0.0, 0.0)), n=(64, 1, 1), L=(30.0, 1.0, 1.0), p=(0.3, 0.6, 0.0), s=1),
+]
+
+
+def _full(d):
+    base = dict(t_in=-4.0, t_out=4.0, n_steps=10, q=(-0.2, 0.1, 0.0), r=1, k=(0, 0, 0), eps=(0, 0, 0), flags=())
+    base.update(d)
+    return base
+
+
+@pytest.mark.parametrize("case", range(len(RHS_CASES)))
+@pytest.mark.parametrize("bg", [0, 1])
+def test_rhs_matches_oracle(env, case, bg):
+    torch, swf, ctx = env
+    d = _full(RHS_CASES[case])
+    rng = np.random.default_rng(10 + case)
+    grid = OA.grid(d)
+    psi = rng.normal(size=(4,) + grid.n) + 1j * rng.normal(size=(4,) + grid.n)
+    t = 0.37
+    ref = O.rhs(OA.field(d), grid, OA.background(d, bg), O.h0_field(grid, OA.background(d, bg).offset()), t, psi)
+    ref_g = OA.to_gpu_layout(ref)
+    inst = swf.from_workload(d)
+    for prec, tol in ((swf.C128, 1e-12), (swf.C64, 2e-6)):
+        dt = np.complex128 if prec == swf.C128 else np.complex64
+        src = OA.to_gpu_layout(psi).astype(dt)
+        x = torch.from_numpy(src.view(np.float64 if prec == swf.C128 else np.float32).copy()).cuda()
+        out = torch.zeros_like(x)
+        ctx.rhs_dev(inst, t, x, out, bg=bg, prec=prec)
+        torch.cuda.synchronize()
+        got = to_complex(out).reshape(ref_g.shape)
+        assert rel_state(got, ref_g) < tol, (prec, rel_state(got, ref_g))
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_march_matches_oracle(env, case):
+    torch, swf, ctx = env
+    d = W.small_parity_cases()[case]
+    grid = OA.grid(d)
+    for bg in (0, 1):
+        ref = O.march_scattered(OA.field(d), grid, OA.background(d, bg), d["t_in"], d["t_out"], d["n_steps"])
+        ref_g = OA.to_gpu_layout(ref)
+        for prec, tol in ((swf.C128, 1e-10), (swf.C64, 2e-5)):
+            elems = 2 * 4 * int(np.prod(d["n"]))
+            out = torch.zeros(elems, dtype=torch.float64 if prec == swf.C128 else torch.float32, device="cuda")
+            ctx.march_dev([swf.from_workload(d)], out, bg=bg, prec=prec)
+            got = to_complex(out).reshape(ref_g.shape)
+            assert rel_state(got, ref_g) < tol, (bg, prec, rel_state(got, ref_g))
+
+
+def test_march_batch_of_distinct_fields(env):
+    """A batch of instances with different field strengths and momenta marches each one alone."""
+    torch, swf, ctx = env
+    ds = W.schwinger_batched(n=24, L=12.0, n_steps=30, t_window=3.0, n_p=2)
+    N = int(np.prod(ds[0]["n"]))
+    out = torch.zeros(len(ds) * 8 * N, dtype=torch.float64, device="cuda")
+    ctx.march_dev([swf.from_workload(d) for d in ds], out, bg=0, prec=swf.C128)
+    got = to_complex(out).reshape(len(ds), 4, 1, 24, 24)
+    for i, d in enumerate(ds):
+        ref = OA.to_gpu_layout(O.march_scattered(OA.field(d), OA.grid(d), OA.background(d, 0),
+                                                 d["t_in"], d["t_out"], d["n_steps"]))
+        assert rel_state(got[i], ref) < 1e-10, i
+
+
+def test_spectrum_matches_oracle(env):
+    torch, swf, ctx = env
+    d = W.small_parity_cases()[1]
+    grid = OA.grid(d)
+    rng = np.random.default_rng(5)
+    psi = rng.normal(size=(4,) + grid.n) + 1j * rng.normal(size=(4,) + grid.n)
+    ref = O.c_spectrum(psi, grid, d["t_in"])
+    x = torch.from_numpy(OA.to_gpu_layout(psi).view(np.float64).copy()).cuda()
+    N = int(np.prod(d["n"]))
+    c_out = torch.zeros(2 * 2 * N, dtype=torch.float64, device="cuda")
+    p_out = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+    ctx.spectrum_dev([swf.from_workload(d)], x, c_out, p_out, prec=swf.C128)
+    got = to_complex(c_out).reshape(2, d["n"][2], d["n"][1], d["n"][0])
+    ref_g = np.transpose(ref, (0, 3, 2, 1))
+    assert rel_state(got, ref_g) < 1e-12
+    assert np.allclose(p_out.cpu().numpy(), (np.abs(ref_g) ** 2).ravel(), rtol=1e-11, atol=0)
+
+
+def test_solve_full_pair_number_matches_oracle(env):
+    torch, swf, ctx = env
+    ds = [dict(d, flags=("spectrum", "full_n")) for d in W.small_parity_cases()[:2]]
+    res, spec = ctx.solve([swf.from_workload(d) for d in ds], swf.SCHWINGER, swf.C128)
+    off = 0
+    for i, d in enumerate(ds):
+        grid = OA.grid(d)
+        bu, bv = OA.background(d, 0), OA.background(d, 1)
+        pu = O.march_scattered(OA.field(d), grid, bu, d["t_in"], d["t_out"], d["n_steps"])
+        pv = O.march_scattered(OA.field(d), grid, bv, d["t_in"], d["t_out"], d["n_steps"])
+        ref = O.pair_number(pu, pv, grid, d["t_in"], d["p"], d["s"], d["q"], d["r"], bu.offset(), bv.offset())
+        r = res[i]
+        for j, key in enumerate(("C", "D", "A", "B")):
+            got = complex(r.amp[2 * j], r.amp[2 * j + 1])
+            assert abs(got - ref[key]) <= 1e-9 * max(abs(ref[key]), 1e-300), (key, got, ref[key])
+        assert abs(r.prob[0] - ref["N_line2"]) <= 1e-9 * ref["N_line2"]
+        assert abs(r.prob[1] - ref["N_line1"]) <= 1e-9 * ref["N_line1"]
+        assert abs(r.diag[0] - O.inner(pu, pu, grid).real) <= 1e-10 * r.diag[0]
+        n = int(np.prod(d["n"]))
+        C = O.c_spectrum(pu, grid, d["t_in"])
+        ref_spec = np.transpose(np.abs(C) ** 2, (0, 3, 2, 1)).ravel()
+        assert np.max(np.abs(spec[off:off + 2 * n] - ref_spec)) <= 1e-10 * np.max(ref_spec)
+        off += 2 * n
+
+
+def test_c64_spectrum_within_tolerance(env):
+    torch, swf, ctx = env
+    d = W.small_parity_cases()[0]
+    grid = OA.grid(d)
+    res, spec = ctx.solve([swf.from_workload(d)], swf.SCHWINGER, swf.C64)
+    pu = O.march_scattered(OA.field(d), grid, OA.background(d, 0), d["t_in"], d["t_out"], d["n_steps"])
+    ref = np.transpose(np.abs(O.c_spectrum(pu, grid, d["t_in"])) ** 2, (0, 3, 2, 1)).ravel()
+    mask = ref > 1e-6 * ref.max()
+    rel = np.abs(spec[mask] - ref[mask]) / ref[mask]
+    assert rel.max() < 1e-4, rel.max()
+
+
+def test_zero_field_is_exactly_zero(env):
+    torch, swf, ctx = env
+    d = dict(W.small_parity_cases()[0], field=("zero", ()))
+    for prec in (swf.C128, swf.C64):
+        res, spec = ctx.solve([swf.from_workload(d)], swf.SCHWINGER, prec)
+        assert res[0].prob[0] == 0.0 and res[0].diag[0] == 0.0
+        assert np.all(spec == 0.0)
+
+
+def test_uneven_grids_in_one_call(env):
+    """Instances with different grids are grouped; each result matches its own solo solve."""
+    torch, swf, ctx = env
+    cases = W.small_parity_cases()
+    insts = [swf.from_workload(d) for d in cases]
+    res_all, spec_all = ctx.solve(insts, swf.SCHWINGER, swf.C128)
+    off = 0
+    for i, inst in enumerate(insts):
+        res1, spec1 = ctx.solve([inst], swf.SCHWINGER, swf.C128)
+        n = 2 * int(np.prod(cases[i]["n"]))
+        assert res_all[i].prob[0] == res1[0].prob[0]
+        assert np.array_equal(spec_all[off:off + n], spec1)
+        off += n
+
+
+def test_validation_errors_are_reported(env):
+    torch, swf, ctx = env
+    d = W.small_parity_cases()[0]
+    bad = [dict(d, n=(7, 24, 1)), dict(d, n_steps=0), dict(d, t_in=5.0, t_out=-5.0), dict(d, s=0),
+           dict(d, n=(1024, 8, 1)), dict(d, L=(0.0, 12.0, 1.0))]
+    for b in bad:
+        with pytest.raises(swf.SwfError) as ei:
+            ctx.solve([swf.from_workload(b)], swf.SCHWINGER, swf.C64)
+        assert ei.value.status == swf.SWF_EINVAL
+    # empty input is a no-op
+    res, spec = ctx.solve([], swf.SCHWINGER, swf.C64)
+    assert len(res) == 0
+
+
+def test_workspace_limit_gives_enomem(env):
+    torch, swf, ctx = env
+    other = swf.Context(0)
+    other.set_workspace_limit(1024)
+    with pytest.raises(swf.SwfError) as ei:
+        other.solve([swf.from_workload(W.small_parity_cases()[0])], swf.SCHWINGER, swf.C64)
+    assert ei.value.status == swf.SWF_ENOMEM
+    other.close()
