@@ -170,6 +170,13 @@ swf_status swf_profile_enable(swf_ctx* ctx, int on);
 swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* total_ms,
                             long long* launches, int* n_entries, long long* total_launches);
 
+/* March path selection: 0 = automatic (the fused cluster kernel for (2+1)D 256 x 256
+ * complex64 marches that keep the z-spin sectors apart, the pass kernels otherwise),
+ * 1 = pass kernels only, 2 = fused kernel with one CTA per SM, 3 = fused kernel with two
+ * CTAs per SM (2 and 3 still fall back to the pass kernels where the fused kernel does not
+ * apply). */
+swf_status swf_set_march_path(swf_ctx* ctx, int path);
+
 /* Caps the context's device workspace (bytes; 0 = no cap).  Requests that need more return
  * SWF_ENOMEM before touching the device. */
 swf_status swf_set_workspace_limit(swf_ctx* ctx, size_t bytes);

@@ -521,6 +521,13 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
   return SWF_OK;
 }
 
+swf_status swf_set_march_path(swf_ctx* ctx, int path) {
+  if (!ctx || path < 0 || path > 3) { set_error("swf_set_march_path: ctx NULL or path not in 0..3"); return SWF_EINVAL; }
+  ctx->use_fused = path != 1;
+  if (path >= 2) ctx->fused_variant = path - 1;
+  return SWF_OK;
+}
+
 swf_status swf_set_workspace_limit(swf_ctx* ctx, size_t bytes) {
   if (!ctx) { set_error("ctx is NULL"); return SWF_EINVAL; }
   ctx->ws.limit = bytes;

@@ -1,0 +1,906 @@
+// Fused, persistent march of (2+1)D scattered waves on 256 x 256 grids in complex64
+// (Sec. II Eq. 6, Sec. II.A: pseudo-spectral derivative, Dormand-Prince in time).
+//
+// Layout of the work.  With n_z = 1 and no momentum along z, alpha^x, alpha^y, beta and A_0
+// never mix the component pairs {0, 3} and {1, 2} (the spin along z is conserved), so each
+// instance splits exactly into two independent two-component "sectors".  One thread-block
+// cluster of 16 CTAs marches one sector through every step: CTA r owns the rows
+// y in [16 r, 16 r + 16) of both components.  Per right-hand-side evaluation:
+//   1. stage combine  Y = y + h sum_j a_ij k_j   (y in shared memory, k_j in the cluster's
+//      global slot, which stays resident in L2), local term Z = -i V (Y + psi_b) to a global
+//      stash, forward x-FFT of the rows in shared memory;
+//   2. cluster barrier; each CTA pulls its 16 columns of every CTA's rows through distributed
+//      shared memory (the transpose), forward y-FFT, -i H0(kappa)/N per mode, inverse y-FFT;
+//   3. cluster barrier; each CTA pulls its rows back, inverse x-FFT, k_i = (that) + Z.
+// Two shared buffers (rows, columns) make each transpose a single pull after one barrier.
+// The 256-point FFTs are two radix-16 passes over lines padded by one element per 16 (and one
+// more per line) so that the passes and the transposes are free of bank conflicts.
+#include <cooperative_groups.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "swf_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace swf {
+
+namespace fused {
+
+constexpr int NT = 512;         // threads per CTA
+constexpr int CL = 16;          // CTAs per cluster
+constexpr int NX = 256;         // points along x
+constexpr int NY = 256;         // points along y
+constexpr int RB = NY / CL;     // rows per CTA
+constexpr int CB = NX / CL;     // columns per CTA
+constexpr int LD = 273;         // padded line stride (complex): 256 + 16 + 1
+constexpr int NSL = 2 * RB * NX;  // complex values in one CTA slab (both components)
+
+__host__ __device__ constexpr int pidx(int i) { return i + (i >> 4); }
+
+struct Sector {      // one marched two-component field
+  int inst;          // instance index (output slot)
+  int c0, c1;        // components of the 4-spinor
+  int sigma;         // +1 for {0, 3}, -1 for {1, 2} (sign of the y coupling)
+};
+
+struct Args {
+  const FieldDesc* fd;     // per instance
+  const Sector* sec;       // per sector
+  int n_sec;
+  float2* slots;           // per cluster: 9 arrays (k1..k7, stash, y low part) of 2 * NX * NY complex
+  float2* psi_out;         // [inst][4][NY][NX] complex64
+  double Lx, Ly, t_out, h;
+  int n_steps;
+};
+
+// shared-memory map (bytes)
+constexpr int OFF_WA = 0;                                   // [2][RB][LD] complex
+constexpr int OFF_WB = OFF_WA + 2 * RB * LD * 8;            // [2][CB][LD] complex
+constexpr int OFF_Y = OFF_WB + 2 * CB * LD * 8;             // [2][RB][NX] complex (state y)
+constexpr int OFF_TW = OFF_Y + NSL * 8;                     // [256] complex twiddles
+constexpr int OFF_EX = OFF_TW + 256 * 8;                    // [NX] complex  exp(i p_x x)
+constexpr int OFF_GX = OFF_EX + NX * 8;                     // [NX] float    field x factor
+constexpr int OFF_EY = OFF_GX + NX * 4;                     // [RB] complex
+constexpr int OFF_GY = OFF_EY + RB * 8;                     // [RB] float
+constexpr int OFF_KX = OFF_GY + RB * 4;                     // [NX] float   kappa_x of the mode
+constexpr int OFF_KY = OFF_KX + NX * 4;                     // [NY] float   sigma kappa_y of the mode
+constexpr int OFF_MISC = OFF_KY + NY * 4;                   // per-stage scalars
+constexpr int SMEM = OFF_MISC + 7 * RB * 4 + 7 * 8 + 16 + 64;
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 scl(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 fma2(float s, float2 a, float2 c) {
+  return make_float2(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y));
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV> __device__ __forceinline__ float2 rot(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// (hi, lo) + s in float-float arithmetic (Knuth's two-sum, then a fast renormalisation):
+// on return hi is the new rounded state, lo its rounding error; s is overwritten with hi.
+__device__ __forceinline__ void ff_add(float hi, float& lo, float& s) {
+  const float t = hi + s;
+  const float bp = t - hi;
+  const float e = (hi - (t - bp)) + (s - bp);
+  const float l = lo + e;
+  const float nh = t + l;
+  lo = l - (nh - t);
+  s = nh;
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = rot<INV>(a1 - a3);
+  a0 = t0 + t2;
+  a2 = t0 - t2;
+  a1 = t1 + t3;
+  a3 = t1 - t3;
+}
+
+// 16-point DFT in registers, natural order in and out (4 x 4 with the W16 twiddles).
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* a) {
+  // stage 1: DFT4 over n1 for each n2 (index n = 4 n1 + n2), result b[k1][n2] at a[4 k1 + n2]
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
+  // twiddles W16^{n2 k1}
+  const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h2 = 0.70710678118654752440f;
+  const float sg = INV ? 1.f : -1.f;  // imaginary sign of W16^m = cos - i sin (forward)
+  // k1 = 1: m = n2
+  a[5] = cmul(a[5], make_float2(c1, sg * s1));
+  a[6] = cmul(a[6], make_float2(h2, sg * h2));
+  a[7] = cmul(a[7], make_float2(s1, sg * c1));
+  // k1 = 2: m = 2 n2
+  a[9] = cmul(a[9], make_float2(h2, sg * h2));
+  a[10] = rot<INV>(a[10]);
+  a[11] = cmul(a[11], make_float2(-h2, sg * h2));
+  // k1 = 3: m = 3 n2
+  a[13] = cmul(a[13], make_float2(s1, sg * c1));
+  a[14] = cmul(a[14], make_float2(-h2, sg * h2));
+  a[15] = cmul(a[15], make_float2(-c1, -sg * s1));
+  // stage 2: DFT4 over n2 for each k1; X[k1 + 4 k2] = result k2
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+  // a[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4x4 index
+  float2 t;
+  t = a[1]; a[1] = a[4]; a[4] = t;
+  t = a[2]; a[2] = a[8]; a[8] = t;
+  t = a[3]; a[3] = a[12]; a[12] = t;
+  t = a[6]; a[6] = a[9]; a[9] = t;
+  t = a[7]; a[7] = a[13]; a[13] = t;
+  t = a[11]; a[11] = a[14]; a[14] = t;
+}
+
+// In-place 256-point FFT of 32 padded lines (stride LD) with 512 threads: thread t works on
+// line t/16, index j = t%16.  Pass 1 combines x[16 n1 + j] over n1 (reads and writes the same
+// addresses); pass 2 combines the 16 values of one row of the 16 x 16 decomposition.
+template <bool INV>
+__device__ __forceinline__ void fft256_lines(float2* buf, const float2* tw) {
+  const int l = threadIdx.x >> 4, j = threadIdx.x & 15;
+  float2* line = buf + l * LD;
+  float2 a[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) a[n1] = line[17 * n1 + j];
+  dft16<INV>(a);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) {
+    const float2 w = tw[(j * k1) & 255];
+    a[k1] = INV ? cmulc(a[k1], w) : cmul(a[k1], w);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) line[17 * k1 + j] = a[k1];
+  __syncthreads();
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) a[n2] = line[17 * j + n2];
+  dft16<INV>(a);
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) line[j + 17 * k2] = a[k2];
+  __syncthreads();
+}
+
+__device__ __forceinline__ double time_factor(const FieldDesc& F, double t, double y) {
+  switch (F.kind) {
+    case SWF_FIELD_SAUTER_GAUSS: {
+      const double c = cosh(F.prm[1] * t);
+      return (F.prm[0] / F.prm[1]) / (c * c);
+    }
+    case SWF_FIELD_PULSE_GAUSS: {
+      const double u = t - y;
+      return F.prm[0] * sin(F.prm[1] * u) * exp(-u * u / (F.prm[2] * F.prm[2]));
+    }
+    case SWF_FIELD_SINGLE_E:
+    case SWF_FIELD_DOUBLE_E: {
+      const double a = F.prm[1] * t;
+      return exp(-a * a);
+    }
+    default:
+      return 0.0;
+  }
+}
+
+__device__ __forceinline__ double single_e_x(const FieldDesc& F, double x) {
+  const double kx = F.prm[2];
+  return -(F.prm[0] / kx) * sin(kx * x) * exp(-(kx * x) * (kx * x));
+}
+
+__device__ double axis_factor(const FieldDesc& F, int axis, double xc) {
+  switch (F.kind) {
+    case SWF_FIELD_SAUTER_GAUSS: {
+      const double lam = F.prm[2];
+      return lam > 0.0 ? exp(-xc * xc / (lam * lam)) : 1.0;
+    }
+    case SWF_FIELD_PULSE_GAUSS:
+      if (axis == 0) return exp(-xc * xc / (F.prm[3] * F.prm[3]));
+      return F.prm[4] > 0.0 ? exp(-xc * xc / (F.prm[4] * F.prm[4])) : 1.0;
+    case SWF_FIELD_SINGLE_E:
+    case SWF_FIELD_DOUBLE_E:
+      if (axis == 0)
+        return F.kind == SWF_FIELD_SINGLE_E ? single_e_x(F, xc)
+                                            : single_e_x(F, xc + F.prm[5]) + single_e_x(F, xc - F.prm[5]);
+      return exp(-(F.prm[3] * xc) * (F.prm[3] * xc));
+    default:
+      return 0.0;
+  }
+}
+
+// V (phi0, phi1) for the sector (components c0, c1) with the one non-zero A_mu = a.
+__device__ __forceinline__ void sector_v(int acomp, int sigma, float a, float2 p0, float2 p1, float2& o0, float2& o1) {
+  if (acomp == 0) {
+    o0 = scl(a, p0);
+    o1 = scl(a, p1);
+  } else if (acomp == 1) {  // alpha^x swaps the pair
+    o0 = scl(a, p1);
+    o1 = scl(a, p0);
+  } else if (acomp == 2) {  // alpha^y: [[0, -i sigma], [i sigma, 0]]
+    const float sa = sigma * a;
+    o0 = make_float2(sa * p1.y, -sa * p1.x);
+    o1 = make_float2(-sa * p0.y, sa * p0.x);
+  } else {
+    o0 = make_float2(0.f, 0.f);
+    o1 = o0;
+  }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  float2* WA = reinterpret_cast<float2*>(sm + OFF_WA);
+  float2* WB = reinterpret_cast<float2*>(sm + OFF_WB);
+  float2* Ys = reinterpret_cast<float2*>(sm + OFF_Y);
+  float2* tw = reinterpret_cast<float2*>(sm + OFF_TW);
+  float2* ex = reinterpret_cast<float2*>(sm + OFF_EX);
+  float* gx = reinterpret_cast<float*>(sm + OFF_GX);
+  float2* ey = reinterpret_cast<float2*>(sm + OFF_EY);
+  float* gy = reinterpret_cast<float*>(sm + OFF_GY);
+  float* kxt = reinterpret_cast<float*>(sm + OFF_KX);
+  float* kyt = reinterpret_cast<float*>(sm + OFF_KY);
+  float* s_ft = reinterpret_cast<float*>(sm + OFF_MISC);                     // [7][RB] field time factor
+  float2* s_tf = reinterpret_cast<float2*>(sm + OFF_MISC + 7 * RB * 4);      // [7] background time phase
+  float2* s_w = reinterpret_cast<float2*>(sm + OFF_MISC + 7 * RB * 4 + 56);  // sector spinor [2]
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int cid = blockIdx.x / CL;
+  const int ncl = gridDim.x / CL;
+  const int tid = threadIdx.x;
+  const int row0 = rank * RB;
+  const size_t plane = (size_t)NX * NY;
+  float2* slot = A.slots + (size_t)cid * 9 * 2 * plane;
+
+  for (int m = tid; m < 256; m += NT) {
+    double s, c;
+    sincospi(-2.0 * m / 256.0, &s, &c);
+    tw[m] = make_float2((float)c, (float)s);
+  }
+  const double dxx = A.Lx / NX, dyy = A.Ly / NY;
+  const float inv_n = 1.0f / (float)(NX * NY);
+  // Dormand-Prince tableau (Dormand & Prince 1980), first same as last
+  const double DPc[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
+  const double DPa[7][6] = {{0, 0, 0, 0, 0, 0},
+                            {0.2, 0, 0, 0, 0, 0},
+                            {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+                            {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+                            {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+                            {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+                            {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+
+  for (int si = cid; si < A.n_sec; si += ncl) {
+    const Sector S = A.sec[si];
+    const FieldDesc& F = A.fd[S.inst];
+    // per-sector tables (FP64, rounded once)
+    for (int i = tid; i < NX; i += NT) {
+      const double xc = -0.5 * A.Lx + i * dxx;
+      gx[i] = (float)axis_factor(F, 0, xc);
+      double s, c;
+      sincos(F.pmom[0] * xc, &s, &c);
+      ex[i] = make_float2((float)c, (float)s);
+    }
+    if (tid < RB) {
+      const double yc = -0.5 * A.Ly + (row0 + tid) * dyy;
+      gy[tid] = (float)axis_factor(F, 1, yc);
+      double s, c;
+      sincos(F.pmom[1] * yc, &s, &c);
+      ey[tid] = make_float2((float)c, (float)s);
+    }
+    for (int i = tid; i < NX; i += NT) kxt[i] = (float)(6.283185307179586476925286766559 * (i < NX / 2 ? i : i - NX) / A.Lx);
+    for (int i = tid; i < NY; i += NT)
+      kyt[i] = (float)(S.sigma * 6.283185307179586476925286766559 * (i < NY / 2 ? i : i - NY) / A.Ly);
+    if (tid < 2) {
+      const int c = tid == 0 ? S.c0 : S.c1;
+      s_w[tid] = make_float2((float)F.w[2 * c], (float)F.w[2 * c + 1]);
+    }
+    for (int i = tid; i < NSL; i += NT) Ys[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < NSL; i += NT) {
+      const int comp = i / (RB * NX), rem = i % (RB * NX);
+      __stcg(slot + (size_t)8 * 2 * plane + comp * plane + (size_t)row0 * NX + rem, make_float2(0.f, 0.f));
+    }
+    __syncthreads();
+
+    int kslot[7] = {0, 1, 2, 3, 4, 5, 6};
+    float2* stash = slot + (size_t)7 * 2 * plane;
+    // evaluations: e = 0 is k_1 = f(t_out, 0); then 6 per step
+    const int n_eval = 1 + 6 * A.n_steps;
+    for (int ev = 0; ev < n_eval; ++ev) {
+      const int step = ev == 0 ? 0 : (ev - 1) / 6;
+      const int stage = ev == 0 ? 0 : 1 + (ev - 1) % 6;  // 0..6 (stage index i)
+      if (ev > 0 && stage == 1 && step > 0) {
+        const int t0 = kslot[0];
+        kslot[0] = kslot[6];
+        kslot[6] = t0;
+      }
+      // time factors of every stage of this step at once (FP64, rounded once): one FP64
+      // latency per step instead of one per evaluation
+      if (ev == 0 || stage == 1) {
+        const int st0 = ev == 0 ? 0 : 1, nst = ev == 0 ? 1 : 6;
+        if (tid < nst * RB) {
+          const int si2 = st0 + tid / RB, r = tid % RB;
+          const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+          const double yc = -0.5 * A.Ly + (row0 + r) * dyy;
+          s_ft[si2 * RB + r] = (float)time_factor(F, ts, yc);
+        } else if (tid >= 128 && tid < 128 + nst) {
+          const int si2 = st0 + tid - 128;
+          const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+          double s, c;
+          sincos(F.tsign * F.e0 * ts, &s, &c);
+          s_tf[si2] = make_float2((float)c, (float)s);
+        }
+        __syncthreads();
+      }
+      // ---- 1. stage combine, local term, rows into WA
+      float coef[6];
+      const float2* kin[6];
+      int nterm = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        coef[j] = 0.f;
+        kin[j] = slot;
+      }
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j < stage && DPa[stage][j] != 0.0) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q)
+            if (q == nterm) {
+              coef[q] = (float)(A.h * DPa[stage][j]);
+              kin[q] = slot + (size_t)kslot[j] * 2 * plane;
+            }
+          ++nterm;
+        }
+      }
+      float2* kout = slot + (size_t)kslot[stage] * 2 * plane;
+      const float2 tf = s_tf[stage];
+      const float* ftr = s_ft + stage * RB;
+      float2* ylo = slot + (size_t)8 * 2 * plane;
+      const float2 w0 = s_w[0], w1 = s_w[1];
+#pragma unroll 2
+      for (int m = 0; m < 4; ++m) {
+        const int sp = tid + NT * m;   // site pair in the slab: 16 rows x 128 pairs
+        const int r = sp >> 7;
+        const int x = (sp & 127) * 2;
+        const size_t g0 = (size_t)(row0 + r) * NX + x;
+        const float4 yh0 = *reinterpret_cast<const float4*>(Ys + r * NX + x);
+        const float4 yh1 = *reinterpret_cast<const float4*>(Ys + RB * NX + r * NX + x);
+        // the last stage accumulates h sum_j b_j k_j separately and adds it to (y, y_low)
+        // in float-float arithmetic; other stages form Y from y directly
+        const bool last = stage == 6;
+        float4 y0 = last ? make_float4(0.f, 0.f, 0.f, 0.f) : yh0;
+        float4 y1 = last ? make_float4(0.f, 0.f, 0.f, 0.f) : yh1;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          if (q < nterm) {
+            const float4 k0 = __ldcg(reinterpret_cast<const float4*>(kin[q] + g0));
+            const float4 k1 = __ldcg(reinterpret_cast<const float4*>(kin[q] + plane + g0));
+            const float c = coef[q];
+            y0.x = fmaf(c, k0.x, y0.x); y0.y = fmaf(c, k0.y, y0.y); y0.z = fmaf(c, k0.z, y0.z); y0.w = fmaf(c, k0.w, y0.w);
+            y1.x = fmaf(c, k1.x, y1.x); y1.y = fmaf(c, k1.y, y1.y); y1.z = fmaf(c, k1.z, y1.z); y1.w = fmaf(c, k1.w, y1.w);
+          }
+        }
+        if (last) {
+          float4 l0 = __ldcg(reinterpret_cast<const float4*>(ylo + g0));
+          float4 l1 = __ldcg(reinterpret_cast<const float4*>(ylo + plane + g0));
+          ff_add(yh0.x, l0.x, y0.x); ff_add(yh0.y, l0.y, y0.y); ff_add(yh0.z, l0.z, y0.z); ff_add(yh0.w, l0.w, y0.w);
+          ff_add(yh1.x, l1.x, y1.x); ff_add(yh1.y, l1.y, y1.y); ff_add(yh1.z, l1.z, y1.z); ff_add(yh1.w, l1.w, y1.w);
+          __stcg(reinterpret_cast<float4*>(ylo + g0), l0);
+          __stcg(reinterpret_cast<float4*>(ylo + plane + g0), l1);
+          *reinterpret_cast<float4*>(Ys + r * NX + x) = y0;
+          *reinterpret_cast<float4*>(Ys + RB * NX + r * NX + x) = y1;
+        }
+        // rows into WA (padded)
+        float2* wa0 = WA + r * LD + pidx(x);
+        float2* wa1 = WA + (RB + r) * LD + pidx(x);
+        wa0[0] = make_float2(y0.x, y0.y);
+        wa0[1] = make_float2(y0.z, y0.w);
+        wa1[0] = make_float2(y1.x, y1.y);
+        wa1[1] = make_float2(y1.z, y1.w);
+        // local term Z = -i V (Y + psi_b) on the two sites
+        const float ft = ftr[r];
+        const float2 phy = cmul(tf, ey[r]);
+        float4 z0, z1;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float2 ph = cmul(phy, ex[x + e]);
+          const float a = ft * gy[r] * gx[x + e];
+          const float2 p0 = (e ? make_float2(y0.z, y0.w) : make_float2(y0.x, y0.y)) + cmul(w0, ph);
+          const float2 p1 = (e ? make_float2(y1.z, y1.w) : make_float2(y1.x, y1.y)) + cmul(w1, ph);
+          float2 v0, v1;
+          sector_v(F.acomp, S.sigma, a, p0, p1, v0, v1);
+          v0 = rot<false>(v0);
+          v1 = rot<false>(v1);
+          if (e) { z0.z = v0.x; z0.w = v0.y; z1.z = v1.x; z1.w = v1.y; }
+          else { z0.x = v0.x; z0.y = v0.y; z1.x = v1.x; z1.y = v1.y; }
+        }
+        __stcg(reinterpret_cast<float4*>(stash + g0), z0);
+        __stcg(reinterpret_cast<float4*>(stash + plane + g0), z1);
+      }
+      __syncthreads();
+      fft256_lines<false>(WA, tw);
+      // ---- 2. transpose rows -> columns through distributed shared memory
+      cluster.sync();
+      {
+        const int comp = tid >> 8, r = (tid >> 4) & 15, col = tid & 15;
+#pragma unroll
+        for (int s = 0; s < CL; ++s) {
+          const float2* src = cluster.map_shared_rank(WA, s);
+          WB[(comp * CB + col) * LD + pidx(s * RB + r)] = src[(comp * RB + r) * LD + pidx(rank * CB + col)];
+        }
+      }
+      __syncthreads();
+      fft256_lines<false>(WB, tw);
+      // -i H0(kappa)/N per mode of the sector
+      {
+#pragma unroll 2
+        for (int m = tid; m < CB * NY; m += NT) {
+          const int col = m >> 8, iy = m & 255;
+          const float kx = kxt[rank * CB + col];
+          const float ky = kyt[iy];
+          float2* pa = WB + col * LD + pidx(iy);
+          float2* pb = WB + (CB + col) * LD + pidx(iy);
+          const float2 a = *pa, b = *pb;
+          // [[1, kx - i ky], [kx + i ky, -1]] (a, b), then times -i/N
+          const float2 h0 = make_float2(a.x + kx * b.x + ky * b.y, a.y + kx * b.y - ky * b.x);
+          const float2 h1 = make_float2(kx * a.x - ky * a.y - b.x, kx * a.y + ky * a.x - b.y);
+          *pa = scl(inv_n, rot<false>(h0));
+          *pb = scl(inv_n, rot<false>(h1));
+        }
+      }
+      __syncthreads();
+      fft256_lines<true>(WB, tw);
+      // ---- 3. transpose columns -> rows, inverse x-FFT, output
+      cluster.sync();
+      {
+        const int comp = tid >> 8, col = (tid >> 4) & 15, r = tid & 15;
+#pragma unroll
+        for (int s = 0; s < CL; ++s) {
+          const float2* src = cluster.map_shared_rank(WB, s);
+          WA[(comp * RB + r) * LD + pidx(s * CB + col)] = src[(comp * CB + col) * LD + pidx(rank * RB + r)];
+        }
+      }
+      __syncthreads();
+      fft256_lines<true>(WA, tw);
+#pragma unroll 4
+      for (int m = 0; m < 4; ++m) {
+        const int sp = tid + NT * m;
+        const int r = sp >> 7;
+        const int x = (sp & 127) * 2;
+        const size_t g0 = (size_t)(row0 + r) * NX + x;
+        const float4 z0 = __ldcg(reinterpret_cast<const float4*>(stash + g0));
+        const float4 z1 = __ldcg(reinterpret_cast<const float4*>(stash + plane + g0));
+        const float2* wa0 = WA + r * LD + pidx(x);
+        const float2* wa1 = WA + (RB + r) * LD + pidx(x);
+        const float4 o0 = make_float4(wa0[0].x + z0.x, wa0[0].y + z0.y, wa0[1].x + z0.z, wa0[1].y + z0.w);
+        const float4 o1 = make_float4(wa1[0].x + z1.x, wa1[0].y + z1.y, wa1[1].x + z1.z, wa1[1].y + z1.w);
+        __stcg(reinterpret_cast<float4*>(kout + g0), o0);
+        __stcg(reinterpret_cast<float4*>(kout + plane + g0), o1);
+      }
+      __syncthreads();
+    }
+    // psi(t_in) of the sector into the 4-component output
+    float2* out0 = A.psi_out + ((size_t)S.inst * 4 + S.c0) * plane + (size_t)row0 * NX;
+    float2* out1 = A.psi_out + ((size_t)S.inst * 4 + S.c1) * plane + (size_t)row0 * NX;
+    for (int i = tid; i < RB * NX; i += NT) {
+      out0[i] = Ys[i];
+      out1[i] = Ys[RB * NX + i];
+    }
+    __syncthreads();
+  }
+}
+
+
+// ------------------------------------------------------------------ two CTAs per SM variant
+// 256 threads and one shared buffer per CTA (about 76 KB), so that two CTAs (of two clusters)
+// share an SM and hide each other's barrier and memory latency.  y and its low part move to
+// the cluster's global slot; each transpose pulls into registers, waits for the whole cluster,
+// and then overwrites the buffer in place (two cluster barriers per transpose).
+namespace v2 {
+constexpr int NT2 = 256;
+constexpr int OFF_W = 0;                            // [2][16][LD] complex
+constexpr int OFF_TW2 = OFF_W + 2 * 16 * LD * 8;
+constexpr int OFF_EX2 = OFF_TW2 + 256 * 8;
+constexpr int OFF_GX2 = OFF_EX2 + NX * 8;
+constexpr int OFF_EY2 = OFF_GX2 + NX * 4;
+constexpr int OFF_GY2 = OFF_EY2 + RB * 8;
+constexpr int OFF_KX2 = OFF_GY2 + RB * 4;
+constexpr int OFF_KY2 = OFF_KX2 + NX * 4;
+constexpr int OFF_MISC2 = OFF_KY2 + NY * 4;
+constexpr int SMEM2 = OFF_MISC2 + 7 * RB * 4 + 7 * 8 + 16 + 64;
+}  // namespace v2
+
+// two lines per thread: lines t/16 and t/16 + 16
+template <bool INV>
+__device__ __forceinline__ void fft256_lines2(float2* buf, const float2* tw) {
+  const int l = threadIdx.x >> 4, j = threadIdx.x & 15;
+  float2* la = buf + l * LD;
+  float2* lb = buf + (l + 16) * LD;
+  float2 a[16], b[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) { a[n1] = la[17 * n1 + j]; b[n1] = lb[17 * n1 + j]; }
+  dft16<INV>(a);
+  dft16<INV>(b);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) {
+    const float2 w = tw[(j * k1) & 255];
+    a[k1] = INV ? cmulc(a[k1], w) : cmul(a[k1], w);
+    b[k1] = INV ? cmulc(b[k1], w) : cmul(b[k1], w);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) { la[17 * k1 + j] = a[k1]; lb[17 * k1 + j] = b[k1]; }
+  __syncthreads();
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) { a[n2] = la[17 * j + n2]; b[n2] = lb[17 * j + n2]; }
+  dft16<INV>(a);
+  dft16<INV>(b);
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) { la[j + 17 * k2] = a[k2]; lb[j + 17 * k2] = b[k2]; }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
+  using namespace v2;
+  extern __shared__ __align__(16) unsigned char sm[];
+  float2* W = reinterpret_cast<float2*>(sm + OFF_W);
+  float2* tw = reinterpret_cast<float2*>(sm + OFF_TW2);
+  float2* ex = reinterpret_cast<float2*>(sm + OFF_EX2);
+  float* gx = reinterpret_cast<float*>(sm + OFF_GX2);
+  float2* ey = reinterpret_cast<float2*>(sm + OFF_EY2);
+  float* gy = reinterpret_cast<float*>(sm + OFF_GY2);
+  float* kxt = reinterpret_cast<float*>(sm + OFF_KX2);
+  float* kyt = reinterpret_cast<float*>(sm + OFF_KY2);
+  float* s_ft = reinterpret_cast<float*>(sm + OFF_MISC2);
+  float2* s_tf = reinterpret_cast<float2*>(sm + OFF_MISC2 + 7 * RB * 4);
+  float2* s_w = reinterpret_cast<float2*>(sm + OFF_MISC2 + 7 * RB * 4 + 56);
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int cid = blockIdx.x / CL;
+  const int ncl = gridDim.x / CL;
+  const int tid = threadIdx.x;
+  const int row0 = rank * RB;
+  const size_t plane = (size_t)NX * NY;
+  float2* slot = A.slots + (size_t)cid * 10 * 2 * plane;
+  float2* stash = slot + (size_t)7 * 2 * plane;
+  float2* yg = slot + (size_t)8 * 2 * plane;
+  float2* ylo = slot + (size_t)9 * 2 * plane;
+
+  for (int m = tid; m < 256; m += NT2) {
+    double sn, cs;
+    sincospi(-2.0 * m / 256.0, &sn, &cs);
+    tw[m] = make_float2((float)cs, (float)sn);
+  }
+  const double dxx = A.Lx / NX, dyy = A.Ly / NY;
+  const float inv_n = 1.0f / (float)(NX * NY);
+  const double DPc[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
+  const double DPa[7][6] = {{0, 0, 0, 0, 0, 0},
+                            {0.2, 0, 0, 0, 0, 0},
+                            {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+                            {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+                            {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+                            {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+                            {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+
+  for (int si = cid; si < A.n_sec; si += ncl) {
+    const Sector S = A.sec[si];
+    const FieldDesc& F = A.fd[S.inst];
+    for (int i = tid; i < NX; i += NT2) {
+      const double xc = -0.5 * A.Lx + i * dxx;
+      gx[i] = (float)axis_factor(F, 0, xc);
+      double sn, cs;
+      sincos(F.pmom[0] * xc, &sn, &cs);
+      ex[i] = make_float2((float)cs, (float)sn);
+      kxt[i] = (float)(6.283185307179586476925286766559 * (i < NX / 2 ? i : i - NX) / A.Lx);
+    }
+    for (int i = tid; i < NY; i += NT2)
+      kyt[i] = (float)(S.sigma * 6.283185307179586476925286766559 * (i < NY / 2 ? i : i - NY) / A.Ly);
+    if (tid < RB) {
+      const double yc = -0.5 * A.Ly + (row0 + tid) * dyy;
+      gy[tid] = (float)axis_factor(F, 1, yc);
+      double sn, cs;
+      sincos(F.pmom[1] * yc, &sn, &cs);
+      ey[tid] = make_float2((float)cs, (float)sn);
+    }
+    if (tid < 2) {
+      const int c = tid == 0 ? S.c0 : S.c1;
+      s_w[tid] = make_float2((float)F.w[2 * c], (float)F.w[2 * c + 1]);
+    }
+    for (int i = tid; i < NSL; i += NT2) {
+      const int comp = i / (RB * NX), rem = i % (RB * NX);
+      const size_t gi = comp * plane + (size_t)row0 * NX + rem;
+      __stcg(yg + gi, make_float2(0.f, 0.f));
+      __stcg(ylo + gi, make_float2(0.f, 0.f));
+    }
+    __syncthreads();
+
+    int kslot[7] = {0, 1, 2, 3, 4, 5, 6};
+    const int n_eval = 1 + 6 * A.n_steps;
+    for (int ev = 0; ev < n_eval; ++ev) {
+      const int step = ev == 0 ? 0 : (ev - 1) / 6;
+      const int stage = ev == 0 ? 0 : 1 + (ev - 1) % 6;
+      if (ev > 0 && stage == 1 && step > 0) {
+        const int t0 = kslot[0];
+        kslot[0] = kslot[6];
+        kslot[6] = t0;
+      }
+      if (ev == 0 || stage == 1) {
+        const int st0 = ev == 0 ? 0 : 1, nst = ev == 0 ? 1 : 6;
+        if (tid < nst * RB) {
+          const int si2 = st0 + tid / RB, r = tid % RB;
+          const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+          const double yc = -0.5 * A.Ly + (row0 + r) * dyy;
+          s_ft[si2 * RB + r] = (float)time_factor(F, ts, yc);
+        } else if (tid >= 128 && tid < 128 + nst) {
+          const int si2 = st0 + tid - 128;
+          const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+          double sn, cs;
+          sincos(F.tsign * F.e0 * ts, &sn, &cs);
+          s_tf[si2] = make_float2((float)cs, (float)sn);
+        }
+        __syncthreads();
+      }
+      float coef[6];
+      const float2* kin[6];
+      int nterm = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        coef[j] = 0.f;
+        kin[j] = slot;
+      }
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j < stage && DPa[stage][j] != 0.0) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q)
+            if (q == nterm) {
+              coef[q] = (float)(A.h * DPa[stage][j]);
+              kin[q] = slot + (size_t)kslot[j] * 2 * plane;
+            }
+          ++nterm;
+        }
+      }
+      float2* kout = slot + (size_t)kslot[stage] * 2 * plane;
+      const float2 tf = s_tf[stage];
+      const float* ftr = s_ft + stage * RB;
+      const float2 w0 = s_w[0], w1 = s_w[1];
+      const bool last = stage == 6;
+      // ---- 1. stage combine and local term
+#pragma unroll 2
+      for (int m = 0; m < 8; ++m) {
+        const int sp = tid + NT2 * m;
+        const int r = sp >> 7;
+        const int x = (sp & 127) * 2;
+        const size_t g0 = (size_t)(row0 + r) * NX + x;
+        const float4 yh0 = __ldcg(reinterpret_cast<const float4*>(yg + g0));
+        const float4 yh1 = __ldcg(reinterpret_cast<const float4*>(yg + plane + g0));
+        float4 y0 = last ? make_float4(0.f, 0.f, 0.f, 0.f) : yh0;
+        float4 y1 = last ? make_float4(0.f, 0.f, 0.f, 0.f) : yh1;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          if (q < nterm) {
+            const float4 k0 = __ldcg(reinterpret_cast<const float4*>(kin[q] + g0));
+            const float4 k1 = __ldcg(reinterpret_cast<const float4*>(kin[q] + plane + g0));
+            const float c = coef[q];
+            y0.x = fmaf(c, k0.x, y0.x); y0.y = fmaf(c, k0.y, y0.y); y0.z = fmaf(c, k0.z, y0.z); y0.w = fmaf(c, k0.w, y0.w);
+            y1.x = fmaf(c, k1.x, y1.x); y1.y = fmaf(c, k1.y, y1.y); y1.z = fmaf(c, k1.z, y1.z); y1.w = fmaf(c, k1.w, y1.w);
+          }
+        }
+        if (last) {
+          float4 l0 = __ldcg(reinterpret_cast<const float4*>(ylo + g0));
+          float4 l1 = __ldcg(reinterpret_cast<const float4*>(ylo + plane + g0));
+          ff_add(yh0.x, l0.x, y0.x); ff_add(yh0.y, l0.y, y0.y); ff_add(yh0.z, l0.z, y0.z); ff_add(yh0.w, l0.w, y0.w);
+          ff_add(yh1.x, l1.x, y1.x); ff_add(yh1.y, l1.y, y1.y); ff_add(yh1.z, l1.z, y1.z); ff_add(yh1.w, l1.w, y1.w);
+          __stcg(reinterpret_cast<float4*>(ylo + g0), l0);
+          __stcg(reinterpret_cast<float4*>(ylo + plane + g0), l1);
+          __stcg(reinterpret_cast<float4*>(yg + g0), y0);
+          __stcg(reinterpret_cast<float4*>(yg + plane + g0), y1);
+        }
+        float2* wa0 = W + r * LD + pidx(x);
+        float2* wa1 = W + (RB + r) * LD + pidx(x);
+        wa0[0] = make_float2(y0.x, y0.y);
+        wa0[1] = make_float2(y0.z, y0.w);
+        wa1[0] = make_float2(y1.x, y1.y);
+        wa1[1] = make_float2(y1.z, y1.w);
+        const float ft = ftr[r];
+        const float2 phy = cmul(tf, ey[r]);
+        float4 z0, z1;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float2 ph = cmul(phy, ex[x + e]);
+          const float a = ft * gy[r] * gx[x + e];
+          const float2 p0 = (e ? make_float2(y0.z, y0.w) : make_float2(y0.x, y0.y)) + cmul(w0, ph);
+          const float2 p1 = (e ? make_float2(y1.z, y1.w) : make_float2(y1.x, y1.y)) + cmul(w1, ph);
+          float2 v0, v1;
+          sector_v(F.acomp, S.sigma, a, p0, p1, v0, v1);
+          v0 = rot<false>(v0);
+          v1 = rot<false>(v1);
+          if (e) { z0.z = v0.x; z0.w = v0.y; z1.z = v1.x; z1.w = v1.y; }
+          else { z0.x = v0.x; z0.y = v0.y; z1.x = v1.x; z1.y = v1.y; }
+        }
+        __stcg(reinterpret_cast<float4*>(stash + g0), z0);
+        __stcg(reinterpret_cast<float4*>(stash + plane + g0), z1);
+      }
+      __syncthreads();
+      fft256_lines2<false>(W, tw);
+      // ---- 2. rows -> columns (pull into registers, barrier, overwrite in place)
+      float2 st[32];
+      cluster.sync();
+      {
+        const int col = tid & 15, r = (tid >> 4) & 15;
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp)
+#pragma unroll
+          for (int s = 0; s < CL; ++s)
+            st[comp * 16 + s] = cluster.map_shared_rank(W, s)[(comp * RB + r) * LD + pidx(rank * CB + col)];
+        cluster.sync();
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp)
+#pragma unroll
+          for (int s = 0; s < CL; ++s) W[(comp * CB + col) * LD + pidx(s * RB + r)] = st[comp * 16 + s];
+      }
+      __syncthreads();
+      fft256_lines2<false>(W, tw);
+#pragma unroll 4
+      for (int m = tid; m < CB * NY; m += NT2) {
+        const int col = m >> 8, iy = m & 255;
+        const float kx = kxt[rank * CB + col];
+        const float ky = kyt[iy];
+        float2* pa = W + col * LD + pidx(iy);
+        float2* pb = W + (CB + col) * LD + pidx(iy);
+        const float2 a = *pa, b = *pb;
+        const float2 h0 = make_float2(a.x + kx * b.x + ky * b.y, a.y + kx * b.y - ky * b.x);
+        const float2 h1 = make_float2(kx * a.x - ky * a.y - b.x, kx * a.y + ky * a.x - b.y);
+        *pa = scl(inv_n, rot<false>(h0));
+        *pb = scl(inv_n, rot<false>(h1));
+      }
+      __syncthreads();
+      fft256_lines2<true>(W, tw);
+      // ---- 3. columns -> rows, inverse x-FFT, output
+      cluster.sync();
+      {
+        const int r = tid & 15, col = (tid >> 4) & 15;
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp)
+#pragma unroll
+          for (int s = 0; s < CL; ++s)
+            st[comp * 16 + s] = cluster.map_shared_rank(W, s)[(comp * CB + col) * LD + pidx(rank * RB + r)];
+        cluster.sync();
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp)
+#pragma unroll
+          for (int s = 0; s < CL; ++s) W[(comp * RB + r) * LD + pidx(s * CB + col)] = st[comp * 16 + s];
+      }
+      __syncthreads();
+      fft256_lines2<true>(W, tw);
+#pragma unroll 4
+      for (int m = 0; m < 8; ++m) {
+        const int sp = tid + NT2 * m;
+        const int r = sp >> 7;
+        const int x = (sp & 127) * 2;
+        const size_t g0 = (size_t)(row0 + r) * NX + x;
+        const float4 z0 = __ldcg(reinterpret_cast<const float4*>(stash + g0));
+        const float4 z1 = __ldcg(reinterpret_cast<const float4*>(stash + plane + g0));
+        const float2* wa0 = W + r * LD + pidx(x);
+        const float2* wa1 = W + (RB + r) * LD + pidx(x);
+        const float4 o0 = make_float4(wa0[0].x + z0.x, wa0[0].y + z0.y, wa0[1].x + z0.z, wa0[1].y + z0.w);
+        const float4 o1 = make_float4(wa1[0].x + z1.x, wa1[0].y + z1.y, wa1[1].x + z1.z, wa1[1].y + z1.w);
+        __stcg(reinterpret_cast<float4*>(kout + g0), o0);
+        __stcg(reinterpret_cast<float4*>(kout + plane + g0), o1);
+      }
+      __syncthreads();
+    }
+    float2* out0 = A.psi_out + ((size_t)S.inst * 4 + S.c0) * plane + (size_t)row0 * NX;
+    float2* out1 = A.psi_out + ((size_t)S.inst * 4 + S.c1) * plane + (size_t)row0 * NX;
+    for (int i = tid; i < RB * NX; i += NT2) {
+      out0[i] = __ldcg(yg + (size_t)row0 * NX + i);
+      out1[i] = __ldcg(yg + plane + (size_t)row0 * NX + i);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace fused
+
+// True when the fused kernel covers this march: (2+1)D 256 x 256 grid, complex64, no
+// momentum along the trivial z axis, and fields that keep the z-spin sectors apart.
+bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_precision prec) {
+  if (prec != SWF_C64) return false;
+  if (g.n[0] != fused::NX || g.n[1] != fused::NY || g.n[2] != 1) return false;
+  for (int f = 0; f < n_f; ++f) {
+    if (fd[f].K[2] != 0.0) return false;
+    if (fd[f].acomp == 3) return false;
+  }
+  return true;
+}
+
+static int g_fused_clusters[2] = {-1, -1};
+
+swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
+                       const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
+  using namespace fused;
+  const int var = ctx->fused_variant == 2 ? 1 : 0;
+  void (*kern)(Args) = var ? k_fused2 : k_fused;
+  const int nthr = var ? v2::NT2 : NT;
+  const int smem = var ? v2::SMEM2 : SMEM;
+  const int narr = var ? 10 : 9;
+  cudaError_t e;
+  auto config = [&](int ncl, cudaLaunchAttribute* at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ncl * CL, 1, 1);
+    cfg.blockDim = dim3(nthr, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    at->id = cudaLaunchAttributeClusterDimension;
+    at->val.clusterDim.x = CL;
+    at->val.clusterDim.y = 1;
+    at->val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+  };
+  if (g_fused_clusters[var] < 0) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return cuda_status(e, "cluster size attribute");
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_status(e, "shared memory attribute");
+    cudaLaunchAttribute at;
+    cudaLaunchConfig_t cfg = config(1, &at);
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+    if (e != cudaSuccess) return cuda_status(e, "cudaOccupancyMaxActiveClusters");
+    if (ncl < 1) {
+      set_error("the fused march kernel cannot be resident on this device");
+      return SWF_EUNSUPPORTED;
+    }
+    g_fused_clusters[var] = ncl;
+  }
+  const int n_sec = 2 * n_f;
+  const int ncl = g_fused_clusters[var] < n_sec ? g_fused_clusters[var] : n_sec;
+  const size_t plane = (size_t)NX * NY;
+  swf_status s;
+  void *pfd, *psec, *pslots;
+  if ((s = ws_get(ctx, "fused.fd", sizeof(FieldDesc) * n_f, &pfd)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "fused.sec", sizeof(Sector) * n_sec, &psec)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "fused.slots", (size_t)ncl * narr * 2 * plane * sizeof(float2), &pslots)) != SWF_OK) return s;
+  std::vector<Sector> sec(n_sec);
+  for (int f = 0; f < n_f; ++f) {
+    sec[2 * f] = {f, 0, 3, +1};
+    sec[2 * f + 1] = {f, 1, 2, -1};
+  }
+  e = cudaMemcpyAsync(pfd, fd_host, sizeof(FieldDesc) * n_f, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload field descriptors");
+  e = cudaMemcpyAsync(psec, sec.data(), sizeof(Sector) * n_sec, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload sector table");
+  Args A;
+  A.fd = (const FieldDesc*)pfd;
+  A.sec = (const Sector*)psec;
+  A.n_sec = n_sec;
+  A.slots = (float2*)pslots;
+  A.psi_out = (float2*)psi_out;
+  A.Lx = g.L[0];
+  A.Ly = g.L[1];
+  A.t_out = t_out;
+  A.h = (t_in - t_out) / n_steps;
+  A.n_steps = n_steps;
+  cudaLaunchAttribute at;
+  cudaLaunchConfig_t cfg = config(ncl, &at);
+  {
+    ProfScope ps(ctx, "k_fused", st);
+    e = cudaLaunchKernelEx(&cfg, kern, A);
+  }
+  if (e != cudaSuccess) return cuda_status(e, "launch fused march");
+  e = cudaStreamSynchronize(st);  // the sector table above is a host temporary
+  if (e != cudaSuccess) return cuda_status(e, "fused march");
+  return SWF_OK;
+}
+
+int fused_clusters() { return g_fused_clusters[0]; }
+
+}  // namespace swf

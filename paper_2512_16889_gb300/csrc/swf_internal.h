@@ -104,6 +104,8 @@ struct swf_ctx {
   swf::Workspace ws;
   swf::TwiddleCache tw;
   swf::Profiler prof;
+  bool use_fused = true;  // route eligible marches to the fused cluster kernel
+  int fused_variant = 2;  // 1: one CTA per SM, 2: two CTAs per SM
 };
 
 namespace swf {
@@ -133,6 +135,11 @@ swf_status twiddles(swf_ctx* ctx, int n, int is_double, const void** ptr);
 swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
                         int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
                         cudaStream_t st);
+// ---- fused cluster march (swf_fused.cu)
+bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_precision prec);
+swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
+                       const FieldDesc* fd_host, void* psi_out, cudaStream_t st);
+int fused_clusters();
 swf_status rhs_eval(swf_ctx* ctx, const GridDesc& g, const FieldDesc& fd, swf_precision prec,
                     double t, const void* psi, void* out, cudaStream_t st);
 

@@ -519,6 +519,11 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
 swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
                         int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
                         cudaStream_t st) {
+  if (ctx->use_fused && fused_applicable(g, n_f, fd_host, prec)) {
+    swf_status s = march_fused(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
+    if (s != SWF_EUNSUPPORTED) return s;
+    ctx->use_fused = false;  // the cluster shape cannot be resident here: pass kernels from now on
+  }
   if (prec == SWF_C64) return march_impl<float>(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
   return march_impl<double>(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
 }

@@ -46,7 +46,7 @@ class Result(C.Structure):
 
 EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
-           "swf_profile_read"]
+           "swf_profile_read", "swf_set_march_path"]
 
 
 class SwfError(RuntimeError):
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_spectrum_dev.argtypes = [vp, ip, inst_p, ip, vp, vp, vp, vp]
     lib.swf_set_workspace_limit.argtypes = [vp, C.c_size_t]
     lib.swf_profile_enable.argtypes = [vp, ip]
+    lib.swf_set_march_path.argtypes = [vp, ip]
     lib.swf_profile_read.argtypes = [vp, ip, C.c_char_p, dbl_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
                                      C.POINTER(C.c_longlong)]
     for name in EXPORTS:
@@ -142,6 +143,10 @@ class Context:
 
     def set_workspace_limit(self, nbytes: int):
         _check(_lib.swf_set_workspace_limit(self._h, int(nbytes)))
+
+    def set_march_path(self, path: int):
+        """0 = automatic (fused cluster kernel where it applies), 1 = pass kernels only."""
+        _check(_lib.swf_set_march_path(self._h, int(path)))
 
     def profile_enable(self, on=True):
         _check(_lib.swf_profile_enable(self._h, 1 if on else 0))
