@@ -177,6 +177,25 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
  * apply). */
 swf_status swf_set_march_path(swf_ctx* ctx, int path);
 
+/* Allocation-free variant of swf_rhs_dev (the paper has no counterpart: this is a service of
+ * the library).  Some callers cannot call cudaMalloc: code that runs while a stream is being
+ * captured into a CUDA graph (an allocation is not captured, and cudaFree synchronises the
+ * device), latency-critical loops that cannot absorb that synchronisation, and host
+ * applications that own all device memory.  This entry point allocates nothing: it needs no
+ * context and takes its workspace from one fixed device array of about 4.1 MiB that every GPU
+ * loading the library holds until the process exits.  The caller passes inputs and outputs
+ * exactly as for swf_rhs_dev; the evaluation runs on the current CUDA device, on `stream`
+ * (NULL = the default stream), asynchronously.
+ * Limit: grids of at most 65536 points (for example 256 x 256 or 64 x 64 x 16) in either
+ * precision; larger grids return SWF_EINVAL with a message.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture begins.  All calls on a device share the array and
+ * it keeps the last call's contents (every value a call reads is written earlier by the same
+ * call), so calls that overlap on the GPU -- on different streams or from different host
+ * threads -- race on it and must be serialised by the caller. */
+swf_status swf_rhs_noalloc(const swf_instance* inst, int bg, swf_precision prec, double t,
+                           const void* psi_dev, void* out_dev, void* stream);
+
 /* Caps the context's device workspace (bytes; 0 = no cap).  Requests that need more return
  * SWF_ENOMEM before touching the device. */
 swf_status swf_set_workspace_limit(swf_ctx* ctx, size_t bytes);

@@ -217,6 +217,10 @@ static swf_status validate(int n_inst, const swf_instance* inst, swf_process pro
   return SWF_OK;
 }
 
+swf_status validate_instances(int n_inst, const swf_instance* inst, swf_precision prec) {
+  return validate(n_inst, inst, SWF_SCHWINGER, prec);
+}
+
 static cudaStream_t pick_stream(swf_ctx* ctx, void* stream) {
   return stream ? (cudaStream_t)stream : ctx->stream;
 }

@@ -111,6 +111,7 @@ struct swf_ctx {
 namespace swf {
 
 void set_error(const std::string& msg);
+swf_status validate_instances(int n_inst, const swf_instance* inst, swf_precision prec);
 
 // Kernel timing: call prof_begin before a launch and prof_end after it (same stream).
 int prof_begin(swf_ctx* ctx, const char* family, cudaStream_t st);
@@ -142,6 +143,10 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
 int fused_clusters();
 swf_status rhs_eval(swf_ctx* ctx, const GridDesc& g, const FieldDesc& fd, swf_precision prec,
                     double t, const void* psi, void* out, cudaStream_t st);
+// The same evaluation with all workspace taken from caller-provided device scratch.
+size_t rhs_scratch_bytes(const GridDesc& g, swf_precision prec);
+swf_status rhs_eval_scratch(const GridDesc& g, const FieldDesc& fd, swf_precision prec, double t, const void* psi,
+                            void* out, void* scratch, cudaStream_t st);
 
 // ---- projections (swf_project.cu)
 // psi [F][4][N] (march precision) -> FP64 transform on every grid mode, with the continuum

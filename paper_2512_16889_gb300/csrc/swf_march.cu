@@ -555,3 +555,111 @@ swf_status rhs_eval(swf_ctx* ctx, const GridDesc& g, const FieldDesc& fd, swf_pr
 }
 
 }  // namespace swf
+
+// ---------------------------------------------------------------- right-hand side in caller scratch
+namespace swf {
+
+template <typename R>
+__global__ void k_twiddles_into(cpx<R>* tw, int n) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * m / (double)n, &s, &c);
+    tw[m] = mk<R>((R)c, (R)s);
+  }
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t rhs_scratch_bytes(const GridDesc& g, swf_precision prec) {
+  const size_t e = prec == SWF_C64 ? 8 : 16, r = prec == SWF_C64 ? 4 : 8;
+  const size_t nt = g.n[0] + g.n[1] + g.n[2];
+  return align256(4 * (size_t)g.N * e) + align256(sizeof(FieldDesc)) + align256(nt * r) +
+         align256((nt + 4) * e) + 3 * align256(512 * e);
+}
+
+// Same evaluation as rhs_eval, with every buffer (FFT workspace, field tables, twiddles, the
+// field descriptor) carved out of `scratch` instead of the context's workspace; no device
+// memory is allocated.
+template <typename R>
+static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, double t, const void* psi, void* out,
+                                   unsigned char* scratch, cudaStream_t st) {
+  constexpr int MAXE = Prec<R>::MAXE;
+  swf_status s = set_smem_attrs<R>();
+  if (s != SWF_OK) return s;
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  unsigned char* p = scratch;
+  cpx<R>* T = (cpx<R>*)p;
+  p += align256((size_t)4 * g.N * sizeof(cpx<R>));
+  FieldDesc* dfd = (FieldDesc*)p;
+  p += align256(sizeof(FieldDesc));
+  R* greal = (R*)p;
+  p += align256((size_t)nt * sizeof(R));
+  cpx<R>* gcplx = (cpx<R>*)p;
+  p += align256((size_t)(nt + 4) * sizeof(cpx<R>));
+  StageArgs<R> A;
+  std::memset(&A, 0, sizeof(A));
+  A.g = g;
+  A.nrows = g.n[1] * g.n[2];
+  for (int a = 0; a < 3; ++a) {
+    if (!make_radix_plan(g.n[a], &A.plan[a])) {
+      set_error("grid size must factor into 2, 3 and 5");
+      return SWF_EINVAL;
+    }
+    cpx<R>* tw = (cpx<R>*)p;
+    p += align256(512 * sizeof(cpx<R>));
+    k_twiddles_into<R><<<(g.n[a] + 127) / 128, 128, 0, st>>>(tw, g.n[a]);
+    A.tw[a] = tw;
+  }
+  cudaError_t e = cudaMemcpyAsync(dfd, &fd, sizeof(FieldDesc), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload field descriptor");
+  k_tables<R><<<dim3((nt + 4 + 127) / 128, 1), 128, 0, st>>>(dfd, g, greal, gcplx);
+  A.fd = dfd;
+  A.greal = greal;
+  A.gcplx = gcplx;
+  A.y = const_cast<cpx<R>*>((const cpx<R>*)psi);
+  A.T = T;
+  A.kout = (cpx<R>*)out;
+  A.t = t;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int cap = elem_cap<R>();
+  int rows = cap / (4 * nx);
+  if (rows > 64) rows = 64;
+  if (rows > A.nrows) rows = A.nrows;
+  if (rows < 1) return SWF_EUNSUPPORTED;
+  const bool only_x = (ny == 1 && nz == 1);
+  const size_t smem = (size_t)4 * rows * nx * sizeof(cpx<R>);
+  const dim3 grid_rows((A.nrows + rows - 1) / rows, 1);
+  k_first<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, nx, only_x ? 1 : 0);
+  if (!only_x) {
+    auto mid = [&](int axis, int fwd, int h0, int inv) {
+      const int n_a = g.n[axis];
+      int TX = cap / (4 * n_a);
+      if (TX > 16) TX = 16;
+      if (TX > nx) TX = nx;
+      if (TX < 1) TX = 1;
+      const int ntx = (nx + TX - 1) / TX;
+      const int other = axis == 1 ? nz : ny;
+      k_mid<R, MAXE><<<dim3(ntx * other, 1), kThreads, (size_t)4 * TX * n_a * sizeof(cpx<R>), st>>>(A, axis, TX, n_a,
+                                                                                                       fwd, h0, inv);
+    };
+    if (ny > 1 && nz > 1) {
+      mid(1, 1, 0, 0);
+      mid(2, 1, 1, 1);
+      mid(1, 0, 0, 1);
+    } else {
+      mid(ny > 1 ? 1 : 2, 1, 1, 1);
+    }
+    k_last<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, nx);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "rhs kernels");
+  return SWF_OK;
+}
+
+swf_status rhs_eval_scratch(const GridDesc& g, const FieldDesc& fd, swf_precision prec, double t, const void* psi,
+                            void* out, void* scratch, cudaStream_t st) {
+  if (prec == SWF_C64) return rhs_scratch_impl<float>(g, fd, t, psi, out, (unsigned char*)scratch, st);
+  return rhs_scratch_impl<double>(g, fd, t, psi, out, (unsigned char*)scratch, st);
+}
+
+}  // namespace swf

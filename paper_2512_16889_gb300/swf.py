@@ -46,7 +46,7 @@ class Result(C.Structure):
 
 EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
-           "swf_profile_read", "swf_set_march_path"]
+           "swf_profile_read", "swf_set_march_path", "swf_rhs_noalloc"]
 
 
 class SwfError(RuntimeError):
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_set_workspace_limit.argtypes = [vp, C.c_size_t]
     lib.swf_profile_enable.argtypes = [vp, ip]
     lib.swf_set_march_path.argtypes = [vp, ip]
+    lib.swf_rhs_noalloc.argtypes = [inst_p, ip, ip, dp, vp, vp, vp]
     lib.swf_profile_read.argtypes = [vp, ip, C.c_char_p, dbl_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
                                      C.POINTER(C.c_longlong)]
     for name in EXPORTS:
@@ -120,6 +121,14 @@ def _stream_ptr(stream):
     if stream is None:
         return None
     return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def rhs_noalloc(instance, t, psi, out, bg=0, prec=C64, stream=None):
+    """swf_rhs_noalloc: one right-hand-side evaluation without any device allocation (see swf.h)."""
+    load_library()
+    arr = instance_array([instance])
+    _check(_lib.swf_rhs_noalloc(arr, bg, prec, float(t), C.c_void_p(psi.data_ptr()), C.c_void_p(out.data_ptr()),
+                                _stream_ptr(stream)))
 
 
 class Context:
