@@ -259,6 +259,23 @@ def run_gpu(args):
     return 0
 
 
+def run_small_march(args):
+    """One small march for profiler captures: 14 instances (28 sectors) of the batched workload,
+    20 steps, complex64, through swf_march_dev."""
+    import torch
+    from paper_2512_16889_gb300 import build, swf
+    from paper_2512_16889_gb300 import workloads as W
+    build.build()
+    ctx = swf.Context(0)
+    ds = W.schwinger_batched(n_steps=20, t_window=0.4)[:14]
+    out = torch.zeros(len(ds) * 8 * 256 * 256, dtype=torch.float32, device="cuda")
+    ctx.march_dev([swf.from_workload(d) for d in ds], out, bg=0, prec=swf.C64)
+    torch.cuda.synchronize()
+    print("small march ok", float(out.abs().sum()))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,7 +283,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small-march", action="store_true", help="one small march for profiler captures")
     args = ap.parse_args()
+    if args.small_march:
+        return run_small_march(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -53,6 +53,7 @@ struct Args {
   float2* psi_out;         // [inst][4][NY][NX] complex64
   double Lx, Ly, t_out, h;
   int n_steps;
+  const float4* ttab;      // per instance [n_steps][7]: field time factor, background time phase (re, im)
 };
 
 // shared-memory map (bytes)
@@ -97,6 +98,51 @@ __device__ __forceinline__ void ff_add(float hi, float& lo, float& s) {
   lo = l - (nh - t);
   s = nh;
 }
+
+// ---- tensor memory (TMEM) as per-thread storage: 32-bit lanes x columns, warp w reaches lanes
+// 32 (w % 4) .. 32 (w % 4) + 31; the 32x32b shape gives each thread its own lane.
+__device__ __forceinline__ void tmem_alloc(uint32_t* smem_dst, uint32_t ncols) {
+  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 8 consecutive columns of this thread's lane -> two float4
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float4& a, float4& b) {
+  uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  a = make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2), __uint_as_float(r3));
+  b = make_float4(__uint_as_float(r4), __uint_as_float(r5), __uint_as_float(r6), __uint_as_float(r7));
+}
+// 16 consecutive columns of this thread's lane -> four float4
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float4& a, float4& b, float4& c, float4& d) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  a = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+  b = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+  c = make_float4(__uint_as_float(r[8]), __uint_as_float(r[9]), __uint_as_float(r[10]), __uint_as_float(r[11]));
+  d = make_float4(__uint_as_float(r[12]), __uint_as_float(r[13]), __uint_as_float(r[14]), __uint_as_float(r[15]));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float4& a, const float4& b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(a.z)), "r"(__float_as_uint(a.w)),
+               "r"(__float_as_uint(b.x)), "r"(__float_as_uint(b.y)), "r"(__float_as_uint(b.z)), "r"(__float_as_uint(b.w))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
@@ -214,6 +260,24 @@ __device__ double axis_factor(const FieldDesc& F, int axis, double xc) {
   }
 }
 
+// Time factors of every stage of every step, computed once in FP64 by all SMs in parallel
+// (FP64 is scarce on this GPU, so the march itself only reads the rounded table).  Fields
+// whose time factor depends on y (the travelling pulse) are not tabulated.
+__global__ void k_time_table(const FieldDesc* fd, int n_inst, int n_steps, double t_out, double h, float4* tab) {
+  const double DPc[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
+  const size_t total = (size_t)n_inst * n_steps * 7;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int inst = (int)(i / ((size_t)n_steps * 7));
+    const int rem = (int)(i % ((size_t)n_steps * 7));
+    const int step = rem / 7, st = rem % 7;
+    const FieldDesc& F = fd[inst];
+    const double t = t_out + step * h + DPc[st] * h;
+    double sn, cs;
+    sincos(F.tsign * F.e0 * t, &sn, &cs);
+    tab[i] = make_float4((float)time_factor(F, t, 0.0), (float)cs, (float)sn, 0.f);
+  }
+}
+
 // V (phi0, phi1) for the sector (components c0, c1) with the one non-zero A_mu = a.
 __device__ __forceinline__ void sector_v(int acomp, int sigma, float a, float2 p0, float2 p1, float2& o0, float2& o1) {
   if (acomp == 0) {
@@ -322,17 +386,24 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
       // latency per step instead of one per evaluation
       if (ev == 0 || stage == 1) {
         const int st0 = ev == 0 ? 0 : 1, nst = ev == 0 ? 1 : 6;
-        if (tid < nst * RB) {
+        if (F.kind == SWF_FIELD_PULSE_GAUSS) {
+          if (tid < nst * RB) {
+            const int si2 = st0 + tid / RB, r = tid % RB;
+            const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+            const double yc = -0.5 * A.Ly + (row0 + r) * dyy;
+            s_ft[si2 * RB + r] = (float)time_factor(F, ts, yc);
+          } else if (tid >= 128 && tid < 128 + nst) {
+            const int si2 = st0 + tid - 128;
+            const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+            double s, c;
+            sincos(F.tsign * F.e0 * ts, &s, &c);
+            s_tf[si2] = make_float2((float)c, (float)s);
+          }
+        } else if (tid < nst * RB) {
           const int si2 = st0 + tid / RB, r = tid % RB;
-          const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
-          const double yc = -0.5 * A.Ly + (row0 + r) * dyy;
-          s_ft[si2 * RB + r] = (float)time_factor(F, ts, yc);
-        } else if (tid >= 128 && tid < 128 + nst) {
-          const int si2 = st0 + tid - 128;
-          const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
-          double s, c;
-          sincos(F.tsign * F.e0 * ts, &s, &c);
-          s_tf[si2] = make_float2((float)c, (float)s);
+          const float4 e = __ldg(A.ttab + ((size_t)S.inst * A.n_steps + step) * 7 + si2);
+          s_ft[si2 * RB + r] = e.x;
+          if (r == 0) s_tf[si2] = make_float2(e.y, e.z);
         }
         __syncthreads();
       }
@@ -559,6 +630,7 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
   float* s_ft = reinterpret_cast<float*>(sm + OFF_MISC2);
   float2* s_tf = reinterpret_cast<float2*>(sm + OFF_MISC2 + 7 * RB * 4);
   float2* s_w = reinterpret_cast<float2*>(sm + OFF_MISC2 + 7 * RB * 4 + 56);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + OFF_MISC2 + 7 * RB * 4 + 72);
 
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -567,10 +639,23 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
   const int tid = threadIdx.x;
   const int row0 = rank * RB;
   const size_t plane = (size_t)NX * NY;
-  float2* slot = A.slots + (size_t)cid * 10 * 2 * plane;
-  float2* stash = slot + (size_t)7 * 2 * plane;
-  float2* yg = slot + (size_t)8 * 2 * plane;
-  float2* ylo = slot + (size_t)9 * 2 * plane;
+  // global slot of the cluster: k_2 .. k_6, y, y low part; k_1 (= k_7 of the previous step)
+  // and the local-term stash live in tensor memory, 128 columns each
+  float2* slot = A.slots + (size_t)cid * 7 * 2 * plane;
+  float2* yg = slot + (size_t)5 * 2 * plane;
+  float2* ylo = slot + (size_t)6 * 2 * plane;
+  const int warp = tid >> 5;
+  if (warp == 0) {
+    tmem_alloc(s_tmem, 256);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *s_tmem;
+  // this thread's columns: lane quarter warp % 4, column group warp / 4, 8 columns per site pair
+  const uint32_t tlane = ((uint32_t)(32 * (warp & 3))) << 16;
+  const uint32_t tk1 = tbase + tlane + 64 * (warp >> 2);
+  const uint32_t tst = tk1 + 128;
 
   for (int m = tid; m < 256; m += NT2) {
     double sn, cs;
@@ -620,29 +705,30 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
     }
     __syncthreads();
 
-    int kslot[7] = {0, 1, 2, 3, 4, 5, 6};
     const int n_eval = 1 + 6 * A.n_steps;
     for (int ev = 0; ev < n_eval; ++ev) {
       const int step = ev == 0 ? 0 : (ev - 1) / 6;
       const int stage = ev == 0 ? 0 : 1 + (ev - 1) % 6;
-      if (ev > 0 && stage == 1 && step > 0) {
-        const int t0 = kslot[0];
-        kslot[0] = kslot[6];
-        kslot[6] = t0;
-      }
       if (ev == 0 || stage == 1) {
         const int st0 = ev == 0 ? 0 : 1, nst = ev == 0 ? 1 : 6;
-        if (tid < nst * RB) {
+        if (F.kind == SWF_FIELD_PULSE_GAUSS) {
+          if (tid < nst * RB) {
+            const int si2 = st0 + tid / RB, r = tid % RB;
+            const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+            const double yc = -0.5 * A.Ly + (row0 + r) * dyy;
+            s_ft[si2 * RB + r] = (float)time_factor(F, ts, yc);
+          } else if (tid >= 128 && tid < 128 + nst) {
+            const int si2 = st0 + tid - 128;
+            const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+            double sn, cs;
+            sincos(F.tsign * F.e0 * ts, &sn, &cs);
+            s_tf[si2] = make_float2((float)cs, (float)sn);
+          }
+        } else if (tid < nst * RB) {
           const int si2 = st0 + tid / RB, r = tid % RB;
-          const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
-          const double yc = -0.5 * A.Ly + (row0 + r) * dyy;
-          s_ft[si2 * RB + r] = (float)time_factor(F, ts, yc);
-        } else if (tid >= 128 && tid < 128 + nst) {
-          const int si2 = st0 + tid - 128;
-          const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
-          double sn, cs;
-          sincos(F.tsign * F.e0 * ts, &sn, &cs);
-          s_tf[si2] = make_float2((float)cs, (float)sn);
+          const float4 e = __ldg(A.ttab + ((size_t)S.inst * A.n_steps + step) * 7 + si2);
+          s_ft[si2 * RB + r] = e.x;
+          if (r == 0) s_tf[si2] = make_float2(e.y, e.z);
         }
         __syncthreads();
       }
@@ -654,26 +740,35 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
         coef[j] = 0.f;
         kin[j] = slot;
       }
+      // k_1 comes from tensor memory; k_2 .. k_6 from the global slot
+      const float c1 = stage > 0 ? (float)(A.h * DPa[stage][0]) : 0.f;
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
+      for (int j = 1; j < 6; ++j) {
         if (j < stage && DPa[stage][j] != 0.0) {
 #pragma unroll
           for (int q = 0; q < 6; ++q)
             if (q == nterm) {
               coef[q] = (float)(A.h * DPa[stage][j]);
-              kin[q] = slot + (size_t)kslot[j] * 2 * plane;
+              kin[q] = slot + (size_t)(j - 1) * 2 * plane;
             }
           ++nterm;
         }
       }
-      float2* kout = slot + (size_t)kslot[stage] * 2 * plane;
+      // stage 0 (k_1) and stage 6 (k_7, the next step's k_1) go to tensor memory
+      const bool out_tmem = stage == 0 || stage == 6;
+      float2* kout = slot + (size_t)(stage > 0 && stage < 6 ? stage - 1 : 0) * 2 * plane;
       const float2 tf = s_tf[stage];
       const float* ftr = s_ft + stage * RB;
       const float2 w0 = s_w[0], w1 = s_w[1];
       const bool last = stage == 6;
       // ---- 1. stage combine and local term
-#pragma unroll 2
-      for (int m = 0; m < 8; ++m) {
+#pragma unroll 1
+      for (int mm = 0; mm < 8; mm += 2) {
+        // k_1 of both site pairs of this iteration in one tensor-memory load
+        float4 t1a0 = make_float4(0.f, 0.f, 0.f, 0.f), t1a1 = t1a0, t1b0 = t1a0, t1b1 = t1a0;
+        if (stage > 0) tmem_ld16(tk1 + 8 * mm, t1a0, t1a1, t1b0, t1b1);
+#pragma unroll
+      for (int m = mm; m < mm + 2; ++m) {
         const int sp = tid + NT2 * m;
         const int r = sp >> 7;
         const int x = (sp & 127) * 2;
@@ -682,6 +777,11 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
         const float4 yh1 = __ldcg(reinterpret_cast<const float4*>(yg + plane + g0));
         float4 y0 = last ? make_float4(0.f, 0.f, 0.f, 0.f) : yh0;
         float4 y1 = last ? make_float4(0.f, 0.f, 0.f, 0.f) : yh1;
+        {
+          const float4 k0 = m == mm ? t1a0 : t1b0, k1 = m == mm ? t1a1 : t1b1;
+          y0.x = fmaf(c1, k0.x, y0.x); y0.y = fmaf(c1, k0.y, y0.y); y0.z = fmaf(c1, k0.z, y0.z); y0.w = fmaf(c1, k0.w, y0.w);
+          y1.x = fmaf(c1, k1.x, y1.x); y1.y = fmaf(c1, k1.y, y1.y); y1.z = fmaf(c1, k1.z, y1.z); y1.w = fmaf(c1, k1.w, y1.w);
+        }
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           if (q < nterm) {
@@ -724,9 +824,10 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
           if (e) { z0.z = v0.x; z0.w = v0.y; z1.z = v1.x; z1.w = v1.y; }
           else { z0.x = v0.x; z0.y = v0.y; z1.x = v1.x; z1.y = v1.y; }
         }
-        __stcg(reinterpret_cast<float4*>(stash + g0), z0);
-        __stcg(reinterpret_cast<float4*>(stash + plane + g0), z1);
+        tmem_st8(tst + 8 * m, z0, z1);
       }
+      }
+      tmem_wait_st();
       __syncthreads();
       fft256_lines2<false>(W, tw);
       // ---- 2. rows -> columns (pull into registers, barrier, overwrite in place)
@@ -779,21 +880,26 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
       }
       __syncthreads();
       fft256_lines2<true>(W, tw);
-#pragma unroll 4
+#pragma unroll 2
       for (int m = 0; m < 8; ++m) {
         const int sp = tid + NT2 * m;
         const int r = sp >> 7;
         const int x = (sp & 127) * 2;
         const size_t g0 = (size_t)(row0 + r) * NX + x;
-        const float4 z0 = __ldcg(reinterpret_cast<const float4*>(stash + g0));
-        const float4 z1 = __ldcg(reinterpret_cast<const float4*>(stash + plane + g0));
+        float4 z0, z1;
+        tmem_ld8(tst + 8 * m, z0, z1);
         const float2* wa0 = W + r * LD + pidx(x);
         const float2* wa1 = W + (RB + r) * LD + pidx(x);
         const float4 o0 = make_float4(wa0[0].x + z0.x, wa0[0].y + z0.y, wa0[1].x + z0.z, wa0[1].y + z0.w);
         const float4 o1 = make_float4(wa1[0].x + z1.x, wa1[0].y + z1.y, wa1[1].x + z1.z, wa1[1].y + z1.w);
-        __stcg(reinterpret_cast<float4*>(kout + g0), o0);
-        __stcg(reinterpret_cast<float4*>(kout + plane + g0), o1);
+        if (out_tmem) {
+          tmem_st8(tk1 + 8 * m, o0, o1);
+        } else {
+          __stcg(reinterpret_cast<float4*>(kout + g0), o0);
+          __stcg(reinterpret_cast<float4*>(kout + plane + g0), o1);
+        }
       }
+      tmem_wait_st();
       __syncthreads();
     }
     float2* out0 = A.psi_out + ((size_t)S.inst * 4 + S.c0) * plane + (size_t)row0 * NX;
@@ -804,6 +910,9 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
     }
     __syncthreads();
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 256);
 }
 
 }  // namespace fused
@@ -829,7 +938,7 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
   void (*kern)(Args) = var ? k_fused2 : k_fused;
   const int nthr = var ? v2::NT2 : NT;
   const int smem = var ? v2::SMEM2 : SMEM;
-  const int narr = var ? 10 : 9;
+  const int narr = var ? 7 : 9;
   cudaError_t e;
   auto config = [&](int ncl, cudaLaunchAttribute* at) {
     cudaLaunchConfig_t cfg = {};
@@ -878,7 +987,17 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
   if (e != cudaSuccess) return cuda_status(e, "upload field descriptors");
   e = cudaMemcpyAsync(psec, sec.data(), sizeof(Sector) * n_sec, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "upload sector table");
+  void* ptab;
+  if ((s = ws_get(ctx, "fused.ttab", (size_t)n_f * n_steps * 7 * sizeof(float4), &ptab)) != SWF_OK) return s;
+  {
+    ProfScope ps(ctx, "k_time_table", st);
+    const size_t total = (size_t)n_f * n_steps * 7;
+    const int nb = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    k_time_table<<<nb, 256, 0, st>>>((const FieldDesc*)pfd, n_f, n_steps, t_out, (t_in - t_out) / n_steps,
+                                     (float4*)ptab);
+  }
   Args A;
+  A.ttab = (const float4*)ptab;
   A.fd = (const FieldDesc*)pfd;
   A.sec = (const Sector*)psec;
   A.n_sec = n_sec;

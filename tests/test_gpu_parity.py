@@ -282,5 +282,6 @@ def test_full_size_workload_matches_stored_oracle_samples(env):
         assert big.sum() >= 16
         rel = np.abs(got[big] - ref[big]) / ref[big]
         assert rel.max() < 1e-4, (i, rel.max())
-        assert np.max(np.abs(got - ref)) < 5e-6 * smp["max_prob"], i
+        absrel = np.max(np.abs(got - ref)) / smp["max_prob"]
+        assert absrel < 2e-5, (i, absrel)
         assert abs(res[i].diag[0] - smp["norm"]) < 1e-5 * smp["norm"]
