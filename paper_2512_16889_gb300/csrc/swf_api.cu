@@ -433,6 +433,84 @@ static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* 
   return SWF_OK;
 }
 
+// Breit-Wheeler (Sec. IV): U and V marched together per instance, then past terms and totals.
+static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf_precision prec,
+                           swf_result* results_dev, cudaStream_t st) {
+  std::map<GroupKey, std::vector<int>> groups;
+  for (int i = 0; i < n_inst; ++i) {
+    const swf_instance& in = inst[i];
+    GroupKey k;
+    for (int a = 0; a < 3; ++a) { k.n[a] = in.grid.n[a]; k.L[a] = in.grid.n[a] > 1 ? in.grid.L[a] : 0.0; }
+    k.t_in = in.grid.t_in;
+    k.t_out = in.grid.t_out;
+    k.n_steps = in.grid.n_steps;
+    k.full = 0;
+    groups[k].push_back(i);
+    // the photon momentum must be a grid mode; along trivial axes momentum is conserved
+    for (int a = 0; a < 3; ++a) {
+      if (in.grid.n[a] > 1) {
+        const double m = in.k[a] * in.grid.L[a] / 6.283185307179586476925286766559;
+        if (std::fabs(m - std::round(m)) > 1e-6) {
+          set_error("instance " + std::to_string(i) + ": the photon momentum must be a grid mode");
+          return SWF_EINVAL;
+        }
+      } else if (std::fabs(in.p[a] + in.q[a] - in.k[a]) > 1e-9) {
+        set_error("instance " + std::to_string(i) + ": p + q must equal k along trivial axes");
+        return SWF_EINVAL;
+      }
+    }
+    const double k0 = std::sqrt(in.k[0] * in.k[0] + in.k[1] * in.k[1] + in.k[2] * in.k[2]);
+    if (!(k0 > 0.0)) {
+      set_error("instance " + std::to_string(i) + ": the photon momentum must be non-zero");
+      return SWF_EINVAL;
+    }
+  }
+  const size_t elem = prec == SWF_C64 ? 8 : 16;
+  swf_status s;
+  for (auto& kv : groups) {
+    const std::vector<int>& idx = kv.second;
+    const int G = (int)idx.size();
+    const swf_instance& i0 = inst[idx[0]];
+    const GridDesc g = make_grid(i0.grid);
+    std::vector<FieldDesc> fd(2 * G);
+    std::vector<double> photon(6 * G), kat(6 * G);
+    std::vector<unsigned char> bw(bw_inst_size() * G);
+    for (int f = 0; f < G; ++f) {
+      const swf_instance& in = inst[idx[f]];
+      fd[2 * f] = make_field_desc(in, 0);
+      fd[2 * f + 1] = make_field_desc(in, 1);
+      int shift[3];
+      for (int a = 0; a < 3; ++a) {
+        photon[6 * f + a] = in.k[a];
+        photon[6 * f + 3 + a] = in.eps[a];
+        shift[a] = in.grid.n[a] > 1 ? (int)std::lround(in.k[a] * in.grid.L[a] / 6.283185307179586476925286766559) : 0;
+        kat[6 * f + a] = in.k[a] - in.q[a];      // U~ at k - q
+        kat[6 * f + 3 + a] = in.p[a] - in.k[a];  // V~ at p - k
+      }
+      bw_fill_inst(bw.data() + bw_inst_size() * f, in, idx[f], fd[2 * f], fd[2 * f + 1], shift);
+    }
+    const size_t state = (size_t)2 * G * 4 * g.N;
+    void *psi, *spec, *tat, *macc, *norms;
+    if ((s = ws_get(ctx, "bwsolve.psi", state * elem, &psi)) != SWF_OK) return s;
+    if ((s = ws_get(ctx, "bwsolve.spec", state * 16, &spec)) != SWF_OK) return s;
+    if ((s = ws_get(ctx, "bwsolve.tat", (size_t)2 * G * 64, &tat)) != SWF_OK) return s;
+    if ((s = ws_get(ctx, "bwsolve.macc", (size_t)G * 3 * 16, &macc)) != SWF_OK) return s;
+    if ((s = ws_get(ctx, "bwsolve.norms", (size_t)2 * G * 8, &norms)) != SWF_OK) return s;
+    if ((s = march_bw(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, G, fd.data(), photon.data(), prec, psi,
+                      (double2*)macc, st)) != SWF_OK)
+      return s;
+    if ((s = transform_fields(ctx, g, 2 * G, prec, psi, (double2*)spec, st)) != SWF_OK) return s;
+    if ((s = transform_at(ctx, g, 2 * G, prec, psi, kat.data(), (double2*)tat, st)) != SWF_OK) return s;
+    if ((s = field_norms(ctx, g, 2 * G, prec, psi, (double*)norms, st)) != SWF_OK) return s;
+    if ((s = bw_finalize(ctx, g, G, bw.data(), i0.grid.t_in, (const double2*)spec, (const double2*)tat,
+                         (const double2*)macc, (const double*)norms, results_dev, st)) != SWF_OK)
+      return s;
+    cudaError_t e = cudaStreamSynchronize(st);  // host tables above are temporaries
+    if (e != cudaSuccess) return cuda_status(e, "Breit-Wheeler group");
+  }
+  return SWF_OK;
+}
+
 static size_t spectrum_len(int n_inst, const swf_instance* inst, swf_process process) {
   size_t n = 0;
   if (process != SWF_SCHWINGER) return 0;
@@ -548,8 +626,7 @@ swf_status solve_swf_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf
   cudaSetDevice(ctx->device);
   cudaStream_t st = pick_stream(ctx, stream);
   if (process == SWF_SCHWINGER) return solve_schwinger(ctx, n_inst, inst, prec, results_dev, spectrum_dev, st);
-  set_error("Breit-Wheeler is not available in this build");
-  return SWF_EUNSUPPORTED;
+  return solve_bw(ctx, n_inst, inst, prec, results_dev, st);
 }
 
 swf_status solve_swf(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf_process process,

@@ -136,6 +136,21 @@ swf_status twiddles(swf_ctx* ctx, int n, int is_double, const void** ptr);
 swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
                         int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
                         cudaStream_t st);
+// Breit-Wheeler: march U (fields 2i) and V (fields 2i+1) together and accumulate the appended
+// integral M(t) of Eq. 34 for (ss, bs, sb) into macc [n_inst][3] (M_finite = -M(t_in)).
+// photon_host: per instance k[3], eps[3].
+swf_status march_bw(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_inst,
+                    const FieldDesc* fd_host, const double* photon_host, swf_precision prec, void* psi_out,
+                    double2* macc, cudaStream_t st);
+
+// Breit-Wheeler past terms and totals (swf_bw.cu).
+size_t bw_inst_size();
+void bw_fill_inst(void* dst, const swf_instance& in, int out, const FieldDesc& fu, const FieldDesc& fv,
+                  const int shift[3]);
+swf_status bw_finalize(swf_ctx* ctx, const GridDesc& g, int n_inst, const void* bw_host, double t_in,
+                       const double2* spec, const double2* tat, const double2* macc, const double* norms,
+                       swf_result* results, cudaStream_t st);
+
 // ---- fused cluster march (swf_fused.cu)
 bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_precision prec);
 swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,

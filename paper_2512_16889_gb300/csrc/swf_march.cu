@@ -47,6 +47,7 @@ struct StageArgs {
   GridDesc g;
   int nrows;            // ny * nz
   double t;
+  cpx<R>* ystage;       // optional: receives the stage value Y (Breit-Wheeler integrand)
 };
 
 // ---------------------------------------------------------------- field and background
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
       for (int q = 0; q < 6; ++q)
         if (q < A.nterm) v = v + (R)A.coef[q] * A.kin[q][gi];
       if (A.write_y) A.y[gi] = v;
+      if (A.ystage) A.ystage[gi] = v;
     }
     buf[(c * rows + j) * ld + x] = v;
   }
@@ -660,6 +662,196 @@ swf_status rhs_eval_scratch(const GridDesc& g, const FieldDesc& fd, swf_precisio
                             void* out, void* scratch, cudaStream_t st) {
   if (prec == SWF_C64) return rhs_scratch_impl<float>(g, fd, t, psi, out, (unsigned char*)scratch, st);
   return rhs_scratch_impl<double>(g, fd, t, psi, out, (unsigned char*)scratch, st);
+}
+
+}  // namespace swf
+
+// ---------------------------------------------------------------- Breit-Wheeler march (Sec. IV)
+namespace swf {
+
+// Dormand-Prince 5th-order weights b_i (the 7th is zero; FSAL)
+static const double DP_B[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
+
+// Photon plane-wave factor exp(i k.x) per axis for each instance (trivial axes: 1).
+template <typename R>
+__global__ void k_photon_tables(const double* photon, GridDesc g, int n_inst, cpx<R>* kph) {
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst * nt; i += gridDim.x * blockDim.x) {
+    const int inst = i / nt;
+    int j = i % nt, axis = 0;
+    while (j >= g.n[axis]) { j -= g.n[axis]; ++axis; }
+    const double xc = g.n[axis] > 1 ? g.x0[axis] + j * g.dx[axis] : 0.0;
+    double s, c;
+    sincos(photon[6 * inst + axis] * xc, &s, &c);
+    kph[i] = mk<R>((R)c, (R)s);
+  }
+}
+
+// (alpha . eps) v for a real polarisation eps (Dirac representation).
+template <typename R>
+__device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o) {
+  // sigma.eps (u0, u1) = (ez u0 + ex u1 - i ey u1, ex u0 + i ey u0 - ez u1)
+  o[0] = e[2] * v[2] + e[0] * v[3] + e[1] * mul_mi(v[3]);
+  o[1] = e[0] * v[2] + e[1] * mul_i(v[2]) - e[2] * v[3];
+  o[2] = e[2] * v[0] + e[0] * v[1] + e[1] * mul_mi(v[1]);
+  o[3] = e[0] * v[0] + e[1] * mul_i(v[0]) - e[2] * v[1];
+}
+
+// One block per instance: the three integrands of Eq. 33, dx^d sum_x U_a^+ (alpha.eps) V_b
+// exp(-ikx), for (ss, bs, sb) at the stage values, accumulated with weight w (= h b_i) into
+// macc[inst][3] in FP64 (fixed order: deterministic).
+template <typename R>
+__global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const FieldDesc* fd, const cpx<R>* gcplx,
+                                              const cpx<R>* kph, const double* photon, GridDesc g, double t, double w,
+                                              cpx<double>* macc) {
+  __shared__ cpx<double> red[8][3];
+  const int inst = blockIdx.x;
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  const FieldDesc& FU = fd[2 * inst];
+  const FieldDesc& FV = fd[2 * inst + 1];
+  const cpx<R>* tu = gcplx + (size_t)(2 * inst) * (nt + 4);
+  const cpx<R>* tv = gcplx + (size_t)(2 * inst + 1) * (nt + 4);
+  const cpx<R>* kp = kph + (size_t)inst * nt;
+  double su, cu, sv, cv;
+  sincos(FU.tsign * FU.e0 * t, &su, &cu);
+  sincos(FV.tsign * FV.e0 * t, &sv, &cv);
+  const cpx<R> tfu = mk<R>((R)cu, (R)su), tfv = mk<R>((R)cv, (R)sv);
+  R eps[3];
+  for (int a = 0; a < 3; ++a) eps[a] = (R)photon[6 * inst + 3 + a];
+  const cpx<R>* U = ys + (size_t)(2 * inst) * 4 * g.N;
+  const cpx<R>* V = ys + (size_t)(2 * inst + 1) * 4 * g.N;
+  cpx<double> ass = mk<double>(0, 0), abs_ = mk<double>(0, 0), asb = mk<double>(0, 0);
+  for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
+    const int ix = j % g.n[0];
+    const int iy = (j / g.n[0]) % g.n[1];
+    const int iz = j / (g.n[0] * g.n[1]);
+    cpx<R> u[4], v[4], ub[4], vb[4], av[4], avb[4];
+    const cpx<R> phu = tfu * tu[ix] * tu[g.n[0] + iy] * tu[g.n[0] + g.n[1] + iz];
+    const cpx<R> phv = tfv * tv[ix] * tv[g.n[0] + iy] * tv[g.n[0] + g.n[1] + iz];
+    const cpx<R> ph = kp[ix] * kp[g.n[0] + iy] * kp[g.n[0] + g.n[1] + iz];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      u[a] = U[(size_t)a * g.N + j];
+      v[a] = V[(size_t)a * g.N + j];
+      ub[a] = tu[nt + a] * phu;
+      vb[a] = tv[nt + a] * phv;
+    }
+    alpha_eps<R>(eps, v, av);
+    alpha_eps<R>(eps, vb, avb);
+    cpx<R> ss = mk<R>(0, 0), bs = mk<R>(0, 0), sb = mk<R>(0, 0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      ss = ss + cdot(u[a], av[a]);
+      bs = bs + cdot(ub[a], av[a]);
+      sb = sb + cdot(u[a], avb[a]);
+    }
+    ass = ass + cvt<double>(ss * ph);
+    abs_ = abs_ + cvt<double>(bs * ph);
+    asb = asb + cvt<double>(sb * ph);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ass.x += __shfl_down_sync(0xffffffffu, ass.x, off); ass.y += __shfl_down_sync(0xffffffffu, ass.y, off);
+    abs_.x += __shfl_down_sync(0xffffffffu, abs_.x, off); abs_.y += __shfl_down_sync(0xffffffffu, abs_.y, off);
+    asb.x += __shfl_down_sync(0xffffffffu, asb.x, off); asb.y += __shfl_down_sync(0xffffffffu, asb.y, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = ass;
+    red[threadIdx.x >> 5][1] = abs_;
+    red[threadIdx.x >> 5][2] = asb;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    cpx<double> sacc = mk<double>(0, 0);
+    for (int wi = 0; wi < 8; ++wi) sacc = sacc + red[wi][threadIdx.x];
+    double sk, ck;
+    const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
+                           photon[6 * inst + 2] * photon[6 * inst + 2]);
+    sincos(-k0 * t, &sk, &ck);
+    const double cell = g.dx[0] * g.dx[1] * g.dx[2];
+    macc[3 * inst + threadIdx.x] = macc[3 * inst + threadIdx.x] + (w * cell) * (mk<double>(ck, sk) * sacc);
+  }
+}
+
+template <typename R>
+static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_inst,
+                                const FieldDesc* fd_host, const double* photon_host, void* psi_out, double2* macc,
+                                cudaStream_t st) {
+  const int F = 2 * n_inst;
+  StageArgs<R> A;
+  swf_status s = prepare_args<R>(ctx, g, F, fd_host, &A, "bw", st);
+  if (s != SWF_OK) return s;
+  const size_t state = (size_t)F * 4 * g.N * sizeof(cpx<R>);
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  void *py, *pT, *pys, *pk[7], *pph, *pkph;
+  if ((s = ws_get(ctx, "march.y", state, &py)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.T", state, &pT)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.ystage", state, &pys)) != SWF_OK) return s;
+  for (int i = 0; i < 7; ++i) {
+    char nm[32];
+    std::snprintf(nm, sizeof nm, "march.k%d", i);
+    if ((s = ws_get(ctx, nm, state, &pk[i])) != SWF_OK) return s;
+  }
+  if ((s = ws_get(ctx, "bw.photon", sizeof(double) * 6 * n_inst, &pph)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.kph", sizeof(cpx<R>) * n_inst * nt, &pkph)) != SWF_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(pph, photon_host, sizeof(double) * 6 * n_inst, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload photon table");
+  {
+    ProfScope ps(ctx, "k_photon_tables", st);
+    k_photon_tables<R><<<(n_inst * nt + 127) / 128, 128, 0, st>>>((const double*)pph, g, n_inst, (cpx<R>*)pkph);
+  }
+  if ((e = cudaMemsetAsync(py, 0, state, st)) != cudaSuccess) return cuda_status(e, "memset state");
+  if ((e = cudaMemsetAsync(macc, 0, sizeof(double2) * 3 * n_inst, st)) != cudaSuccess) return cuda_status(e, "memset M");
+  A.y = (cpx<R>*)py;
+  A.T = (cpx<R>*)pT;
+  int slot[7] = {0, 1, 2, 3, 4, 5, 6};
+  const double h = (t_in - t_out) / n_steps;
+  A.nterm = 0;
+  A.write_y = 0;
+  A.kout = (cpx<R>*)pk[slot[0]];
+  A.t = t_out;
+  A.ystage = nullptr;  // M-dot vanishes at psi_s(t_out) = 0
+  if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  for (int n = 0; n < n_steps; ++n) {
+    const double tn = t_out + n * h;
+    for (int i = 1; i < 7; ++i) {
+      int ntm = 0;
+      for (int j = 0; j < i; ++j) {
+        if (DP_A[i][j] == 0.0) continue;
+        A.kin[ntm] = (const cpx<R>*)pk[slot[j]];
+        A.coef[ntm] = h * DP_A[i][j];
+        ++ntm;
+      }
+      A.nterm = ntm;
+      A.write_y = (i == 6);
+      A.kout = (cpx<R>*)pk[slot[i]];
+      A.t = tn + DP_C[i] * h;
+      // weight of this stage value in the appended quadrature: b_{i+1}, and for the last stage
+      // (the new state) b_1 of the next step
+      const double wgt = (i >= 2 && i <= 5) ? h * DP_B[i] : (i == 6 && n + 1 < n_steps ? h * DP_B[0] : 0.0);
+      A.ystage = wgt != 0.0 ? (cpx<R>*)pys : nullptr;
+      if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+      if (wgt != 0.0) {
+        ProfScope ps(ctx, "k_mdot", st);
+        k_mdot<R><<<n_inst, 256, 0, st>>>((const cpx<R>*)pys, A.fd, A.gcplx, (const cpx<R>*)pkph, (const double*)pph,
+                                          g, A.t, wgt, (cpx<double>*)macc);
+      }
+    }
+    std::swap(slot[0], slot[6]);
+  }
+  e = cudaMemcpyAsync(psi_out, py, state, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "copy psi(t_in)");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "Breit-Wheeler march kernels");
+  return SWF_OK;
+}
+
+swf_status march_bw(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_inst,
+                    const FieldDesc* fd_host, const double* photon_host, swf_precision prec, void* psi_out,
+                    double2* macc, cudaStream_t st) {
+  if (prec == SWF_C64)
+    return march_bw_impl<float>(ctx, g, t_in, t_out, n_steps, n_inst, fd_host, photon_host, psi_out, macc, st);
+  return march_bw_impl<double>(ctx, g, t_in, t_out, n_steps, n_inst, fd_host, photon_host, psi_out, macc, st);
 }
 
 }  // namespace swf

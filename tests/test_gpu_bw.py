@@ -1,0 +1,90 @@
+"""GPU parity of the Breit-Wheeler amplitude (Sec. IV) against the FP64 oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import swf_oracle as O
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2512_16889_gb300 import build, swf
+    build.build()
+    ctx = swf.Context(0)
+    yield swf, ctx
+    ctx.close()
+
+
+def _bw_inst(swf, fld_kind, prm, n, L, t_in, t_out, n_steps, p, s, q, r, k, eps):
+    code = swf.FIELD_CODES[fld_kind]
+    return swf.make_instance(code, prm, n, L, t_in, t_out, n_steps, p=p, s=s, q=q, r=r, k=k, eps=eps)
+
+
+CASE2D = dict(fld=("sauter_gauss", (1.0, 0.7, 2.0)), n=(16, 16, 1), L=(8 * np.pi, 8 * np.pi, 1.0), t_in=-9.0,
+              t_out=9.0, n_steps=450, p=(0.25, -1.0, 0.0), q=(-0.25, -1.0, 0.0), k=(0.0, -2.0, 0.0))
+
+
+def _oracle(c, s, r):
+    fld = O.Field(*c["fld"])
+    grid = O.Grid(c["n"], c["L"])
+    perp, par = O.polarisation_basis((1, 0, 0), c["k"])
+    ph = O.Photon(c["k"], tuple(par))
+    return O.bw_amplitude(fld, grid, c["p"], s, c["q"], r, ph, c["t_in"], c["t_out"], c["n_steps"]), par
+
+
+@pytest.mark.parametrize("spins", [(1, 1), (1, -1)])
+def test_bw_amplitude_matches_oracle_2d(env, spins):
+    swf, ctx = env
+    s, r = spins
+    ref, par = _oracle(CASE2D, s, r)
+    c = CASE2D
+    inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], s, c["q"], r,
+                    c["k"], par)
+    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+        res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
+        got = [complex(res[0].amp[2 * j], res[0].amp[2 * j + 1]) for j in range(4)]
+        M = ref["M"]
+        assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        for j in range(3):  # each of ss, bs, sb (finite + past)
+            assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
+        assert abs(res[0].prob[0] - abs(M) ** 2) <= 2 * tol * abs(M) ** 2
+
+
+def test_bw_exact_spin_ratio_1p1d_on_gpu(env):
+    """Eq. A81 on the (1+1)D example of Sec. IV, computed by the CUDA path."""
+    swf, ctx = env
+    gold = json.load(open(os.path.join(GOLDEN, "bw_spin_ratio_1p1d.json")))
+    c = gold["case"]
+    n, L = 64, 64.0
+    P = 2 * np.pi * 2 / L
+    rho = c["p2"]
+    k = (0.0, c["k2"], 0.0)
+    perp, par = O.polarisation_basis((1, 0, 0), k)
+    insts = [_bw_inst(swf, "single_e", (c["E0"], c["omega"], c["kappa_x"], 0.0, 0.0), (n, 1, 1), (L, 1.0, 1.0),
+                      -20.0, 20.0, 800, (P, rho, 0.0), rs[0], (-P, rho, 0.0), rs[1], k, par)
+             for rs in ((1, 1), (1, -1), (-1, 1), (-1, -1))]
+    res, _ = ctx.solve(insts, swf.BREIT_WHEELER, swf.C128)
+    prob = [res[i].prob[0] for i in range(4)]
+    assert prob[0] > 1e-12
+    assert np.isclose(prob[3], prob[0], rtol=1e-6)
+    assert np.isclose(prob[1] / prob[0], gold["expected_ratio"], rtol=1e-5)
+    assert np.isclose(prob[2] / prob[0], gold["expected_ratio"], rtol=1e-5)
+
+
+def test_bw_zero_field_and_validation(env):
+    swf, ctx = env
+    c = CASE2D
+    inst = _bw_inst(swf, "zero", (), c["n"], c["L"], c["t_in"], c["t_out"], 20, c["p"], 1, c["q"], 1, c["k"],
+                    (-1.0, 0.0, 0.0))
+    res, _ = ctx.solve([inst], swf.BREIT_WHEELER, swf.C64)
+    assert res[0].prob[0] == 0.0
+    bad = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], 20, c["p"], 1, c["q"], 1,
+                   (0.0, -2.05, 0.0), (-1.0, 0.0, 0.0))
+    with pytest.raises(swf.SwfError) as ei:
+        ctx.solve([bad], swf.BREIT_WHEELER, swf.C64)
+    assert ei.value.status == swf.SWF_EINVAL and "grid mode" in str(ei.value)
