@@ -101,7 +101,8 @@ typedef struct {
 
 /* Per-instance scalar results (complex values as (re, im) pairs).
  * Schwinger: amp = {C(m,n), D(m,n), A(m,n), B(m,n)} for the listed positron n = (r, q);
- *            prob = {|C + D|^2, |A + B|^2} (without SWF_WANT_FULL_N: {|C|^2, 0}, D = A = B = 0).
+ *            prob = {|C + D|^2, |A + B|^2}.  Without SWF_WANT_FULL_N: amp = {C(m,(r,q)),
+ *            C(m,(-r,q)), 0, 0} and prob = {|C(m,(r,q))|^2, |C(m,(-r,q))|^2}.
  * Breit-Wheeler: amp = {M_ss, M_bs, M_sb, M}, prob = {|M|^2, 0}.
  * diag = {||psi_U(t_in)||^2, ||psi_V(t_in)||^2} (grid inner product, Eq. 9). */
 typedef struct {
@@ -199,6 +200,34 @@ swf_status swf_rhs_noalloc(const swf_instance* inst, int bg, swf_precision prec,
 /* Caps the context's device workspace (bytes; 0 = no cap).  Requests that need more return
  * SWF_ENOMEM before touching the device. */
 swf_status swf_set_workspace_limit(swf_ctx* ctx, size_t bytes);
+
+/* ---------------------------------------------------------------------------------------
+ * Surrogate network for parameter and momentum scans.  The paper scans with the worldline-
+ * instanton approximation (App. A) and improves points with the SWF solver (Sec. V); here a
+ * multilayer perceptron trained on solver outputs plays that screening role:
+ *   x = (E, omega, lambda, p_x, p_y, s) -> 4 x [256, GELU] -> (mu, log sigma^2),
+ * mu estimating ln P with P = sum_r |C((s,p),(r,q = -p))|^2 and sigma its own error estimate
+ * (Gaussian negative log-likelihood L = mean[(y - mu)^2 exp(-l) + l]/2 on the standardised
+ * target).  BF16 operands on the tensor cores, FP32 accumulation, FP32 master weights, Adam.
+ * Parameters: per layer W [out][in] row-major then b [out], layers 6->256->256->256->256->2,
+ * FP32, swf_mlp_param_count() values in all.  norm (14 floats): feature shifts [6], feature
+ * scales [6] (x' = (x - shift) * scale), target shift y0 and scale ys (y' = (y - y0) * ys).
+ * x: [B][6] float, y: [B] float, out: [B][2] float (mu and log sigma^2 in the target's units),
+ * all device pointers; calls are asynchronous on `stream` (NULL = default stream). */
+typedef struct swf_mlp swf_mlp;
+int swf_mlp_param_count(void);
+swf_status swf_mlp_create(swf_mlp** m, int device, const float* init_params /* host */, int max_batch,
+                          const float* norm /* host, 14 floats */);
+swf_status swf_mlp_destroy(swf_mlp* m);
+swf_status swf_mlp_forward(swf_mlp* m, const float* x_dev, int B, float* out_dev, void* stream);
+/* Gradient of the loss on one batch (B <= max_batch) into grad_dev (param_count floats,
+ * optional) and the loss into loss_dev (optional); parameters unchanged. */
+swf_status swf_mlp_gradients(swf_mlp* m, const float* x_dev, const float* y_dev, int B, float* grad_dev,
+                             float* loss_dev, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on one batch with learning rate lr. */
+swf_status swf_mlp_train_step(swf_mlp* m, const float* x_dev, const float* y_dev, int B, float lr,
+                              float* loss_dev, void* stream);
+swf_status swf_mlp_get_params(swf_mlp* m, float* params_host);
 
 #ifdef __cplusplus
 }

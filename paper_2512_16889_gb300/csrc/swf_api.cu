@@ -301,6 +301,13 @@ __global__ void __launch_bounds__(256) k_finalize(const InstDev* id, GridDesc g,
   double sn, cs;
   sincos(energy3(I.q) * t_in, &sn, &cs);
   C = mk<double>(cs, sn) * C;
+  // without the full pair number: C for the other positron spin as well
+  cpx<double> C2 = mk<double>(0, 0);
+  if (!I.full) {
+    spinor_uv(I.q, -I.r, true, sp);
+    for (int a = 0; a < 4; ++a) C2 = C2 + cdot(uq[4 * f + a], mk<double>(sp[2 * a], sp[2 * a + 1]));
+    C2 = mk<double>(cs, sn) * C2;
+  }
   cpx<double> A = mk<double>(0, 0);
   if (I.full) {
     // A = (U_back(s, p) | V_scat) = exp(i p0 t_in) u_s(p)^+ V~(p)
@@ -311,12 +318,16 @@ __global__ void __launch_bounds__(256) k_finalize(const InstDev* id, GridDesc g,
   }
   swf_result& o = res[I.out];
   o.amp[0] = C.x; o.amp[1] = C.y;
-  o.amp[2] = D.x; o.amp[3] = D.y;
+  if (I.full) {
+    o.amp[2] = D.x; o.amp[3] = D.y;
+  } else {
+    o.amp[2] = C2.x; o.amp[3] = C2.y;
+  }
   o.amp[4] = A.x; o.amp[5] = A.y;
   o.amp[6] = B.x; o.amp[7] = B.y;
   const cpx<double> CD = C + D, AB = A + B;
   o.prob[0] = CD.x * CD.x + CD.y * CD.y;
-  o.prob[1] = I.full ? AB.x * AB.x + AB.y * AB.y : 0.0;
+  o.prob[1] = I.full ? AB.x * AB.x + AB.y * AB.y : C2.x * C2.x + C2.y * C2.y;
   o.diag[0] = normU[f];
   o.diag[1] = (I.full && normV) ? normV[f] : 0.0;
 }

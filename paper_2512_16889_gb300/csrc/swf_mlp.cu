@@ -1,0 +1,408 @@
+// Surrogate network for scans of the pair probability: a multilayer perceptron
+//   (E, omega, lambda, p_x, p_y, s) -> 4 x [256, GELU] -> (mu, log sigma^2)
+// trained on solver outputs.  BF16 operands on the tensor cores with FP32 accumulation
+// (mma.sync m16n8k16), FP32 master weights, Adam, Gaussian negative log-likelihood
+//   L = mean_b [ (y_b - mu_b)^2 exp(-l_b) + l_b ] / 2.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "swf_internal.h"
+
+namespace swf {
+namespace mlp {
+
+constexpr int NL = 5;                                // layers
+constexpr int DIN[NL] = {6, 256, 256, 256, 256};
+constexpr int DOUT[NL] = {256, 256, 256, 256, 2};
+
+__host__ __device__ constexpr int n_params() {
+  int n = 0;
+  for (int l = 0; l < NL; ++l) n += DIN[l] * DOUT[l] + DOUT[l];
+  return n;
+}
+
+// ---------------------------------------------------------------- BF16 GEMM (FP32 accumulate)
+// C(m, n) = sum_k A(m, k) B(k, n); element (i, j) of a matrix X at X[i * sr + j * sc].
+struct Mat {
+  const __nv_bfloat16* p;
+  long sr, sc;
+};
+
+enum Epi { EPI_FWD_HIDDEN = 0, EPI_FWD_OUT = 1, EPI_DX = 2, EPI_DW = 3 };
+
+struct EpiArgs {
+  int mode;
+  const float* bias;          // FWD: [N]
+  float* z;                   // FWD: pre-activation out [M][N]; DW: gradient out [M][N]
+  __nv_bfloat16* act;         // FWD_HIDDEN: bf16 GELU(z) [M][N]; DX: bf16 dZ of the previous layer
+  float* dz32;                // DX: fp32 dZ of the previous layer [M][N]
+  const float* zprev;         // DX: pre-activation of the previous layer [M][N]
+};
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+
+constexpr int TM = 64, TN = 64, TK = 16, SP = 24;  // tile, k step, padded smem row (bf16)
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, int M, int N, int K, EpiArgs E) {
+  __shared__ __align__(16) __nv_bfloat16 As[TM][SP];   // [m][k]
+  __shared__ __align__(16) __nv_bfloat16 Bs[TN][SP];   // [n][k]
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t4 = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int e = threadIdx.x; e < TM * TK; e += blockDim.x) {
+      const int r = e / TK, c = e % TK;
+      const int m = m0 + r, k = k0 + c;
+      As[r][c] = (m < M && k < K) ? A.p[m * A.sr + k * A.sc] : zero;
+      const int n = n0 + r;
+      Bs[r][c] = (n < N && k < K) ? B.p[k * B.sr + n * B.sc] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int ra = wm + 16 * i;
+      uint32_t a0 = ld32(&As[ra + g][2 * t4]), a1 = ld32(&As[ra + g + 8][2 * t4]);
+      uint32_t a2 = ld32(&As[ra + g][2 * t4 + 8]), a3 = ld32(&As[ra + g + 8][2 * t4 + 8]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int nb = wn + 8 * j;
+        uint32_t b0 = ld32(&Bs[nb + g][2 * t4]), b1 = ld32(&Bs[nb + g][2 * t4 + 8]);
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%0, %1, %2, %3};"
+            : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm + 16 * i + g + (r >> 1) * 8;
+        const int n = n0 + wn + 8 * j + 2 * t4 + (r & 1);
+        if (m >= M || n >= N) continue;
+        const float v = acc[i][j][r];
+        const long o = (long)m * N + n;
+        if (E.mode == EPI_FWD_HIDDEN) {
+          const float z = v + E.bias[n];
+          E.z[o] = z;
+          E.act[o] = __float2bfloat16(gelu(z));
+        } else if (E.mode == EPI_FWD_OUT) {
+          E.z[o] = v + E.bias[n];
+        } else if (E.mode == EPI_DX) {
+          const float d = v * gelu_grad(E.zprev[o]);
+          E.dz32[o] = d;
+          E.act[o] = __float2bfloat16(d);
+        } else {
+          E.z[o] = v;
+        }
+      }
+}
+
+// ---------------------------------------------------------------- small kernels
+// network input: standardised features, x' = (x - shift) * scale per feature
+__global__ void k_inputs(const float* x, const float* shift, const float* scale, __nv_bfloat16* y, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(i % 6);
+    y[i] = __float2bfloat16((x[i] - shift[f]) * scale[f]);
+  }
+}
+
+// network output in the target's units: mu = mu'/ys + y0, log sigma^2 = l' - 2 ln ys
+__global__ void k_outputs(const float* z, float y0, float ys, float* out, int B) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    out[2 * b] = z[2 * b] / ys + y0;
+    out[2 * b + 1] = z[2 * b + 1] - 2.0f * logf(ys);
+  }
+}
+
+__global__ void k_to_bf16(const float* x, __nv_bfloat16* y, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16(x[i]);
+}
+
+// Gaussian NLL of the two output heads on the standardised target y' = (y - y0) ys: loss (mean
+// over the batch) and dL/d(mu', l').
+__global__ void k_nll(const float* out, const float* y, float y0, float ys, int B, float* dz32, __nv_bfloat16* dz16,
+                      float* loss) {
+  __shared__ float red[256];
+  float acc = 0.f;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const float mu = out[2 * b], l = out[2 * b + 1];
+    const float r = (y[b] - y0) * ys - mu, w = __expf(-l);
+    acc += 0.5f * (r * r * w + l);
+    const float dmu = -r * w / B, dl = 0.5f * (1.0f - r * r * w) / B;
+    dz32[2 * b] = dmu;
+    dz32[2 * b + 1] = dl;
+    dz16[2 * b] = __float2bfloat16(dmu);
+    dz16[2 * b + 1] = __float2bfloat16(dl);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) *loss = red[0] / B;
+}
+
+// db(n) = sum_b dZ(b, n), one thread per output unit, fixed order
+__global__ void k_bias_grad(const float* dz, int B, int N, float* db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += dz[(long)b * N + n];
+  db[n] = s;
+}
+
+// Adam on the FP32 master parameters, then the BF16 copies of the weight matrices.
+__global__ void k_adam(float* p, const float* g, float* m, float* v, long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+}  // namespace mlp
+}  // namespace swf
+
+using namespace swf;
+using namespace swf::mlp;
+
+struct swf_mlp {
+  int device;
+  int max_batch;
+  long step;
+  float* params;             // FP32 master: per layer W [out][in] then b [out]
+  float* grads;
+  float* adam_m;
+  float* adam_v;
+  __nv_bfloat16* wbf;        // BF16 copy of all parameters (same layout)
+  __nv_bfloat16* act[NL];    // bf16 input of layer l: [B][DIN[l]]
+  float* z[NL];              // fp32 pre-activation of layer l: [B][DOUT[l]]
+  float* dz32[NL];           // fp32 dL/dz of layer l
+  __nv_bfloat16* dz16[NL];   // bf16 copy
+  float* loss;
+  float* in_shift;           // [6] feature standardisation
+  float* in_scale;           // [6]
+  float y0, ys;              // target standardisation
+  std::vector<void*> allocs;
+};
+
+namespace {
+long woff(int l) {
+  long o = 0;
+  for (int i = 0; i < l; ++i) o += (long)DIN[i] * DOUT[i] + DOUT[i];
+  return o;
+}
+long boff(int l) { return woff(l) + (long)DIN[l] * DOUT[l]; }
+
+swf_status mlp_alloc(swf_mlp* m, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc failed for the surrogate network");
+    return SWF_ENOMEM;
+  }
+  m->allocs.push_back(*p);
+  return SWF_OK;
+}
+
+void gemm(const Mat& A, const Mat& B, int M, int N, int K, const EpiArgs& E, cudaStream_t st) {
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+  k_gemm<<<grid, 128, 0, st>>>(A, B, M, N, K, E);
+}
+
+void refresh_bf16(swf_mlp* m, cudaStream_t st) {
+  k_to_bf16<<<128, 256, 0, st>>>(m->params, m->wbf, n_params());
+}
+
+// forward pass on x (fp32 [B][6]); leaves activations for the backward pass; output in z[NL-1]
+void forward(swf_mlp* m, const float* x, int B, cudaStream_t st) {
+  k_inputs<<<64, 256, 0, st>>>(x, m->in_shift, m->in_scale, m->act[0], (long)B * DIN[0]);
+  for (int l = 0; l < NL; ++l) {
+    const Mat A = {m->act[l], DIN[l], 1};
+    const Mat W = {m->wbf + woff(l), 1, DIN[l]};  // B(k, n) = W[n][k]
+    EpiArgs E = {};
+    E.mode = l < NL - 1 ? EPI_FWD_HIDDEN : EPI_FWD_OUT;
+    E.bias = m->params + boff(l);
+    E.z = m->z[l];
+    E.act = l < NL - 1 ? m->act[l + 1] : nullptr;
+    gemm(A, W, B, DOUT[l], DIN[l], E, st);
+  }
+}
+
+// backward pass from dz of the output layer; fills m->grads
+void backward(swf_mlp* m, int B, cudaStream_t st) {
+  for (int l = NL - 1; l >= 0; --l) {
+    // dW(n, k) = sum_b dZ(b, n) X(b, k)
+    const Mat dZt = {m->dz16[l], 1, DOUT[l]};  // A(n, b) = dZ[b][n]
+    const Mat X = {m->act[l], DIN[l], 1};      // B(b, k) = X[b][k]
+    EpiArgs E = {};
+    E.mode = EPI_DW;
+    E.z = m->grads + woff(l);
+    gemm(dZt, X, DOUT[l], DIN[l], B, E, st);
+    k_bias_grad<<<(DOUT[l] + 127) / 128, 128, 0, st>>>(m->dz32[l], B, DOUT[l], m->grads + boff(l));
+    if (l > 0) {
+      // dX(b, k) = sum_n dZ(b, n) W(n, k), then times GELU'(z_{l-1})
+      const Mat dZ = {m->dz16[l], DOUT[l], 1};
+      const Mat W = {m->wbf + woff(l), DIN[l], 1};  // B(n, k) = W[n][k]
+      EpiArgs D = {};
+      D.mode = EPI_DX;
+      D.zprev = m->z[l - 1];
+      D.dz32 = m->dz32[l - 1];
+      D.act = m->dz16[l - 1];
+      gemm(dZ, W, B, DIN[l], DOUT[l], D, st);
+    }
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int swf_mlp_param_count(void) { return n_params(); }
+
+swf_status swf_mlp_create(swf_mlp** out, int device, const float* init_params, int max_batch, const float* norm) {
+  if (!out || !init_params || !norm || max_batch < 1) { set_error("swf_mlp_create: invalid arguments"); return SWF_EINVAL; }
+  if (!(norm[13] > 0.f)) { set_error("swf_mlp_create: target scale must be positive"); return SWF_EINVAL; }
+  *out = nullptr;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_status(e, "cudaSetDevice");
+  swf_mlp* m = new swf_mlp();
+  m->device = device;
+  m->max_batch = max_batch;
+  m->step = 0;
+  const size_t np = n_params();
+  swf_status s;
+  auto fail = [&](swf_status st) {
+    for (void* p : m->allocs) cudaFree(p);
+    delete m;
+    return st;
+  };
+  if ((s = mlp_alloc(m, (void**)&m->params, np * 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->grads, np * 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->adam_m, np * 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->adam_v, np * 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->wbf, np * 2)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->loss, 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->in_shift, 6 * 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->in_scale, 6 * 4)) != SWF_OK) return fail(s);
+  m->y0 = norm[12];
+  m->ys = norm[13];
+  for (int l = 0; l < NL; ++l) {
+    if ((s = mlp_alloc(m, (void**)&m->act[l], (size_t)max_batch * DIN[l] * 2)) != SWF_OK) return fail(s);
+    if ((s = mlp_alloc(m, (void**)&m->z[l], (size_t)max_batch * DOUT[l] * 4)) != SWF_OK) return fail(s);
+    if ((s = mlp_alloc(m, (void**)&m->dz32[l], (size_t)max_batch * DOUT[l] * 4)) != SWF_OK) return fail(s);
+    if ((s = mlp_alloc(m, (void**)&m->dz16[l], (size_t)max_batch * DOUT[l] * 2)) != SWF_OK) return fail(s);
+  }
+  e = cudaMemcpy(m->params, init_params, np * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(cuda_status(e, "upload parameters"));
+  e = cudaMemcpy(m->in_shift, norm, 6 * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(cuda_status(e, "upload normalisation"));
+  e = cudaMemcpy(m->in_scale, norm + 6, 6 * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(cuda_status(e, "upload normalisation"));
+  cudaMemset(m->adam_m, 0, np * 4);
+  cudaMemset(m->adam_v, 0, np * 4);
+  refresh_bf16(m, 0);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(cuda_status(e, "surrogate set-up"));
+  *out = m;
+  return SWF_OK;
+}
+
+swf_status swf_mlp_destroy(swf_mlp* m) {
+  if (!m) return SWF_OK;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  for (void* p : m->allocs) cudaFree(p);
+  delete m;
+  return SWF_OK;
+}
+
+swf_status swf_mlp_forward(swf_mlp* m, const float* x_dev, int B, float* out_dev, void* stream) {
+  if (!m || !x_dev || !out_dev || B < 1) { set_error("swf_mlp_forward: invalid arguments"); return SWF_EINVAL; }
+  cudaSetDevice(m->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int b0 = 0; b0 < B; b0 += m->max_batch) {
+    const int nb = B - b0 < m->max_batch ? B - b0 : m->max_batch;
+    forward(m, x_dev + (long)b0 * DIN[0], nb, st);
+    k_outputs<<<(nb + 255) / 256, 256, 0, st>>>(m->z[NL - 1], m->y0, m->ys, out_dev + (long)b0 * 2, nb);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "surrogate forward");
+  return SWF_OK;
+}
+
+swf_status swf_mlp_gradients(swf_mlp* m, const float* x_dev, const float* y_dev, int B, float* grad_dev,
+                             float* loss_dev, void* stream) {
+  if (!m || !x_dev || !y_dev || B < 1 || B > m->max_batch) {
+    set_error("swf_mlp_gradients: invalid arguments (batch must be in [1, max_batch])");
+    return SWF_EINVAL;
+  }
+  cudaSetDevice(m->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  forward(m, x_dev, B, st);
+  k_nll<<<1, 256, 0, st>>>(m->z[NL - 1], y_dev, m->y0, m->ys, B, m->dz32[NL - 1], m->dz16[NL - 1],
+                           loss_dev ? loss_dev : m->loss);
+  backward(m, B, st);
+  if (grad_dev) {
+    cudaError_t e = cudaMemcpyAsync(grad_dev, m->grads, (size_t)n_params() * 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "copy gradients");
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "surrogate gradients");
+  return SWF_OK;
+}
+
+swf_status swf_mlp_train_step(swf_mlp* m, const float* x_dev, const float* y_dev, int B, float lr, float* loss_dev,
+                              void* stream) {
+  swf_status s = swf_mlp_gradients(m, x_dev, y_dev, B, nullptr, loss_dev, stream);
+  if (s != SWF_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  m->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - (float)std::pow((double)b1, (double)m->step);
+  const float c2 = 1.f - (float)std::pow((double)b2, (double)m->step);
+  k_adam<<<128, 256, 0, st>>>(m->params, m->grads, m->adam_m, m->adam_v, n_params(), lr, b1, b2, 1e-8f, c1, c2);
+  refresh_bf16(m, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "surrogate update");
+  return SWF_OK;
+}
+
+swf_status swf_mlp_get_params(swf_mlp* m, float* params_host) {
+  if (!m || !params_host) { set_error("swf_mlp_get_params: invalid arguments"); return SWF_EINVAL; }
+  cudaSetDevice(m->device);
+  cudaError_t e = cudaMemcpy(params_host, m->params, (size_t)n_params() * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e, "download parameters");
+  return SWF_OK;
+}
+
+}  // extern "C"

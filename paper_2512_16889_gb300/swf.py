@@ -46,7 +46,8 @@ class Result(C.Structure):
 
 EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
-           "swf_profile_read", "swf_set_march_path", "swf_rhs_noalloc"]
+           "swf_profile_read", "swf_set_march_path", "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
+           "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_gradients", "swf_mlp_train_step", "swf_mlp_get_params"]
 
 
 class SwfError(RuntimeError):
@@ -80,6 +81,14 @@ def load_library(path: str = LIB_PATH):
     lib.swf_profile_enable.argtypes = [vp, ip]
     lib.swf_set_march_path.argtypes = [vp, ip]
     lib.swf_rhs_noalloc.argtypes = [inst_p, ip, ip, dp, vp, vp, vp]
+    fp = C.POINTER(C.c_float)
+    lib.swf_mlp_param_count.argtypes = []
+    lib.swf_mlp_create.argtypes = [C.POINTER(vp), ip, fp, ip, fp]
+    lib.swf_mlp_destroy.argtypes = [vp]
+    lib.swf_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
+    lib.swf_mlp_gradients.argtypes = [vp, vp, vp, ip, vp, vp, vp]
+    lib.swf_mlp_train_step.argtypes = [vp, vp, vp, ip, C.c_float, vp, vp]
+    lib.swf_mlp_get_params.argtypes = [vp, fp]
     lib.swf_profile_read.argtypes = [vp, ip, C.c_char_p, dbl_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
                                      C.POINTER(C.c_longlong)]
     for name in EXPORTS:
@@ -224,3 +233,53 @@ def from_workload(d) -> Instance:
         flags |= FLAG_CODES[f]
     return make_instance(FIELD_CODES[kind], prm, d["n"], d["L"], d["t_in"], d["t_out"], d["n_steps"],
                          p=d["p"], s=d["s"], q=d["q"], r=d["r"], k=d["k"], eps=d["eps"], flags=flags)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Surrogate:
+    """The surrogate network of swf.h (swf_mlp_*); tensors are torch CUDA float32 tensors."""
+
+    def __init__(self, init_params, norm, max_batch=4096, device=0):
+        load_library()
+        p = np.ascontiguousarray(init_params, dtype=np.float32)
+        n = np.ascontiguousarray(norm, dtype=np.float32)
+        assert p.size == _lib.swf_mlp_param_count() and n.size == 14
+        self._h = C.c_void_p()
+        _check(_lib.swf_mlp_create(C.byref(self._h), int(device), p.ctypes.data_as(C.POINTER(C.c_float)),
+                                   int(max_batch), n.ctypes.data_as(C.POINTER(C.c_float))))
+        self.max_batch = max_batch
+
+    @staticmethod
+    def param_count():
+        load_library()
+        return _lib.swf_mlp_param_count()
+
+    def close(self):
+        if self._h:
+            _lib.swf_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, x, out, stream=None):
+        _check(_lib.swf_mlp_forward(self._h, _ptr(x), x.shape[0], _ptr(out), _stream_ptr(stream)))
+
+    def gradients(self, x, y, grad=None, loss=None, stream=None):
+        _check(_lib.swf_mlp_gradients(self._h, _ptr(x), _ptr(y), x.shape[0], _ptr(grad), _ptr(loss),
+                                      _stream_ptr(stream)))
+
+    def train_step(self, x, y, lr, loss=None, stream=None):
+        _check(_lib.swf_mlp_train_step(self._h, _ptr(x), _ptr(y), x.shape[0], float(lr), _ptr(loss),
+                                       _stream_ptr(stream)))
+
+    def params(self):
+        out = np.zeros(_lib.swf_mlp_param_count(), dtype=np.float32)
+        _check(_lib.swf_mlp_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out

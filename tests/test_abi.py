@@ -26,7 +26,7 @@ def declared_functions():
             continue
         text = open(os.path.join(INCLUDE, fn)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:swf_status|const char\s*\*)\s*(\w+)\s*\(", text, flags=re.M):
+        for m in re.finditer(r"^\s*(?:swf_status|const char\s*\*|int)\s*(\w+)\s*\(", text, flags=re.M):
             names.append(m.group(1))
     return names
 

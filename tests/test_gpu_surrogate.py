@@ -1,0 +1,90 @@
+"""Surrogate network: GPU kernels against the FP64 oracle (forward and gradients), and a reduced
+end-to-end run showing what the trained network gains over solving every scan point."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+
+pytestmark = pytest.mark.gpu
+
+
+def _table(n, seed):
+    from paper_2512_16889_gb300 import workloads as W
+    return W.surrogate_samples(n, seed=seed)
+
+
+def test_forward_and_gradients_match_oracle():
+    import torch
+    from paper_2512_16889_gb300 import build, surrogate as S, swf
+    build.build()
+    t = _table(192, seed=11)
+    X = S.features(t)
+    y = (-12.0 + 3.0 * np.tanh(X[:, 0] * 5 - 1.0) + 0.5 * X[:, 3] * X[:, 4]).astype(np.float32)
+    norm = S.normalisation(X, y)
+    p0 = S.init_params(seed=3)
+    p0[np.arange(p0.size) % 7 == 0] *= 0.5  # break symmetry of the zero biases' neighbourhood
+    sur = swf.Surrogate(p0, norm, max_batch=256)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    out = torch.zeros(len(X), 2, dtype=torch.float32, device="cuda")
+    sur.forward(Xd, out)
+    ref_out, _, _ = M.forward(p0.astype(float), X.astype(float), norm.astype(float), bf=True)
+    ys = float(norm[13])
+    mu_ref = ref_out[:, 0] / ys + float(norm[12])
+    got = out.cpu().numpy()
+    assert np.max(np.abs(got[:, 0] - mu_ref)) <= 1e-2 * max(1.0, np.max(np.abs(mu_ref)))
+    grad = torch.zeros(swf.Surrogate.param_count(), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sur.gradients(Xd, yd, grad, loss)
+    ref_loss, ref_g = M.loss_and_grad(p0.astype(float), X.astype(float), y.astype(float), norm.astype(float), bf=True)
+    g = grad.cpu().numpy().astype(float)
+    assert abs(loss.item() - ref_loss) <= 1e-3 * abs(ref_loss)
+    off = 0
+    for i, o in zip(M.DIN, M.DOUT):  # per layer, weights and biases
+        for size in (i * o, o):
+            a, b = g[off:off + size], ref_g[off:off + size]
+            assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-12, (off, size)
+            off += size
+    sur.close()
+
+
+def _momentum_scan(n, seed):
+    """A momentum scan at the fixed field of the batched workload (E = 0.3, omega = 0.5, lambda = 5)."""
+    rng = np.random.default_rng(seed)
+    return {"E": np.full(n, 0.3), "omega": np.full(n, 0.5), "lam": np.full(n, 5.0),
+            "px": rng.uniform(-1, 1, n), "py": rng.uniform(-1, 1, n), "s": rng.choice([1, -1], n)}
+
+
+def test_surrogate_screens_a_momentum_scan():
+    """Reduced scale (64^2 grid, 200 steps, 2048 training points): train on solver output,
+    calibrate the sigma threshold on held-out solver data, then scan; the accepted points need no
+    solve and the rest fall back to the solver, so the scan is exact there."""
+    from paper_2512_16889_gb300 import build, surrogate as S, swf
+    build.build()
+    grid = dict(n=64, L=40.0, n_steps=200, t_window=20.0)
+    ctx = swf.Context(0)
+    tr, ho, sc = _momentum_scan(2048, 4), _momentum_scan(256, 5), _momentum_scan(512, 6)
+    y_tr = S.solve_targets(ctx, tr, **grid)
+    y_ho = S.solve_targets(ctx, ho, **grid)
+    X_tr = S.features(tr)
+    sur = swf.Surrogate(S.init_params(0), S.normalisation(X_tr, y_tr), max_batch=512)
+    hist = S.train(sur, X_tr, y_tr, epochs=800, batch=256, lr=1e-3)
+    assert hist[-1] < hist[0]
+    tol = 5e-2  # in ln P (5 % in P): what this training-set size reaches on part of the scan
+    thr = S.calibrate(sur, S.features(ho), y_ho, tol, coverage=0.95)
+    assert thr > 0
+    t0 = time.perf_counter()
+    y_all = S.solve_targets(ctx, sc, **grid)  # the method without the network: solve every point
+    t_all = time.perf_counter() - t0
+    vals, acc, t_net, t_sol = S.screened_scan(sur, ctx, sc, thr, **grid)
+    frac = acc.mean()
+    err = np.abs(vals - y_all)
+    print(f"accepted {frac:.1%} of the scan; screened {t_net + t_sol:.2f} s vs all-solver {t_all:.2f} s; "
+          f"accepted within tol: {(err[acc] <= tol).mean():.1%}")
+    assert frac > 0.15
+    assert (err[acc] <= tol).mean() >= 0.85
+    assert np.all(err[~acc] == 0.0)  # the fallback is the solver itself
+    assert t_net + t_sol < t_all
+    sur.close()
+    ctx.close()
