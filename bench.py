@@ -91,6 +91,22 @@ def run_reference(args):
     return 0
 
 
+def measured_traffic():
+    """DRAM bytes (read + write) of one full-size launch of the march kernel from the committed
+    ncu counters, or None when the kernel source changed since they were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_fused_counters.json")) as fh:
+            d = json.load(fh)
+        with open(os.path.join(ROOT, d["source"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != d["source_sha256"]:
+                return None
+        full = d.get("full_launch")
+        return float(full["dram_bytes_read"] + full["dram_bytes_write"]) if full else None
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------------ clocks during the timed region
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -232,7 +248,7 @@ def run_gpu(args):
     achieved = alg_bytes / (march_ms / 1e3) / 1e9 if march_ms > 0 else None
     roof = {"bound": "hbm", "kernel": "+".join(sorted(march)) + " (the march, per solve)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm if achieved else None, "traffic": None,
+            "frac": achieved / hbm if achieved else None, "traffic": measured_traffic(),
             "peak_kind": peak_kind + " (burst copy)", "launches_per_step": march_launches / args.steps,
             "algorithmic_bytes_per_step": alg_bytes}
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}

@@ -68,7 +68,7 @@ constexpr int OFF_GY = OFF_EY + RB * 8;                     // [RB] float
 constexpr int OFF_KX = OFF_GY + RB * 4;                     // [NX] float   kappa_x of the mode
 constexpr int OFF_KY = OFF_KX + NX * 4;                     // [NY] float   sigma kappa_y of the mode
 constexpr int OFF_MISC = OFF_KY + NY * 4;                   // per-stage scalars
-constexpr int SMEM = OFF_MISC + 7 * RB * 4 + 7 * 8 + 16 + 64;
+constexpr int SMEM = OFF_MISC + 7 * RB * 4 + 7 * 8 + 16 + 64 + 16;
 
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -136,6 +136,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float4& a, float4& b, 
   c = make_float4(__uint_as_float(r[8]), __uint_as_float(r[9]), __uint_as_float(r[10]), __uint_as_float(r[11]));
   d = make_float4(__uint_as_float(r[12]), __uint_as_float(r[13]), __uint_as_float(r[14]), __uint_as_float(r[15]));
 }
+// 8 columns without waiting (pair with tmem_wait_ld before the registers are read)
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float4& a, const float4& b) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
                "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(a.z)), "r"(__float_as_uint(a.w)),
@@ -311,6 +318,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
   float* s_ft = reinterpret_cast<float*>(sm + OFF_MISC);                     // [7][RB] field time factor
   float2* s_tf = reinterpret_cast<float2*>(sm + OFF_MISC + 7 * RB * 4);      // [7] background time phase
   float2* s_w = reinterpret_cast<float2*>(sm + OFF_MISC + 7 * RB * 4 + 56);  // sector spinor [2]
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 7 * RB * 4 + 72);
 
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -319,7 +327,19 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
   const int tid = threadIdx.x;
   const int row0 = rank * RB;
   const size_t plane = (size_t)NX * NY;
-  float2* slot = A.slots + (size_t)cid * 9 * 2 * plane;
+  // global slot of the cluster: k_4, k_5, k_6 and the low part of y; k_1 (= k_7 of the previous
+  // step), k_2, k_3 and the local-term stash live in tensor memory, 128 columns each
+  float2* slot = A.slots + (size_t)cid * 4 * 2 * plane;
+  const int warp = tid >> 5;
+  if (warp == 0) {
+    tmem_alloc(s_tmem, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *s_tmem;
+  // this thread's 32 columns in each slab: lane quarter warp % 4, column group warp / 4
+  const uint32_t tme = tbase + (((uint32_t)(32 * (warp & 3))) << 16) + 32 * (warp >> 2);
 
   for (int m = tid; m < 256; m += NT) {
     double s, c;
@@ -366,22 +386,15 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
     for (int i = tid; i < NSL; i += NT) Ys[i] = make_float2(0.f, 0.f);
     for (int i = tid; i < NSL; i += NT) {
       const int comp = i / (RB * NX), rem = i % (RB * NX);
-      __stcg(slot + (size_t)8 * 2 * plane + comp * plane + (size_t)row0 * NX + rem, make_float2(0.f, 0.f));
+      __stcg(slot + (size_t)3 * 2 * plane + comp * plane + (size_t)row0 * NX + rem, make_float2(0.f, 0.f));
     }
     __syncthreads();
 
-    int kslot[7] = {0, 1, 2, 3, 4, 5, 6};
-    float2* stash = slot + (size_t)7 * 2 * plane;
     // evaluations: e = 0 is k_1 = f(t_out, 0); then 6 per step
     const int n_eval = 1 + 6 * A.n_steps;
     for (int ev = 0; ev < n_eval; ++ev) {
       const int step = ev == 0 ? 0 : (ev - 1) / 6;
       const int stage = ev == 0 ? 0 : 1 + (ev - 1) % 6;  // 0..6 (stage index i)
-      if (ev > 0 && stage == 1 && step > 0) {
-        const int t0 = kslot[0];
-        kslot[0] = kslot[6];
-        kslot[6] = t0;
-      }
       // time factors of every stage of this step at once (FP64, rounded once): one FP64
       // latency per step instead of one per evaluation
       if (ev == 0 || stage == 1) {
@@ -416,22 +429,29 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
         coef[j] = 0.f;
         kin[j] = slot;
       }
+      // k_1, k_2, k_3 from tensor memory (coefficients ct[]), k_4 .. k_6 from the global slot
+      float ct[3];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
+      for (int j = 0; j < 3; ++j) ct[j] = (j < stage) ? (float)(A.h * DPa[stage][j]) : 0.f;
+      const int ntm = stage < 3 ? stage : 3;
+#pragma unroll
+      for (int j = 3; j < 6; ++j) {
         if (j < stage && DPa[stage][j] != 0.0) {
 #pragma unroll
           for (int q = 0; q < 6; ++q)
             if (q == nterm) {
               coef[q] = (float)(A.h * DPa[stage][j]);
-              kin[q] = slot + (size_t)kslot[j] * 2 * plane;
+              kin[q] = slot + (size_t)(j - 3) * 2 * plane;
             }
           ++nterm;
         }
       }
-      float2* kout = slot + (size_t)kslot[stage] * 2 * plane;
+      // output: stages 0 and 6 (k_1, k_7) -> slab 0, stages 1, 2 -> slabs 1, 2, stages 3..5 -> global
+      const int oslab = stage == 0 || stage == 6 ? 0 : (stage <= 2 ? stage : -1);
+      float2* kout = slot + (size_t)(stage >= 3 && stage <= 5 ? stage - 3 : 0) * 2 * plane;
       const float2 tf = s_tf[stage];
       const float* ftr = s_ft + stage * RB;
-      float2* ylo = slot + (size_t)8 * 2 * plane;
+      float2* ylo = slot + (size_t)3 * 2 * plane;
       const float2 w0 = s_w[0], w1 = s_w[1];
 #pragma unroll 2
       for (int m = 0; m < 4; ++m) {
@@ -446,6 +466,23 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
         const bool last = stage == 6;
         float4 y0 = last ? make_float4(0.f, 0.f, 0.f, 0.f) : yh0;
         float4 y1 = last ? make_float4(0.f, 0.f, 0.f, 0.f) : yh1;
+        if (ntm > 0) {
+          uint32_t tr[3][8];
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            if (j < ntm) tmem_ld8_nowait(tme + 128 * j + 8 * m, tr[j]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            if (j < ntm) {
+              const float c = ct[j];
+              y0.x = fmaf(c, __uint_as_float(tr[j][0]), y0.x); y0.y = fmaf(c, __uint_as_float(tr[j][1]), y0.y);
+              y0.z = fmaf(c, __uint_as_float(tr[j][2]), y0.z); y0.w = fmaf(c, __uint_as_float(tr[j][3]), y0.w);
+              y1.x = fmaf(c, __uint_as_float(tr[j][4]), y1.x); y1.y = fmaf(c, __uint_as_float(tr[j][5]), y1.y);
+              y1.z = fmaf(c, __uint_as_float(tr[j][6]), y1.z); y1.w = fmaf(c, __uint_as_float(tr[j][7]), y1.w);
+            }
+          }
+        }
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           if (q < nterm) {
@@ -490,9 +527,9 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
           if (e) { z0.z = v0.x; z0.w = v0.y; z1.z = v1.x; z1.w = v1.y; }
           else { z0.x = v0.x; z0.y = v0.y; z1.x = v1.x; z1.y = v1.y; }
         }
-        __stcg(reinterpret_cast<float4*>(stash + g0), z0);
-        __stcg(reinterpret_cast<float4*>(stash + plane + g0), z1);
+        tmem_st8(tme + 128 * 3 + 8 * m, z0, z1);
       }
+      tmem_wait_st();
       __syncthreads();
       fft256_lines<false>(WA, tw);
       // ---- 2. transpose rows -> columns through distributed shared memory
@@ -500,7 +537,8 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
       {
         const int comp = tid >> 8, r = (tid >> 4) & 15, col = tid & 15;
 #pragma unroll
-        for (int s = 0; s < CL; ++s) {
+        for (int i = 0; i < CL; ++i) {
+          const int s = (rank + i) & (CL - 1);  // rotated order: no source CTA is read by all at once
           const float2* src = cluster.map_shared_rank(WA, s);
           WB[(comp * CB + col) * LD + pidx(s * RB + r)] = src[(comp * RB + r) * LD + pidx(rank * CB + col)];
         }
@@ -531,7 +569,8 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
       {
         const int comp = tid >> 8, col = (tid >> 4) & 15, r = tid & 15;
 #pragma unroll
-        for (int s = 0; s < CL; ++s) {
+        for (int i = 0; i < CL; ++i) {
+          const int s = (rank + i) & (CL - 1);
           const float2* src = cluster.map_shared_rank(WB, s);
           WA[(comp * RB + r) * LD + pidx(s * CB + col)] = src[(comp * CB + col) * LD + pidx(rank * RB + r)];
         }
@@ -544,15 +583,20 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
         const int r = sp >> 7;
         const int x = (sp & 127) * 2;
         const size_t g0 = (size_t)(row0 + r) * NX + x;
-        const float4 z0 = __ldcg(reinterpret_cast<const float4*>(stash + g0));
-        const float4 z1 = __ldcg(reinterpret_cast<const float4*>(stash + plane + g0));
+        float4 z0, z1;
+        tmem_ld8(tme + 128 * 3 + 8 * m, z0, z1);
         const float2* wa0 = WA + r * LD + pidx(x);
         const float2* wa1 = WA + (RB + r) * LD + pidx(x);
         const float4 o0 = make_float4(wa0[0].x + z0.x, wa0[0].y + z0.y, wa0[1].x + z0.z, wa0[1].y + z0.w);
         const float4 o1 = make_float4(wa1[0].x + z1.x, wa1[0].y + z1.y, wa1[1].x + z1.z, wa1[1].y + z1.w);
-        __stcg(reinterpret_cast<float4*>(kout + g0), o0);
-        __stcg(reinterpret_cast<float4*>(kout + plane + g0), o1);
+        if (oslab >= 0) {
+          tmem_st8(tme + 128 * oslab + 8 * m, o0, o1);
+        } else {
+          __stcg(reinterpret_cast<float4*>(kout + g0), o0);
+          __stcg(reinterpret_cast<float4*>(kout + plane + g0), o1);
+        }
       }
+      tmem_wait_st();
       __syncthreads();
     }
     // psi(t_in) of the sector into the 4-component output
@@ -564,6 +608,11 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
     }
     __syncthreads();
   }
+  // no CTA may exit while another CTA of the cluster can still read its shared memory
+  cluster.sync();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
 
@@ -838,13 +887,18 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
 #pragma unroll
         for (int comp = 0; comp < 2; ++comp)
 #pragma unroll
-          for (int s = 0; s < CL; ++s)
-            st[comp * 16 + s] = cluster.map_shared_rank(W, s)[(comp * RB + r) * LD + pidx(rank * CB + col)];
+          for (int i = 0; i < CL; ++i) {
+            const int s = (rank + i) & (CL - 1);  // rotated order spreads the reads over the cluster
+            st[comp * 16 + i] = cluster.map_shared_rank(W, s)[(comp * RB + r) * LD + pidx(rank * CB + col)];
+          }
         cluster.sync();
 #pragma unroll
         for (int comp = 0; comp < 2; ++comp)
 #pragma unroll
-          for (int s = 0; s < CL; ++s) W[(comp * CB + col) * LD + pidx(s * RB + r)] = st[comp * 16 + s];
+          for (int i = 0; i < CL; ++i) {
+            const int s = (rank + i) & (CL - 1);
+            W[(comp * CB + col) * LD + pidx(s * RB + r)] = st[comp * 16 + i];
+          }
       }
       __syncthreads();
       fft256_lines2<false>(W, tw);
@@ -870,13 +924,18 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
 #pragma unroll
         for (int comp = 0; comp < 2; ++comp)
 #pragma unroll
-          for (int s = 0; s < CL; ++s)
-            st[comp * 16 + s] = cluster.map_shared_rank(W, s)[(comp * CB + col) * LD + pidx(rank * RB + r)];
+          for (int i = 0; i < CL; ++i) {
+            const int s = (rank + i) & (CL - 1);
+            st[comp * 16 + i] = cluster.map_shared_rank(W, s)[(comp * CB + col) * LD + pidx(rank * RB + r)];
+          }
         cluster.sync();
 #pragma unroll
         for (int comp = 0; comp < 2; ++comp)
 #pragma unroll
-          for (int s = 0; s < CL; ++s) W[(comp * RB + r) * LD + pidx(s * CB + col)] = st[comp * 16 + s];
+          for (int i = 0; i < CL; ++i) {
+            const int s = (rank + i) & (CL - 1);
+            W[(comp * RB + r) * LD + pidx(s * CB + col)] = st[comp * 16 + i];
+          }
       }
       __syncthreads();
       fft256_lines2<true>(W, tw);
@@ -910,6 +969,8 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
     }
     __syncthreads();
   }
+  // no CTA may exit while another CTA of the cluster can still read its shared memory
+  cluster.sync();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, 256);
@@ -938,7 +999,7 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
   void (*kern)(Args) = var ? k_fused2 : k_fused;
   const int nthr = var ? v2::NT2 : NT;
   const int smem = var ? v2::SMEM2 : SMEM;
-  const int narr = var ? 7 : 9;
+  const int narr = var ? 7 : 4;
   cudaError_t e;
   auto config = [&](int ncl, cudaLaunchAttribute* at) {
     cudaLaunchConfig_t cfg = {};

@@ -105,7 +105,7 @@ struct swf_ctx {
   swf::TwiddleCache tw;
   swf::Profiler prof;
   bool use_fused = true;  // route eligible marches to the fused cluster kernel
-  int fused_variant = 2;  // 1: one CTA per SM, 2: two CTAs per SM
+  int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
 };
 
 namespace swf {
