@@ -159,6 +159,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+def aggregate(local_ms, units_per_rank, steps, world, device=None):
+    """Max-over-ranks time and whole-job throughput: every rank processed units_per_rank units
+    per step (weak scaling); the job's time is the slowest rank's."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * units_per_rank * steps / (ms_max / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -217,12 +230,8 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     ctx.profile_enable(False)
     prof, launches = ctx.profile_read()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, value = aggregate(ms, site_updates, args.steps, world, device="cuda")
     ms_step = ms_max / args.steps
-    value = world * site_updates * args.steps / (ms_max / 1e3)
 
     # end to end through the host-pointer API (copies of inputs and outputs included)
     e2e_steps = max(1, min(args.steps, 2))
@@ -232,10 +241,7 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         ctx.solve(insts, swf.SCHWINGER, prec)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = world * site_updates / float(tt.item())
+    _, e2e_value = aggregate(e2e_s * 1e3, site_updates, 1, world, device="cuda")
 
     # roofline of the march kernels (algorithmic 14 S bytes per site-update, S = 32 B in c64)
     hbm, peak_kind = peaks()

@@ -1,0 +1,44 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks, max-over-ranks timing and the
+whole-job (weak-scaling) throughput."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    local_ms = [1000.0, 1500.0][rank]  # the second rank is slower
+    ms_max, value = bench.aggregate(local_ms, units_per_rank=100, steps=3, world=world)
+    q.put((rank, ms_max, value))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time_and_sum_the_work():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, ms_max, value in got:
+        assert ms_max == 1500.0
+        assert value == pytest.approx(2 * 100 * 3 / 1.5)
