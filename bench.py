@@ -281,6 +281,61 @@ def run_gpu(args):
     return 0
 
 
+def run_workload(args):
+    """Times another workload of the benchmark family on one GPU (not the headline line):
+    schwinger_fp64_single (128^2, complex128, full pair number), schwinger_batched_fp64 (the
+    headline workload marched in complex128 on the pass kernels: the plain FP64 GPU march),
+    bw_uneven (Breit-Wheeler, uneven grids) and schwinger_3d ((3+1)D 256^3).  --limit bounds the
+    number of instances and --max-steps the Dormand-Prince steps; both are reported."""
+    import numpy as np
+    import torch
+    from paper_2512_16889_gb300 import build, swf
+    from paper_2512_16889_gb300 import workloads as W
+    build.build()
+    name = args.workload
+    process, prec = swf.SCHWINGER, swf.C64
+    if name == "schwinger_fp64_single":
+        ds = [dict(d, flags=("spectrum", "full_n")) for d in W.schwinger_fp64_single()]
+        prec = swf.C128
+    elif name == "schwinger_batched_fp64":
+        ds, prec = W.schwinger_batched(), swf.C128
+    elif name == "bw_uneven":
+        ds, process = W.bw_uneven(), swf.BREIT_WHEELER
+    elif name == "schwinger_3d":
+        ds = W.schwinger_3d()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if args.limit:
+        ds = ds[:args.limit]
+    if args.max_steps:
+        for d in ds:
+            if d["n_steps"] > args.max_steps:
+                frac = args.max_steps / d["n_steps"]
+                d["t_in"] = d["t_out"] - frac * (d["t_out"] - d["t_in"])
+                d["n_steps"] = args.max_steps
+    insts = [swf.from_workload(d) for d in ds]
+    fields = 2 if process == swf.BREIT_WHEELER else (2 if name == "schwinger_fp64_single" else 1)
+    su = sum(int(np.prod(d["n"])) * d["n_steps"] * fields for d in ds)
+    ctx = swf.Context(0)
+    ctx.solve(insts[:1], process, prec)  # warm-up (build plans, first launches)
+    times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, _ = ctx.solve(insts, process, prec)
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    line = {"metric": METRIC, "value": su / t, "unit": UNIT, "n_gpus": 1, "steps": len(times), "warmup": 1,
+            "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f64" if prec == swf.C128 else "f32",
+            "data": "synthetic", "config": {"workload": name, "instances": len(ds),
+                                             "n_steps": ds[0]["n_steps"], "grids": sorted({d["n"] for d in ds}),
+                                             "precision": "complex128" if prec == swf.C128 else "complex64"},
+            "results_per_s": len(ds) / t, "site_updates_per_step": su}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_small_march(args):
     """One small march for profiler captures: 14 instances (28 sectors) of the batched workload,
     20 steps, complex64, through swf_march_dev."""
@@ -306,9 +361,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small-march", action="store_true", help="one small march for profiler captures")
+    ap.add_argument("--workload", default=None, help="time another workload (see run_workload)")
+    ap.add_argument("--limit", type=int, default=0, help="at most this many instances (--workload)")
+    ap.add_argument("--max-steps", type=int, default=0, help="at most this many steps (--workload)")
     args = ap.parse_args()
     if args.small_march:
         return run_small_march(args)
+    if args.workload:
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
