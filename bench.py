@@ -258,6 +258,17 @@ def run_gpu(args):
             "peak_kind": peak_kind + " (burst copy)", "launches_per_step": march_launches / args.steps,
             "algorithmic_bytes_per_step": alg_bytes}
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
+    # FFT flops alongside: 5 N log2 N per complex transform, 8 transforms (4 components forward
+    # and back) per evaluation, 6 evaluations per FSAL step; FP32 lane peak = SMs x 128 lanes x
+    # 2 (FMA) x the maximum SM clock
+    n_sites = 256 * 256
+    fft_flops = 6 * 8 * 5 * np.log2(n_sites) * site_updates
+    props = torch.cuda.get_device_properties(local)
+    sm_max = (clk.get("sm_max_mhz") or 2070.0) * 1e6
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max
+    fft_rate = fft_flops / (march_ms / 1e3) if march_ms > 0 else None
+    alu = {"fft_flops_per_site_update": fft_flops / site_updates, "achieved_tflops": fft_rate / 1e12 if fft_rate else None,
+           "fp32_peak_tflops": fp32_peak / 1e12, "frac": fft_rate / fp32_peak if fft_rate else None}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -267,7 +278,7 @@ def run_gpu(args):
                            "precision": "complex64 march, FP64 projections",
                            "l2": "inputs larger than L2 (2.3 GB working set per GPU)"},
                 "probabilities_per_s": world * probs * args.steps / (ms_max / 1e3),
-                "roofline": roof, "kernels": kernels, "dominant_kernel": dominant,
+                "roofline": roof, "fft_flops": alu, "kernels": kernels, "dominant_kernel": dominant,
                 "gpu_launches": int(launches),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_inst * swf.C.sizeof(swf.Instance),
                         "d2h_bytes_per_step": n_inst * swf.C.sizeof(swf.Result) + probs * 8},
@@ -325,12 +336,18 @@ def run_workload(args):
         res, _ = ctx.solve(insts, process, prec)
         times.append(time.perf_counter() - t0)
     t = min(times)
+    ctx.profile_read()  # per-kernel device times of one more solve
+    ctx.profile_enable(True)
+    ctx.solve(insts, process, prec)
+    ctx.profile_enable(False)
+    prof, _ = ctx.profile_read()
     line = {"metric": METRIC, "value": su / t, "unit": UNIT, "n_gpus": 1, "steps": len(times), "warmup": 1,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f64" if prec == swf.C128 else "f32",
             "data": "synthetic", "config": {"workload": name, "instances": len(ds),
                                              "n_steps": ds[0]["n_steps"], "grids": sorted({d["n"] for d in ds}),
                                              "precision": "complex128" if prec == swf.C128 else "complex64"},
-            "results_per_s": len(ds) / t, "site_updates_per_step": su}
+            "results_per_s": len(ds) / t, "site_updates_per_step": su,
+            "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0

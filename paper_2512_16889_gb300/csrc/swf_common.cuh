@@ -97,20 +97,30 @@ template <typename R> struct Dft<R, 5> {
 // tw[m] = exp(-2 pi i m/n) for m < n (rounded once from FP64).  All reads of the pass finish
 // (barrier) before any write, so the pass works in place.  SLOTS*blockDim must cover the
 // pass's butterflies.
+// Unsigned division by d via a multiply-high with M = ceil(2^32 / d) (the round-up variant of
+// Granlund & Montgomery, 1994): floor(x M / 2^32) = floor(x / d) whenever x (M d - 2^32) < 2^32,
+// which holds for every x < 2^32 / d; the butterfly indices here stay below 2^16 and d <= 512.
+struct FastDiv {
+  unsigned d, mag;
+  __device__ __forceinline__ explicit FastDiv(unsigned d_) : d(d_), mag(d_ > 1 ? 0xFFFFFFFFu / d_ + 1u : 0u) {}
+  __device__ __forceinline__ unsigned div(unsigned x) const { return d > 1 ? __umulhi(x, mag) : x; }
+};
+
 template <typename R, int RAD, int SLOTS>
 __device__ __forceinline__ void stockham_pass(cpx<R>* buf, int ld, int nlines, int n, int p,
                                               bool inv, const cpx<R>* __restrict__ tw) {
   const int m = n / RAD;
   const int nb = nlines * m;
   const int twstep = n / (p * RAD);
+  const FastDiv fm((unsigned)m), fp((unsigned)p);
   cpx<R> v[SLOTS][RAD];
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int b = threadIdx.x + s * blockDim.x;
     if (b < nb) {
-      const int line = b / m;
+      const int line = (int)fm.div((unsigned)b);
       const int i = b - line * m;
-      const int k = i % p;
+      const int k = i - p * (int)fp.div((unsigned)i);
       const cpx<R>* src = buf + line * ld;
 #pragma unroll
       for (int q = 0; q < RAD; ++q) v[s][q] = src[i + q * m];
@@ -130,9 +140,9 @@ __device__ __forceinline__ void stockham_pass(cpx<R>* buf, int ld, int nlines, i
   for (int s = 0; s < SLOTS; ++s) {
     const int b = threadIdx.x + s * blockDim.x;
     if (b < nb) {
-      const int line = b / m;
+      const int line = (int)fm.div((unsigned)b);
       const int i = b - line * m;
-      const int k = i % p;
+      const int k = i - p * (int)fp.div((unsigned)i);
       cpx<R>* dst = buf + line * ld + (i - k) * RAD + k;
 #pragma unroll
       for (int q = 0; q < RAD; ++q) dst[q * p] = v[s][q];

@@ -11,6 +11,7 @@
 //   last pass (x lines):   inverse x-FFT and k = (that) + Z.
 // Gauge field and background are analytic and evaluated on the fly from per-field 1D tables
 // (every field kind is a product of a time factor and one factor per axis).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -163,8 +164,19 @@ __device__ __forceinline__ double kappa_of(int j, int n, double L, double K) {
 }
 
 // ---------------------------------------------------------------- pass kernels
+// In-place FFT of `nlines` lines, `chunk` lines at a time (the per-thread register budget MAXE
+// bounds how many elements one fft_lines call may hold).
 template <typename R, int MAXE>
-__global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
+__device__ __forceinline__ void fft_chunks(cpx<R>* buf, int ld, int nlines, int chunk, const RadixPlan& pl, bool inv,
+                                           const cpx<R>* __restrict__ tw) {
+  for (int l0 = 0; l0 < nlines; l0 += chunk)
+    fft_lines<R, MAXE>(buf + (size_t)l0 * ld, ld, min(chunk, nlines - l0), pl, inv, tw);
+}
+
+// x lines of `rows` grid rows (4 components each): stage combine, local term, forward x-FFT
+// (and the whole derivative when x is the only non-trivial axis).
+template <typename R, int MAXE>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   __shared__ double s_ft[64];
@@ -185,25 +197,6 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
     sincos(F->tsign * F->e0 * A.t, &sn, &cs);
     s_tf = mk<R>((R)cs, (R)sn);
   }
-  const int per = rows * nx;
-  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
-    const int c = e / per;
-    const int rem = e - c * per;
-    const int j = rem / nx;
-    const int x = rem - j * nx;
-    const int row = row0 + j;
-    cpx<R> v = mk<R>(0, 0);
-    if (row < A.nrows) {
-      const size_t gi = fo + (size_t)c * N + (size_t)row * nx + x;
-      v = A.y[gi];
-#pragma unroll
-      for (int q = 0; q < 6; ++q)
-        if (q < A.nterm) v = v + (R)A.coef[q] * A.kin[q][gi];
-      if (A.write_y) A.y[gi] = v;
-      if (A.ystage) A.ystage[gi] = v;
-    }
-    buf[(c * rows + j) * ld + x] = v;
-  }
   __syncthreads();
   const int nt = nx + ny + nz;
   const R* gx = A.greal + (size_t)f * nt;
@@ -213,29 +206,59 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
   const cpx<R>* ey = ex + nx;
   const cpx<R>* ez = ey + ny;
   const cpx<R>* wsp = ez + nz;
+  const int acomp = F->acomp;
+  const int per = rows * nx;
+  const size_t cs = (size_t)N;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
-    const int j = e / nx, x = e - j * nx;
+    const int j = e / nx;
+    const int x = e - j * nx;
     const int row = row0 + j;
-    if (row >= A.nrows) continue;
-    const int iy = row % ny, iz = row / ny;
-    const R a = (R)s_ft[j] * gx[x] * gy[iy] * gz[iz];
-    const cpx<R> ph = s_tf * ex[x] * ey[iy] * ez[iz];
-    cpx<R> phi[4], vz[4];
+    cpx<R> v[4];
+    if (row < A.nrows) {
+      const size_t gi = fo + (size_t)row * nx + x;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) phi[c] = buf[(c * rows + j) * ld + x] + wsp[c] * ph;
-    apply_v<R>(F->acomp, a, phi, vz);
+      for (int c = 0; c < 4; ++c) v[c] = A.y[gi + c * cs];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) A.kout[fo + (size_t)c * N + (size_t)row * nx + x] = mul_mi(vz[c]);
+      for (int q = 0; q < 6; ++q)
+        if (q < A.nterm) {
+          const R co = (R)A.coef[q];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) v[c] = v[c] + co * A.kin[q][gi + c * cs];
+        }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (A.write_y) A.y[gi + c * cs] = v[c];
+        if (A.ystage) A.ystage[gi + c * cs] = v[c];
+      }
+      // local term Z = -i V (Y + psi_b), kept in the output slot until the last pass
+      const int iy = row % ny, iz = row / ny;
+      const R a = (R)s_ft[j] * gx[x] * gy[iy] * gz[iz];
+      const cpx<R> ph = s_tf * ex[x] * ey[iy] * ez[iz];
+      cpx<R> phi[4], vz[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) phi[c] = v[c] + wsp[c] * ph;
+      apply_v<R>(acomp, a, phi, vz);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) A.kout[gi + c * cs] = mul_mi(vz[c]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = mk<R>(0, 0);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) buf[(c * rows + j) * ld + x] = v[c];
   }
+  __syncthreads();
   fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], false, A.tw[0]);
   if (!only_x) {
-    for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
-      const int c = e / per;
-      const int rem = e - c * per;
-      const int j = rem / nx;
-      const int x = rem - j * nx;
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int j = e / nx;
+      const int x = e - j * nx;
       const int row = row0 + j;
-      if (row < A.nrows) A.T[fo + (size_t)c * N + (size_t)row * nx + x] = buf[(c * rows + j) * ld + x];
+      if (row < A.nrows) {
+        const size_t gi = fo + (size_t)row * nx + x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) A.T[gi + c * cs] = buf[(c * rows + j) * ld + x];
+      }
     }
     return;
   }
@@ -253,45 +276,50 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
   }
   __syncthreads();
   fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], true, A.tw[0]);
-  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
-    const int c = e / per;
-    const int rem = e - c * per;
-    const int j = rem / nx;
-    const int x = rem - j * nx;
+  for (int e = threadIdx.x; e < per; e += blockDim.x) {
+    const int j = e / nx;
+    const int x = e - j * nx;
     const int row = row0 + j;
     if (row < A.nrows) {
-      const size_t gi = fo + (size_t)c * N + (size_t)row * nx + x;
-      A.kout[gi] = A.kout[gi] + buf[(c * rows + j) * ld + x];
+      const size_t gi = fo + (size_t)row * nx + x;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) A.kout[gi + c * cs] = A.kout[gi + c * cs] + buf[(c * rows + j) * ld + x];
     }
   }
 }
 
+// Lines along axis 1 (y) or 2 (z) of a tile of TX = 2^lgtx consecutive x columns: forward FFT,
+// -i H0(kappa)/N, inverse FFT, as selected.  The tile sits in shared memory as 4 TX lines of
+// stride ld (the axis length padded so that the transposing loads and stores spread over the
+// banks).
 template <typename R, int MAXE>
-__global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int TX, int ld, int do_fwd,
-                                             int do_h0, int do_inv) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_mid(StageArgs<R> A, int axis, int lgtx, int ld,
+                                                                      int chunk, int do_fwd, int do_h0, int do_inv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   const int f = blockIdx.y;
   const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
   const int N = A.g.N;
   const int na = A.g.n[axis];
-  const int ntx = (nx + TX - 1) / TX;
+  const int TX = 1 << lgtx;
+  const int ntx = (nx + TX - 1) >> lgtx;
   const int xt = blockIdx.x % ntx;
   const int o = blockIdx.x / ntx;  // z index (axis 1) or y index (axis 2)
   const size_t base = axis == 1 ? (size_t)o * nx * ny : (size_t)o * nx;
   const size_t stride = axis == 1 ? (size_t)nx : (size_t)nx * ny;
   const size_t fo = (size_t)f * 4 * N;
+  const size_t cs = (size_t)N;
   const int per = TX * na;
-  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
-    const int c = e / per;
-    const int rem = e - c * per;
-    const int m = rem / TX;
-    const int t = rem - m * TX;
+  for (int e = threadIdx.x; e < per; e += blockDim.x) {
+    const int m = e >> lgtx;
+    const int t = e & (TX - 1);
     const int x = xt * TX + t;
-    buf[(c * TX + t) * ld + m] = x < nx ? A.T[fo + (size_t)c * N + base + m * stride + x] : mk<R>(0, 0);
+    const size_t gi = fo + base + m * stride + x;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) buf[(c * TX + t) * ld + m] = x < nx ? A.T[gi + c * cs] : mk<R>(0, 0);
   }
   __syncthreads();
-  if (do_fwd) fft_lines<R, MAXE>(buf, ld, 4 * TX, A.plan[axis], false, A.tw[axis]);
+  if (do_fwd) fft_chunks<R, MAXE>(buf, ld, 4 * TX, chunk, A.plan[axis], false, A.tw[axis]);
   if (do_h0) {
     const FieldDesc* F = A.fd + f;
     const R sc = (R)(1.0 / (double)N);
@@ -311,19 +339,22 @@ __global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int TX, i
     }
     __syncthreads();
   }
-  if (do_inv) fft_lines<R, MAXE>(buf, ld, 4 * TX, A.plan[axis], true, A.tw[axis]);
-  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
-    const int c = e / per;
-    const int rem = e - c * per;
-    const int m = rem / TX;
-    const int t = rem - m * TX;
+  if (do_inv) fft_chunks<R, MAXE>(buf, ld, 4 * TX, chunk, A.plan[axis], true, A.tw[axis]);
+  for (int e = threadIdx.x; e < per; e += blockDim.x) {
+    const int m = e >> lgtx;
+    const int t = e & (TX - 1);
     const int x = xt * TX + t;
-    if (x < nx) A.T[fo + (size_t)c * N + base + m * stride + x] = buf[(c * TX + t) * ld + m];
+    if (x < nx) {
+      const size_t gi = fo + base + m * stride + x;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) A.T[gi + c * cs] = buf[(c * TX + t) * ld + m];
+    }
   }
 }
 
+// x lines: inverse x-FFT, k = (that) + Z.
 template <typename R, int MAXE>
-__global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_last(StageArgs<R> A, int rows, int ld) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   const int f = blockIdx.y;
@@ -331,40 +362,84 @@ __global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) 
   const int nx = A.g.n[0];
   const int N = A.g.N;
   const size_t fo = (size_t)f * 4 * N;
+  const size_t cs = (size_t)N;
   const int per = rows * nx;
-  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
-    const int c = e / per;
-    const int rem = e - c * per;
-    const int j = rem / nx;
-    const int x = rem - j * nx;
+  for (int e = threadIdx.x; e < per; e += blockDim.x) {
+    const int j = e / nx;
+    const int x = e - j * nx;
     const int row = row0 + j;
-    buf[(c * rows + j) * ld + x] =
-        row < A.nrows ? A.T[fo + (size_t)c * N + (size_t)row * nx + x] : mk<R>(0, 0);
+    const size_t gi = fo + (size_t)row * nx + x;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) buf[(c * rows + j) * ld + x] = row < A.nrows ? A.T[gi + c * cs] : mk<R>(0, 0);
   }
   __syncthreads();
   fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], true, A.tw[0]);
-  for (int e = threadIdx.x; e < 4 * per; e += blockDim.x) {
-    const int c = e / per;
-    const int rem = e - c * per;
-    const int j = rem / nx;
-    const int x = rem - j * nx;
+  for (int e = threadIdx.x; e < per; e += blockDim.x) {
+    const int j = e / nx;
+    const int x = e - j * nx;
     const int row = row0 + j;
     if (row < A.nrows) {
-      const size_t gi = fo + (size_t)c * N + (size_t)row * nx + x;
-      A.kout[gi] = A.kout[gi] + buf[(c * rows + j) * ld + x];
+      const size_t gi = fo + (size_t)row * nx + x;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) A.kout[gi + c * cs] = A.kout[gi + c * cs] + buf[(c * rows + j) * ld + x];
     }
   }
 }
 
 // ---------------------------------------------------------------- host side
 template <typename R> struct Prec;
-template <> struct Prec<float> { static constexpr int MAXE = 36; static constexpr int is_double = 0; };
-template <> struct Prec<double> { static constexpr int MAXE = 20; static constexpr int is_double = 1; };
+template <> struct Prec<float> { static constexpr int MAXE = 12; static constexpr int is_double = 0; };
+template <> struct Prec<double> { static constexpr int MAXE = 12; static constexpr int is_double = 1; };
 
 static const int kThreads = 256;
 
 template <typename R>
 static int elem_cap() { return kThreads * (Prec<R>::MAXE - 4); }
+
+// Shared memory of one k_mid tile: 3 blocks of 256 threads fit an SM.
+static const size_t kMidSmem = 72 * 1024;
+
+// Tile of a y or z pass: the widest power-of-two column count TX <= 16 whose tile fits kMidSmem,
+// and a line stride ld = n_a + pad with ld = 32/TX modulo the elements of one 128-byte
+// shared-memory wavefront, so that the transposing accesses of a warp (TX columns x 32/TX lines)
+// fall on distinct banks.
+struct MidShape {
+  int lgtx, ld, chunk;
+  size_t smem;
+};
+
+// Streaming multiprocessors of the current device (cached per device).
+static int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+// `tiles` = the number of (field, other-axis index) pairs of the pass.  Small grids trade tile
+// width (down to 32 bytes of contiguous x per line) for blocks, up to two per SM.
+template <typename R>
+static MidShape mid_shape(int n_a, int nx, long tiles) {
+  const int esz = (int)sizeof(cpx<R>);
+  const int unit = 128 / esz;
+  const int min_lg = esz == 8 ? 2 : 1;
+  int lg = 4;
+  while (lg > 0 && ((1 << lg) > nx || (size_t)4 * (1 << lg) * (n_a + unit) * esz > kMidSmem)) --lg;
+  while (lg > min_lg && tiles * ((nx + (1 << lg) - 1) >> lg) < 2L * sm_count()) --lg;
+  MidShape m{};
+  const int TX = 1 << lg;
+  const int pad = (((32 / TX) % unit - n_a % unit) % unit + unit) % unit;
+  m.lgtx = lg;
+  m.ld = n_a + pad;
+  m.smem = (size_t)4 * TX * m.ld * esz;
+  m.chunk = elem_cap<R>() / n_a;
+  return m;
+}
 
 template <typename R>
 static swf_status set_smem_attrs() {
@@ -374,7 +449,7 @@ static swf_status set_smem_attrs() {
   cudaError_t e;
   e = cudaFuncSetAttribute(k_first<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_first)");
-  e = cudaFuncSetAttribute(k_mid<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(k_mid<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmem);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_mid)");
   e = cudaFuncSetAttribute(k_last<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last)");
@@ -391,7 +466,9 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
   int rows = cap / (4 * nx);
   if (rows > 64) rows = 64;
   if (rows > A.nrows) rows = A.nrows;
-  if (rows < 1) return SWF_EUNSUPPORTED;
+  if (rows < 1 || 4 * ny > cap || 4 * nz > cap) return SWF_EUNSUPPORTED;  // one spinor line per block at least
+  // small grids: fewer rows per block, for up to two blocks per SM
+  while (rows > 1 && (long)F * ((A.nrows + rows - 1) / rows) < 2L * sm_count()) rows = (rows + 1) / 2;
   const int ld = nx;
   const bool only_x = (ny == 1 && nz == 1);
   size_t smem = (size_t)4 * rows * ld * sizeof(cpx<R>);
@@ -405,17 +482,12 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
   if (ny > 1) axes[na++] = 1;
   if (nz > 1) axes[na++] = 2;
   auto mid = [&](int axis, int fwd, int h0, int inv) {
-    const int n_a = A.g.n[axis];
-    int TX = cap / (4 * n_a);
-    if (TX > 16) TX = 16;
-    if (TX > nx) TX = nx;
-    if (TX < 1) TX = 1;
-    const int ntx = (nx + TX - 1) / TX;
     const int other = axis == 1 ? nz : ny;
+    const MidShape ms = mid_shape<R>(A.g.n[axis], nx, (long)other * F);
+    const int ntx = (nx + (1 << ms.lgtx) - 1) >> ms.lgtx;
     dim3 grid(ntx * other, F);
-    size_t sm = (size_t)4 * TX * n_a * sizeof(cpx<R>);
     ProfScope ps(ctx, "k_mid", st);
-    k_mid<R, MAXE><<<grid, kThreads, sm, st>>>(A, axis, TX, n_a, fwd, h0, inv);
+    k_mid<R, MAXE><<<grid, kThreads, ms.smem, st>>>(A, axis, ms.lgtx, ms.ld, ms.chunk, fwd, h0, inv);
   };
   if (na == 1) {
     mid(axes[0], 1, 1, 1);
@@ -627,22 +699,17 @@ static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, doubl
   int rows = cap / (4 * nx);
   if (rows > 64) rows = 64;
   if (rows > A.nrows) rows = A.nrows;
-  if (rows < 1) return SWF_EUNSUPPORTED;
+  if (rows < 1 || 4 * ny > cap || 4 * nz > cap) return SWF_EUNSUPPORTED;
   const bool only_x = (ny == 1 && nz == 1);
   const size_t smem = (size_t)4 * rows * nx * sizeof(cpx<R>);
   const dim3 grid_rows((A.nrows + rows - 1) / rows, 1);
   k_first<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, nx, only_x ? 1 : 0);
   if (!only_x) {
     auto mid = [&](int axis, int fwd, int h0, int inv) {
-      const int n_a = g.n[axis];
-      int TX = cap / (4 * n_a);
-      if (TX > 16) TX = 16;
-      if (TX > nx) TX = nx;
-      if (TX < 1) TX = 1;
-      const int ntx = (nx + TX - 1) / TX;
       const int other = axis == 1 ? nz : ny;
-      k_mid<R, MAXE><<<dim3(ntx * other, 1), kThreads, (size_t)4 * TX * n_a * sizeof(cpx<R>), st>>>(A, axis, TX, n_a,
-                                                                                                       fwd, h0, inv);
+      const MidShape ms = mid_shape<R>(g.n[axis], nx, other);
+      const int ntx = (nx + (1 << ms.lgtx) - 1) >> ms.lgtx;
+      k_mid<R, MAXE><<<dim3(ntx * other, 1), kThreads, ms.smem, st>>>(A, axis, ms.lgtx, ms.ld, ms.chunk, fwd, h0, inv);
     };
     if (ny > 1 && nz > 1) {
       mid(1, 1, 0, 0);
@@ -697,15 +764,17 @@ __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o
   o[3] = e[0] * v[0] + e[1] * mul_i(v[0]) - e[2] * v[1];
 }
 
-// One block per instance: the three integrands of Eq. 33, dx^d sum_x U_a^+ (alpha.eps) V_b
-// exp(-ikx), for (ss, bs, sb) at the stage values, accumulated with weight w (= h b_i) into
-// macc[inst][3] in FP64 (fixed order: deterministic).
+// The three integrands of Eq. 33, dx^d sum_x U_a^+ (alpha.eps) V_b exp(-ikx), for (ss, bs, sb)
+// at the stage values.  Block (b, inst) sums the sites j = b*256 + threadIdx.x (stride
+// gridDim.x*256) of instance inst in FP64 and writes part[inst][b][3]; k_mdot_final adds the
+// parts in a fixed order (deterministic) and accumulates them with weight w (= h b_i) into
+// macc[inst][3].
 template <typename R>
 __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const FieldDesc* fd, const cpx<R>* gcplx,
-                                              const cpx<R>* kph, const double* photon, GridDesc g, double t, double w,
-                                              cpx<double>* macc) {
+                                              const cpx<R>* kph, const double* photon, GridDesc g, double t,
+                                              cpx<double>* part) {
   __shared__ cpx<double> red[8][3];
-  const int inst = blockIdx.x;
+  const int inst = blockIdx.y;
   const int nt = g.n[0] + g.n[1] + g.n[2];
   const FieldDesc& FU = fd[2 * inst];
   const FieldDesc& FV = fd[2 * inst + 1];
@@ -721,7 +790,7 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   const cpx<R>* U = ys + (size_t)(2 * inst) * 4 * g.N;
   const cpx<R>* V = ys + (size_t)(2 * inst + 1) * 4 * g.N;
   cpx<double> ass = mk<double>(0, 0), abs_ = mk<double>(0, 0), asb = mk<double>(0, 0);
-  for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.N; j += gridDim.x * blockDim.x) {
     const int ix = j % g.n[0];
     const int iy = (j / g.n[0]) % g.n[1];
     const int iz = j / (g.n[0] * g.n[1]);
@@ -764,13 +833,24 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   if (threadIdx.x < 3) {
     cpx<double> sacc = mk<double>(0, 0);
     for (int wi = 0; wi < 8; ++wi) sacc = sacc + red[wi][threadIdx.x];
-    double sk, ck;
-    const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
-                           photon[6 * inst + 2] * photon[6 * inst + 2]);
-    sincos(-k0 * t, &sk, &ck);
-    const double cell = g.dx[0] * g.dx[1] * g.dx[2];
-    macc[3 * inst + threadIdx.x] = macc[3 * inst + threadIdx.x] + (w * cell) * (mk<double>(ck, sk) * sacc);
+    part[((size_t)inst * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = sacc;
   }
+}
+
+// macc[inst][q] += w dx^d exp(-i k0 t) sum_b part[inst][b][q], parts added in order of b.
+__global__ void k_mdot_final(const cpx<double>* __restrict__ part, int nb, const double* photon, GridDesc g,
+                             double t, double w, cpx<double>* macc) {
+  const int inst = blockIdx.x;
+  const int q = threadIdx.x;
+  if (q >= 3) return;
+  cpx<double> sacc = mk<double>(0, 0);
+  for (int b = 0; b < nb; ++b) sacc = sacc + part[((size_t)inst * nb + b) * 3 + q];
+  double sk, ck;
+  const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
+                         photon[6 * inst + 2] * photon[6 * inst + 2]);
+  sincos(-k0 * t, &sk, &ck);
+  const double cell = g.dx[0] * g.dx[1] * g.dx[2];
+  macc[3 * inst + q] = macc[3 * inst + q] + (w * cell) * (mk<double>(ck, sk) * sacc);
 }
 
 template <typename R>
@@ -794,6 +874,13 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   }
   if ((s = ws_get(ctx, "bw.photon", sizeof(double) * 6 * n_inst, &pph)) != SWF_OK) return s;
   if ((s = ws_get(ctx, "bw.kph", sizeof(cpx<R>) * n_inst * nt, &pkph)) != SWF_OK) return s;
+  // blocks per instance of the M-dot reduction: about four waves of the GPU in total, at least
+  // 1024 sites per block
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int nb = std::max(1, std::min((g.N + 1023) / 1024, (4 * nsm + n_inst - 1) / n_inst));
+  void* ppart;
+  if ((s = ws_get(ctx, "bw.mpart", sizeof(cpx<double>) * 3 * (size_t)nb * n_inst, &ppart)) != SWF_OK) return s;
   cudaError_t e = cudaMemcpyAsync(pph, photon_host, sizeof(double) * 6 * n_inst, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "upload photon table");
   {
@@ -833,8 +920,13 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
       if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
       if (wgt != 0.0) {
         ProfScope ps(ctx, "k_mdot", st);
-        k_mdot<R><<<n_inst, 256, 0, st>>>((const cpx<R>*)pys, A.fd, A.gcplx, (const cpx<R>*)pkph, (const double*)pph,
-                                          g, A.t, wgt, (cpx<double>*)macc);
+        k_mdot<R><<<dim3(nb, n_inst), 256, 0, st>>>((const cpx<R>*)pys, A.fd, A.gcplx, (const cpx<R>*)pkph,
+                                                    (const double*)pph, g, A.t, (cpx<double>*)ppart);
+      }
+      if (wgt != 0.0) {
+        ProfScope ps(ctx, "k_mdot_final", st);
+        k_mdot_final<<<n_inst, 32, 0, st>>>((const cpx<double>*)ppart, nb, (const double*)pph, g, A.t, wgt,
+                                            (cpx<double>*)macc);
       }
     }
     std::swap(slot[0], slot[6]);

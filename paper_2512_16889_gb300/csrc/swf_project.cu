@@ -124,11 +124,11 @@ __device__ __forceinline__ cpx<double> ld_d(const void* p, size_t i) {
 // One block per field: dx^d sum_x psi_a(x) exp(-i kappa.x) for a = 0..3 (deterministic order).
 template <typename Rin>
 __global__ void __launch_bounds__(kT) k_transform_at(const void* psi, GridDesc g, const double* kappa,
-                                                     cpx<double>* out) {
+                                                     cpx<double>* part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<double>* ph = reinterpret_cast<cpx<double>*>(smem_raw);  // nx + ny + nz phases
   __shared__ cpx<double> red[kT / 32][4];
-  const int f = blockIdx.x;
+  const int f = blockIdx.y;
   const int nt = g.n[0] + g.n[1] + g.n[2];
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {
     int axis = 0, j = i;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kT) k_transform_at(const void* psi, GridDesc g
 #pragma unroll
   for (int a = 0; a < 4; ++a) acc[a] = mk<double>(0, 0);
   const size_t fo = (size_t)f * 4 * g.N;
-  for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.N; j += gridDim.x * blockDim.x) {
     const int ix = j % g.n[0];
     const int iy = (j / g.n[0]) % g.n[1];
     const int iz = j / (g.n[0] * g.n[1]);
@@ -169,18 +169,43 @@ __global__ void __launch_bounds__(kT) k_transform_at(const void* psi, GridDesc g
   if (threadIdx.x < 4) {
     cpx<double> s = mk<double>(0, 0);
     for (int w = 0; w < kT / 32; ++w) s = s + red[w][threadIdx.x];
-    const double cell = g.dx[0] * g.dx[1] * g.dx[2];
-    out[4 * f + threadIdx.x] = cell * s;
+    part[((size_t)f * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = s;
   }
 }
 
-template <typename Rin>
-__global__ void __launch_bounds__(kT) k_norms(const void* psi, GridDesc g, double* out) {
-  __shared__ double red[kT / 32];
+// out[f][q] = scale * sum_b part[f][b][q], the parts added in order of b (deterministic).
+template <typename T>
+__global__ void k_sum_parts(const T* __restrict__ part, int nb, int width, double scale, T* out) {
   const int f = blockIdx.x;
+  for (int q = threadIdx.x; q < width; q += blockDim.x) {
+    T s{};
+    for (int b = 0; b < nb; ++b) s = s + part[((size_t)f * nb + b) * width + q];
+    out[(size_t)f * width + q] = scale * s;
+  }
+}
+
+// Blocks per field of a grid reduction: about four waves of the GPU, at least 8 elements a thread.
+int reduction_blocks(size_t elems, int n_f) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || nsm <= 0)
+      nsm = 152;
+  }
+  const size_t by_size = (elems + 8 * kT - 1) / (8 * kT);
+  const size_t by_gpu = (4 * (size_t)nsm + n_f - 1) / n_f;
+  size_t nb = by_size < by_gpu ? by_size : by_gpu;
+  return nb < 1 ? 1 : (int)nb;
+}
+
+template <typename Rin>
+__global__ void __launch_bounds__(kT) k_norms(const void* psi, GridDesc g, double* part) {
+  __shared__ double red[kT / 32];
+  const int f = blockIdx.y;
   const size_t fo = (size_t)f * 4 * g.N;
   double acc = 0.0;
-  for (size_t i = threadIdx.x; i < (size_t)4 * g.N; i += blockDim.x) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)4 * g.N; i += (size_t)gridDim.x * blockDim.x) {
     const cpx<double> v = ld_d<Rin>(psi, fo + i);
     acc += v.x * v.x + v.y * v.y;
   }
@@ -190,7 +215,7 @@ __global__ void __launch_bounds__(kT) k_norms(const void* psi, GridDesc g, doubl
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kT / 32; ++w) s += red[w];
-    out[f] = s * g.dx[0] * g.dx[1] * g.dx[2];
+    part[(size_t)f * gridDim.x + blockIdx.x] = s;
   }
 }
 
@@ -281,11 +306,21 @@ swf_status transform_at(swf_ctx* ctx, const GridDesc& g, int n_f, swf_precision 
   cudaError_t e = cudaMemcpyAsync(pk, kappa_host, sizeof(double) * 3 * n_f, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "upload wave vectors");
   const size_t sm = (size_t)(g.n[0] + g.n[1] + g.n[2]) * sizeof(cpx<double>);
-  ProfScope ps(ctx, "k_transform_at", st);
-  if (prec == SWF_C64)
-    k_transform_at<float><<<n_f, kT, sm, st>>>(psi, g, (const double*)pk, (cpx<double>*)out);
-  else
-    k_transform_at<double><<<n_f, kT, sm, st>>>(psi, g, (const double*)pk, (cpx<double>*)out);
+  const int nb = reduction_blocks(g.N, n_f);
+  void* part = nullptr;
+  if ((s = ws_get(ctx, "proj.part", sizeof(cpx<double>) * 4 * (size_t)nb * n_f, &part)) != SWF_OK) return s;
+  {
+    ProfScope ps(ctx, "k_transform_at", st);
+    if (prec == SWF_C64)
+      k_transform_at<float><<<dim3(nb, n_f), kT, sm, st>>>(psi, g, (const double*)pk, (cpx<double>*)part);
+    else
+      k_transform_at<double><<<dim3(nb, n_f), kT, sm, st>>>(psi, g, (const double*)pk, (cpx<double>*)part);
+  }
+  {
+    ProfScope ps(ctx, "k_sum_parts", st);
+    k_sum_parts<cpx<double>><<<n_f, 32, 0, st>>>((const cpx<double>*)part, nb, 4, g.dx[0] * g.dx[1] * g.dx[2],
+                                                 (cpx<double>*)out);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "direct transform kernel");
   return SWF_OK;
@@ -293,9 +328,19 @@ swf_status transform_at(swf_ctx* ctx, const GridDesc& g, int n_f, swf_precision 
 
 swf_status field_norms(swf_ctx* ctx, const GridDesc& g, int n_f, swf_precision prec, const void* psi,
                        double* out, cudaStream_t st) {
-  ProfScope ps(ctx, "k_norms", st);
-  if (prec == SWF_C64) k_norms<float><<<n_f, kT, 0, st>>>(psi, g, out);
-  else k_norms<double><<<n_f, kT, 0, st>>>(psi, g, out);
+  const int nb = reduction_blocks((size_t)4 * g.N, n_f);
+  void* part = nullptr;
+  swf_status s = ws_get(ctx, "proj.norm_part", sizeof(double) * (size_t)nb * n_f, &part);
+  if (s != SWF_OK) return s;
+  {
+    ProfScope ps(ctx, "k_norms", st);
+    if (prec == SWF_C64) k_norms<float><<<dim3(nb, n_f), kT, 0, st>>>(psi, g, (double*)part);
+    else k_norms<double><<<dim3(nb, n_f), kT, 0, st>>>(psi, g, (double*)part);
+  }
+  {
+    ProfScope ps(ctx, "k_sum_parts", st);
+    k_sum_parts<double><<<n_f, 32, 0, st>>>((const double*)part, nb, 1, g.dx[0] * g.dx[1] * g.dx[2], (double*)out);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "norm kernel");
   return SWF_OK;
