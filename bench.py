@@ -292,6 +292,71 @@ def run_gpu(args):
     return 0
 
 
+def run_surrogate(args):
+    """Times the surrogate network on one GPU: inference over 10^6 scan points (the screening
+    pass) and Adam training steps at batch 256, against the measured BF16 tensor peak."""
+    import numpy as np
+    import torch
+    from paper_2512_16889_gb300 import build, surrogate as S, swf
+    build.build()
+    rng = np.random.default_rng(8)
+    n_inf = args.limit or 1_000_000
+    X = np.stack([rng.choice([0.2, 0.3, 0.4], n_inf), rng.uniform(0.3, 0.7, n_inf), rng.uniform(3, 8, n_inf),
+                  rng.uniform(-1, 1, n_inf), rng.uniform(-1, 1, n_inf), rng.choice([1.0, -1.0], n_inf)],
+                 axis=1).astype(np.float32)
+    y = (-10.0 + np.tanh(X[:, 0] * 4) + 0.3 * X[:, 3] * X[:, 4]).astype(np.float32)
+    sur = swf.Surrogate(S.init_params(0), S.normalisation(X, y), max_batch=65536)
+    Xd = torch.from_numpy(X).cuda()
+    yd = torch.from_numpy(y).cuda()
+    out = torch.empty(n_inf, 2, dtype=torch.float32, device="cuda")
+    flops_fwd = 2.0 * sum(i * o for i, o in zip((6, 256, 256, 256, 256), (256, 256, 256, 256, 2)))
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        sur.forward(Xd, out)
+    torch.cuda.synchronize()
+    reps = max(1, args.steps)
+    ev0.record(stream)
+    for _ in range(reps):
+        sur.forward(Xd, out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_inf = ev0.elapsed_time(ev1) / 1e3 / reps
+    # training: Adam steps at batch 256 (forward, backward, update)
+    bt = 256
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    xb, yb = Xd[:bt].contiguous(), yd[:bt].contiguous()
+    for _ in range(5):
+        sur.train_step(xb, yb, 1e-4, loss)
+    torch.cuda.synchronize()
+    n_tr = 200
+    ev0.record(stream)
+    for _ in range(n_tr):
+        sur.train_step(xb, yb, 1e-4, loss)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_tr = ev0.elapsed_time(ev1) / 1e3 / n_tr
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+        kind = "measured"
+    except Exception:
+        bf16, kind = 1900.0, "fallback"
+    inf_tflops = flops_fwd * n_inf / t_inf / 1e12
+    line = {"metric": "surrogate scan points/s", "value": n_inf / t_inf, "unit": "points/s", "n_gpus": 1,
+            "steps": reps, "warmup": 3, "ms_per_step": 1e3 * t_inf, "higher_is_better": True, "dtype": "bf16",
+            "data": "synthetic", "config": {"workload": "surrogate: MLP 6-4x256(GELU)-2, BF16 operands, FP32 accumulate",
+                                             "inference_points": n_inf, "train_batch": bt},
+            "roofline": {"bound": "tensor", "achieved": inf_tflops, "peak": bf16, "unit": "TFLOP/s",
+                         "frac": inf_tflops / bf16, "peak_kind": kind + " (burst bf16)",
+                         "flops_per_point": flops_fwd},
+            "train": {"ms_per_step": 1e3 * t_tr, "samples_per_s": bt / t_tr,
+                      "tflops": 3 * flops_fwd * bt / t_tr / 1e12}}
+    print(json.dumps(line), flush=True)
+    sur.close()
+    return 0
+
+
 def run_workload(args):
     """Times another workload of the benchmark family on one GPU (not the headline line):
     schwinger_fp64_single (128^2, complex128, full pair number), schwinger_batched_fp64 (the
@@ -384,6 +449,8 @@ def main():
     args = ap.parse_args()
     if args.small_march:
         return run_small_march(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     if args.workload:
         return run_workload(args)
     if args.impl == "reference":

@@ -219,7 +219,13 @@ int swf_mlp_param_count(void);
 swf_status swf_mlp_create(swf_mlp** m, int device, const float* init_params /* host */, int max_batch,
                           const float* norm /* host, 14 floats */);
 swf_status swf_mlp_destroy(swf_mlp* m);
+/* Inference over any number of rows B >= 1 (one persistent tensor-core kernel, no workspace
+ * beyond the network's own). */
 swf_status swf_mlp_forward(swf_mlp* m, const float* x_dev, int B, float* out_dev, void* stream);
+/* Waits for the network's last inference call and reports SWF_ETIMEOUT if one of its waits on
+ * the tensor cores or on a weight copy gave up (about two seconds each; the kernel then returns
+ * with its outputs incomplete), else SWF_OK. */
+swf_status swf_mlp_status(swf_mlp* m);
 /* Gradient of the loss on one batch (B <= max_batch) into grad_dev (param_count floats,
  * optional) and the loss into loss_dev (optional); parameters unchanged. */
 swf_status swf_mlp_gradients(swf_mlp* m, const float* x_dev, const float* y_dev, int B, float* grad_dev,

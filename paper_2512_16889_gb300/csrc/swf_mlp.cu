@@ -190,6 +190,277 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, long n, flo
   }
 }
 
+
+// ---------------------------------------------------------------- fused inference on tcgen05
+// One CTA (256 threads) per SM, persistent over tiles of 128 rows.  Layer 0 (K = 6) and the
+// output layer (N = 2) run on the CUDA cores; the three 256 x 256 layers are single-CTA
+// tcgen05.mma (kind::f16, BF16 operands, M = 128, N = 256, K = 16 per instruction) from shared
+// memory into an FP32 accumulator of 256 tensor-memory columns.  Operands use the K-major
+// no-swizzle canonical layout: element (r, k) of a 256-wide operand at byte
+//     (r / 8) * 4096 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// i.e. 8 x 8 core matrices of 128 contiguous bytes, K-adjacent core matrices 128 B apart (the
+// descriptor's leading byte offset) and 8-row groups 4096 B apart (its stride byte offset).
+// The weights of layers 1-3 are kept in global memory in exactly that image (packed after every
+// update) and brought in with one bulk asynchronous copy per layer, overlapping the previous
+// layer's epilogue.  The epilogue adds the bias, applies GELU and writes the BF16 activation
+// back into the operand buffer; after layer 3 it contracts with the output weights.
+namespace tc {
+
+constexpr int THREADS = 256;
+constexpr int TILE = 128;
+constexpr uint32_t OP_BYTES_A = TILE * 256 * 2;   // 64 KB
+constexpr uint32_t OP_BYTES_W = 256 * 256 * 2;    // 128 KB
+constexpr uint32_t OFF_A = 0;
+constexpr uint32_t OFF_W = OFF_A + OP_BYTES_A;
+constexpr uint32_t OFF_W0 = OFF_W + OP_BYTES_W;   // float [256][6]
+constexpr uint32_t OFF_B = OFF_W0 + 256 * 6 * 4;  // float [4][256]: b0..b3
+constexpr uint32_t OFF_W4 = OFF_B + 4 * 256 * 4;  // float [2][256]
+constexpr uint32_t OFF_RED = OFF_W4 + 2 * 256 * 4;  // float [2][128][2]
+constexpr uint32_t OFF_MISC = OFF_RED + 2 * TILE * 2 * 4;
+constexpr uint32_t SMEM = OFF_MISC + 64;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // about two seconds at the maximum clock
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__host__ __device__ __forceinline__ uint32_t op_offset(int r, int k) {
+  return (uint32_t)((r >> 3) * 4096 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(4096u >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Waits for the phase with the given parity to complete; false after WAIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void load_weights(uint32_t dst, const void* src, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(OP_BYTES_W) : "memory");
+  for (uint32_t c = 0; c < OP_BYTES_W; c += 32768)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst + c),
+                 "l"((const char*)src + c), "r"(32768u), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_layer(uint32_t tmem_d, uint32_t a_base, uint32_t w_base) {
+#pragma unroll
+  for (int kk = 0; kk < 16; ++kk) {
+    const uint64_t ad = smem_desc(a_base + kk * 256), bd = smem_desc(w_base + kk * 256);
+    const uint32_t acc = kk > 0 ? 1u : 0u;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            tmem_d),
+        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ float round_bf16(float a) { return __bfloat162float(__float2bfloat16(a)); }
+
+// x [B][6] fp32 features; wpack: layers 1-3 in the operand image; wbf: all parameters in BF16
+// (W0 and W4 read from it); params: FP32 parameters (biases read from it).  Writes out [B][2]
+// = (mu, log sigma^2) in the target's units.  *err is set to 1 if a wait timed out.
+__global__ void __launch_bounds__(THREADS, 1)
+k_mlp_forward(const float* __restrict__ x, int B, const __nv_bfloat16* __restrict__ wpack,
+              const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ params, const float* __restrict__ shift,
+              const float* __restrict__ scale, float y0, float ys, float* __restrict__ out, int* err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float* sW0 = reinterpret_cast<float*>(sm + OFF_W0);
+  float* sB = reinterpret_cast<float*>(sm + OFF_B);
+  float* sW4 = reinterpret_cast<float*>(sm + OFF_W4);
+  float* sRed = reinterpret_cast<float*>(sm + OFF_RED);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_MISC);  // [0] weights loaded, [1] MMA done
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 16);
+  int* sAbort = reinterpret_cast<int*>(sm + OFF_MISC + 20);
+  float* sB4 = reinterpret_cast<float*>(sm + OFF_MISC + 24);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t a_base = saddr(sm + OFF_A), w_base = saddr(sm + OFF_W);
+  const uint32_t barW = saddr(&bars[0]), barM = saddr(&bars[1]);
+  const int ntiles = (B + TILE - 1) / TILE;
+
+  // small parameters (BF16 weights as the GEMM path rounds them, FP32 biases)
+  constexpr long W0OFF = 0, B0OFF = 6 * 256;
+  for (int i = tid; i < 256 * 6; i += THREADS) sW0[i] = __bfloat162float(wbf[W0OFF + i]);
+  for (int l = 0; l < 4; ++l) {
+    const long bo = (l == 0) ? B0OFF : B0OFF + 256 + (long)(l - 1) * (256 * 256 + 256) + 256 * 256;
+    for (int i = tid; i < 256; i += THREADS) sB[l * 256 + i] = params[bo + i];
+  }
+  const long w4off = B0OFF + 256 + 3L * (256 * 256 + 256);
+  for (int i = tid; i < 2 * 256; i += THREADS) sW4[i] = __bfloat162float(wbf[w4off + i]);
+  if (tid < 2) sB4[tid] = params[w4off + 2 * 256 + tid];
+  if (tid == 0) {
+    *sAbort = 0;
+    mbar_init(barW, 1);
+    mbar_init(barM, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    const uint32_t dst = saddr(sTmem);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(256u) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *sTmem;
+  uint32_t phW = 0, phM = 0;
+  if (tid == 0 && blockIdx.x < ntiles) load_weights(w_base, wpack, barW);
+
+  const int q = warp & 3, half = warp >> 2;  // TMEM lane quarter and column half of this warp
+  const int erow = 32 * q + (tid & 31);       // epilogue row
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const bool more = tile + (int)gridDim.x < ntiles;
+    // layer 0 on the CUDA cores: row r, columns [128 h, 128 h + 128)
+    {
+      const int r = tid & (TILE - 1), h = tid >> 7;
+      const long row = (long)tile * TILE + r;
+      float xin[6];
+#pragma unroll
+      for (int f = 0; f < 6; ++f) xin[f] = row < B ? round_bf16((x[row * 6 + f] - shift[f]) * scale[f]) : 0.f;
+      for (int c0 = 128 * h; c0 < 128 * h + 128; c0 += 8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          float z[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const float* wr = sW0 + (c0 + j + u) * 6;
+            float acc = 0.f;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) acc = fmaf(xin[f], wr[f], acc);
+            z[u] = gelu(acc + sB[c0 + j + u]);
+          }
+          w[j >> 1] = pack_bf16(z[0], z[1]);
+        }
+        *reinterpret_cast<uint4*>(sm + OFF_A + op_offset(r, c0)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    for (int l = 1; l <= 3; ++l) {
+      if (tid == 0) {
+        if (!mbar_wait(barW, phW)) {
+          *sAbort = 1;
+        } else {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          mma_layer(tmem, a_base, w_base);
+          mma_commit(barM);
+        }
+      }
+      phW ^= 1;
+      __syncthreads();
+      if (*sAbort) break;
+      if (!mbar_wait(barM, phM)) atomicExch(sAbort, 1);
+      phM ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (*sAbort) break;
+      // the weight buffer is free again: bring in the next layer's (or the next tile's first)
+      if (tid == 0 && (l < 3 || more))
+        load_weights(w_base, wpack + (size_t)(l < 3 ? l : 0) * 256 * 256, barW);
+      const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+      const float* bias = sB + l * 256;
+      float o0 = 0.f, o1 = 0.f;
+      for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + bias[c0 + i]);
+        if (l < 3) {
+          uint4 w0, w1;
+          w0.x = pack_bf16(v[0], v[1]);   w0.y = pack_bf16(v[2], v[3]);
+          w0.z = pack_bf16(v[4], v[5]);   w0.w = pack_bf16(v[6], v[7]);
+          w1.x = pack_bf16(v[8], v[9]);   w1.y = pack_bf16(v[10], v[11]);
+          w1.z = pack_bf16(v[12], v[13]); w1.w = pack_bf16(v[14], v[15]);
+          *reinterpret_cast<uint4*>(sm + OFF_A + op_offset(erow, c0)) = w0;
+          *reinterpret_cast<uint4*>(sm + OFF_A + op_offset(erow, c0 + 8)) = w1;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float a = round_bf16(v[i]);
+            o0 = fmaf(a, sW4[c0 + i], o0);
+            o1 = fmaf(a, sW4[256 + c0 + i], o1);
+          }
+        }
+      }
+      if (l == 3) {
+        sRed[(half * TILE + erow) * 2] = o0;
+        sRed[(half * TILE + erow) * 2 + 1] = o1;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+    if (*sAbort) break;
+    if (tid < TILE) {
+      const long row = (long)tile * TILE + tid;
+      if (row < B) {
+        const float z0 = sRed[tid * 2] + sRed[(TILE + tid) * 2] + sB4[0];
+        const float z1 = sRed[tid * 2 + 1] + sRed[(TILE + tid) * 2 + 1] + sB4[1];
+        out[row * 2] = z0 / ys + y0;
+        out[row * 2 + 1] = z1 - 2.0f * logf(ys);
+      }
+    }
+  }
+  if (*sAbort && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+}
+
+// Operand image of the weights of layers 1-3 (W[n][k] as the B operand: row n, column k).
+__global__ void k_pack_weights(const __nv_bfloat16* __restrict__ wbf, __nv_bfloat16* __restrict__ wpack) {
+  const long per = 256L * 256;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 3 * per; i += (long)gridDim.x * blockDim.x) {
+    const int l = (int)(i / per) + 1;
+    const int n = (int)((i % per) / 256), k = (int)(i % 256);
+    const long woffl = 6 * 256 + 256 + (long)(l - 1) * (256 * 256 + 256);
+    wpack[(l - 1) * per + op_offset(n, k) / 2] = wbf[woffl + (long)n * 256 + k];
+  }
+}
+
+}  // namespace tc
 }  // namespace mlp
 }  // namespace swf
 
@@ -213,6 +484,10 @@ struct swf_mlp {
   float* in_shift;           // [6] feature standardisation
   float* in_scale;           // [6]
   float y0, ys;              // target standardisation
+  __nv_bfloat16* wpack;      // layers 1-3 in the tensor-core operand image (inference kernel)
+  int* err;                  // set by the inference kernel when a wait timed out
+  int nsm;
+  cudaStream_t last_stream;
   std::vector<void*> allocs;
 };
 
@@ -242,6 +517,7 @@ void gemm(const Mat& A, const Mat& B, int M, int N, int K, const EpiArgs& E, cud
 
 void refresh_bf16(swf_mlp* m, cudaStream_t st) {
   k_to_bf16<<<128, 256, 0, st>>>(m->params, m->wbf, n_params());
+  tc::k_pack_weights<<<192, 256, 0, st>>>(m->wbf, m->wpack);
 }
 
 // forward pass on x (fp32 [B][6]); leaves activations for the backward pass; output in z[NL-1]
@@ -314,6 +590,14 @@ swf_status swf_mlp_create(swf_mlp** out, int device, const float* init_params, i
   if ((s = mlp_alloc(m, (void**)&m->loss, 4)) != SWF_OK) return fail(s);
   if ((s = mlp_alloc(m, (void**)&m->in_shift, 6 * 4)) != SWF_OK) return fail(s);
   if ((s = mlp_alloc(m, (void**)&m->in_scale, 6 * 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->wpack, (size_t)3 * 256 * 256 * 2)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->err, sizeof(int))) != SWF_OK) return fail(s);
+  m->last_stream = 0;
+  m->nsm = 0;
+  e = cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess || m->nsm < 1) return fail(cuda_status(e, "SM count"));
+  e = cudaFuncSetAttribute(tc::k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaFuncSetAttribute(k_mlp_forward)"));
   m->y0 = norm[12];
   m->ys = norm[13];
   for (int l = 0; l < NL; ++l) {
@@ -330,6 +614,7 @@ swf_status swf_mlp_create(swf_mlp** out, int device, const float* init_params, i
   if (e != cudaSuccess) return fail(cuda_status(e, "upload normalisation"));
   cudaMemset(m->adam_m, 0, np * 4);
   cudaMemset(m->adam_v, 0, np * 4);
+  cudaMemset(m->err, 0, sizeof(int));
   refresh_bf16(m, 0);
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(cuda_status(e, "surrogate set-up"));
@@ -350,13 +635,28 @@ swf_status swf_mlp_forward(swf_mlp* m, const float* x_dev, int B, float* out_dev
   if (!m || !x_dev || !out_dev || B < 1) { set_error("swf_mlp_forward: invalid arguments"); return SWF_EINVAL; }
   cudaSetDevice(m->device);
   cudaStream_t st = (cudaStream_t)stream;
-  for (int b0 = 0; b0 < B; b0 += m->max_batch) {
-    const int nb = B - b0 < m->max_batch ? B - b0 : m->max_batch;
-    forward(m, x_dev + (long)b0 * DIN[0], nb, st);
-    k_outputs<<<(nb + 255) / 256, 256, 0, st>>>(m->z[NL - 1], m->y0, m->ys, out_dev + (long)b0 * 2, nb);
-  }
+  const int ntiles = (B + tc::TILE - 1) / tc::TILE;
+  const int grid = ntiles < m->nsm ? ntiles : m->nsm;
+  tc::k_mlp_forward<<<grid, tc::THREADS, tc::SMEM, st>>>(x_dev, B, m->wpack, m->wbf, m->params, m->in_shift,
+                                                         m->in_scale, m->y0, m->ys, out_dev, m->err);
+  m->last_stream = st;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "surrogate forward");
+  return SWF_OK;
+}
+
+swf_status swf_mlp_status(swf_mlp* m) {
+  if (!m) { set_error("swf_mlp_status: invalid arguments"); return SWF_EINVAL; }
+  cudaSetDevice(m->device);
+  cudaError_t e = cudaStreamSynchronize(m->last_stream);
+  if (e != cudaSuccess) return cuda_status(e, "surrogate status");
+  int flag = 0;
+  e = cudaMemcpy(&flag, m->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e, "surrogate status");
+  if (flag) {
+    set_error("surrogate inference: a tensor-core wait timed out");
+    return SWF_ETIMEOUT;
+  }
   return SWF_OK;
 }
 

@@ -47,7 +47,8 @@ class Result(C.Structure):
 EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
-           "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_gradients", "swf_mlp_train_step", "swf_mlp_get_params"]
+           "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
+           "swf_mlp_get_params"]
 
 
 class SwfError(RuntimeError):
@@ -86,6 +87,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_mlp_create.argtypes = [C.POINTER(vp), ip, fp, ip, fp]
     lib.swf_mlp_destroy.argtypes = [vp]
     lib.swf_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
+    lib.swf_mlp_status.argtypes = [vp]
     lib.swf_mlp_gradients.argtypes = [vp, vp, vp, ip, vp, vp, vp]
     lib.swf_mlp_train_step.argtypes = [vp, vp, vp, ip, C.c_float, vp, vp]
     lib.swf_mlp_get_params.argtypes = [vp, fp]
@@ -270,6 +272,10 @@ class Surrogate:
 
     def forward(self, x, out, stream=None):
         _check(_lib.swf_mlp_forward(self._h, _ptr(x), x.shape[0], _ptr(out), _stream_ptr(stream)))
+
+    def status(self):
+        """Waits for the last inference call; raises SwfError if one of its waits timed out."""
+        _check(_lib.swf_mlp_status(self._h))
 
     def gradients(self, x, y, grad=None, loss=None, stream=None):
         _check(_lib.swf_mlp_gradients(self._h, _ptr(x), _ptr(y), x.shape[0], _ptr(grad), _ptr(loss),

@@ -28,24 +28,61 @@ def test_forward_and_gradients_match_oracle():
     sur = swf.Surrogate(p0, norm, max_batch=256)
     Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
     out = torch.zeros(len(X), 2, dtype=torch.float32, device="cuda")
-    sur.forward(Xd, out)
-    ref_out, _, _ = M.forward(p0.astype(float), X.astype(float), norm.astype(float), bf=True)
-    ys = float(norm[13])
-    mu_ref = ref_out[:, 0] / ys + float(norm[12])
+    sur.forward(Xd, out)  # 192 rows: one full tile of 128 and a ragged one
+    sur.status()
+    mu_ref, lv_ref = _heads(M.forward(p0.astype(float), X.astype(float), norm.astype(float), bf=True)[0], norm)
     got = out.cpu().numpy()
     assert np.max(np.abs(got[:, 0] - mu_ref)) <= 1e-2 * max(1.0, np.max(np.abs(mu_ref)))
+    assert np.max(np.abs(got[:, 1] - lv_ref)) <= 1e-2 * max(1.0, np.max(np.abs(lv_ref)))
     grad = torch.zeros(swf.Surrogate.param_count(), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     sur.gradients(Xd, yd, grad, loss)
     ref_loss, ref_g = M.loss_and_grad(p0.astype(float), X.astype(float), y.astype(float), norm.astype(float), bf=True)
     g = grad.cpu().numpy().astype(float)
     assert abs(loss.item() - ref_loss) <= 1e-3 * abs(ref_loss)
+    # the inference kernel (tensor memory) and the training path's forward give the same loss
+    r = (y - norm[12]) * norm[13] - (got[:, 0] - norm[12]) * norm[13]
+    lvs = got[:, 1] + 2.0 * np.log(norm[13])
+    assert abs(0.5 * np.mean(r * r * np.exp(-lvs) + lvs) - loss.item()) <= 1e-3 * abs(loss.item())
     off = 0
     for i, o in zip(M.DIN, M.DOUT):  # per layer, weights and biases
         for size in (i * o, o):
             a, b = g[off:off + size], ref_g[off:off + size]
             assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-12, (off, size)
             off += size
+    sur.close()
+
+
+def _heads(z, norm):
+    """Network outputs in the target's units: mu = mu'/ys + y0, log sigma^2 = l' - 2 ln ys."""
+    ys = float(norm[13])
+    return z[:, 0] / ys + float(norm[12]), z[:, 1] - 2.0 * np.log(ys)
+
+
+@pytest.mark.parametrize("n_rows", [1, 127, 40000])
+def test_inference_tiles_match_oracle(n_rows):
+    """The persistent inference kernel on a single row, on one ragged tile, and on 313 tiles
+    (more tiles than SMs, so CTAs loop), against the oracle on sampled rows."""
+    import torch
+    from paper_2512_16889_gb300 import build, surrogate as S, swf
+    build.build()
+    t = _table(n_rows, seed=21)
+    X = S.features(t)
+    y = (-9.0 + np.tanh(3 * X[:, 0]) + 0.4 * X[:, 3]).astype(np.float32)
+    norm = S.normalisation(X, y) if n_rows > 1 else np.concatenate([np.zeros(6), np.ones(6), [-9.0, 1.0]]).astype(np.float32)
+    p0 = S.init_params(seed=5)
+    p0[np.arange(p0.size) % 5 == 0] *= -0.7
+    sur = swf.Surrogate(p0, norm, max_batch=256)
+    out = torch.full((n_rows, 2), float("nan"), dtype=torch.float32, device="cuda")
+    sur.forward(torch.from_numpy(X).cuda(), out)
+    sur.status()
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    rows = np.unique(np.concatenate([np.arange(min(n_rows, 64)), np.arange(max(0, n_rows - 64), n_rows),
+                                     np.random.default_rng(1).integers(0, n_rows, 256)]))
+    mu_ref, lv_ref = _heads(M.forward(p0.astype(float), X[rows].astype(float), norm.astype(float), bf=True)[0], norm)
+    assert np.max(np.abs(got[rows, 0] - mu_ref)) <= 1e-2 * max(1.0, np.max(np.abs(mu_ref)))
+    assert np.max(np.abs(got[rows, 1] - lv_ref)) <= 1e-2 * max(1.0, np.max(np.abs(lv_ref)))
     sur.close()
 
 
