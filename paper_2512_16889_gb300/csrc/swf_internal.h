@@ -120,8 +120,10 @@ struct ProfScope {
   swf_ctx* ctx;
   int mark;
   cudaStream_t st;
-  ProfScope(swf_ctx* c, const char* fam, cudaStream_t s) : ctx(c), mark(prof_begin(c, fam, s)), st(s) {}
-  ~ProfScope() { prof_end(ctx, mark, st); }
+  ProfScope(swf_ctx* c, const char* fam, cudaStream_t s) : ctx(c), mark(c ? prof_begin(c, fam, s) : -1), st(s) {}
+  ~ProfScope() {
+    if (ctx) prof_end(ctx, mark, st);
+  }
 };
 swf_status cuda_status(cudaError_t e, const char* what);
 

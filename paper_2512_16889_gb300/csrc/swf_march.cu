@@ -163,22 +163,211 @@ __device__ __forceinline__ double kappa_of(int j, int n, double L, double K) {
   return n > 1 ? mode_kappa(j, n, L) : K;
 }
 
-// ---------------------------------------------------------------- pass kernels
-// In-place FFT of `nlines` lines, `chunk` lines at a time (the per-thread register budget MAXE
-// bounds how many elements one fft_lines call may hold).
-template <typename R, int MAXE>
-__device__ __forceinline__ void fft_chunks(cpx<R>* buf, int ld, int nlines, int chunk, const RadixPlan& pl, bool inv,
-                                           const cpx<R>* __restrict__ tw) {
-  for (int l0 = 0; l0 < nlines; l0 += chunk)
-    fft_lines<R, MAXE>(buf + (size_t)l0 * ld, ld, min(chunk, nlines - l0), pl, inv, tw);
+
+// ---------------------------------------------------------------- composite DFTs in registers
+// cos and sin of 2 pi e / N for the composite radices (written out to 25 digits).
+__host__ __device__ constexpr double tw_const(int N, int e, bool want_cos) {
+  if (N == 8) {
+    switch (e) {
+      case 0: return want_cos ? 1.0000000000000000000000000 : 0.0000000000000000000000000;
+      case 1: return want_cos ? 0.7071067811865475244008444 : 0.7071067811865475244008444;
+      case 2: return want_cos ? -0.0000000000000000000000000 : 1.0000000000000000000000000;
+      case 3: return want_cos ? -0.7071067811865475244008444 : 0.7071067811865475244008444;
+      case 4: return want_cos ? -1.0000000000000000000000000 : 0.0000000000000000000000000;
+      case 5: return want_cos ? -0.7071067811865475244008444 : -0.7071067811865475244008444;
+      case 6: return want_cos ? -0.0000000000000000000000000 : -1.0000000000000000000000000;
+      case 7: return want_cos ? 0.7071067811865475244008444 : -0.7071067811865475244008444;
+    }
+  }
+  if (N == 12) {
+    switch (e) {
+      case 0: return want_cos ? 1.0000000000000000000000000 : 0.0000000000000000000000000;
+      case 1: return want_cos ? 0.8660254037844386467637232 : 0.5000000000000000000000000;
+      case 2: return want_cos ? 0.5000000000000000000000000 : 0.8660254037844386467637232;
+      case 3: return want_cos ? -0.0000000000000000000000000 : 1.0000000000000000000000000;
+      case 4: return want_cos ? -0.5000000000000000000000000 : 0.8660254037844386467637232;
+      case 5: return want_cos ? -0.8660254037844386467637232 : 0.5000000000000000000000000;
+      case 6: return want_cos ? -1.0000000000000000000000000 : 0.0000000000000000000000000;
+      case 7: return want_cos ? -0.8660254037844386467637232 : -0.5000000000000000000000000;
+      case 8: return want_cos ? -0.5000000000000000000000000 : -0.8660254037844386467637232;
+      case 9: return want_cos ? -0.0000000000000000000000000 : -1.0000000000000000000000000;
+      case 10: return want_cos ? 0.5000000000000000000000000 : -0.8660254037844386467637232;
+      case 11: return want_cos ? 0.8660254037844386467637232 : -0.5000000000000000000000000;
+    }
+  }
+  if (N == 16) {
+    switch (e) {
+      case 0: return want_cos ? 1.0000000000000000000000000 : 0.0000000000000000000000000;
+      case 1: return want_cos ? 0.9238795325112867561281832 : 0.3826834323650897717284600;
+      case 2: return want_cos ? 0.7071067811865475244008444 : 0.7071067811865475244008444;
+      case 3: return want_cos ? 0.3826834323650897717284600 : 0.9238795325112867561281832;
+      case 4: return want_cos ? -0.0000000000000000000000000 : 1.0000000000000000000000000;
+      case 5: return want_cos ? -0.3826834323650897717284600 : 0.9238795325112867561281832;
+      case 6: return want_cos ? -0.7071067811865475244008444 : 0.7071067811865475244008444;
+      case 7: return want_cos ? -0.9238795325112867561281832 : 0.3826834323650897717284600;
+      case 8: return want_cos ? -1.0000000000000000000000000 : 0.0000000000000000000000000;
+      case 9: return want_cos ? -0.9238795325112867561281832 : -0.3826834323650897717284600;
+      case 10: return want_cos ? -0.7071067811865475244008444 : -0.7071067811865475244008444;
+      case 11: return want_cos ? -0.3826834323650897717284600 : -0.9238795325112867561281832;
+      case 12: return want_cos ? -0.0000000000000000000000000 : -1.0000000000000000000000000;
+      case 13: return want_cos ? 0.3826834323650897717284600 : -0.9238795325112867561281832;
+      case 14: return want_cos ? 0.7071067811865475244008444 : -0.7071067811865475244008444;
+      case 15: return want_cos ? 0.9238795325112867561281832 : -0.3826834323650897717284600;
+    }
+  }
+  if (N == 20) {
+    switch (e) {
+      case 0: return want_cos ? 1.0000000000000000000000000 : 0.0000000000000000000000000;
+      case 1: return want_cos ? 0.9510565162951535721164393 : 0.3090169943749474241022934;
+      case 2: return want_cos ? 0.8090169943749474241022934 : 0.5877852522924731291687060;
+      case 3: return want_cos ? 0.5877852522924731291687060 : 0.8090169943749474241022934;
+      case 4: return want_cos ? 0.3090169943749474241022934 : 0.9510565162951535721164393;
+      case 5: return want_cos ? -0.0000000000000000000000000 : 1.0000000000000000000000000;
+      case 6: return want_cos ? -0.3090169943749474241022934 : 0.9510565162951535721164393;
+      case 7: return want_cos ? -0.5877852522924731291687060 : 0.8090169943749474241022934;
+      case 8: return want_cos ? -0.8090169943749474241022934 : 0.5877852522924731291687060;
+      case 9: return want_cos ? -0.9510565162951535721164393 : 0.3090169943749474241022934;
+      case 10: return want_cos ? -1.0000000000000000000000000 : 0.0000000000000000000000000;
+      case 11: return want_cos ? -0.9510565162951535721164393 : -0.3090169943749474241022934;
+      case 12: return want_cos ? -0.8090169943749474241022934 : -0.5877852522924731291687060;
+      case 13: return want_cos ? -0.5877852522924731291687060 : -0.8090169943749474241022934;
+      case 14: return want_cos ? -0.3090169943749474241022934 : -0.9510565162951535721164393;
+      case 15: return want_cos ? -0.0000000000000000000000000 : -1.0000000000000000000000000;
+      case 16: return want_cos ? 0.3090169943749474241022934 : -0.9510565162951535721164393;
+      case 17: return want_cos ? 0.5877852522924731291687060 : -0.8090169943749474241022934;
+      case 18: return want_cos ? 0.8090169943749474241022934 : -0.5877852522924731291687060;
+      case 19: return want_cos ? 0.9510565162951535721164393 : -0.3090169943749474241022934;
+    }
+  }
+  return 0.0;
 }
+
+// v * W_N^e (forward, W = exp(-2 pi i / N)) or v * conj(W_N^e) (inverse); quarter turns exact.
+template <typename R>
+__device__ __forceinline__ cpx<R> twiddle_const(cpx<R> v, int N, int e, bool inv) {
+  if (e == 0) return v;
+  if ((4 * e) % N == 0) {
+    const int q = (4 * e / N) & 3;
+    if (q == 2) return mk<R>(-v.x, -v.y);
+    if ((q == 1) != inv) return mul_mi(v);
+    return mul_i(v);
+  }
+  const R c = (R)tw_const(N, e, true), s = (R)tw_const(N, e, false);
+  return v * mk<R>(c, inv ? s : -s);
+}
+
+// DFT of length A*B in registers (Cooley-Tukey): index n = B n1 + n2 in, k = k1 + A k2 out.
+template <typename R, int A, int B>
+struct DftCT {
+  __device__ __forceinline__ static void run(cpx<R>* a, bool inv) {
+    constexpr int N = A * B;
+    cpx<R> y[N];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) {
+      cpx<R> t[A];
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) t[n1] = a[B * n1 + n2];
+      Dft<R, A>::run(t, inv);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) y[n2 * A + k1] = twiddle_const<R>(t[k1], N, n2 * k1, inv);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      cpx<R> t[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2 * A + k1];
+      Dft<R, B>::run(t, inv);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) a[k1 + A * k2] = t[k2];
+    }
+  }
+};
+template <typename R> struct Dft<R, 8> : DftCT<R, 4, 2> {};
+template <typename R> struct Dft<R, 12> : DftCT<R, 4, 3> {};
+template <typename R> struct Dft<R, 16> : DftCT<R, 4, 4> {};
+template <typename R> struct Dft<R, 20> : DftCT<R, 4, 5> {};
+
+// ---------------------------------------------------------------- out-of-place line FFT
+// Element e of a line sits at e + e/32 (a gap every 32 elements spreads the strided stores of
+// the early passes over the shared-memory banks).
+__host__ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
+static inline int padded_len(int n) { return pad32(n - 1) + 1; }
+
+// One self-sorting (Stockham) radix-RAD pass from `src` to `dst` over `nlines` lines of length
+// n (stride ld, padded positions): butterfly (line, i < n/RAD) reads elements i + q n/RAD,
+// multiplies by exp(-+ 2 pi i q k/(p RAD)) (k = i mod p, p = product of the radices so far),
+// applies the RAD-point DFT and writes elements (i - k) RAD + k + q p.  Out of place, so each
+// butterfly finishes before the next starts (one barrier per pass).
+template <typename R, int RAD>
+__device__ __forceinline__ void pp_pass(const cpx<R>* __restrict__ src, cpx<R>* __restrict__ dst, int ld,
+                                        int nlines, int n, int p, bool inv, const cpx<R>* __restrict__ tw) {
+  const int m = n / RAD;
+  const int nb = nlines * m;
+  const int twstep = n / (p * RAD);
+  const FastDiv fm((unsigned)m), fp((unsigned)p);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int line = (int)fm.div((unsigned)b);
+    const int i = b - line * m;
+    const int k = i - p * (int)fp.div((unsigned)i);
+    const cpx<R>* s = src + line * ld;
+    cpx<R>* d = dst + line * ld;
+    cpx<R> v[RAD];
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) v[q] = s[pad32(i + q * m)];
+    if (k != 0) {
+#pragma unroll
+      for (int q = 1; q < RAD; ++q) {
+        cpx<R> w = tw[q * k * twstep];
+        if (inv) w.y = -w.y;
+        v[q] = v[q] * w;
+      }
+    }
+    Dft<R, RAD>::run(v, inv);
+    const int o = (i - k) * RAD + k;
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) d[pad32(o + q * p)] = v[q];
+  }
+  __syncthreads();
+}
+
+// Full FFT of `nlines` lines held in `a` (padded layout; the caller has synchronised after
+// writing them), using `b` as the second buffer.  Returns the buffer holding the result.
+template <typename R>
+__device__ cpx<R>* fft_pp(cpx<R>* a, cpx<R>* b, int ld, int nlines, const RadixPlan& pl, bool inv,
+                          const cpx<R>* __restrict__ tw) {
+  int p = 1;
+  for (int ps = 0; ps < pl.npass; ++ps) {
+    const int r = pl.rad[ps];
+    switch (r) {
+      case 16: pp_pass<R, 16>(a, b, ld, nlines, pl.n, p, inv, tw); break;
+      case 20: pp_pass<R, 20>(a, b, ld, nlines, pl.n, p, inv, tw); break;
+      case 12: pp_pass<R, 12>(a, b, ld, nlines, pl.n, p, inv, tw); break;
+      case 8: pp_pass<R, 8>(a, b, ld, nlines, pl.n, p, inv, tw); break;
+      case 4: pp_pass<R, 4>(a, b, ld, nlines, pl.n, p, inv, tw); break;
+      case 2: pp_pass<R, 2>(a, b, ld, nlines, pl.n, p, inv, tw); break;
+      case 3: pp_pass<R, 3>(a, b, ld, nlines, pl.n, p, inv, tw); break;
+      default: pp_pass<R, 5>(a, b, ld, nlines, pl.n, p, inv, tw); break;
+    }
+    cpx<R>* t = a;
+    a = b;
+    b = t;
+    p *= r;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------- pass kernels
+// Shared memory of every pass kernel: two line buffers (the FFT works out of place) within
+// kPassSmem, so that three blocks of 256 threads fit an SM.
+static const size_t kPassSmem = 72 * 1024;
 
 // x lines of `rows` grid rows (4 components each): stage combine, local term, forward x-FFT
 // (and the whole derivative when x is the only non-trivial axis).
-template <typename R, int MAXE>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* buf2 = buf + 4 * rows * ld;
   __shared__ double s_ft[64];
   __shared__ cpx<R> s_tf;
   const int f = blockIdx.y;
@@ -245,10 +434,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_first(StageArgs
       for (int c = 0; c < 4; ++c) v[c] = mk<R>(0, 0);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) buf[(c * rows + j) * ld + x] = v[c];
+    for (int c = 0; c < 4; ++c) buf[(c * rows + j) * ld + pad32(x)] = v[c];
   }
   __syncthreads();
-  fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], false, A.tw[0]);
+  cpx<R>* res = fft_pp<R>(buf, buf2, ld, 4 * rows, A.plan[0], false, A.tw[0]);
   if (!only_x) {
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / nx;
@@ -257,7 +446,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_first(StageArgs
       if (row < A.nrows) {
         const size_t gi = fo + (size_t)row * nx + x;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) A.T[gi + c * cs] = buf[(c * rows + j) * ld + x];
+        for (int c = 0; c < 4; ++c) A.T[gi + c * cs] = res[(c * rows + j) * ld + pad32(x)];
       }
     }
     return;
@@ -269,13 +458,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_first(StageArgs
     const int j = e / nx, x = e - j * nx;
     cpx<R> v[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] = buf[(c * rows + j) * ld + x];
+    for (int c = 0; c < 4; ++c) v[c] = res[(c * rows + j) * ld + pad32(x)];
     h0_mi<R>(v, (R)kappa_of(x, nx, A.g.L[0], F->K[0]), ky, kz, sc);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) buf[(c * rows + j) * ld + x] = v[c];
+    for (int c = 0; c < 4; ++c) res[(c * rows + j) * ld + pad32(x)] = v[c];
   }
   __syncthreads();
-  fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], true, A.tw[0]);
+  res = fft_pp<R>(res, res == buf ? buf2 : buf, ld, 4 * rows, A.plan[0], true, A.tw[0]);
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / nx;
     const int x = e - j * nx;
@@ -283,18 +472,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_first(StageArgs
     if (row < A.nrows) {
       const size_t gi = fo + (size_t)row * nx + x;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) A.kout[gi + c * cs] = A.kout[gi + c * cs] + buf[(c * rows + j) * ld + x];
+      for (int c = 0; c < 4; ++c) A.kout[gi + c * cs] = A.kout[gi + c * cs] + res[(c * rows + j) * ld + pad32(x)];
     }
   }
 }
 
 // Lines along axis 1 (y) or 2 (z) of a tile of TX = 2^lgtx consecutive x columns: forward FFT,
 // -i H0(kappa)/N, inverse FFT, as selected.  The tile sits in shared memory as 4 TX lines of
-// stride ld (the axis length padded so that the transposing loads and stores spread over the
-// banks).
-template <typename R, int MAXE>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_mid(StageArgs<R> A, int axis, int lgtx, int ld,
-                                                                      int chunk, int do_fwd, int do_h0, int do_inv) {
+// stride ld (chosen so that the transposing loads and stores of a warp spread over the banks).
+template <typename R>
+__global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int lgtx, int ld, int do_fwd, int do_h0,
+                                             int do_inv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   const int f = blockIdx.y;
@@ -302,6 +490,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_mid(StageArgs<R
   const int N = A.g.N;
   const int na = A.g.n[axis];
   const int TX = 1 << lgtx;
+  cpx<R>* buf2 = buf + 4 * TX * ld;
   const int ntx = (nx + TX - 1) >> lgtx;
   const int xt = blockIdx.x % ntx;
   const int o = blockIdx.x / ntx;  // z index (axis 1) or y index (axis 2)
@@ -316,10 +505,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_mid(StageArgs<R
     const int x = xt * TX + t;
     const size_t gi = fo + base + m * stride + x;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) buf[(c * TX + t) * ld + m] = x < nx ? A.T[gi + c * cs] : mk<R>(0, 0);
+    for (int c = 0; c < 4; ++c) buf[(c * TX + t) * ld + pad32(m)] = x < nx ? A.T[gi + c * cs] : mk<R>(0, 0);
   }
   __syncthreads();
-  if (do_fwd) fft_chunks<R, MAXE>(buf, ld, 4 * TX, chunk, A.plan[axis], false, A.tw[axis]);
+  cpx<R>* res = buf;
+  if (do_fwd) res = fft_pp<R>(res, buf2, ld, 4 * TX, A.plan[axis], false, A.tw[axis]);
   if (do_h0) {
     const FieldDesc* F = A.fd + f;
     const R sc = (R)(1.0 / (double)N);
@@ -331,15 +521,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_mid(StageArgs<R
       const int iz = axis == 2 ? m : o;
       cpx<R> v[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) v[c] = buf[(c * TX + t) * ld + m];
+      for (int c = 0; c < 4; ++c) v[c] = res[(c * TX + t) * ld + pad32(m)];
       h0_mi<R>(v, (R)kappa_of(x, nx, A.g.L[0], F->K[0]), (R)kappa_of(iy, ny, A.g.L[1], F->K[1]),
                (R)kappa_of(iz, nz, A.g.L[2], F->K[2]), sc);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) buf[(c * TX + t) * ld + m] = v[c];
+      for (int c = 0; c < 4; ++c) res[(c * TX + t) * ld + pad32(m)] = v[c];
     }
     __syncthreads();
   }
-  if (do_inv) fft_chunks<R, MAXE>(buf, ld, 4 * TX, chunk, A.plan[axis], true, A.tw[axis]);
+  if (do_inv) res = fft_pp<R>(res, res == buf ? buf2 : buf, ld, 4 * TX, A.plan[axis], true, A.tw[axis]);
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int m = e >> lgtx;
     const int t = e & (TX - 1);
@@ -347,16 +537,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_mid(StageArgs<R
     if (x < nx) {
       const size_t gi = fo + base + m * stride + x;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) A.T[gi + c * cs] = buf[(c * TX + t) * ld + m];
+      for (int c = 0; c < 4; ++c) A.T[gi + c * cs] = res[(c * TX + t) * ld + pad32(m)];
     }
   }
 }
 
 // x lines: inverse x-FFT, k = (that) + Z.
-template <typename R, int MAXE>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_last(StageArgs<R> A, int rows, int ld) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* buf2 = buf + 4 * rows * ld;
   const int f = blockIdx.y;
   const int row0 = blockIdx.x * rows;
   const int nx = A.g.n[0];
@@ -370,10 +561,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_last(StageArgs<
     const int row = row0 + j;
     const size_t gi = fo + (size_t)row * nx + x;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) buf[(c * rows + j) * ld + x] = row < A.nrows ? A.T[gi + c * cs] : mk<R>(0, 0);
+    for (int c = 0; c < 4; ++c)
+      buf[(c * rows + j) * ld + pad32(x)] = row < A.nrows ? A.T[gi + c * cs] : mk<R>(0, 0);
   }
   __syncthreads();
-  fft_lines<R, MAXE>(buf, ld, 4 * rows, A.plan[0], true, A.tw[0]);
+  cpx<R>* res = fft_pp<R>(buf, buf2, ld, 4 * rows, A.plan[0], true, A.tw[0]);
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / nx;
     const int x = e - j * nx;
@@ -381,32 +573,32 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_last(StageArgs<
     if (row < A.nrows) {
       const size_t gi = fo + (size_t)row * nx + x;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) A.kout[gi + c * cs] = A.kout[gi + c * cs] + buf[(c * rows + j) * ld + x];
+      for (int c = 0; c < 4; ++c) A.kout[gi + c * cs] = A.kout[gi + c * cs] + res[(c * rows + j) * ld + pad32(x)];
     }
   }
 }
 
 // ---------------------------------------------------------------- host side
 template <typename R> struct Prec;
-template <> struct Prec<float> { static constexpr int MAXE = 12; static constexpr int is_double = 0; };
-template <> struct Prec<double> { static constexpr int MAXE = 12; static constexpr int is_double = 1; };
+template <> struct Prec<float> { static constexpr int is_double = 0; };
+template <> struct Prec<double> { static constexpr int is_double = 1; };
 
 static const int kThreads = 256;
 
-template <typename R>
-static int elem_cap() { return kThreads * (Prec<R>::MAXE - 4); }
-
-// Shared memory of one k_mid tile: 3 blocks of 256 threads fit an SM.
-static const size_t kMidSmem = 72 * 1024;
-
-// Tile of a y or z pass: the widest power-of-two column count TX <= 16 whose tile fits kMidSmem,
-// and a line stride ld = n_a + pad with ld = 32/TX modulo the elements of one 128-byte
-// shared-memory wavefront, so that the transposing accesses of a warp (TX columns x 32/TX lines)
-// fall on distinct banks.
-struct MidShape {
-  int lgtx, ld, chunk;
-  size_t smem;
-};
+// Radix plan of the march's line FFTs: radix 16 first, then the composite radices 20 and 12,
+// then 8, 4, 2, 3, 5 (every length of the form 2^a 3^b 5^c).
+static bool make_march_plan(int n, RadixPlan* pl) {
+  pl->n = n;
+  pl->npass = 0;
+  int m = n;
+  const int order[8] = {16, 20, 12, 8, 4, 2, 3, 5};
+  for (int r : order)
+    while (m % r == 0 && pl->npass < 12) {
+      pl->rad[pl->npass++] = r;
+      m /= r;
+    }
+  return m == 1;
+}
 
 // Streaming multiprocessors of the current device (cached per device).
 static int sm_count() {
@@ -421,23 +613,45 @@ static int sm_count() {
   return cache[dev];
 }
 
-// `tiles` = the number of (field, other-axis index) pairs of the pass.  Small grids trade tile
-// width (down to 32 bytes of contiguous x per line) for blocks, up to two per SM.
+// Rows per block of the x passes: as many as fit kPassSmem (at most 64), fewer on small grids
+// (up to two blocks per SM).  0 if one row does not fit.
+template <typename R>
+static int x_rows(int nx, int nrows, int F) {
+  const size_t line = (size_t)2 * 4 * padded_len(nx) * sizeof(cpx<R>);
+  int rows = (int)(kPassSmem / line);
+  if (rows > 64) rows = 64;
+  if (rows > nrows) rows = nrows;
+  while (rows > 1 && (long)F * ((nrows + rows - 1) / rows) < 2L * sm_count()) rows = (rows + 1) / 2;
+  return rows;
+}
+
+// Tile of a y or z pass: the widest power-of-two column count TX <= 16 whose two buffers fit
+// kPassSmem, narrowed on small grids (down to 32 bytes of contiguous x per line) for up to two
+// blocks per SM; line stride ld >= the padded length with ld = 32/TX modulo the elements of one
+// 128-byte shared-memory wavefront, so that the transposing accesses of a warp (TX columns x
+// 32/TX lines) fall on distinct banks.  `tiles` = (field, other-axis index) pairs of the pass.
+struct MidShape {
+  int lgtx, ld;
+  size_t smem;
+};
+
 template <typename R>
 static MidShape mid_shape(int n_a, int nx, long tiles) {
   const int esz = (int)sizeof(cpx<R>);
   const int unit = 128 / esz;
   const int min_lg = esz == 8 ? 2 : 1;
+  auto stride = [&](int lg) {
+    const int base = padded_len(n_a);
+    const int pad = (((32 >> lg) % unit - base % unit) % unit + unit) % unit;
+    return base + pad;
+  };
   int lg = 4;
-  while (lg > 0 && ((1 << lg) > nx || (size_t)4 * (1 << lg) * (n_a + unit) * esz > kMidSmem)) --lg;
+  while (lg > 0 && ((1 << lg) > nx || (size_t)2 * 4 * (1 << lg) * stride(lg) * esz > kPassSmem)) --lg;
   while (lg > min_lg && tiles * ((nx + (1 << lg) - 1) >> lg) < 2L * sm_count()) --lg;
   MidShape m{};
-  const int TX = 1 << lg;
-  const int pad = (((32 / TX) % unit - n_a % unit) % unit + unit) % unit;
   m.lgtx = lg;
-  m.ld = n_a + pad;
-  m.smem = (size_t)4 * TX * m.ld * esz;
-  m.chunk = elem_cap<R>() / n_a;
+  m.ld = stride(lg);
+  m.smem = (size_t)2 * 4 * (1 << lg) * m.ld * esz;
   return m;
 }
 
@@ -445,37 +659,30 @@ template <typename R>
 static swf_status set_smem_attrs() {
   static bool done = false;
   if (done) return SWF_OK;
-  const int bytes = elem_cap<R>() * (int)sizeof(cpx<R>);
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_first<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(k_first<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_first)");
-  e = cudaFuncSetAttribute(k_mid<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmem);
+  e = cudaFuncSetAttribute(k_mid<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_mid)");
-  e = cudaFuncSetAttribute(k_last<R, Prec<R>::MAXE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(k_last<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last)");
   done = true;
   return SWF_OK;
 }
 
-// Launches one right-hand-side evaluation for F fields.
+// Launches one right-hand-side evaluation for F fields (ctx may be null: no profiling).
 template <typename R>
 static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaStream_t st) {
-  constexpr int MAXE = Prec<R>::MAXE;
   const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
-  const int cap = elem_cap<R>();
-  int rows = cap / (4 * nx);
-  if (rows > 64) rows = 64;
-  if (rows > A.nrows) rows = A.nrows;
-  if (rows < 1 || 4 * ny > cap || 4 * nz > cap) return SWF_EUNSUPPORTED;  // one spinor line per block at least
-  // small grids: fewer rows per block, for up to two blocks per SM
-  while (rows > 1 && (long)F * ((A.nrows + rows - 1) / rows) < 2L * sm_count()) rows = (rows + 1) / 2;
-  const int ld = nx;
+  const int rows = x_rows<R>(nx, A.nrows, F);
+  if (rows < 1) return SWF_EUNSUPPORTED;
+  const int ld = padded_len(nx);
   const bool only_x = (ny == 1 && nz == 1);
-  size_t smem = (size_t)4 * rows * ld * sizeof(cpx<R>);
+  const size_t smem = (size_t)2 * 4 * rows * ld * sizeof(cpx<R>);
   dim3 grid_rows((A.nrows + rows - 1) / rows, F);
   {
     ProfScope ps(ctx, "k_first", st);
-    k_first<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, ld, only_x ? 1 : 0);
+    k_first<R><<<grid_rows, kThreads, smem, st>>>(A, rows, ld, only_x ? 1 : 0);
   }
   if (only_x) return SWF_OK;
   int axes[2], na = 0;
@@ -487,7 +694,7 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
     const int ntx = (nx + (1 << ms.lgtx) - 1) >> ms.lgtx;
     dim3 grid(ntx * other, F);
     ProfScope ps(ctx, "k_mid", st);
-    k_mid<R, MAXE><<<grid, kThreads, ms.smem, st>>>(A, axis, ms.lgtx, ms.ld, ms.chunk, fwd, h0, inv);
+    k_mid<R><<<grid, kThreads, ms.smem, st>>>(A, axis, ms.lgtx, ms.ld, fwd, h0, inv);
   };
   if (na == 1) {
     mid(axes[0], 1, 1, 1);
@@ -498,7 +705,7 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
   }
   {
     ProfScope ps(ctx, "k_last", st);
-    k_last<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, ld);
+    k_last<R><<<grid_rows, kThreads, smem, st>>>(A, rows, ld);
   }
   return SWF_OK;
 }
@@ -512,7 +719,7 @@ static swf_status prepare_args(swf_ctx* ctx, const GridDesc& g, int F, const Fie
   A->g = g;
   A->nrows = g.n[1] * g.n[2];
   for (int a = 0; a < 3; ++a) {
-    if (!make_radix_plan(g.n[a], &A->plan[a])) {
+    if (!make_march_plan(g.n[a], &A->plan[a])) {
       set_error("grid size must factor into 2, 3 and 5");
       return SWF_EINVAL;
     }
@@ -657,7 +864,6 @@ size_t rhs_scratch_bytes(const GridDesc& g, swf_precision prec) {
 template <typename R>
 static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, double t, const void* psi, void* out,
                                    unsigned char* scratch, cudaStream_t st) {
-  constexpr int MAXE = Prec<R>::MAXE;
   swf_status s = set_smem_attrs<R>();
   if (s != SWF_OK) return s;
   const int nt = g.n[0] + g.n[1] + g.n[2];
@@ -675,7 +881,7 @@ static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, doubl
   A.g = g;
   A.nrows = g.n[1] * g.n[2];
   for (int a = 0; a < 3; ++a) {
-    if (!make_radix_plan(g.n[a], &A.plan[a])) {
+    if (!make_march_plan(g.n[a], &A.plan[a])) {
       set_error("grid size must factor into 2, 3 and 5");
       return SWF_EINVAL;
     }
@@ -694,32 +900,8 @@ static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, doubl
   A.T = T;
   A.kout = (cpx<R>*)out;
   A.t = t;
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int cap = elem_cap<R>();
-  int rows = cap / (4 * nx);
-  if (rows > 64) rows = 64;
-  if (rows > A.nrows) rows = A.nrows;
-  if (rows < 1 || 4 * ny > cap || 4 * nz > cap) return SWF_EUNSUPPORTED;
-  const bool only_x = (ny == 1 && nz == 1);
-  const size_t smem = (size_t)4 * rows * nx * sizeof(cpx<R>);
-  const dim3 grid_rows((A.nrows + rows - 1) / rows, 1);
-  k_first<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, nx, only_x ? 1 : 0);
-  if (!only_x) {
-    auto mid = [&](int axis, int fwd, int h0, int inv) {
-      const int other = axis == 1 ? nz : ny;
-      const MidShape ms = mid_shape<R>(g.n[axis], nx, other);
-      const int ntx = (nx + (1 << ms.lgtx) - 1) >> ms.lgtx;
-      k_mid<R, MAXE><<<dim3(ntx * other, 1), kThreads, ms.smem, st>>>(A, axis, ms.lgtx, ms.ld, ms.chunk, fwd, h0, inv);
-    };
-    if (ny > 1 && nz > 1) {
-      mid(1, 1, 0, 0);
-      mid(2, 1, 1, 1);
-      mid(1, 0, 0, 1);
-    } else {
-      mid(ny > 1 ? 1 : 2, 1, 1, 1);
-    }
-    k_last<R, MAXE><<<grid_rows, kThreads, smem, st>>>(A, rows, nx);
-  }
+  s = launch_eval<R>(nullptr, A, 1, st);
+  if (s != SWF_OK) return s;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "rhs kernels");
   return SWF_OK;
