@@ -315,11 +315,29 @@ __device__ __forceinline__ void pp_pass(const cpx<R>* __restrict__ src, cpx<R>* 
 #pragma unroll
     for (int q = 0; q < RAD; ++q) v[q] = s[pad32(i + q * m)];
     if (k != 0) {
+      const int ks = k * twstep;
+      if (RAD <= 5) {
 #pragma unroll
-      for (int q = 1; q < RAD; ++q) {
-        cpx<R> w = tw[q * k * twstep];
-        if (inv) w.y = -w.y;
-        v[q] = v[q] * w;
+        for (int q = 1; q < RAD; ++q) {
+          cpx<R> w = tw[q * ks];
+          if (inv) w.y = -w.y;
+          v[q] = v[q] * w;
+        }
+      } else {
+        // w^q for q < RAD from the table entries at the powers of two (at most three products
+        // per factor: a few units in the last place)
+        cpx<R> w[RAD];
+#pragma unroll
+        for (int q = 1; q < RAD; ++q) {
+          if ((q & (q - 1)) == 0) {
+            w[q] = tw[q * ks];
+            if (inv) w[q].y = -w[q].y;
+          } else {
+            const int lo = q & (-q);  // lowest set bit: w^q = w^lo w^(q - lo)
+            w[q] = w[lo] * w[q - lo];
+          }
+          v[q] = v[q] * w[q];
+        }
       }
     }
     Dft<R, RAD>::run(v, inv);
@@ -971,7 +989,8 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   for (int a = 0; a < 3; ++a) eps[a] = (R)photon[6 * inst + 3 + a];
   const cpx<R>* U = ys + (size_t)(2 * inst) * 4 * g.N;
   const cpx<R>* V = ys + (size_t)(2 * inst + 1) * 4 * g.N;
-  cpx<double> ass = mk<double>(0, 0), abs_ = mk<double>(0, 0), asb = mk<double>(0, 0);
+  // per-thread sums in the march precision (a few sites each), then FP64 across threads
+  cpx<R> tss = mk<R>(0, 0), tbs = mk<R>(0, 0), tsb = mk<R>(0, 0);
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.N; j += gridDim.x * blockDim.x) {
     const int ix = j % g.n[0];
     const int iy = (j / g.n[0]) % g.n[1];
@@ -996,10 +1015,11 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
       bs = bs + cdot(ub[a], av[a]);
       sb = sb + cdot(u[a], avb[a]);
     }
-    ass = ass + cvt<double>(ss * ph);
-    abs_ = abs_ + cvt<double>(bs * ph);
-    asb = asb + cvt<double>(sb * ph);
+    tss = tss + ss * ph;
+    tbs = tbs + bs * ph;
+    tsb = tsb + sb * ph;
   }
+  cpx<double> ass = cvt<double>(tss), abs_ = cvt<double>(tbs), asb = cvt<double>(tsb);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     ass.x += __shfl_down_sync(0xffffffffu, ass.x, off); ass.y += __shfl_down_sync(0xffffffffu, ass.y, off);
@@ -1019,14 +1039,20 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   }
 }
 
-// macc[inst][q] += w dx^d exp(-i k0 t) sum_b part[inst][b][q], parts added in order of b.
-__global__ void k_mdot_final(const cpx<double>* __restrict__ part, int nb, const double* photon, GridDesc g,
-                             double t, double w, cpx<double>* macc) {
+// macc[inst][q] += w dx^d exp(-i k0 t) sum_b part[inst][b][q]: warp q of block inst adds the
+// parts b = lane, lane + 32, ... in order, then a fixed shuffle tree (deterministic).
+__global__ void __launch_bounds__(96) k_mdot_final(const cpx<double>* __restrict__ part, int nb, const double* photon,
+                                                   GridDesc g, double t, double w, cpx<double>* macc) {
   const int inst = blockIdx.x;
-  const int q = threadIdx.x;
-  if (q >= 3) return;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   cpx<double> sacc = mk<double>(0, 0);
-  for (int b = 0; b < nb; ++b) sacc = sacc + part[((size_t)inst * nb + b) * 3 + q];
+  for (int b = lane; b < nb; b += 32) sacc = sacc + part[((size_t)inst * nb + b) * 3 + q];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sacc.x += __shfl_down_sync(0xffffffffu, sacc.x, off);
+    sacc.y += __shfl_down_sync(0xffffffffu, sacc.y, off);
+  }
+  if (lane != 0) return;
   double sk, ck;
   const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
                          photon[6 * inst + 2] * photon[6 * inst + 2]);
@@ -1107,7 +1133,7 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
       }
       if (wgt != 0.0) {
         ProfScope ps(ctx, "k_mdot_final", st);
-        k_mdot_final<<<n_inst, 32, 0, st>>>((const cpx<double>*)ppart, nb, (const double*)pph, g, A.t, wgt,
+        k_mdot_final<<<n_inst, 96, 0, st>>>((const cpx<double>*)ppart, nb, (const double*)pph, g, A.t, wgt,
                                             (cpx<double>*)macc);
       }
     }
