@@ -621,6 +621,12 @@ swf_status swf_set_march_path(swf_ctx* ctx, int path) {
   return SWF_OK;
 }
 
+swf_status swf_set_autotune(swf_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) { set_error("swf_set_autotune: ctx NULL or on not 0 or 1"); return SWF_EINVAL; }
+  ctx->tune.on = on != 0;
+  return SWF_OK;
+}
+
 swf_status swf_set_workspace_limit(swf_ctx* ctx, size_t bytes) {
   if (!ctx) { set_error("ctx is NULL"); return SWF_EINVAL; }
   ctx->ws.limit = bytes;

@@ -98,12 +98,21 @@ struct Profiler {
 };
 }  // namespace swf
 
+namespace swf {
+// Launch shapes of the pass kernels chosen by timing, per shape key (see the march).
+struct TuneCache {
+  bool on = true;
+  std::map<std::string, int> best;
+};
+}  // namespace swf
+
 struct swf_ctx {
   int device;
   cudaStream_t stream;
   swf::Workspace ws;
   swf::TwiddleCache tw;
   swf::Profiler prof;
+  swf::TuneCache tune;
   bool use_fused = true;  // route eligible marches to the fused cluster kernel
   int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
 };

@@ -654,23 +654,54 @@ struct MidShape {
 };
 
 template <typename R>
-static MidShape mid_shape(int n_a, int nx, long tiles) {
-  const int esz = (int)sizeof(cpx<R>);
-  const int unit = 128 / esz;
-  const int min_lg = esz == 8 ? 2 : 1;
-  auto stride = [&](int lg) {
-    const int base = padded_len(n_a);
-    const int pad = (((32 >> lg) % unit - base % unit) % unit + unit) % unit;
-    return base + pad;
-  };
+static int mid_stride(int n_a, int lg) {
+  const int unit = 128 / (int)sizeof(cpx<R>);
+  const int base = padded_len(n_a);
+  const int pad = (((32 >> lg) % unit - base % unit) % unit + unit) % unit;
+  return base + pad;
+}
+
+template <typename R>
+static size_t mid_smem(int n_a, int lg) {
+  return (size_t)2 * 4 * (1 << lg) * mid_stride<R>(n_a, lg) * sizeof(cpx<R>);
+}
+
+// widest tile that fits (TX <= nx as well)
+template <typename R>
+static int mid_max_lg(int n_a, int nx) {
   int lg = 4;
-  while (lg > 0 && ((1 << lg) > nx || (size_t)2 * 4 * (1 << lg) * stride(lg) * esz > kPassSmem)) --lg;
-  while (lg > min_lg && tiles * ((nx + (1 << lg) - 1) >> lg) < 2L * sm_count()) --lg;
+  while (lg > 0 && ((1 << lg) > nx || mid_smem<R>(n_a, lg) > kPassSmem)) --lg;
+  return lg;
+}
+
+template <typename R>
+static MidShape mid_shape_lg(int n_a, int lg) {
   MidShape m{};
   m.lgtx = lg;
-  m.ld = stride(lg);
-  m.smem = (size_t)2 * 4 * (1 << lg) * m.ld * esz;
+  m.ld = mid_stride<R>(n_a, lg);
+  m.smem = mid_smem<R>(n_a, lg);
   return m;
+}
+
+template <typename R>
+static MidShape mid_shape(int n_a, int nx, long tiles) {
+  const int min_lg = sizeof(cpx<R>) == 8 ? 2 : 1;
+  int lg = mid_max_lg<R>(n_a, nx);
+  while (lg > min_lg && tiles * ((nx + (1 << lg) - 1) >> lg) < 2L * sm_count()) --lg;
+  return mid_shape_lg<R>(n_a, lg);
+}
+
+// Keys of the tuned shapes: pass kind, element size and the sizes that decide the launch.
+static std::string tune_key(char kind, int esz, int a, int b, int c, long d) {
+  char buf[96];
+  std::snprintf(buf, sizeof buf, "%c/%d/%d/%d/%d/%ld", kind, esz, a, b, c, d);
+  return buf;
+}
+
+static int tune_lookup(swf_ctx* ctx, const std::string& key, int fallback) {
+  if (!ctx || !ctx->tune.on) return fallback;
+  auto it = ctx->tune.best.find(key);
+  return it == ctx->tune.best.end() ? fallback : it->second;
 }
 
 template <typename R>
@@ -692,7 +723,8 @@ static swf_status set_smem_attrs() {
 template <typename R>
 static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaStream_t st) {
   const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
-  const int rows = x_rows<R>(nx, A.nrows, F);
+  constexpr int esz = (int)sizeof(cpx<R>);
+  const int rows = tune_lookup(ctx, tune_key('x', esz, nx, A.nrows, 0, F), x_rows<R>(nx, A.nrows, F));
   if (rows < 1) return SWF_EUNSUPPORTED;
   const int ld = padded_len(nx);
   const bool only_x = (ny == 1 && nz == 1);
@@ -708,7 +740,9 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
   if (nz > 1) axes[na++] = 2;
   auto mid = [&](int axis, int fwd, int h0, int inv) {
     const int other = axis == 1 ? nz : ny;
-    const MidShape ms = mid_shape<R>(A.g.n[axis], nx, (long)other * F);
+    const int lg_h = mid_shape<R>(A.g.n[axis], nx, (long)other * F).lgtx;
+    const int lg = tune_lookup(ctx, tune_key('m', esz, axis * 8 + fwd * 4 + h0 * 2 + inv, A.g.n[axis], nx, (long)other * F), lg_h);
+    const MidShape ms = mid_shape_lg<R>(A.g.n[axis], lg);
     const int ntx = (nx + (1 << ms.lgtx) - 1) >> ms.lgtx;
     dim3 grid(ntx * other, F);
     ProfScope ps(ctx, "k_mid", st);
@@ -726,6 +760,92 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
     k_last<R><<<grid_rows, kThreads, smem, st>>>(A, rows, ld);
   }
   return SWF_OK;
+}
+
+// Times the candidate launch shapes of one evaluation's pass kernels and records the fastest
+// in ctx->tune (once per shape key).  B must be harmless to run repeatedly: it may write only
+// T and its output slot, and read y and its input slots (the march calls this before its first
+// evaluation, when those hold nothing yet).  The shape decides only which lines a block
+// transforms, never the arithmetic of a line, so results do not depend on the choice.
+template <typename R>
+static swf_status autotune_eval(swf_ctx* ctx, const StageArgs<R>& B, int F, cudaStream_t st) {
+  if (!ctx || !ctx->tune.on) return SWF_OK;
+  constexpr int esz = (int)sizeof(cpx<R>);
+  const int nx = B.g.n[0], ny = B.g.n[1], nz = B.g.n[2];
+  const bool only_x = (ny == 1 && nz == 1);
+  cudaEvent_t ev[2];
+  if (cudaEventCreate(&ev[0]) != cudaSuccess) return cuda_status(cudaGetLastError(), "tuning events");
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return cuda_status(cudaGetLastError(), "tuning events");
+  }
+  swf_status status = SWF_OK;
+  // time `launch` (one warm-up, then three back to back); +inf on a launch error
+  auto timed = [&](auto&& launch) -> float {
+    launch();
+    cudaEventRecord(ev[0], st);
+    for (int r = 0; r < 3; ++r) launch();
+    cudaEventRecord(ev[1], st);
+    cudaError_t e = cudaEventSynchronize(ev[1]);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      status = cuda_status(e, "tuning launches");
+      return 3.4e38f;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    return ms;
+  };
+  const std::string xkey = tune_key('x', esz, nx, B.nrows, 0, F);
+  if (!ctx->tune.best.count(xkey)) {
+    const size_t line = (size_t)2 * 4 * padded_len(nx) * esz;
+    int rmax = (int)(kPassSmem / line);
+    rmax = std::min(std::min(rmax, 64), B.nrows);
+    int best = x_rows<R>(nx, B.nrows, F);
+    float tbest = 3.4e38f;
+    const int ld = padded_len(nx);
+    for (int rows = 1; rows <= rmax && status == SWF_OK; rows *= 2) {
+      const size_t smem = (size_t)2 * 4 * rows * ld * esz;
+      const dim3 grid((B.nrows + rows - 1) / rows, F);
+      const float t = timed([&] {
+        k_first<R><<<grid, kThreads, smem, st>>>(B, rows, ld, only_x ? 1 : 0);
+        if (!only_x) k_last<R><<<grid, kThreads, smem, st>>>(B, rows, ld);
+      });
+      if (t < tbest) { tbest = t; best = rows; }
+    }
+    if (status == SWF_OK) ctx->tune.best[xkey] = best;
+  }
+  if (!only_x) {
+    int axes[2], na = 0;
+    if (ny > 1) axes[na++] = 1;
+    if (nz > 1) axes[na++] = 2;
+    const int combos1[1][4] = {{0, 1, 1, 1}};
+    const int combos2[3][4] = {{1, 1, 0, 0}, {2, 1, 1, 1}, {1, 0, 0, 1}};
+    const int nc = na == 1 ? 1 : 3;
+    for (int ci = 0; ci < nc && status == SWF_OK; ++ci) {
+      const int* cb = na == 1 ? combos1[ci] : combos2[ci];
+      const int axis = na == 1 ? axes[0] : cb[0];
+      const int other = axis == 1 ? nz : ny;
+      const int n_a = B.g.n[axis];
+      const std::string key = tune_key('m', esz, axis * 8 + cb[1] * 4 + cb[2] * 2 + cb[3], n_a, nx, (long)other * F);
+      if (ctx->tune.best.count(key)) continue;
+      int best = mid_shape<R>(n_a, nx, (long)other * F).lgtx;
+      float tbest = 3.4e38f;
+      for (int lg = mid_max_lg<R>(n_a, nx); lg >= 0 && status == SWF_OK; --lg) {
+        const MidShape ms = mid_shape_lg<R>(n_a, lg);
+        const int ntx = (nx + (1 << lg) - 1) >> lg;
+        const dim3 grid(ntx * other, F);
+        const float t = timed([&] {
+          k_mid<R><<<grid, kThreads, ms.smem, st>>>(B, axis, lg, ms.ld, cb[1], cb[2], cb[3]);
+        });
+        if (t < tbest) { tbest = t; best = lg; }
+      }
+      if (status == SWF_OK) ctx->tune.best[key] = best;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return status;
 }
 
 template <typename R>
@@ -782,6 +902,20 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
   if (e != cudaSuccess) return cuda_status(e, "memset state");
   A.y = (cpx<R>*)py;
   A.T = (cpx<R>*)pT;
+  {
+    // shapes by timing, on the slots before they hold anything (the heaviest stage: six inputs)
+    StageArgs<R> B = A;
+    B.nterm = 6;
+    for (int q = 0; q < 6; ++q) {
+      B.kin[q] = (const cpx<R>*)pk[q + 1];
+      B.coef[q] = 0.0;
+    }
+    B.write_y = 0;
+    B.ystage = nullptr;
+    B.kout = (cpx<R>*)pk[0];
+    B.t = t_out;
+    if ((s = autotune_eval<R>(ctx, B, F, st)) != SWF_OK) return s;
+  }
   int slot[7] = {0, 1, 2, 3, 4, 5, 6};
   const double h = (t_in - t_out) / n_steps;
   // k_1 = f(t_out, 0)
@@ -1099,6 +1233,19 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   if ((e = cudaMemsetAsync(macc, 0, sizeof(double2) * 3 * n_inst, st)) != cudaSuccess) return cuda_status(e, "memset M");
   A.y = (cpx<R>*)py;
   A.T = (cpx<R>*)pT;
+  {
+    StageArgs<R> B = A;  // shapes by timing, as in the plain march
+    B.nterm = 6;
+    for (int q = 0; q < 6; ++q) {
+      B.kin[q] = (const cpx<R>*)pk[q + 1];
+      B.coef[q] = 0.0;
+    }
+    B.write_y = 0;
+    B.ystage = nullptr;
+    B.kout = (cpx<R>*)pk[0];
+    B.t = t_out;
+    if ((s = autotune_eval<R>(ctx, B, F, st)) != SWF_OK) return s;
+  }
   int slot[7] = {0, 1, 2, 3, 4, 5, 6};
   const double h = (t_in - t_out) / n_steps;
   A.nterm = 0;

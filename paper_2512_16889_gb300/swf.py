@@ -46,7 +46,7 @@ class Result(C.Structure):
 
 EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
-           "swf_profile_read", "swf_set_march_path", "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
+           "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
            "swf_mlp_get_params"]
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_set_workspace_limit.argtypes = [vp, C.c_size_t]
     lib.swf_profile_enable.argtypes = [vp, ip]
     lib.swf_set_march_path.argtypes = [vp, ip]
+    lib.swf_set_autotune.argtypes = [vp, ip]
     lib.swf_rhs_noalloc.argtypes = [inst_p, ip, ip, dp, vp, vp, vp]
     fp = C.POINTER(C.c_float)
     lib.swf_mlp_param_count.argtypes = []
@@ -167,6 +168,10 @@ class Context:
     def set_march_path(self, path: int):
         """0 = automatic (fused cluster kernel where it applies), 1 = pass kernels only."""
         _check(_lib.swf_set_march_path(self._h, int(path)))
+
+    def set_autotune(self, on: bool):
+        """Pass-kernel launch shapes by timing (True, default) or by the fixed rule (False)."""
+        _check(_lib.swf_set_autotune(self._h, 1 if on else 0))
 
     def profile_enable(self, on=True):
         _check(_lib.swf_profile_enable(self._h, 1 if on else 0))

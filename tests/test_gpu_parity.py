@@ -285,3 +285,24 @@ def test_full_size_workload_matches_stored_oracle_samples(env):
         absrel = np.max(np.abs(got - ref)) / smp["max_prob"]
         assert absrel < 2e-5, (i, absrel)
         assert abs(res[i].diag[0] - smp["norm"]) < 1e-5 * smp["norm"]
+
+
+def test_tuned_launch_shapes_give_bitwise_identical_marches(env):
+    """The pass kernels' launch shapes (chosen by timing, or by the fixed rule) decide only which
+    lines a block transforms: marches agree bit for bit (x-only, 2D, 3D; both precisions)."""
+    torch, swf, _ = env
+    cases = [W.small_parity_cases()[i] for i in (0, 1)] + [dict(_full(RHS_CASES[i]), flags=()) for i in (4, 5)]
+    for d in cases:
+        for prec in (swf.C128, swf.C64):
+            outs = []
+            for tuned in (False, True):
+                ctx = swf.Context(0)
+                ctx.set_march_path(1)
+                ctx.set_autotune(tuned)
+                out = torch.zeros(2 * 4 * int(np.prod(d["n"])), device="cuda",
+                                  dtype=torch.float64 if prec == swf.C128 else torch.float32)
+                ctx.march_dev([swf.from_workload(d)], out, bg=0, prec=prec)
+                ctx.march_dev([swf.from_workload(d)], out, bg=0, prec=prec)  # second call: cached shapes
+                outs.append(out.cpu().numpy())
+                ctx.close()
+            assert np.array_equal(outs[0], outs[1]), (d["n"], prec)
