@@ -206,7 +206,7 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, long n, flo
 // back into the operand buffer; after layer 3 it contracts with the output weights.
 namespace tc {
 
-constexpr int THREADS = 256;
+constexpr int THREADS = 512;
 constexpr int TILE = 128;
 constexpr uint32_t OP_BYTES_A = TILE * 256 * 2;   // 64 KB
 constexpr uint32_t OP_BYTES_W = 256 * 256 * 2;    // 128 KB
@@ -215,13 +215,13 @@ constexpr uint32_t OFF_W = OFF_A + OP_BYTES_A;
 constexpr uint32_t OFF_W0 = OFF_W + OP_BYTES_W;   // float [256][6]
 constexpr uint32_t OFF_B = OFF_W0 + 256 * 6 * 4;  // float [4][256]: b0..b3
 constexpr uint32_t OFF_W4 = OFF_B + 4 * 256 * 4;  // float [2][256]
-constexpr uint32_t OFF_RED = OFF_W4 + 2 * 256 * 4;  // float [2][128][2]
-constexpr uint32_t OFF_MISC = OFF_RED + 2 * TILE * 2 * 4;
+constexpr uint32_t OFF_RED = OFF_W4 + 2 * 256 * 4;  // float [4][128][2]
+constexpr uint32_t OFF_MISC = OFF_RED + 4 * TILE * 2 * 4;
 constexpr uint32_t SMEM = OFF_MISC + 64;
 constexpr long long WAIT_CYCLES = 4000000000LL;   // about two seconds at the maximum clock
 
-// instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 128 (one column half), M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __host__ __device__ __forceinline__ uint32_t op_offset(int r, int k) {
   return (uint32_t)((r >> 3) * 4096 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
@@ -261,7 +261,8 @@ __device__ __forceinline__ void load_weights(uint32_t dst, const void* src, uint
                  : "memory");
 }
 
-__device__ __forceinline__ void mma_layer(uint32_t tmem_d, uint32_t a_base, uint32_t w_base) {
+// D[:, 0:128) = A W_half^T over K = 256 (16 instructions); W_half = rows [128 h, 128 h + 128) of W
+__device__ __forceinline__ void mma_half(uint32_t tmem_d, uint32_t a_base, uint32_t w_base) {
 #pragma unroll
   for (int kk = 0; kk < 16; ++kk) {
     const uint64_t ad = smem_desc(a_base + kk * 256), bd = smem_desc(w_base + kk * 256);
@@ -301,6 +302,10 @@ __device__ __forceinline__ float round_bf16(float a) { return __bfloat162float(_
 // x [B][6] fp32 features; wpack: layers 1-3 in the operand image; wbf: all parameters in BF16
 // (W0 and W4 read from it); params: FP32 parameters (biases read from it).  Writes out [B][2]
 // = (mu, log sigma^2) in the target's units.  *err is set to 1 if a wait timed out.
+// 16 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its rows) and columns
+// [64 (w / 4), + 64).  Each layer's MMAs run as two column halves with their own commits, so
+// the warps of half 0 start their epilogue while half 1 is still multiplying; every warp holds
+// its BF16 results in registers until both halves are done (all of A feeds both halves).
 __global__ void __launch_bounds__(THREADS, 1)
 k_mlp_forward(const float* __restrict__ x, int B, const __nv_bfloat16* __restrict__ wpack,
               const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ params, const float* __restrict__ shift,
@@ -310,13 +315,13 @@ k_mlp_forward(const float* __restrict__ x, int B, const __nv_bfloat16* __restric
   float* sB = reinterpret_cast<float*>(sm + OFF_B);
   float* sW4 = reinterpret_cast<float*>(sm + OFF_W4);
   float* sRed = reinterpret_cast<float*>(sm + OFF_RED);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_MISC);  // [0] weights loaded, [1] MMA done
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 16);
-  int* sAbort = reinterpret_cast<int*>(sm + OFF_MISC + 20);
-  float* sB4 = reinterpret_cast<float*>(sm + OFF_MISC + 24);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_MISC);  // [0] weights, [1] MMA half 0, [2] MMA half 1
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 24);
+  int* sAbort = reinterpret_cast<int*>(sm + OFF_MISC + 28);
+  float* sB4 = reinterpret_cast<float*>(sm + OFF_MISC + 32);
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t a_base = saddr(sm + OFF_A), w_base = saddr(sm + OFF_W);
-  const uint32_t barW = saddr(&bars[0]), barM = saddr(&bars[1]);
+  const uint32_t barW = saddr(&bars[0]), barM0 = saddr(&bars[1]), barM1 = saddr(&bars[2]);
   const int ntiles = (B + TILE - 1) / TILE;
 
   // small parameters (BF16 weights as the GEMM path rounds them, FP32 biases)
@@ -332,7 +337,8 @@ k_mlp_forward(const float* __restrict__ x, int B, const __nv_bfloat16* __restric
   if (tid == 0) {
     *sAbort = 0;
     mbar_init(barW, 1);
-    mbar_init(barM, 1);
+    mbar_init(barM0, 1);
+    mbar_init(barM1, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -347,18 +353,20 @@ k_mlp_forward(const float* __restrict__ x, int B, const __nv_bfloat16* __restric
   uint32_t phW = 0, phM = 0;
   if (tid == 0 && blockIdx.x < ntiles) load_weights(w_base, wpack, barW);
 
-  const int q = warp & 3, half = warp >> 2;  // TMEM lane quarter and column half of this warp
-  const int erow = 32 * q + (tid & 31);       // epilogue row
+  const int q = warp & 3, cq = warp >> 2;    // TMEM lane quarter and column quarter of this warp
+  const int half = cq >> 1;                  // MMA column half whose commit this warp waits for
+  const int erow = 32 * q + (tid & 31);      // epilogue row
+  const uint32_t bar_mine = half ? barM1 : barM0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const bool more = tile + (int)gridDim.x < ntiles;
-    // layer 0 on the CUDA cores: row r, columns [128 h, 128 h + 128)
+    // layer 0 on the CUDA cores: row r, columns [64 h, 64 h + 64)
     {
       const int r = tid & (TILE - 1), h = tid >> 7;
       const long row = (long)tile * TILE + r;
       float xin[6];
 #pragma unroll
       for (int f = 0; f < 6; ++f) xin[f] = row < B ? round_bf16((x[row * 6 + f] - shift[f]) * scale[f]) : 0.f;
-      for (int c0 = 128 * h; c0 < 128 * h + 128; c0 += 8) {
+      for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 8) {
         uint32_t w[4];
 #pragma unroll
         for (int j = 0; j < 8; j += 2) {
@@ -384,60 +392,77 @@ k_mlp_forward(const float* __restrict__ x, int B, const __nv_bfloat16* __restric
           *sAbort = 1;
         } else {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          mma_layer(tmem, a_base, w_base);
-          mma_commit(barM);
+          mma_half(tmem, a_base, w_base);
+          mma_commit(barM0);
+          mma_half(tmem + 128, a_base, w_base + 65536);
+          mma_commit(barM1);
         }
       }
       phW ^= 1;
       __syncthreads();
       if (*sAbort) break;
-      if (!mbar_wait(barM, phM)) atomicExch(sAbort, 1);
-      phM ^= 1;
+      // warp-uniform outcome: tcgen05.ld below is a warp-wide instruction
+      bool ok = __all_sync(0xffffffffu, mbar_wait(bar_mine, phM));
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      __syncthreads();
-      if (*sAbort) break;
-      // the weight buffer is free again: bring in the next layer's (or the next tile's first)
-      if (tid == 0 && (l < 3 || more))
-        load_weights(w_base, wpack + (size_t)(l < 3 ? l : 0) * 256 * 256, barW);
       const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
       const float* bias = sB + l * 256;
+      uint32_t packed[32];
       float o0 = 0.f, o1 = 0.f;
-      for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 16) {
-        float v[16];
-        tmem_ld16(trow + c0, v);
+      if (ok) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + bias[c0 + i]);
-        if (l < 3) {
-          uint4 w0, w1;
-          w0.x = pack_bf16(v[0], v[1]);   w0.y = pack_bf16(v[2], v[3]);
-          w0.z = pack_bf16(v[4], v[5]);   w0.w = pack_bf16(v[6], v[7]);
-          w1.x = pack_bf16(v[8], v[9]);   w1.y = pack_bf16(v[10], v[11]);
-          w1.z = pack_bf16(v[12], v[13]); w1.w = pack_bf16(v[14], v[15]);
-          *reinterpret_cast<uint4*>(sm + OFF_A + op_offset(erow, c0)) = w0;
-          *reinterpret_cast<uint4*>(sm + OFF_A + op_offset(erow, c0 + 8)) = w1;
-        } else {
+        for (int cc = 0; cc < 4; ++cc) {
+          const int c0 = 64 * cq + 16 * cc;
+          float v[16];
+          tmem_ld16(trow + c0, v);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float a = round_bf16(v[i]);
-            o0 = fmaf(a, sW4[c0 + i], o0);
-            o1 = fmaf(a, sW4[256 + c0 + i], o1);
+          for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + bias[c0 + i]);
+          if (l < 3) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) packed[8 * cc + i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float a = round_bf16(v[i]);
+              o0 = fmaf(a, sW4[c0 + i], o0);
+              o1 = fmaf(a, sW4[256 + c0 + i], o1);
+            }
           }
         }
       }
+      // every MMA of the layer is done before the operand buffers are overwritten; the weight
+      // buffer is then free for the next layer's (or the next tile's first) weights
+      if (half == 0 && l < 3) ok = __all_sync(0xffffffffu, ok && mbar_wait(barM1, phM));
+      if (!ok) atomicExch(sAbort, 1);
+      phM ^= 1;
+      if (tid == 256 && ok && (l < 3 || more))
+        load_weights(w_base, wpack + (size_t)(l < 3 ? l : 0) * 256 * 256, barW);
+      if (ok && l < 3) {
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          const int c0 = 64 * cq + 8 * cc;
+          *reinterpret_cast<uint4*>(sm + OFF_A + op_offset(erow, c0)) =
+              make_uint4(packed[4 * cc], packed[4 * cc + 1], packed[4 * cc + 2], packed[4 * cc + 3]);
+        }
+      }
       if (l == 3) {
-        sRed[(half * TILE + erow) * 2] = o0;
-        sRed[(half * TILE + erow) * 2 + 1] = o1;
+        sRed[(cq * TILE + erow) * 2] = o0;
+        sRed[(cq * TILE + erow) * 2 + 1] = o1;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
+      if (*sAbort) break;
     }
     if (*sAbort) break;
     if (tid < TILE) {
       const long row = (long)tile * TILE + tid;
       if (row < B) {
-        const float z0 = sRed[tid * 2] + sRed[(TILE + tid) * 2] + sB4[0];
-        const float z1 = sRed[tid * 2 + 1] + sRed[(TILE + tid) * 2 + 1] + sB4[1];
+        float z0 = sB4[0], z1 = sB4[1];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          z0 += sRed[(c * TILE + tid) * 2];
+          z1 += sRed[(c * TILE + tid) * 2 + 1];
+        }
         out[row * 2] = z0 / ys + y0;
         out[row * 2 + 1] = z1 - 2.0f * logf(ys);
       }
