@@ -179,7 +179,7 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
 swf_status swf_set_march_path(swf_ctx* ctx, int path);
 
 /* Launch shapes of the pass kernels (rows per block of the x passes, tile width of the y and z
- * passes).  on = 1 (default): the first march of each grid shape in this context times the
+ * passes, 256 or 128 threads per block).  on = 1 (default): the first march of each grid shape in this context times the
  * candidate shapes (a few launches each, before the march starts) and keeps the fastest;
  * on = 0: a fixed rule from the grid size.  A shape only decides which lines a block
  * transforms, so results are bitwise the same either way.  Part of the batching design

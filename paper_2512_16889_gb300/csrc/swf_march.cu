@@ -724,7 +724,10 @@ template <typename R>
 static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaStream_t st) {
   const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
   constexpr int esz = (int)sizeof(cpx<R>);
-  const int rows = tune_lookup(ctx, tune_key('x', esz, nx, A.nrows, 0, F), x_rows<R>(nx, A.nrows, F));
+  // tuned values: rows (x passes) or log2 TX (y, z passes) times 4, plus 1 for 128-thread blocks
+  const int xv = tune_lookup(ctx, tune_key('x', esz, nx, A.nrows, 0, F), 4 * x_rows<R>(nx, A.nrows, F));
+  const int rows = xv >> 2;
+  const int xthr = (xv & 3) ? kThreads / 2 : kThreads;
   if (rows < 1) return SWF_EUNSUPPORTED;
   const int ld = padded_len(nx);
   const bool only_x = (ny == 1 && nz == 1);
@@ -732,7 +735,7 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
   dim3 grid_rows((A.nrows + rows - 1) / rows, F);
   {
     ProfScope ps(ctx, "k_first", st);
-    k_first<R><<<grid_rows, kThreads, smem, st>>>(A, rows, ld, only_x ? 1 : 0);
+    k_first<R><<<grid_rows, xthr, smem, st>>>(A, rows, ld, only_x ? 1 : 0);
   }
   if (only_x) return SWF_OK;
   int axes[2], na = 0;
@@ -741,12 +744,13 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
   auto mid = [&](int axis, int fwd, int h0, int inv) {
     const int other = axis == 1 ? nz : ny;
     const int lg_h = mid_shape<R>(A.g.n[axis], nx, (long)other * F).lgtx;
-    const int lg = tune_lookup(ctx, tune_key('m', esz, axis * 8 + fwd * 4 + h0 * 2 + inv, A.g.n[axis], nx, (long)other * F), lg_h);
-    const MidShape ms = mid_shape_lg<R>(A.g.n[axis], lg);
+    const int mv = tune_lookup(ctx, tune_key('m', esz, axis * 8 + fwd * 4 + h0 * 2 + inv, A.g.n[axis], nx, (long)other * F),
+                               4 * lg_h);
+    const MidShape ms = mid_shape_lg<R>(A.g.n[axis], mv >> 2);
     const int ntx = (nx + (1 << ms.lgtx) - 1) >> ms.lgtx;
     dim3 grid(ntx * other, F);
     ProfScope ps(ctx, "k_mid", st);
-    k_mid<R><<<grid, kThreads, ms.smem, st>>>(A, axis, ms.lgtx, ms.ld, fwd, h0, inv);
+    k_mid<R><<<grid, (mv & 3) ? kThreads / 2 : kThreads, ms.smem, st>>>(A, axis, ms.lgtx, ms.ld, fwd, h0, inv);
   };
   if (na == 1) {
     mid(axes[0], 1, 1, 1);
@@ -757,13 +761,13 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
   }
   {
     ProfScope ps(ctx, "k_last", st);
-    k_last<R><<<grid_rows, kThreads, smem, st>>>(A, rows, ld);
+    k_last<R><<<grid_rows, xthr, smem, st>>>(A, rows, ld);
   }
   return SWF_OK;
 }
 
-// Times the candidate launch shapes of one evaluation's pass kernels and records the fastest
-// in ctx->tune (once per shape key).  B must be harmless to run repeatedly: it may write only
+// Times the candidate launch shapes of one evaluation's pass kernels (rows per block or tile
+// width, and 256- or 128-thread blocks) and records the fastest in ctx->tune (once per shape key).  B must be harmless to run repeatedly: it may write only
 // T and its output slot, and read y and its input slots (the march calls this before its first
 // evaluation, when those hold nothing yet).  The shape decides only which lines a block
 // transforms, never the arithmetic of a line, so results do not depend on the choice.
@@ -801,17 +805,20 @@ static swf_status autotune_eval(swf_ctx* ctx, const StageArgs<R>& B, int F, cuda
     const size_t line = (size_t)2 * 4 * padded_len(nx) * esz;
     int rmax = (int)(kPassSmem / line);
     rmax = std::min(std::min(rmax, 64), B.nrows);
-    int best = x_rows<R>(nx, B.nrows, F);
+    int best = 4 * x_rows<R>(nx, B.nrows, F);
     float tbest = 3.4e38f;
     const int ld = padded_len(nx);
     for (int rows = 1; rows <= rmax && status == SWF_OK; rows *= 2) {
-      const size_t smem = (size_t)2 * 4 * rows * ld * esz;
-      const dim3 grid((B.nrows + rows - 1) / rows, F);
-      const float t = timed([&] {
-        k_first<R><<<grid, kThreads, smem, st>>>(B, rows, ld, only_x ? 1 : 0);
-        if (!only_x) k_last<R><<<grid, kThreads, smem, st>>>(B, rows, ld);
-      });
-      if (t < tbest) { tbest = t; best = rows; }
+      for (int half = 0; half < 2 && status == SWF_OK; ++half) {
+        const int thr = half ? kThreads / 2 : kThreads;
+        const size_t smem = (size_t)2 * 4 * rows * ld * esz;
+        const dim3 grid((B.nrows + rows - 1) / rows, F);
+        const float t = timed([&] {
+          k_first<R><<<grid, thr, smem, st>>>(B, rows, ld, only_x ? 1 : 0);
+          if (!only_x) k_last<R><<<grid, thr, smem, st>>>(B, rows, ld);
+        });
+        if (t < tbest) { tbest = t; best = 4 * rows + half; }
+      }
     }
     if (status == SWF_OK) ctx->tune.best[xkey] = best;
   }
@@ -829,16 +836,18 @@ static swf_status autotune_eval(swf_ctx* ctx, const StageArgs<R>& B, int F, cuda
       const int n_a = B.g.n[axis];
       const std::string key = tune_key('m', esz, axis * 8 + cb[1] * 4 + cb[2] * 2 + cb[3], n_a, nx, (long)other * F);
       if (ctx->tune.best.count(key)) continue;
-      int best = mid_shape<R>(n_a, nx, (long)other * F).lgtx;
+      int best = 4 * mid_shape<R>(n_a, nx, (long)other * F).lgtx;
       float tbest = 3.4e38f;
       for (int lg = mid_max_lg<R>(n_a, nx); lg >= 0 && status == SWF_OK; --lg) {
-        const MidShape ms = mid_shape_lg<R>(n_a, lg);
-        const int ntx = (nx + (1 << lg) - 1) >> lg;
-        const dim3 grid(ntx * other, F);
-        const float t = timed([&] {
-          k_mid<R><<<grid, kThreads, ms.smem, st>>>(B, axis, lg, ms.ld, cb[1], cb[2], cb[3]);
-        });
-        if (t < tbest) { tbest = t; best = lg; }
+        for (int half = 0; half < 2 && status == SWF_OK; ++half) {
+          const MidShape ms = mid_shape_lg<R>(n_a, lg);
+          const int ntx = (nx + (1 << lg) - 1) >> lg;
+          const dim3 grid(ntx * other, F);
+          const float t = timed([&] {
+            k_mid<R><<<grid, half ? kThreads / 2 : kThreads, ms.smem, st>>>(B, axis, lg, ms.ld, cb[1], cb[2], cb[3]);
+          });
+          if (t < tbest) { tbest = t; best = 4 * lg + half; }
+        }
       }
       if (status == SWF_OK) ctx->tune.best[key] = best;
     }
