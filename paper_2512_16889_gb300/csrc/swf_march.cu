@@ -1108,14 +1108,14 @@ __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o
 }
 
 // The three integrands of Eq. 33, dx^d sum_x U_a^+ (alpha.eps) V_b exp(-ikx), for (ss, bs, sb)
-// at the stage values.  Block (b, inst) sums the sites j = b*256 + threadIdx.x (stride
-// gridDim.x*256) of instance inst in FP64 and writes part[inst][b][3]; k_mdot_final adds the
-// parts in a fixed order (deterministic) and accumulates them with weight w (= h b_i) into
-// macc[inst][3].
+// at the stage values, integrated with weight w (= h b_i).  Block (b, inst) sums the sites
+// j = b*256 + threadIdx.x (stride gridDim.x*256) of instance inst and adds w dx^d e^{-i k0 t}
+// times its sum to its own accumulator acc[inst][b][3] (FP64; no other block touches it, so
+// the march's sum is deterministic); k_mdot_final adds the accumulators in a fixed order.
 template <typename R>
 __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const FieldDesc* fd, const cpx<R>* gcplx,
                                               const cpx<R>* kph, const double* photon, GridDesc g, double t,
-                                              cpx<double>* part) {
+                                              double w, cpx<double>* acc) {
   __shared__ cpx<double> red[8][3];
   const int inst = blockIdx.y;
   const int nt = g.n[0] + g.n[1] + g.n[2];
@@ -1124,10 +1124,16 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   const cpx<R>* tu = gcplx + (size_t)(2 * inst) * (nt + 4);
   const cpx<R>* tv = gcplx + (size_t)(2 * inst + 1) * (nt + 4);
   const cpx<R>* kp = kph + (size_t)inst * nt;
-  double su, cu, sv, cv;
-  sincos(FU.tsign * FU.e0 * t, &su, &cu);
-  sincos(FV.tsign * FV.e0 * t, &sv, &cv);
-  const cpx<R> tfu = mk<R>((R)cu, (R)su), tfv = mk<R>((R)cv, (R)sv);
+  // background time phases: FP64 (scarce on this GPU) by two threads, shared with the block
+  __shared__ cpx<R> s_tf[2];
+  if (threadIdx.x < 2) {
+    const FieldDesc& Fb = threadIdx.x == 0 ? FU : FV;
+    double sn, cs;
+    sincos(Fb.tsign * Fb.e0 * t, &sn, &cs);
+    s_tf[threadIdx.x] = mk<R>((R)cs, (R)sn);
+  }
+  __syncthreads();
+  const cpx<R> tfu = s_tf[0], tfv = s_tf[1];
   R eps[3];
   for (int a = 0; a < 3; ++a) eps[a] = (R)photon[6 * inst + 3 + a];
   const cpx<R>* U = ys + (size_t)(2 * inst) * 4 * g.N;
@@ -1178,30 +1184,29 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   if (threadIdx.x < 3) {
     cpx<double> sacc = mk<double>(0, 0);
     for (int wi = 0; wi < 8; ++wi) sacc = sacc + red[wi][threadIdx.x];
-    part[((size_t)inst * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = sacc;
+    double sk, ck;
+    const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
+                           photon[6 * inst + 2] * photon[6 * inst + 2]);
+    sincos(-k0 * t, &sk, &ck);
+    const double cell = g.dx[0] * g.dx[1] * g.dx[2];
+    cpx<double>& a = acc[((size_t)inst * gridDim.x + blockIdx.x) * 3 + threadIdx.x];
+    a = a + (w * cell) * (mk<double>(ck, sk) * sacc);
   }
 }
 
-// macc[inst][q] += w dx^d exp(-i k0 t) sum_b part[inst][b][q]: warp q of block inst adds the
-// parts b = lane, lane + 32, ... in order, then a fixed shuffle tree (deterministic).
-__global__ void __launch_bounds__(96) k_mdot_final(const cpx<double>* __restrict__ part, int nb, const double* photon,
-                                                   GridDesc g, double t, double w, cpx<double>* macc) {
+// macc[inst][q] = sum_b acc[inst][b][q]: warp q of block inst adds the accumulators
+// b = lane, lane + 32, ... in order, then a fixed shuffle tree (deterministic).
+__global__ void __launch_bounds__(96) k_mdot_final(const cpx<double>* __restrict__ acc, int nb, cpx<double>* macc) {
   const int inst = blockIdx.x;
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   cpx<double> sacc = mk<double>(0, 0);
-  for (int b = lane; b < nb; b += 32) sacc = sacc + part[((size_t)inst * nb + b) * 3 + q];
+  for (int b = lane; b < nb; b += 32) sacc = sacc + acc[((size_t)inst * nb + b) * 3 + q];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     sacc.x += __shfl_down_sync(0xffffffffu, sacc.x, off);
     sacc.y += __shfl_down_sync(0xffffffffu, sacc.y, off);
   }
-  if (lane != 0) return;
-  double sk, ck;
-  const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
-                         photon[6 * inst + 2] * photon[6 * inst + 2]);
-  sincos(-k0 * t, &sk, &ck);
-  const double cell = g.dx[0] * g.dx[1] * g.dx[2];
-  macc[3 * inst + q] = macc[3 * inst + q] + (w * cell) * (mk<double>(ck, sk) * sacc);
+  if (lane == 0) macc[3 * inst + q] = sacc;
 }
 
 template <typename R>
@@ -1239,7 +1244,8 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
     k_photon_tables<R><<<(n_inst * nt + 127) / 128, 128, 0, st>>>((const double*)pph, g, n_inst, (cpx<R>*)pkph);
   }
   if ((e = cudaMemsetAsync(py, 0, state, st)) != cudaSuccess) return cuda_status(e, "memset state");
-  if ((e = cudaMemsetAsync(macc, 0, sizeof(double2) * 3 * n_inst, st)) != cudaSuccess) return cuda_status(e, "memset M");
+  if ((e = cudaMemsetAsync(ppart, 0, sizeof(cpx<double>) * 3 * (size_t)nb * n_inst, st)) != cudaSuccess)
+    return cuda_status(e, "memset M accumulators");
   A.y = (cpx<R>*)py;
   A.T = (cpx<R>*)pT;
   {
@@ -1285,15 +1291,14 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
       if (wgt != 0.0) {
         ProfScope ps(ctx, "k_mdot", st);
         k_mdot<R><<<dim3(nb, n_inst), 256, 0, st>>>((const cpx<R>*)pys, A.fd, A.gcplx, (const cpx<R>*)pkph,
-                                                    (const double*)pph, g, A.t, (cpx<double>*)ppart);
-      }
-      if (wgt != 0.0) {
-        ProfScope ps(ctx, "k_mdot_final", st);
-        k_mdot_final<<<n_inst, 96, 0, st>>>((const cpx<double>*)ppart, nb, (const double*)pph, g, A.t, wgt,
-                                            (cpx<double>*)macc);
+                                                    (const double*)pph, g, A.t, wgt, (cpx<double>*)ppart);
       }
     }
     std::swap(slot[0], slot[6]);
+  }
+  {
+    ProfScope ps(ctx, "k_mdot_final", st);
+    k_mdot_final<<<n_inst, 96, 0, st>>>((const cpx<double>*)ppart, nb, (cpx<double>*)macc);
   }
   e = cudaMemcpyAsync(psi_out, py, state, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "copy psi(t_in)");
