@@ -1097,6 +1097,34 @@ __global__ void k_photon_tables(const double* photon, GridDesc g, int n_inst, cp
   }
 }
 
+// Per instance, step and stage (Dormand-Prince nodes c_i): the background time phases of U and V
+// at t = t_out + (step + c_i) h and the quadrature factor w_i dx^d e^{-i k0 t} of the M-dot
+// integral, with w_i = h b_{i+1} for i = 2..5 and h b_1 (of the next step) for the last stage,
+// 0 elsewhere.  FP64, computed once per march so that the integrand kernel needs none.
+__global__ void k_bw_phase_table(const FieldDesc* fd, const double* photon, int n_inst, int n_steps, double t_out,
+                                 double h, double cell, cpx<double>* tab) {
+  const double DPc[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
+  const double DPb[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
+  const long total = (long)n_inst * n_steps * 7;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int inst = (int)(e / (7L * n_steps));
+    const int step = (int)((e / 7) % n_steps), i = (int)(e % 7);
+    const double t = t_out + (step + DPc[i]) * h;
+    const double w = (i >= 2 && i <= 5) ? h * DPb[i] : (i == 6 && step + 1 < n_steps ? h * DPb[0] : 0.0);
+    double sn, cs;
+    const FieldDesc& FU = fd[2 * inst];
+    const FieldDesc& FV = fd[2 * inst + 1];
+    sincos(FU.tsign * FU.e0 * t, &sn, &cs);
+    tab[3 * e] = mk<double>(cs, sn);
+    sincos(FV.tsign * FV.e0 * t, &sn, &cs);
+    tab[3 * e + 1] = mk<double>(cs, sn);
+    const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
+                           photon[6 * inst + 2] * photon[6 * inst + 2]);
+    sincos(-k0 * t, &sn, &cs);
+    tab[3 * e + 2] = mk<double>(w * cell * cs, w * cell * sn);
+  }
+}
+
 // (alpha . eps) v for a real polarisation eps (Dirac representation).
 template <typename R>
 __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o) {
@@ -1110,36 +1138,28 @@ __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o
 // The three integrands of Eq. 33, dx^d sum_x U_a^+ (alpha.eps) V_b exp(-ikx), for (ss, bs, sb)
 // at the stage values, integrated with weight w (= h b_i).  Block (b, inst) sums the sites
 // j = b*256 + threadIdx.x (stride gridDim.x*256) of instance inst and adds w dx^d e^{-i k0 t}
-// times its sum to its own accumulator acc[inst][b][3] (FP64; no other block touches it, so
+// (from the phase table) times its sum to its own accumulator acc[inst][b][3] (FP64; no other block touches it, so
 // the march's sum is deterministic); k_mdot_final adds the accumulators in a fixed order.
 template <typename R>
-__global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const FieldDesc* fd, const cpx<R>* gcplx,
-                                              const cpx<R>* kph, const double* photon, GridDesc g, double t,
-                                              double w, cpx<double>* acc) {
+__global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const cpx<R>* gcplx, const cpx<R>* kph,
+                                              const double* photon, GridDesc g, const cpx<double>* __restrict__ ptab,
+                                              long tab_row, int tab_stride, cpx<double>* acc) {
   __shared__ cpx<double> red[8][3];
   const int inst = blockIdx.y;
   const int nt = g.n[0] + g.n[1] + g.n[2];
-  const FieldDesc& FU = fd[2 * inst];
-  const FieldDesc& FV = fd[2 * inst + 1];
   const cpx<R>* tu = gcplx + (size_t)(2 * inst) * (nt + 4);
   const cpx<R>* tv = gcplx + (size_t)(2 * inst + 1) * (nt + 4);
   const cpx<R>* kp = kph + (size_t)inst * nt;
-  // background time phases: FP64 (scarce on this GPU) by two threads, shared with the block
-  __shared__ cpx<R> s_tf[2];
-  if (threadIdx.x < 2) {
-    const FieldDesc& Fb = threadIdx.x == 0 ? FU : FV;
-    double sn, cs;
-    sincos(Fb.tsign * Fb.e0 * t, &sn, &cs);
-    s_tf[threadIdx.x] = mk<R>((R)cs, (R)sn);
-  }
-  __syncthreads();
-  const cpx<R> tfu = s_tf[0], tfv = s_tf[1];
+  // this instance's row of the phase table: U and V time phases, quadrature factor
+  const cpx<double>* trow = ptab + 3 * (tab_row + (long)inst * tab_stride);
+  const cpx<R> tfu = cvt<R>(trow[0]), tfv = cvt<R>(trow[1]);
   R eps[3];
   for (int a = 0; a < 3; ++a) eps[a] = (R)photon[6 * inst + 3 + a];
   const cpx<R>* U = ys + (size_t)(2 * inst) * 4 * g.N;
   const cpx<R>* V = ys + (size_t)(2 * inst + 1) * 4 * g.N;
   // per-thread sums in the march precision (a few sites each), then FP64 across threads
   cpx<R> tss = mk<R>(0, 0), tbs = mk<R>(0, 0), tsb = mk<R>(0, 0);
+#pragma unroll 2
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.N; j += gridDim.x * blockDim.x) {
     const int ix = j % g.n[0];
     const int iy = (j / g.n[0]) % g.n[1];
@@ -1184,13 +1204,8 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   if (threadIdx.x < 3) {
     cpx<double> sacc = mk<double>(0, 0);
     for (int wi = 0; wi < 8; ++wi) sacc = sacc + red[wi][threadIdx.x];
-    double sk, ck;
-    const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
-                           photon[6 * inst + 2] * photon[6 * inst + 2]);
-    sincos(-k0 * t, &sk, &ck);
-    const double cell = g.dx[0] * g.dx[1] * g.dx[2];
     cpx<double>& a = acc[((size_t)inst * gridDim.x + blockIdx.x) * 3 + threadIdx.x];
-    a = a + (w * cell) * (mk<double>(ck, sk) * sacc);
+    a = a + trow[2] * sacc;
   }
 }
 
@@ -1232,9 +1247,10 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   if ((s = ws_get(ctx, "bw.kph", sizeof(cpx<R>) * n_inst * nt, &pkph)) != SWF_OK) return s;
   // blocks per instance of the M-dot reduction: about four waves of the GPU in total, at least
   // 1024 sites per block
-  int nsm = 152;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-  const int nb = std::max(1, std::min((g.N + 1023) / 1024, (4 * nsm + n_inst - 1) / n_inst));
+  const int nb = std::max(1, std::min((g.N + 1023) / 1024, (4 * sm_count() + n_inst - 1) / n_inst));
+  void* ptab;
+  if ((s = ws_get(ctx, "bw.phase_table", sizeof(cpx<double>) * 3 * 7 * (size_t)n_steps * n_inst, &ptab)) != SWF_OK)
+    return s;
   void* ppart;
   if ((s = ws_get(ctx, "bw.mpart", sizeof(cpx<double>) * 3 * (size_t)nb * n_inst, &ppart)) != SWF_OK) return s;
   cudaError_t e = cudaMemcpyAsync(pph, photon_host, sizeof(double) * 6 * n_inst, cudaMemcpyHostToDevice, st);
@@ -1242,6 +1258,13 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   {
     ProfScope ps(ctx, "k_photon_tables", st);
     k_photon_tables<R><<<(n_inst * nt + 127) / 128, 128, 0, st>>>((const double*)pph, g, n_inst, (cpx<R>*)pkph);
+  }
+  {
+    const long total = (long)n_inst * n_steps * 7;
+    ProfScope ps(ctx, "k_bw_phase_table", st);
+    k_bw_phase_table<<<(int)std::min((total + 127) / 128, 4096L), 128, 0, st>>>(
+        A.fd, (const double*)pph, n_inst, n_steps, t_out, (t_in - t_out) / n_steps, g.dx[0] * g.dx[1] * g.dx[2],
+        (cpx<double>*)ptab);
   }
   if ((e = cudaMemsetAsync(py, 0, state, st)) != cudaSuccess) return cuda_status(e, "memset state");
   if ((e = cudaMemsetAsync(ppart, 0, sizeof(cpx<double>) * 3 * (size_t)nb * n_inst, st)) != cudaSuccess)
@@ -1290,8 +1313,9 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
       if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
       if (wgt != 0.0) {
         ProfScope ps(ctx, "k_mdot", st);
-        k_mdot<R><<<dim3(nb, n_inst), 256, 0, st>>>((const cpx<R>*)pys, A.fd, A.gcplx, (const cpx<R>*)pkph,
-                                                    (const double*)pph, g, A.t, wgt, (cpx<double>*)ppart);
+        k_mdot<R><<<dim3(nb, n_inst), 256, 0, st>>>((const cpx<R>*)pys, A.gcplx, (const cpx<R>*)pkph,
+                                                    (const double*)pph, g, (const cpx<double>*)ptab,
+                                                    (long)n * 7 + i, 7 * n_steps, (cpx<double>*)ppart);
       }
     }
     std::swap(slot[0], slot[6]);
