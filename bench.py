@@ -357,6 +357,47 @@ def run_surrogate(args):
     return 0
 
 
+def run_pair_scan(args):
+    """Times the all-pairs full pair number on one GPU: 128 electrons x 128 positrons of one
+    field on the 256^2 grid (1000 steps, complex64 march, FP64 overlaps) through swf_pair_matrix:
+    256 marches plus the overlap products, against 2 x 128 x 128 marches pair by pair."""
+    import torch
+    from paper_2512_16889_gb300 import build, swf
+    from paper_2512_16889_gb300 import workloads as W
+    build.build()
+    els, pos = W.pair_scan()
+    if args.limit:
+        els, pos = els[:args.limit], pos[:args.limit]
+    E = [swf.from_workload(d) for d in els]
+    P = [swf.from_workload(d) for d in pos]
+    ctx = swf.Context(0)
+    ctx.pair_matrix(E[:2], P[:2], swf.C64)  # warm-up
+    times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.pair_matrix(E, P, swf.C64)
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    ctx.profile_read()
+    ctx.profile_enable(True)
+    ctx.pair_matrix(E, P, swf.C64)
+    ctx.profile_enable(False)
+    prof, _ = ctx.profile_read()
+    n_pairs = len(E) * len(P)
+    su = (len(E) + len(P)) * 256 * 256 * els[0]["n_steps"]
+    line = {"metric": "full pair numbers N(m, n)/s", "value": n_pairs / t, "unit": "pairs/s", "n_gpus": 1,
+            "steps": len(times), "warmup": 1, "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "pair_scan: 256^2, box 40, 1000 steps, E = 0.3",
+                                             "electrons": len(E), "positrons": len(P),
+                                             "precision": "complex64 march, FP64 overlaps"},
+            "site_updates_per_s": su / t, "marches": len(E) + len(P),
+            "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_workload(args):
     """Times another workload of the benchmark family on one GPU (not the headline line):
     schwinger_fp64_single (128^2, complex128, full pair number), schwinger_batched_fp64 (the
@@ -451,6 +492,8 @@ def main():
         return run_small_march(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "pair_scan":
+        return run_pair_scan(args)
     if args.workload:
         return run_workload(args)
     if args.impl == "reference":

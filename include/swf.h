@@ -139,6 +139,19 @@ swf_status solve_swf_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf
                          swf_precision prec, swf_result* results_dev, double* spectrum_dev,
                          void* stream);
 
+/* Full Schwinger pair numbers N(m, n) (Eq. 8, both lines; Eq. 9 inner product) for every
+ * electron m = (s, p) of `electrons` and every positron n = (r, q) of `positrons`, as a scan over
+ * momenta (Sec. II.A).  All instances must share field, grid and time window (EINVAL
+ * otherwise); along trivial axes (n = 1) every p must be equal and every q = -p.  Only p, s of
+ * the electrons and q, r of the positrons are read.  Marches each electron's U wave and each
+ * positron's V wave once (n_e + n_p marches rather than 2 n_e n_p) and forms C, A, B and D as
+ * complex FP64 matrix products over the grid (components x sites).
+ * results: host array of n_e * n_p swf_result, row-major [m][n], with the layout of a
+ * SWF_WANT_FULL_N instance: amp = {C, D, A, B}, prob = {|C + D|^2, |A + B|^2},
+ * diag = {||psi_U,m||^2, ||psi_V,n||^2}.  Synchronous; uses the context's stream and workspace. */
+swf_status swf_pair_matrix(swf_ctx* ctx, int n_e, const swf_instance* electrons, int n_p,
+                           const swf_instance* positrons, swf_precision prec, swf_result* results);
+
 /* Lower-level: march n_inst instances' electron (bg = 0, background u_s(p) e^{-ipx}) or
  * positron (bg = 1, background v_r(q) e^{+iqx}) scattered wave from psi_s(t_out) = 0 to t_in
  * (Eqs. 6-7) and write psi_s(t_in) to psi_out_dev: per instance 4*nx*ny*nz complex values in

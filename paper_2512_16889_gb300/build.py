@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswf.so")
-SOURCES = ["swf_api.cu", "swf_march.cu", "swf_project.cu", "swf_fused.cu", "swf_noalloc.cu", "swf_bw.cu", "swf_mlp.cu"]
+SOURCES = ["swf_api.cu", "swf_march.cu", "swf_project.cu", "swf_fused.cu", "swf_noalloc.cu", "swf_bw.cu", "swf_mlp.cu",
+           "swf_pairs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -44,7 +44,7 @@ class Result(C.Structure):
     _fields_ = [("amp", C.c_double * 8), ("prob", C.c_double * 2), ("diag", C.c_double * 2)]
 
 
-EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_march_dev",
+EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_pair_matrix", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_last_error.restype = C.c_char_p
     lib.solve_swf.argtypes = [vp, ip, inst_p, ip, ip, res_p, dbl_p]
     lib.solve_swf_dev.argtypes = [vp, ip, inst_p, ip, ip, vp, vp, vp]
+    lib.swf_pair_matrix.argtypes = [vp, ip, inst_p, ip, inst_p, ip, res_p]
     lib.swf_march_dev.argtypes = [vp, ip, inst_p, ip, ip, vp, vp]
     lib.swf_rhs_dev.argtypes = [vp, inst_p, ip, ip, dp, vp, vp, vp]
     lib.swf_spectrum_dev.argtypes = [vp, ip, inst_p, ip, vp, vp, vp, vp]
@@ -200,6 +201,15 @@ class Context:
         _check(_lib.solve_swf(self._h, len(instances), arr, process, prec, res,
                               spec.ctypes.data_as(C.POINTER(C.c_double))))
         return res, spec[:nspec]
+
+    def pair_matrix(self, electrons, positrons, prec=C64):
+        """swf_pair_matrix: full N for every (electron, positron) pair; returns an n_e x n_p list
+        of lists of Result."""
+        ea, pa = instance_array(electrons), instance_array(positrons)
+        res = (Result * (len(electrons) * len(positrons)))()
+        _check(_lib.swf_pair_matrix(self._h, len(electrons), ea, len(positrons), pa, prec, res))
+        n_p = len(positrons)
+        return [[res[m * n_p + n] for n in range(n_p)] for m in range(len(electrons))]
 
     # -- device buffers (torch tensors), asynchronous on `stream`
     def solve_dev(self, instances, results_dev, spectrum_dev=None, process=SCHWINGER, prec=C64, stream=None,

@@ -61,6 +61,21 @@ def schwinger_batched(n=256, L=40.0, n_steps=1000, t_window=20.0, n_p=8, omega=0
     return out
 
 
+def pair_scan(n=256, L=40.0, n_steps=1000, t_window=20.0, n_p=8, E=0.3, omega=0.5, lam=5.0):
+    """A momentum scan in one field (the batched workload's grid and window at E = 0.3):
+    electrons (s, p) over an n_p x n_p momentum lattice in [-1, 1]^2 and both spins, and the
+    positrons (r, q = -p) of the same lattice, for the all-pairs full pair number."""
+    ps = np.linspace(-1.0, 1.0, n_p)
+    base = (("sauter_gauss", (E, omega, lam)), (n, n, 1), (L, L, 1.0), -t_window, t_window, n_steps)
+    els, pos = [], []
+    for px in ps:
+        for py in ps:
+            for s in (1, -1):
+                els.append(_inst(*base, p=(px, py, 0.0), s=s, q=(0.0, 0.0, 0.0), r=1))
+                pos.append(_inst(*base, p=(0.0, 0.0, 0.0), s=1, q=(-px, -py, 0.0), r=s))
+    return els, pos
+
+
 def bw_uneven(count=128, sizes=(192, 256, 320, 384), seed=7, h=0.05, a0=1.0, omega0=0.5, tau=10.0, w=8.0):
     L = 16.0 * math.pi
     ns = np.random.default_rng(seed).choice(list(sizes), count)

@@ -306,3 +306,57 @@ def test_tuned_launch_shapes_give_bitwise_identical_marches(env):
                 outs.append(out.cpu().numpy())
                 ctx.close()
             assert np.array_equal(outs[0], outs[1]), (d["n"], prec)
+
+
+def _pair_scan(n=(24, 20, 1), L=(12.0, 10.0, 1.0)):
+    """Three electrons and two positrons in one field: off-grid momenta and both spins."""
+    base = dict(field=("sauter_gauss", (0.8, 0.6, 2.5)), n=n, L=L, t_in=-5.0, t_out=5.0, n_steps=60,
+                k=(0, 0, 0), eps=(0, 0, 0), flags=())
+    els = [dict(base, p=p, s=s, q=(0.0, 0.0, 0.0), r=1) for p, s in
+           (((0.3, -0.2, 0.0), 1), ((-0.45, 0.1, 0.0), -1), ((0.05, 0.35, 0.0), 1))]
+    pos = [dict(base, p=(0.0, 0.0, 0.0), s=1, q=q, r=r) for q, r in (((-0.25, 0.15, 0.0), -1), ((0.4, -0.3, 0.0), 1))]
+    return els, pos
+
+
+def test_pair_matrix_matches_oracle_and_pair_path(env):
+    """swf_pair_matrix (n_e + n_p marches, overlaps as FP64 matrix products) against the oracle's
+    Eq. 8 per pair (complex128), and against the one-pair-per-instance path (both precisions)."""
+    torch, swf, ctx = env
+    els, pos = _pair_scan()
+    grid = OA.grid(els[0])
+    mat = ctx.pair_matrix([swf.from_workload(d) for d in els], [swf.from_workload(d) for d in pos], swf.C128)
+    for m, de in enumerate(els):
+        bu = OA.background(de, 0)
+        pu = O.march_scattered(OA.field(de), grid, bu, de["t_in"], de["t_out"], de["n_steps"])
+        for n, dp in enumerate(pos):
+            pair = dict(de, q=dp["q"], r=dp["r"])
+            bv = OA.background(pair, 1)
+            pv = O.march_scattered(OA.field(pair), grid, bv, de["t_in"], de["t_out"], de["n_steps"])
+            ref = O.pair_number(pu, pv, grid, de["t_in"], de["p"], de["s"], dp["q"], dp["r"], bu.offset(), bv.offset())
+            r = mat[m][n]
+            for j, key in enumerate(("C", "D", "A", "B")):
+                got = complex(r.amp[2 * j], r.amp[2 * j + 1])
+                assert abs(got - ref[key]) <= 1e-9 * max(abs(ref[key]), 1e-300), (m, n, key, got, ref[key])
+            assert abs(r.prob[0] - ref["N_line2"]) <= 1e-9 * ref["N_line2"]
+            assert abs(r.prob[1] - ref["N_line1"]) <= 1e-9 * ref["N_line1"]
+    # the same pairs through solve_swf with SWF_WANT_FULL_N: same marches, other summation order
+    for prec, tol in ((swf.C128, 1e-11), (swf.C64, 1e-6)):
+        mat = ctx.pair_matrix([swf.from_workload(d) for d in els], [swf.from_workload(d) for d in pos], prec)
+        pairs = [dict(de, q=dp["q"], r=dp["r"], flags=("full_n",)) for de in els for dp in pos]
+        res, _ = ctx.solve([swf.from_workload(d) for d in pairs], swf.SCHWINGER, prec)
+        for i, d in enumerate(pairs):
+            r, ref = mat[i // len(pos)][i % len(pos)], res[i]
+            for k in range(8):
+                assert abs(r.amp[k] - ref.amp[k]) <= tol * max(abs(x) for x in ref.amp), (prec, i, k)
+            assert abs(r.diag[0] - ref.diag[0]) <= tol * ref.diag[0]
+            assert abs(r.diag[1] - ref.diag[1]) <= tol * ref.diag[1]
+
+
+def test_pair_matrix_validation(env):
+    torch, swf, ctx = env
+    els, pos = _pair_scan()
+    bad = [dict(pos[0], field=("sauter_gauss", (0.7, 0.6, 2.5)))]
+    with pytest.raises(swf.SwfError, match="share the field"):
+        ctx.pair_matrix([swf.from_workload(d) for d in els], [swf.from_workload(d) for d in bad], swf.C128)
+    with pytest.raises(swf.SwfError):
+        ctx.pair_matrix([], [swf.from_workload(d) for d in pos], swf.C128)
