@@ -203,6 +203,9 @@ def run_gpu(args):
     site_updates = sum(int(np.prod(d["n"])) * d["n_steps"] for d in ds)
     probs = sum(2 * int(np.prod(d["n"])) for d in ds)
     ctx = swf.Context(local)
+    # every instance is marched (the workload's stated work): the library's exact reuse of the
+    # other spin's march, which would skip the instances whose two spins share a field, is off
+    ctx.set_dedupe(False)
     stream = torch.cuda.current_stream()
     res_dev = torch.empty(n_inst * swf.C.sizeof(swf.Result), dtype=torch.uint8, device="cuda")
     spec_dev = torch.empty(probs, dtype=torch.float64, device="cuda")
@@ -373,11 +376,13 @@ def run_pair_scan(args):
     ctx = swf.Context(0)
     ctx.pair_matrix(E[:2], P[:2], swf.C64)  # warm-up
     times = []
+    m0 = ctx.fields_marched()
     for _ in range(max(1, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.pair_matrix(E, P, swf.C64)
         times.append(time.perf_counter() - t0)
+    marched = (ctx.fields_marched() - m0) // len(times)
     t = min(times)
     ctx.profile_read()
     ctx.profile_enable(True)
@@ -385,13 +390,13 @@ def run_pair_scan(args):
     ctx.profile_enable(False)
     prof, _ = ctx.profile_read()
     n_pairs = len(E) * len(P)
-    su = (len(E) + len(P)) * 256 * 256 * els[0]["n_steps"]
+    su = marched * 256 * 256 * els[0]["n_steps"]  # site-updates actually marched
     line = {"metric": "full pair numbers N(m, n)/s", "value": n_pairs / t, "unit": "pairs/s", "n_gpus": 1,
             "steps": len(times), "warmup": 1, "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"workload": "pair_scan: 256^2, box 40, 1000 steps, E = 0.3",
                                              "electrons": len(E), "positrons": len(P),
                                              "precision": "complex64 march, FP64 overlaps"},
-            "site_updates_per_s": su / t, "marches": len(E) + len(P),
+            "site_updates_per_s": su / t, "fields": len(E) + len(P), "fields_marched": marched,
             "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     ctx.close()

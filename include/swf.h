@@ -191,6 +191,16 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
  * apply). */
 swf_status swf_set_march_path(swf_ctx* ctx, int path);
 
+/* Repeated marches.  on = 1 (default): within one call, a field whose march repeats another's
+ * is marched once: the same field, window and background wave, or (with the z axis trivial,
+ * p_z = 0 and A_3 = 0, where the spin along z is conserved) the other spin s = -1 vs +1 (or r),
+ * whose scattered wave is exactly the first with components 1 and 2 negated (R_- = diag(1, -1,
+ * -1, 1) R_+ and every operator of Eq. 6 keeps {0, 3} and {1, 2} apart; App. A.5 Eq. A44).
+ * on = 0 marches every field.  Results agree either way (up to the sign of zeros). */
+swf_status swf_set_dedupe(swf_ctx* ctx, int on);
+/* Fields (U or V waves) actually marched by this context since its creation. */
+swf_status swf_fields_marched(swf_ctx* ctx, long long* count);
+
 /* Launch shapes of the pass kernels (rows per block of the x passes, tile width of the y and z
  * passes, 256 or 128 threads per block).  on = 1 (default): the first march of each grid shape in this context times the
  * candidate shapes (a few launches each, before the march starts) and keeps the fastest;

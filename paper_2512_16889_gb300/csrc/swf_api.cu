@@ -621,6 +621,18 @@ swf_status swf_set_march_path(swf_ctx* ctx, int path) {
   return SWF_OK;
 }
 
+swf_status swf_set_dedupe(swf_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) { set_error("swf_set_dedupe: ctx NULL or on not 0 or 1"); return SWF_EINVAL; }
+  ctx->dedupe = on != 0;
+  return SWF_OK;
+}
+
+swf_status swf_fields_marched(swf_ctx* ctx, long long* count) {
+  if (!ctx || !count) { set_error("swf_fields_marched: NULL argument"); return SWF_EINVAL; }
+  *count = ctx->fields_marched;
+  return SWF_OK;
+}
+
 swf_status swf_set_autotune(swf_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) { set_error("swf_set_autotune: ctx NULL or on not 0 or 1"); return SWF_EINVAL; }
   ctx->tune.on = on != 0;

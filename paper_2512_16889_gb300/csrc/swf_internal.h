@@ -114,6 +114,8 @@ struct swf_ctx {
   swf::Profiler prof;
   swf::TuneCache tune;
   bool use_fused = true;  // route eligible marches to the fused cluster kernel
+  bool dedupe = true;     // march fields that repeat another (the other spin) once
+  long long fields_marched = 0;  // fields actually marched since the last profile read
   int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
 };
 

@@ -958,9 +958,69 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
   return SWF_OK;
 }
 
-swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
-                        int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
-                        cudaStream_t st) {
+// psi_out[f] = psi_u[rep[f]] with the components {1, 2} times sgn[f] (+1 or -1).
+template <typename R>
+__global__ void k_expand_fields(const cpx<R>* __restrict__ psi_u, const int* __restrict__ rep,
+                                const int* __restrict__ sgn, size_t N, cpx<R>* __restrict__ psi_out) {
+  const int f = blockIdx.y;
+  const int c = blockIdx.z;
+  const R s = (c == 1 || c == 2) ? (R)sgn[f] : (R)1;
+  const cpx<R>* src = psi_u + ((size_t)rep[f] * 4 + c) * N;
+  cpx<R>* dst = psi_out + ((size_t)f * 4 + c) * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = s * src[i];
+}
+
+static bool same_desc_but_spinor(const FieldDesc& a, const FieldDesc& b) {
+  if (a.kind != b.kind || a.acomp != b.acomp || a.e0 != b.e0 || a.tsign != b.tsign) return false;
+  for (int k = 0; k < 8; ++k)
+    if (a.prm[k] != b.prm[k]) return false;
+  for (int k = 0; k < 3; ++k)
+    if (a.K[k] != b.K[k] || a.pmom[k] != b.pmom[k]) return false;
+  return true;
+}
+
+// Fields whose march repeats another's: the same field, background momentum and energy, and a
+// background spinor that is the same or (when the spin along z is conserved) the same with the
+// components {1, 2} negated.  The second case is the other spin: R_- = diag(1, -1, -1, 1) R_+,
+// and (1 +- p-slash), alpha^x, alpha^y, beta and A_0 never mix {0, 3} with {1, 2} when p_z = 0,
+// the z axis is trivial and A_3 = 0, so the scattered wave of the other spin is the same wave
+// with {1, 2} negated, exactly.  rep[f] indexes the unique list; sgn[f] is the sign of {1, 2}.
+static int dedupe_fields(const GridDesc& g, int n_f, const FieldDesc* fd, std::vector<int>& rep,
+                         std::vector<int>& sgn, std::vector<FieldDesc>& uniq) {
+  rep.assign(n_f, 0);
+  sgn.assign(n_f, 1);
+  uniq.clear();
+  std::vector<int> first;  // field index of each unique entry
+  for (int f = 0; f < n_f; ++f) {
+    const FieldDesc& a = fd[f];
+    const bool zsym = g.n[2] == 1 && a.K[2] == 0.0 && a.acomp != 3;
+    int found = -1, sign = 1;
+    for (size_t u = 0; u < uniq.size() && found < 0; ++u) {
+      const FieldDesc& b = uniq[u];
+      if (!same_desc_but_spinor(a, b)) continue;
+      bool eq = true, flip = zsym;
+      for (int k = 0; k < 8; ++k) {
+        const bool in_b = (k >> 1) == 1 || (k >> 1) == 2;  // components 1 and 2
+        if (a.w[k] != b.w[k]) eq = false;
+        if (a.w[k] != (in_b ? -b.w[k] : b.w[k])) flip = false;
+      }
+      if (eq) { found = (int)u; sign = 1; }
+      else if (flip) { found = (int)u; sign = -1; }
+    }
+    if (found < 0) {
+      found = (int)uniq.size();
+      uniq.push_back(a);
+      first.push_back(f);
+    }
+    rep[f] = found;
+    sgn[f] = sign;
+  }
+  return (int)uniq.size();
+}
+
+static swf_status march_unique(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
+                               const FieldDesc* fd_host, swf_precision prec, void* psi_out, cudaStream_t st) {
   if (ctx->use_fused && fused_applicable(g, n_f, fd_host, prec)) {
     swf_status s = march_fused(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
     if (s != SWF_EUNSUPPORTED) return s;
@@ -968,6 +1028,40 @@ swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_o
   }
   if (prec == SWF_C64) return march_impl<float>(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
   return march_impl<double>(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
+}
+
+swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
+                        int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
+                        cudaStream_t st) {
+  std::vector<int> rep, sgn;
+  std::vector<FieldDesc> uniq;
+  const int n_u = ctx->dedupe ? dedupe_fields(g, n_f, fd_host, rep, sgn, uniq) : n_f;
+  ctx->fields_marched += n_u;
+  if (n_u == n_f) return march_unique(ctx, g, t_in, t_out, n_steps, n_f, fd_host, prec, psi_out, st);
+  const size_t elem = prec == SWF_C64 ? 8 : 16;
+  void *pu = nullptr, *ptab = nullptr;
+  swf_status s = ws_get(ctx, "march.unique", (size_t)n_u * 4 * g.N * elem, &pu);
+  if (s != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.unique_map", sizeof(int) * 2 * (size_t)n_f, &ptab)) != SWF_OK) return s;
+  if ((s = march_unique(ctx, g, t_in, t_out, n_steps, n_u, uniq.data(), prec, pu, st)) != SWF_OK) return s;
+  std::vector<int> tab(rep);
+  tab.insert(tab.end(), sgn.begin(), sgn.end());
+  cudaError_t e = cudaMemcpyAsync(ptab, tab.data(), sizeof(int) * 2 * (size_t)n_f, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload field map");
+  const dim3 grid((unsigned)std::min<size_t>((g.N + 255) / 256, 1024), n_f, 4);
+  ProfScope ps(ctx, "k_expand_fields", st);
+  if (prec == SWF_C64)
+    k_expand_fields<float><<<grid, 256, 0, st>>>((const cpx<float>*)pu, (const int*)ptab, (const int*)ptab + n_f,
+                                                 (size_t)g.N, (cpx<float>*)psi_out);
+  else
+    k_expand_fields<double><<<grid, 256, 0, st>>>((const cpx<double>*)pu, (const int*)ptab, (const int*)ptab + n_f,
+                                                  (size_t)g.N, (cpx<double>*)psi_out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "expand fields");
+  // the host table must outlive its asynchronous upload
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "expand fields");
+  return SWF_OK;
 }
 
 template <typename R>

@@ -46,7 +46,8 @@ class Result(C.Structure):
 
 EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_pair_matrix", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
-           "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
+           "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_set_dedupe", "swf_fields_marched",
+           "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
            "swf_mlp_get_params"]
 
@@ -83,6 +84,8 @@ def load_library(path: str = LIB_PATH):
     lib.swf_profile_enable.argtypes = [vp, ip]
     lib.swf_set_march_path.argtypes = [vp, ip]
     lib.swf_set_autotune.argtypes = [vp, ip]
+    lib.swf_set_dedupe.argtypes = [vp, ip]
+    lib.swf_fields_marched.argtypes = [vp, C.POINTER(C.c_longlong)]
     lib.swf_rhs_noalloc.argtypes = [inst_p, ip, ip, dp, vp, vp, vp]
     fp = C.POINTER(C.c_float)
     lib.swf_mlp_param_count.argtypes = []
@@ -169,6 +172,15 @@ class Context:
     def set_march_path(self, path: int):
         """0 = automatic (fused cluster kernel where it applies), 1 = pass kernels only."""
         _check(_lib.swf_set_march_path(self._h, int(path)))
+
+    def set_dedupe(self, on: bool):
+        """March repeated fields (the other spin of a z-spin-conserving field) once (True, default)."""
+        _check(_lib.swf_set_dedupe(self._h, 1 if on else 0))
+
+    def fields_marched(self):
+        n = C.c_longlong()
+        _check(_lib.swf_fields_marched(self._h, C.byref(n)))
+        return n.value
 
     def set_autotune(self, on: bool):
         """Pass-kernel launch shapes by timing (True, default) or by the fixed rule (False)."""

@@ -360,3 +360,32 @@ def test_pair_matrix_validation(env):
         ctx.pair_matrix([swf.from_workload(d) for d in els], [swf.from_workload(d) for d in bad], swf.C128)
     with pytest.raises(swf.SwfError):
         ctx.pair_matrix([], [swf.from_workload(d) for d in pos], swf.C128)
+
+
+@pytest.mark.parametrize("n", [(24, 20, 1), (256, 256, 1)])
+def test_spin_pairs_are_marched_once_with_identical_results(env, n):
+    """Within one call the other spin's march (components {1, 2} negated source) and exact
+    repeats are taken from one march; the states agree with marching every field (pass kernels
+    at 24 x 20, the fused cluster kernel at 256 x 256)."""
+    torch, swf, _ = env
+    L = (12.0, 10.0, 1.0) if n[0] == 24 else (40.0, 40.0, 1.0)
+    base = dict(field=("sauter_gauss", (0.8, 0.6, 2.5)), n=n, L=L, t_in=-2.0, t_out=2.0, n_steps=8,
+                q=(-0.2, 0.1, 0.0), r=1, k=(0, 0, 0), eps=(0, 0, 0), flags=())
+    ds = [dict(base, p=(0.3, -0.2, 0.0), s=1), dict(base, p=(0.3, -0.2, 0.0), s=-1),
+          dict(base, p=(-0.1, 0.4, 0.0), s=-1), dict(base, p=(0.3, -0.2, 0.0), s=1)]
+    precs = (swf.C128, swf.C64) if n[0] == 24 else (swf.C64,)
+    for prec in precs:
+        outs, marched = [], []
+        for dedupe in (False, True):
+            ctx = swf.Context(0)
+            ctx.set_dedupe(dedupe)
+            out = torch.zeros(len(ds) * 8 * int(np.prod(n)), device="cuda",
+                              dtype=torch.float64 if prec == swf.C128 else torch.float32)
+            before = ctx.fields_marched()
+            ctx.march_dev([swf.from_workload(d) for d in ds], out, bg=0, prec=prec)
+            marched.append(ctx.fields_marched() - before)
+            outs.append(out.cpu().numpy())
+            ctx.close()
+        assert marched == [4, 2], marched
+        assert np.array_equal(outs[0], outs[1]), prec
+        assert np.max(np.abs(outs[1])) > 0
