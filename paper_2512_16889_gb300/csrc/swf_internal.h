@@ -115,6 +115,7 @@ struct swf_ctx {
   swf::TuneCache tune;
   bool use_fused = true;  // route eligible marches to the fused cluster kernel
   bool dedupe = true;     // march fields that repeat another (the other spin) once
+  bool use_graphs = true; // replay pass-kernel march steps from CUDA graphs
   long long fields_marched = 0;  // fields actually marched since the last profile read
   int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
 };

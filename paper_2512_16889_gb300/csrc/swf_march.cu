@@ -47,9 +47,37 @@ struct StageArgs {
   RadixPlan plan[3];
   GridDesc g;
   int nrows;            // ny * nz
-  double t;
+  double t;             // stage time when clk is null
   cpx<R>* ystage;       // optional: receives the stage value Y (Breit-Wheeler integrand)
+  const struct MarchClock* clk;  // march clock (graph replays), or null
+  int ls;               // step within the replayed pair of steps (0 or 1)
+  double c;             // Dormand-Prince node c_i of the stage
 };
+
+// Device clock of a march whose steps are replayed from a CUDA graph: the stage time is
+// (t_out + (step + ls) h) + c_i h, the host loop's arithmetic, with `step` advanced on the device
+// after each replay.
+struct MarchClock {
+  double t_out, h;
+  int step;
+  int pad;
+};
+
+template <typename R>
+__device__ __forceinline__ double stage_time(const StageArgs<R>& A) {
+  if (!A.clk) return A.t;
+  const double tn = A.clk->t_out + (A.clk->step + A.ls) * A.clk->h;
+  return tn + A.c * A.clk->h;
+}
+
+__global__ void k_clock_set(MarchClock* c, double t_out, double h) {
+  c->t_out = t_out;
+  c->h = h;
+  c->step = 0;
+  c->pad = 0;
+}
+
+__global__ void k_clock_advance(MarchClock* c, int by) { c->step += by; }
 
 // ---------------------------------------------------------------- field and background
 __device__ __forceinline__ double field_time_factor(const FieldDesc& F, double t, double y) {
@@ -394,14 +422,15 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
   const int N = A.g.N;
   const size_t fo = (size_t)f * 4 * N;
   const FieldDesc* F = A.fd + f;
+  const double tst = stage_time(A);
   for (int j = threadIdx.x; j < rows; j += blockDim.x) {
     const int iy = (row0 + j) % ny;
     const double yc = ny > 1 ? A.g.x0[1] + iy * A.g.dx[1] : 0.0;
-    s_ft[j] = field_time_factor(*F, A.t, yc);
+    s_ft[j] = field_time_factor(*F, tst, yc);
   }
   if (threadIdx.x == 0) {
     double sn, cs;
-    sincos(F->tsign * F->e0 * A.t, &sn, &cs);
+    sincos(F->tsign * F->e0 * tst, &sn, &cs);
     s_tf = mk<R>((R)cs, (R)sn);
   }
   __syncthreads();
@@ -892,6 +921,61 @@ static swf_status prepare_args(swf_ctx* ctx, const GridDesc& g, int F, const Fie
   return SWF_OK;
 }
 
+// Runs `pairs` repetitions of two Dormand-Prince steps recorded by `record` (launches only, on
+// st), each followed by advancing the march clock by two steps.  Unless kernel timing is on or
+// st is the legacy default stream, the pair is captured once into a CUDA graph and replayed:
+// one launch per two steps instead of one per kernel.  The slots rotate with period two, so
+// the recorded pointers repeat; the stage times come from the device clock.
+template <typename Rec>
+static swf_status run_step_pairs(swf_ctx* ctx, cudaStream_t st, int pairs, MarchClock* clk, Rec&& record) {
+  if (pairs <= 0) return SWF_OK;
+  swf_status s = SWF_OK;
+  bool graph = !ctx->prof.on && st != 0 && ctx->use_graphs;
+  cudaGraphExec_t exec = nullptr;
+  long long per_pair = 0;
+  if (graph) {
+    const long long l0 = ctx->prof.launches;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      graph = false;
+    } else {
+      s = record();
+      k_clock_advance<<<1, 1, 0, st>>>(clk, 2);
+      cudaGraph_t gr = nullptr;
+      cudaError_t e = cudaStreamEndCapture(st, &gr);
+      per_pair = ctx->prof.launches - l0 + 1;
+      ctx->prof.launches = l0;
+      if (s != SWF_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_status(e, "capture of the march steps");
+      e = cudaGraphInstantiate(&exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return cuda_status(e, "instantiate the march graph");
+    }
+  }
+  if (!graph) {
+    for (int p = 0; p < pairs && s == SWF_OK; ++p) {
+      s = record();
+      k_clock_advance<<<1, 1, 0, st>>>(clk, 2);
+      ++ctx->prof.launches;
+    }
+    return s;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < pairs && e == cudaSuccess; ++p) {
+    e = cudaGraphLaunch(exec, st);
+    ctx->prof.launches += per_pair;
+  }
+  // the executable graph is released once its launches have run
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return cuda_status(e, "launch the march graph");
+  if (e2 != cudaSuccess) return cuda_status(e2, "march graph");
+  return SWF_OK;
+}
+
 template <typename R>
 static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
                              int F, const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
@@ -927,14 +1011,21 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
   }
   int slot[7] = {0, 1, 2, 3, 4, 5, 6};
   const double h = (t_in - t_out) / n_steps;
+  void* pclk = nullptr;
+  if ((s = ws_get(ctx, "march.clock", sizeof(MarchClock), &pclk)) != SWF_OK) return s;
+  MarchClock* clk = (MarchClock*)pclk;
+  k_clock_set<<<1, 1, 0, st>>>(clk, t_out, h);
+  A.clk = clk;
   // k_1 = f(t_out, 0)
   A.nterm = 0;
   A.write_y = 0;
   A.kout = (cpx<R>*)pk[slot[0]];
-  A.t = t_out;
+  A.ls = 0;
+  A.c = 0.0;
   if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
-  for (int n = 0; n < n_steps; ++n) {
-    const double tn = t_out + n * h;
+  // one step at clock offset ls (stage times from the clock: the same arithmetic as
+  // tn = t_out + n h, t = tn + c_i h)
+  auto step = [&](int ls) -> swf_status {
     for (int i = 1; i < 7; ++i) {
       int nt = 0;
       for (int j = 0; j < i; ++j) {
@@ -946,11 +1037,20 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
       A.nterm = nt;
       A.write_y = (i == 6);
       A.kout = (cpx<R>*)pk[slot[i]];
-      A.t = tn + DP_C[i] * h;
-      if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+      A.ls = ls;
+      A.c = DP_C[i];
+      swf_status r = launch_eval<R>(ctx, A, F, st);
+      if (r != SWF_OK) return r;
     }
     std::swap(slot[0], slot[6]);
-  }
+    return SWF_OK;
+  };
+  s = run_step_pairs(ctx, st, n_steps / 2, clk, [&]() -> swf_status {
+    swf_status r = step(0);
+    return r == SWF_OK ? step(1) : r;
+  });
+  if (s != SWF_OK) return s;
+  if (n_steps % 2 && (s = step(0)) != SWF_OK) return s;
   e = cudaMemcpyAsync(psi_out, py, state, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "copy psi(t_in)");
   e = cudaGetLastError();
@@ -1174,7 +1274,6 @@ swf_status rhs_eval_scratch(const GridDesc& g, const FieldDesc& fd, swf_precisio
 namespace swf {
 
 // Dormand-Prince 5th-order weights b_i (the 7th is zero; FSAL)
-static const double DP_B[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
 
 // Photon plane-wave factor exp(i k.x) per axis for each instance (trivial axes: 1).
 template <typename R>
@@ -1237,7 +1336,9 @@ __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o
 template <typename R>
 __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const cpx<R>* gcplx, const cpx<R>* kph,
                                               const double* photon, GridDesc g, const cpx<double>* __restrict__ ptab,
-                                              long tab_row, int tab_stride, cpx<double>* acc) {
+                                              const MarchClock* clk, int ls, int stage, int tab_stride,
+                                              cpx<double>* acc) {
+  const long tab_row = (long)(clk->step + ls) * 7 + stage;
   __shared__ cpx<double> red[8][3];
   const int inst = blockIdx.y;
   const int nt = g.n[0] + g.n[1] + g.n[2];
@@ -1380,14 +1481,19 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   }
   int slot[7] = {0, 1, 2, 3, 4, 5, 6};
   const double h = (t_in - t_out) / n_steps;
+  void* pclk = nullptr;
+  if ((s = ws_get(ctx, "march.clock", sizeof(MarchClock), &pclk)) != SWF_OK) return s;
+  MarchClock* clk = (MarchClock*)pclk;
+  k_clock_set<<<1, 1, 0, st>>>(clk, t_out, h);
+  A.clk = clk;
   A.nterm = 0;
   A.write_y = 0;
   A.kout = (cpx<R>*)pk[slot[0]];
-  A.t = t_out;
+  A.ls = 0;
+  A.c = 0.0;
   A.ystage = nullptr;  // M-dot vanishes at psi_s(t_out) = 0
   if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
-  for (int n = 0; n < n_steps; ++n) {
-    const double tn = t_out + n * h;
+  auto step = [&](int ls) -> swf_status {
     for (int i = 1; i < 7; ++i) {
       int ntm = 0;
       for (int j = 0; j < i; ++j) {
@@ -1399,21 +1505,31 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
       A.nterm = ntm;
       A.write_y = (i == 6);
       A.kout = (cpx<R>*)pk[slot[i]];
-      A.t = tn + DP_C[i] * h;
-      // weight of this stage value in the appended quadrature: b_{i+1}, and for the last stage
-      // (the new state) b_1 of the next step
-      const double wgt = (i >= 2 && i <= 5) ? h * DP_B[i] : (i == 6 && n + 1 < n_steps ? h * DP_B[0] : 0.0);
-      A.ystage = wgt != 0.0 ? (cpx<R>*)pys : nullptr;
-      if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
-      if (wgt != 0.0) {
+      A.ls = ls;
+      A.c = DP_C[i];
+      // stage values with a quadrature weight: b_{i+1} for i = 2..5 and, for the new state
+      // (i = 6), b_1 of the next step (the phase table holds 0 there on the last step, so every
+      // step launches the same kernels)
+      const bool weighted = i >= 2;
+      A.ystage = weighted ? (cpx<R>*)pys : nullptr;
+      swf_status r = launch_eval<R>(ctx, A, F, st);
+      if (r != SWF_OK) return r;
+      if (weighted) {
         ProfScope ps(ctx, "k_mdot", st);
         k_mdot<R><<<dim3(nb, n_inst), 256, 0, st>>>((const cpx<R>*)pys, A.gcplx, (const cpx<R>*)pkph,
-                                                    (const double*)pph, g, (const cpx<double>*)ptab,
-                                                    (long)n * 7 + i, 7 * n_steps, (cpx<double>*)ppart);
+                                                    (const double*)pph, g, (const cpx<double>*)ptab, clk, ls, i,
+                                                    7 * n_steps, (cpx<double>*)ppart);
       }
     }
     std::swap(slot[0], slot[6]);
-  }
+    return SWF_OK;
+  };
+  s = run_step_pairs(ctx, st, n_steps / 2, clk, [&]() -> swf_status {
+    swf_status r = step(0);
+    return r == SWF_OK ? step(1) : r;
+  });
+  if (s != SWF_OK) return s;
+  if (n_steps % 2 && (s = step(0)) != SWF_OK) return s;
   {
     ProfScope ps(ctx, "k_mdot_final", st);
     k_mdot_final<<<n_inst, 96, 0, st>>>((const cpx<double>*)ppart, nb, (cpx<double>*)macc);

@@ -88,3 +88,21 @@ def test_bw_zero_field_and_validation(env):
     with pytest.raises(swf.SwfError) as ei:
         ctx.solve([bad], swf.BREIT_WHEELER, swf.C64)
     assert ei.value.status == swf.SWF_EINVAL and "grid mode" in str(ei.value)
+
+
+def test_bw_graph_replay_matches_plain_launches():
+    """The Breit-Wheeler march replayed from CUDA graphs gives the same amplitudes as kernel-by-
+    kernel launches (kernel timing on), for an odd step count."""
+    from paper_2512_16889_gb300 import build, swf
+    build.build()
+    c = CASE2D
+    perp, par = O.polarisation_basis((1, 0, 0), c["k"])
+    inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], 451, c["p"], 1, c["q"], 1, c["k"], par)
+    res = []
+    for timed in (False, True):
+        ctx = swf.Context(0)
+        ctx.profile_enable(timed)
+        r, _ = ctx.solve([inst], swf.BREIT_WHEELER, swf.C64)
+        res.append(list(r[0].amp) + list(r[0].prob))
+        ctx.close()
+    assert res[0] == res[1]

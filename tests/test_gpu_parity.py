@@ -389,3 +389,23 @@ def test_spin_pairs_are_marched_once_with_identical_results(env, n):
         assert marched == [4, 2], marched
         assert np.array_equal(outs[0], outs[1]), prec
         assert np.max(np.abs(outs[1])) > 0
+
+
+def test_graph_replayed_march_matches_plain_launches(env):
+    """Pass-kernel marches replay pairs of steps from a CUDA graph with stage times from a device
+    clock; with kernel timing on they launch kernel by kernel.  Both give the same bits (odd and
+    even step counts)."""
+    torch, swf, _ = env
+    for d in (W.small_parity_cases()[0], dict(W.small_parity_cases()[1], n_steps=7)):
+        for prec in (swf.C128, swf.C64):
+            outs = []
+            for timed in (False, True):
+                ctx = swf.Context(0)
+                ctx.profile_enable(timed)
+                out = torch.zeros(2 * 4 * int(np.prod(d["n"])), device="cuda",
+                                  dtype=torch.float64 if prec == swf.C128 else torch.float32)
+                ctx.march_dev([swf.from_workload(d)], out, bg=0, prec=prec)
+                torch.cuda.synchronize()
+                outs.append(out.cpu().numpy())
+                ctx.close()
+            assert np.array_equal(outs[0], outs[1]), (d["n_steps"], prec)
