@@ -174,9 +174,28 @@ class Field:
     prm: tuple = ()
 
 
-def gauge_potential(fld: Field, t: float, X, Y, Z):
+@dataclass
+class GaugeShift:
+    """The potential of `base` plus the gradient of chi(t, x) = chi0 exp(-t^2/tau^2 - r^2/sigma^2)
+    (r over the non-trivial axes): A_mu -> A_mu + d_mu chi, covariant components, so that with
+    D_mu = d_mu + i A_mu (Eq. 2) a solution psi becomes exp(-i chi) psi."""
+
+    base: Field
+    chi0: float
+    tau: float
+    sigma: float
+
+
+def gauge_potential(fld, t: float, X, Y, Z):
     """Return (A_0, A_1, A_2, A_3) on the coordinate arrays at time t."""
     zero = np.zeros(np.broadcast(X, Y, Z).shape)
+    if isinstance(fld, GaugeShift):
+        a = list(gauge_potential(fld.base, t, X, Y, Z))
+        chi = fld.chi0 * np.exp(-t * t / fld.tau**2 - (X * X + Y * Y + Z * Z) / fld.sigma**2)
+        a[0] = a[0] + (-2.0 * t / fld.tau**2) * chi          # d_t chi
+        for k, xk in enumerate((X, Y, Z)):
+            a[k + 1] = a[k + 1] + (-2.0 * xk / fld.sigma**2) * chi  # d_k chi = d chi / d x^k
+        return tuple(a)
     if fld.kind == "zero":
         return zero, zero, zero, zero
     if fld.kind == "sauter_gauss":

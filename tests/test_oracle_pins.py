@@ -371,3 +371,37 @@ def test_rhs_solves_covariant_equation():
     psib = bg.values(grid, t0)
     rhs = sum(np.einsum("ab,b...->a...", O.GAMMA[mu], A[mu][None] * psib) for mu in range(4))
     assert np.allclose(lhs, rhs, atol=1e-11)
+
+
+def test_gauge_transformation_leaves_amplitudes_unchanged():
+    """A_mu -> A_mu + d_mu chi with chi localised in space and time (negligible at t_in and
+    t_out): psi -> exp(-i chi) psi, so the amplitudes at t_in (Eq. 8) do not change.  On the grid
+    the spectral derivative and the multiplication by exp(-i chi) commute only up to aliasing,
+    so the agreement improves with refinement; mid-march, where chi is large, the waves differ."""
+    fld = O.Field("sauter_gauss", (0.8, 0.6, 2.5))
+    shifted = O.GaugeShift(fld, chi0=0.6, tau=1.2, sigma=1.8)
+    bg = O.Background("U", (0.3, -0.2, 0.0), 1)
+    errs = []
+    for n in (16, 32):
+        grid = O.Grid((n, n, 1), (14.0, 14.0, 1.0))
+        c0 = O.c_spectrum(O.march_scattered(fld, grid, bg, -6.0, 6.0, 300), grid, -6.0)
+        c1 = O.c_spectrum(O.march_scattered(shifted, grid, bg, -6.0, 6.0, 300), grid, -6.0)
+        errs.append(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))
+    assert errs[1] < 1e-5 and errs[1] < errs[0] / 100, errs
+    grid = O.Grid((16, 16, 1), (14.0, 14.0, 1.0))
+    m0 = O.c_spectrum(O.march_scattered(fld, grid, bg, 0.0, 6.0, 150), grid, 0.0)
+    m1 = O.c_spectrum(O.march_scattered(shifted, grid, bg, 0.0, 6.0, 150), grid, 0.0)
+    assert np.max(np.abs(m1 - m0)) / np.max(np.abs(m0)) > 0.1
+
+
+@pytest.mark.parametrize("gam", [0.5, 1.0, 2.0])
+def test_weak_field_exponent_of_the_sauter_spectrum(gam):
+    """Weak field at fixed gamma = omega/E: ln n(p = 0) of E(t) = E sech^2(omega t) falls linearly
+    in 1/E with the worldline-instanton exponent pi (2/(1 + sqrt(1 + gamma^2))) (constant-field
+    limit pi).  Pins the closed form that pins the mode solver, which pins the oracle (above)."""
+    Es = (0.05, 0.04, 0.03)
+    ln = [np.log(R.sauter_pair_density(E, gam * E, 0.0)) for E in Es]
+    slope = (ln[2] - ln[0]) / (1 / Es[2] - 1 / Es[0])
+    expo = np.pi * 2 / (1 + np.sqrt(1 + gam ** 2))
+    assert abs(slope + expo) < 1e-6 * expo, (slope, expo)
+    assert abs((ln[1] - ln[0]) / (1 / Es[1] - 1 / Es[0]) + expo) < 1e-6 * expo
