@@ -405,3 +405,22 @@ def test_weak_field_exponent_of_the_sauter_spectrum(gam):
     expo = np.pi * 2 / (1 + np.sqrt(1 + gam ** 2))
     assert abs(slope + expo) < 1e-6 * expo, (slope, expo)
     assert abs((ln[1] - ln[0]) / (1 / Es[1] - 1 / Es[0]) + expo) < 1e-6 * expo
+
+
+def test_spectral_convergence_under_grid_refinement():
+    """Fixed box and a field negligible at its edge (exp(-36)): the amplitude C at fixed physical
+    positron modes converges faster than any power as the grid is refined (brute force on tiny
+    grids, 12^2 .. 36^2 against 48^2; measured 2e-2, 1.4e-4, 2.9e-6, 1.2e-11)."""
+    fld = O.Field("sauter_gauss", (0.8, 0.6, 1.2))
+    L = 12.0
+    bg = O.Background("U", (2 * np.pi / L, 0.0, 0.0), 1)
+
+    def c_at(n):
+        grid = O.Grid((n, n, 1), (L, L, 1.0))
+        C = O.c_spectrum(O.march_scattered(fld, grid, bg, -5.0, 5.0, 200), grid, -5.0)
+        return C[0, 1, 0, 0], C[0, n - 1, 1, 0]  # modes (1, 0) and (-1, 1) in units of 2 pi / L
+
+    ref = np.array(c_at(48))
+    errs = [np.max(np.abs(np.array(c_at(n)) - ref)) / np.max(np.abs(ref)) for n in (12, 18, 24, 36)]
+    assert all(errs[i] > 10 * errs[i + 1] for i in range(3)), errs
+    assert errs[-1] < 1e-9, errs
