@@ -990,7 +990,7 @@ bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_preci
   return true;
 }
 
-static int g_fused_clusters[2] = {-1, -1};
+static int g_fused_clusters[64][2];  // per device and variant: resident clusters + 1 (0: not set up)
 
 swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
                        const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
@@ -1015,7 +1015,8 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
     cfg.numAttrs = 1;
     return cfg;
   };
-  if (g_fused_clusters[var] < 0) {
+  int* ncl_slot = &g_fused_clusters[dev_slot()][var];
+  if (*ncl_slot == 0) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return cuda_status(e, "cluster size attribute");
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1029,10 +1030,10 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
       set_error("the fused march kernel cannot be resident on this device");
       return SWF_EUNSUPPORTED;
     }
-    g_fused_clusters[var] = ncl;
+    *ncl_slot = ncl + 1;
   }
   const int n_sec = 2 * n_f;
-  const int ncl = g_fused_clusters[var] < n_sec ? g_fused_clusters[var] : n_sec;
+  const int ncl = *ncl_slot - 1 < n_sec ? *ncl_slot - 1 : n_sec;
   const size_t plane = (size_t)NX * NY;
   swf_status s;
   void *pfd, *psec, *pslots;
@@ -1081,6 +1082,6 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
   return SWF_OK;
 }
 
-int fused_clusters() { return g_fused_clusters[0]; }
+int fused_clusters() { return g_fused_clusters[dev_slot()][0] - 1; }
 
 }  // namespace swf

@@ -72,6 +72,13 @@ FieldDesc make_field_desc(const swf_instance& in, int bg);
 // Builds the radix plan (radices 4, 2, 3, 5) of a length; false if n has another factor.
 bool make_radix_plan(int n, RadixPlan* pl);
 
+// Index of the current device for per-device set-up flags (kernel attributes are per device).
+inline int dev_slot() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) d = 0;
+  return d;
+}
+
 // Device workspace: a growable pool of named buffers owned by the context.
 struct Workspace {
   std::map<std::string, std::pair<void*, size_t>> bufs;

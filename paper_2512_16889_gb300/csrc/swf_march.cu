@@ -735,8 +735,9 @@ static int tune_lookup(swf_ctx* ctx, const std::string& key, int fallback) {
 
 template <typename R>
 static swf_status set_smem_attrs() {
-  static bool done = false;
-  if (done) return SWF_OK;
+  static bool done[64] = {false};
+  const int dv = dev_slot();
+  if (done[dv]) return SWF_OK;
   cudaError_t e;
   e = cudaFuncSetAttribute(k_first<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_first)");
@@ -744,7 +745,7 @@ static swf_status set_smem_attrs() {
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_mid)");
   e = cudaFuncSetAttribute(k_last<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last)");
-  done = true;
+  done[dv] = true;
   return SWF_OK;
 }
 

@@ -219,14 +219,15 @@ __global__ void __launch_bounds__(kT) k_norms(const void* psi, GridDesc g, doubl
   }
 }
 
-bool smem_ready = false;
+bool smem_ready[64] = {false};
 
 swf_status ensure_smem() {
-  if (smem_ready) return SWF_OK;
+  const int dv = dev_slot();
+  if (smem_ready[dv]) return SWF_OK;
   cudaError_t e = cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kT * (kMaxE - 4) * (int)sizeof(cpx<double>));
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_fft_axis)");
-  smem_ready = true;
+  smem_ready[dv] = true;
   return SWF_OK;
 }
 
