@@ -360,6 +360,58 @@ def run_surrogate(args):
     return 0
 
 
+def run_surrogate_scan(args):
+    """The learned screen end to end on one GPU, at a reduced solver resolution (64^2 grid, box
+    40, 200 steps): a momentum scan (p in [-1, 1]^2, both spins) of the E = 0.3 field; train on
+    8192 solver samples (3000 epochs, Adam 5e-4), calibrate the sigma threshold on 1024 held-out
+    samples for tolerances 5e-2 and 1e-2 in ln P, then screen a 16384-point scan and solve the
+    rejected points.  Reports acceptance, accuracy of the accepted points against the solver, and
+    the time of the screened scan against solving every point."""
+    import numpy as np
+    import torch
+    from paper_2512_16889_gb300 import build, surrogate as S, swf
+    build.build()
+    grid = dict(n=64, L=40.0, n_steps=200, t_window=20.0)
+    ctx = swf.Context(0)
+
+    def scan(n, seed):
+        rng = np.random.default_rng(seed)
+        return {"E": np.full(n, 0.3), "omega": np.full(n, 0.5), "lam": np.full(n, 5.0),
+                "px": rng.uniform(-1, 1, n), "py": rng.uniform(-1, 1, n), "s": rng.choice([1, -1], n)}
+
+    n_tr, n_sc = (args.limit or 8192), 16384
+    tr, ho, sc = scan(n_tr, 4), scan(1024, 5), scan(n_sc, 6)
+    t0 = time.perf_counter()
+    y_tr = S.solve_targets(ctx, tr, **grid)
+    t_train_data = time.perf_counter() - t0
+    y_ho = S.solve_targets(ctx, ho, **grid)
+    t0 = time.perf_counter()
+    y_sc = S.solve_targets(ctx, sc, **grid)  # the method without the network
+    t_all = time.perf_counter() - t0
+    X_tr = S.features(tr)
+    sur = swf.Surrogate(S.init_params(0), S.normalisation(X_tr, y_tr), max_batch=512)
+    t0 = time.perf_counter()
+    hist = S.train(sur, X_tr, y_tr, epochs=3000, batch=256, lr=5e-4)
+    t_fit = time.perf_counter() - t0
+    out = {"metric": "surrogate-screened scan", "unit": "s", "higher_is_better": False, "n_gpus": 1,
+           "data": "synthetic", "config": {"workload": "surrogate_scan: momentum scan of E = 0.3, 64^2 grid, 200 steps",
+                                            "train_samples": n_tr, "scan_points": n_sc, "epochs": 3000},
+           "solver_s_per_point": t_all / n_sc, "train_data_s": t_train_data, "fit_s": t_fit,
+           "final_loss": hist[-1], "all_solver_s": t_all, "screens": []}
+    for tol, cov in ((5e-2, 0.95), (1e-2, 0.99)):
+        thr = S.calibrate(sur, S.features(ho), y_ho, tol, coverage=cov)
+        vals, acc, t_net, t_sol = S.screened_scan(sur, ctx, sc, thr, **grid)
+        err = np.abs(vals - y_sc)
+        out["screens"].append({"tol_lnP": tol, "coverage": cov, "accepted": float(acc.mean()),
+                               "accepted_within_tol": float((err[acc] <= tol).mean()) if acc.any() else None,
+                               "screened_s": t_net + t_sol, "speedup_vs_all_solver": t_all / (t_net + t_sol)})
+    out["value"] = out["screens"][0]["screened_s"]
+    print(json.dumps(out), flush=True)
+    sur.close()
+    ctx.close()
+    return 0
+
+
 def run_pair_scan(args):
     """Times the all-pairs full pair number on one GPU: 128 electrons x 128 positrons of one
     field on the 256^2 grid (1000 steps, complex64 march, FP64 overlaps) through swf_pair_matrix:
@@ -499,6 +551,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "pair_scan":
         return run_pair_scan(args)
+    if args.workload == "surrogate_scan":
+        return run_surrogate_scan(args)
     if args.workload:
         return run_workload(args)
     if args.impl == "reference":
