@@ -87,6 +87,13 @@ template <bool INV> __device__ __forceinline__ float2 rot(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// y += c k on both complex halves of a float4 (two-lane FP32 fused multiply-adds)
+__device__ __forceinline__ void fma4(float2 c, const float4& k, float4& y) {
+  const float2 lo = __ffma2_rn(c, make_float2(k.x, k.y), make_float2(y.x, y.y));
+  const float2 hi = __ffma2_rn(c, make_float2(k.z, k.w), make_float2(y.z, y.w));
+  y = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 // (hi, lo) + s in float-float arithmetic (Knuth's two-sum, then a fast renormalisation):
 // on return hi is the new rounded state, lo its rounding error; s is overwritten with hi.
 __device__ __forceinline__ void ff_add(float hi, float& lo, float& s) {
@@ -151,13 +158,24 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float4& a, const 
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 4-point DFT on packed pairs: each complex add or subtract is one two-lane FP32 instruction
+// (add.f32x2 / fma.f32x2 with an exact +-1 factor, so every result is the same single rounding
+// as the scalar form); the +-i rotation is a lane swap with the sign folded into the factor.
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  const float2 t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = rot<INV>(a1 - a3);
-  a0 = t0 + t2;
-  a2 = t0 - t2;
-  a1 = t1 + t3;
-  a3 = t1 - t3;
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 t0 = __fadd2_rn(a0, a2);
+  const float2 t1 = __ffma2_rn(a2, m1, a0);
+  const float2 t2 = __fadd2_rn(a1, a3);
+  const float2 d = __ffma2_rn(a3, m1, a1);
+  const float2 sw = make_float2(d.y, d.x);
+  // rot(d) = -i d = (d.y, -d.x) forward, +i d = (-d.y, d.x) inverse
+  const float2 sp = INV ? make_float2(-1.f, 1.f) : make_float2(1.f, -1.f);
+  const float2 sn = INV ? make_float2(1.f, -1.f) : make_float2(-1.f, 1.f);
+  a0 = __fadd2_rn(t0, t2);
+  a2 = __ffma2_rn(t2, m1, t0);
+  a1 = __ffma2_rn(sw, sp, t1);
+  a3 = __ffma2_rn(sw, sn, t1);
 }
 
 // 16-point DFT in registers, natural order in and out (4 x 4 with the W16 twiddles).
@@ -475,11 +493,11 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             if (j < ntm) {
-              const float c = ct[j];
-              y0.x = fmaf(c, __uint_as_float(tr[j][0]), y0.x); y0.y = fmaf(c, __uint_as_float(tr[j][1]), y0.y);
-              y0.z = fmaf(c, __uint_as_float(tr[j][2]), y0.z); y0.w = fmaf(c, __uint_as_float(tr[j][3]), y0.w);
-              y1.x = fmaf(c, __uint_as_float(tr[j][4]), y1.x); y1.y = fmaf(c, __uint_as_float(tr[j][5]), y1.y);
-              y1.z = fmaf(c, __uint_as_float(tr[j][6]), y1.z); y1.w = fmaf(c, __uint_as_float(tr[j][7]), y1.w);
+              const float2 c = make_float2(ct[j], ct[j]);
+              fma4(c, make_float4(__uint_as_float(tr[j][0]), __uint_as_float(tr[j][1]), __uint_as_float(tr[j][2]),
+                                  __uint_as_float(tr[j][3])), y0);
+              fma4(c, make_float4(__uint_as_float(tr[j][4]), __uint_as_float(tr[j][5]), __uint_as_float(tr[j][6]),
+                                  __uint_as_float(tr[j][7])), y1);
             }
           }
         }
@@ -488,9 +506,9 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
           if (q < nterm) {
             const float4 k0 = __ldcg(reinterpret_cast<const float4*>(kin[q] + g0));
             const float4 k1 = __ldcg(reinterpret_cast<const float4*>(kin[q] + plane + g0));
-            const float c = coef[q];
-            y0.x = fmaf(c, k0.x, y0.x); y0.y = fmaf(c, k0.y, y0.y); y0.z = fmaf(c, k0.z, y0.z); y0.w = fmaf(c, k0.w, y0.w);
-            y1.x = fmaf(c, k1.x, y1.x); y1.y = fmaf(c, k1.y, y1.y); y1.z = fmaf(c, k1.z, y1.z); y1.w = fmaf(c, k1.w, y1.w);
+            const float2 c = make_float2(coef[q], coef[q]);
+            fma4(c, k0, y0);
+            fma4(c, k1, y1);
           }
         }
         if (last) {
