@@ -198,12 +198,14 @@ swf_status swf_set_march_path(swf_ctx* ctx, int path);
  * -1, 1) R_+ and every operator of Eq. 6 keeps {0, 3} and {1, 2} apart; App. A.5 Eq. A44).
  * on = 0 marches every field.  Results agree either way (up to the sign of zeros). */
 swf_status swf_set_dedupe(swf_ctx* ctx, int on);
-/* Fields (U or V waves) actually marched by this context since its creation. */
+/* Fields (U or V waves) actually marched by this context since its creation (a diagnostic of
+ * the library; the paper has no counterpart). */
 swf_status swf_fields_marched(swf_ctx* ctx, long long* count);
 
 /* Launch shapes of the pass kernels (rows per block of the x passes, tile width of the y and z
- * passes, 256 or 128 threads per block).  on = 1 (default): the first march of each grid shape in this context times the
- * candidate shapes (a few launches each, before the march starts) and keeps the fastest;
+ * passes, 256 or 128 threads per block).  on = 1 (default): the first march of each grid
+ * shape in this context times the candidate shapes (a few launches each, before the march
+ * starts) and keeps the fastest;
  * on = 0: a fixed rule from the grid size.  A shape only decides which lines a block
  * transforms, so results are bitwise the same either way.  Part of the batching design
  * (Sec. II.A: many instances per launch); the paper names no tuner. */

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <map>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -122,6 +123,12 @@ __global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, int M, int N, int K,
 }
 
 // ---------------------------------------------------------------- small kernels
+__global__ void k_set_hyper(float* hyper, float lr, float c1, float c2) {
+  hyper[0] = lr;
+  hyper[1] = c1;
+  hyper[2] = c2;
+}
+
 // network input: standardised features, x' = (x - shift) * scale per feature
 __global__ void k_inputs(const float* x, const float* shift, const float* scale, __nv_bfloat16* y, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -177,9 +184,12 @@ __global__ void k_bias_grad(const float* dz, int B, int N, float* db) {
   db[n] = s;
 }
 
-// Adam on the FP32 master parameters, then the BF16 copies of the weight matrices.
-__global__ void k_adam(float* p, const float* g, float* m, float* v, long n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+// Adam on the FP32 master parameters, then the BF16 copies of the weight matrices.  The step's
+// learning rate and bias corrections come from device memory (hyper = {lr, 1 - b1^t, 1 - b2^t}),
+// so that a captured training step can be replayed.
+__global__ void k_adam(float* p, const float* g, float* m, float* v, long n, const float* hyper, float b1, float b2,
+                       float eps) {
+  const float lr = hyper[0], c1 = hyper[1], c2 = hyper[2];
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -513,6 +523,11 @@ struct swf_mlp {
   int* err;                  // set by the inference kernel when a wait timed out
   int nsm;
   cudaStream_t last_stream;
+  float* xs;                 // training batch staged for the captured step: [max_batch][6]
+  float* ysg;                // [max_batch]
+  float* hyper;              // {lr, 1 - b1^t, 1 - b2^t} of the current step
+  cudaStream_t cap_stream;   // stream the training step is captured on
+  std::map<int, cudaGraphExec_t> train_graphs;  // captured training step per batch size
   std::vector<void*> allocs;
 };
 
@@ -604,6 +619,7 @@ swf_status swf_mlp_create(swf_mlp** out, int device, const float* init_params, i
   swf_status s;
   auto fail = [&](swf_status st) {
     for (void* p : m->allocs) cudaFree(p);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     delete m;
     return st;
   };
@@ -617,12 +633,18 @@ swf_status swf_mlp_create(swf_mlp** out, int device, const float* init_params, i
   if ((s = mlp_alloc(m, (void**)&m->in_scale, 6 * 4)) != SWF_OK) return fail(s);
   if ((s = mlp_alloc(m, (void**)&m->wpack, (size_t)3 * 256 * 256 * 2)) != SWF_OK) return fail(s);
   if ((s = mlp_alloc(m, (void**)&m->err, sizeof(int))) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->xs, (size_t)max_batch * DIN[0] * 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->ysg, (size_t)max_batch * 4)) != SWF_OK) return fail(s);
+  if ((s = mlp_alloc(m, (void**)&m->hyper, 4 * sizeof(float))) != SWF_OK) return fail(s);
+  m->cap_stream = nullptr;
   m->last_stream = 0;
   m->nsm = 0;
   e = cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess || m->nsm < 1) return fail(cuda_status(e, "SM count"));
   e = cudaFuncSetAttribute(tc::k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaFuncSetAttribute(k_mlp_forward)"));
+  e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(cuda_status(e, "capture stream"));
   m->y0 = norm[12];
   m->ys = norm[13];
   for (int l = 0; l < NL; ++l) {
@@ -651,6 +673,8 @@ swf_status swf_mlp_destroy(swf_mlp* m) {
   if (!m) return SWF_OK;
   cudaSetDevice(m->device);
   cudaDeviceSynchronize();
+  for (auto& kv : m->train_graphs) cudaGraphExecDestroy(kv.second);
+  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   for (void* p : m->allocs) cudaFree(p);
   delete m;
   return SWF_OK;
@@ -706,18 +730,54 @@ swf_status swf_mlp_gradients(swf_mlp* m, const float* x_dev, const float* y_dev,
   return SWF_OK;
 }
 
+// The kernels of one training step on the staged batch (forward, loss, backward, Adam, BF16
+// copies and operand image), B rows.
+static void record_train_step(swf_mlp* m, int B, cudaStream_t st) {
+  forward(m, m->xs, B, st);
+  k_nll<<<1, 256, 0, st>>>(m->z[NL - 1], m->ysg, m->y0, m->ys, B, m->dz32[NL - 1], m->dz16[NL - 1], m->loss);
+  backward(m, B, st);
+  k_adam<<<128, 256, 0, st>>>(m->params, m->grads, m->adam_m, m->adam_v, n_params(), m->hyper, 0.9f, 0.999f, 1e-8f);
+  refresh_bf16(m, st);
+}
+
 swf_status swf_mlp_train_step(swf_mlp* m, const float* x_dev, const float* y_dev, int B, float lr, float* loss_dev,
                               void* stream) {
-  swf_status s = swf_mlp_gradients(m, x_dev, y_dev, B, nullptr, loss_dev, stream);
-  if (s != SWF_OK) return s;
+  if (!m || !x_dev || !y_dev || B < 1 || B > m->max_batch) {
+    set_error("swf_mlp_train_step: invalid arguments (batch must be in [1, max_batch])");
+    return SWF_EINVAL;
+  }
+  cudaSetDevice(m->device);
   cudaStream_t st = (cudaStream_t)stream;
+  // the step runs as one CUDA graph per batch size (about 25 kernels, captured once) on the
+  // staged batch; the batch, the learning rate and the bias corrections are set before it
+  cudaError_t e = cudaMemcpyAsync(m->xs, x_dev, (size_t)B * DIN[0] * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->ysg, y_dev, (size_t)B * 4, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "stage the training batch");
   m->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - (float)std::pow((double)b1, (double)m->step);
-  const float c2 = 1.f - (float)std::pow((double)b2, (double)m->step);
-  k_adam<<<128, 256, 0, st>>>(m->params, m->grads, m->adam_m, m->adam_v, n_params(), lr, b1, b2, 1e-8f, c1, c2);
-  refresh_bf16(m, st);
-  cudaError_t e = cudaGetLastError();
+  const double b1 = 0.9, b2 = 0.999;
+  k_set_hyper<<<1, 1, 0, st>>>(m->hyper, lr, (float)(1.0 - std::pow(b1, (double)m->step)),
+                               (float)(1.0 - std::pow(b2, (double)m->step)));
+  auto it = m->train_graphs.find(B);
+  if (it == m->train_graphs.end()) {
+    cudaGraphExec_t exec = nullptr;
+    e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      record_train_step(m, B, m->cap_stream);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(m->cap_stream, &g);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "capture the training step");
+    it = m->train_graphs.emplace(B, exec).first;
+  }
+  e = cudaGraphLaunch(it->second, st);
+  if (e != cudaSuccess) return cuda_status(e, "training step");
+  if (loss_dev) {
+    e = cudaMemcpyAsync(loss_dev, m->loss, 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "copy loss");
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "surrogate update");
   return SWF_OK;
 }

@@ -125,3 +125,35 @@ def test_surrogate_screens_a_momentum_scan():
     assert t_net + t_sol < t_all
     sur.close()
     ctx.close()
+
+
+def test_train_step_is_one_adam_step_on_the_gradient():
+    """The captured training step (one CUDA graph per batch size) applies Adam to the gradient of
+    swf_mlp_gradients: first step m = (1 - b1) g, v = (1 - b2) g^2, p -= lr (m/c1)/(sqrt(v/c2) + eps);
+    a second batch size and a repeat of the first reuse or capture their own graphs."""
+    import torch
+    from paper_2512_16889_gb300 import build, surrogate as S, swf
+    build.build()
+    t = _table(256, seed=31)
+    X = S.features(t)
+    y = (-11.0 + 2.0 * np.tanh(X[:, 0] * 4) + 0.3 * X[:, 4]).astype(np.float32)
+    norm = S.normalisation(X, y)
+    p0 = S.init_params(seed=7)
+    sur = swf.Surrogate(p0, norm, max_batch=256)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    g = torch.zeros(swf.Surrogate.param_count(), dtype=torch.float32, device="cuda")
+    sur.gradients(Xd, yd, g)
+    g = g.cpu().numpy().astype(np.float64)
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sur.train_step(Xd, yd, lr, loss)
+    p1 = sur.params().astype(np.float64)
+    m, v = (1 - b1) * g, (1 - b2) * g * g
+    ref = p0.astype(np.float64) - lr * (m / (1 - b1)) / (np.sqrt(v / (1 - b2)) + eps)
+    assert np.max(np.abs(p1 - ref)) <= 1e-6 + 1e-5 * np.max(np.abs(ref)), np.max(np.abs(p1 - ref))
+    assert np.isfinite(loss.item())
+    sur.train_step(Xd[:128].contiguous(), yd[:128].contiguous(), lr, loss)
+    sur.train_step(Xd, yd, lr, loss)
+    assert np.all(np.isfinite(sur.params()))
+    assert np.max(np.abs(sur.params() - p1)) > 0
+    sur.close()
