@@ -1,11 +1,17 @@
-"""Writes oracle-only reference samples for the full-size batched Schwinger workload.
+"""Writes oracle-only reference values for full-size workloads (no CUDA involved).
 
-Runs the FP64 oracle (no CUDA involved) on selected instances of the 256^2, 128-instance,
-1000-step workload and stores, per instance, the C-spectrum |C(m,(r,q))|^2 at the 64 largest
-modes, 64 modes spread over the spectrum, and ||psi_scat(t_in)||^2.  The GPU test compares the
-benchmark's own solve against these values.
+* batched Schwinger (256^2, 128 instances, 1000 steps): per selected instance the C-spectrum
+  |C(m,(r,q))|^2 at the 64 largest modes and 64 modes spread over the spectrum, and
+  ||psi_scat(t_in)||^2 -> schwinger_batched_samples.json;
+* single FP64 Schwinger (128^2, 1000 steps): the full pair number (both lines of Eq. 8 and the
+  amplitudes C, D, A, B) for r = +1 and -1, and C-spectrum samples -> schwinger_fp64_single.json;
+* Breit-Wheeler uneven grids: the amplitude terms of one instance of the smallest grid (192^2,
+  2605 steps) -> bw_uneven_sample.json.
+The GPU tests compare the library's solves of the same instances against these values.
 
-    python tests/golden/make_full_size_reference.py [instance ...]
+    python tests/golden/make_full_size_reference.py [instance ...]     # batched Schwinger
+    python tests/golden/make_full_size_reference.py --single
+    python tests/golden/make_full_size_reference.py --bw
 """
 import json
 import os
@@ -39,7 +45,55 @@ def sample(i):
             "seconds": time.time() - t0}
 
 
+def single_fp64():
+    """Full N of the single FP64 Schwinger workload for both positron spins."""
+    d0 = W.schwinger_fp64_single()[0]
+    g = OA.grid(d0)
+    t0 = time.time()
+    pu = O.march_scattered(OA.field(d0), g, OA.background(d0, 0), d0["t_in"], d0["t_out"], d0["n_steps"])
+    C = O.c_spectrum(pu, g, d0["t_in"])
+    prob = np.transpose(np.abs(C) ** 2, (0, 3, 2, 1)).ravel()
+    top = np.argsort(prob)[::-1][:64]
+    out = {"citation": "oracle/swf_oracle.py on paper_2512_16889_gb300.workloads.schwinger_fp64_single()",
+           "spectrum_modes": [int(v) for v in top], "spectrum_prob": [float(prob[v]) for v in top],
+           "norm_u": float(O.inner(pu, pu, g).real), "pairs": []}
+    for r in (1, -1):
+        d = dict(d0, r=r)
+        bv = OA.background(d, 1)
+        pv = O.march_scattered(OA.field(d), g, bv, d["t_in"], d["t_out"], d["n_steps"])
+        ref = O.pair_number(pu, pv, g, d["t_in"], d["p"], d["s"], d["q"], d["r"], OA.background(d, 0).offset(),
+                            bv.offset())
+        out["pairs"].append({"r": r, **{k: [ref[k].real, ref[k].imag] for k in ("C", "D", "A", "B")},
+                             "N_line1": float(ref["N_line1"]), "N_line2": float(ref["N_line2"]),
+                             "norm_v": float(O.inner(pv, pv, g).real)})
+    out["seconds"] = time.time() - t0
+    json.dump(out, open(os.path.join(os.path.dirname(OUT), "schwinger_fp64_single.json"), "w"), indent=1)
+
+
+def bw_sample():
+    """Amplitude terms of the first 192^2 instance of the Breit-Wheeler uneven-grid workload."""
+    ds = W.bw_uneven()
+    i = next(j for j, d in enumerate(ds) if d["n"][0] == 192)
+    d = ds[i]
+    g = OA.grid(d)
+    t0 = time.time()
+    ph = O.Photon(tuple(d["k"]), tuple(d["eps"]))
+    ref = O.bw_amplitude(OA.field(d), g, d["p"], d["s"], d["q"], d["r"], ph, d["t_in"], d["t_out"], d["n_steps"])
+    out = {"citation": "oracle/swf_oracle.py on paper_2512_16889_gb300.workloads.bw_uneven()",
+           "instance": i, "n": list(d["n"]), "n_steps": d["n_steps"],
+           "terms": [[complex(v).real, complex(v).imag] for v in ref["terms"]], "M": [ref["M"].real, ref["M"].imag],
+           "norm_u": float(O.inner(ref["psi_u"], ref["psi_u"], g).real),
+           "norm_v": float(O.inner(ref["psi_v"], ref["psi_v"], g).real), "seconds": time.time() - t0}
+    json.dump(out, open(os.path.join(os.path.dirname(OUT), "bw_uneven_sample.json"), "w"), indent=1)
+
+
 if __name__ == "__main__":
+    if sys.argv[1:] == ["--single"]:
+        single_fp64()
+        sys.exit(0)
+    if sys.argv[1:] == ["--bw"]:
+        bw_sample()
+        sys.exit(0)
     which = [int(v) for v in sys.argv[1:]] or [0, 77]
     data = {"citation": "oracle/swf_oracle.py on paper_2512_16889_gb300.workloads.schwinger_batched()",
             "samples": []}

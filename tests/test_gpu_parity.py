@@ -409,3 +409,83 @@ def test_graph_replayed_march_matches_plain_launches(env):
                 outs.append(out.cpu().numpy())
                 ctx.close()
             assert np.array_equal(outs[0], outs[1]), (d["n_steps"], prec)
+
+
+@pytest.mark.parametrize("n", [(512, 6, 1), (6, 512, 1), (4, 6, 512)])
+def test_march_at_the_maximum_axis_length(env, n):
+    """The largest axis length (512 = 16 x 16 x 2 in the line FFTs) along x, y and z, both
+    precisions, against the oracle."""
+    torch, swf, ctx = env
+    L = tuple(40.0 if k == 512 else (6.0 if k > 1 else 1.0) for k in n)
+    p = (0.2, 0.1, 0.0) if n[2] == 1 else (0.2, 0.1, 0.05)
+    # h = 0.05: |kappa|_max h = 2 at 512 points on a box of 40, inside the Dormand-Prince region
+    d = dict(field=("sauter_gauss", (0.6, 0.5, 3.0)), n=n, L=L, t_in=-1.5, t_out=1.5, n_steps=60, p=p, s=1,
+             q=(-0.1, 0.0, 0.0), r=1, k=(0, 0, 0), eps=(0, 0, 0), flags=())
+    ref = OA.to_gpu_layout(O.march_scattered(OA.field(d), OA.grid(d), OA.background(d, 0), d["t_in"], d["t_out"],
+                                             d["n_steps"]))
+    for prec, tol in ((swf.C128, 1e-10), (swf.C64, 2e-5)):
+        out = torch.zeros(2 * 4 * int(np.prod(n)), dtype=torch.float64 if prec == swf.C128 else torch.float32,
+                          device="cuda")
+        ctx.march_dev([swf.from_workload(d)], out, bg=0, prec=prec)
+        got = to_complex(out).reshape(ref.shape)
+        assert rel_state(got, ref) < tol, (n, prec, rel_state(got, ref))
+
+
+def test_single_fp64_workload_matches_stored_oracle(env):
+    """The full-size single FP64 workload (128^2, 1000 steps) with the full pair number for both
+    positron spins, against oracle values written by tests/golden/make_full_size_reference.py."""
+    import json
+    import os
+    torch, swf, ctx = env
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "schwinger_fp64_single.json")))
+    d0 = W.schwinger_fp64_single()[0]
+    ds = [dict(d0, r=pr["r"], flags=("spectrum", "full_n")) for pr in golden["pairs"]]
+    res, spec = ctx.solve([swf.from_workload(d) for d in ds], swf.SCHWINGER, swf.C128)
+    # r = -1 is forbidden here (spin along x conserved for p_perp = 0): compare on the common scale
+    scale = max(np.hypot(*pr[k]) for pr in golden["pairs"] for k in ("C", "D", "A", "B"))
+    n_scale = max(max(pr["N_line1"], pr["N_line2"]) for pr in golden["pairs"])
+    for r, pr in zip(res, golden["pairs"]):
+        for j, key in enumerate(("C", "D", "A", "B")):
+            got = complex(r.amp[2 * j], r.amp[2 * j + 1])
+            assert abs(got - complex(*pr[key])) <= 1e-10 * scale, (pr["r"], key)
+        assert abs(r.prob[0] - pr["N_line2"]) <= 1e-9 * n_scale
+        assert abs(r.prob[1] - pr["N_line1"]) <= 1e-9 * n_scale
+        assert abs(r.diag[0] - golden["norm_u"]) <= 1e-10 * golden["norm_u"]
+        assert abs(r.diag[1] - pr["norm_v"]) <= 1e-10 * pr["norm_v"]
+    modes = np.array(golden["spectrum_modes"])
+    ref = np.array(golden["spectrum_prob"])
+    assert np.max(np.abs(spec[modes] - ref)) <= 1e-10 * ref.max()
+
+
+def test_full_3d_grid_conserves_the_norm_of_the_full_wave(env):
+    """(3+1)D at the workload's full grid (256^3, box 48, its field): for a grid-mode momentum the
+    full wave psi_b + psi_s evolves unitarily, so ||psi_b + psi_s||^2 = L^3 at t_in (a property
+    that holds at any size), and the zero field gives exactly zero."""
+    torch, swf, ctx = env
+    L = 48.0
+    p = (2 * np.pi / L * 3, 0.0, 0.0)
+    # the workload's step (h = 0.025: |kappa|_max h = 0.42, inside the Dormand-Prince region)
+    base = dict(n=(256, 256, 256), L=(L, L, L), t_in=-0.75, t_out=0.75, n_steps=60, p=p, s=1,
+                q=(-p[0], 0.0, 0.0), r=1, k=(0, 0, 0), eps=(0, 0, 0), flags=())
+    d = dict(base, field=("sauter_gauss", (0.3, 0.4, 6.0)))
+    N = 256 ** 3
+    out = torch.zeros(2 * 4 * N, dtype=torch.float32, device="cuda")
+    ctx.march_dev([swf.from_workload(d)], out, bg=0, prec=swf.C64)
+    psi = torch.view_as_complex(out.view(4, N, 2))
+    assert float(psi.abs().max()) > 1e-3  # the field acts
+    dx = L / 256
+    x = -L / 2 + dx * torch.arange(256, device="cuda", dtype=torch.float64)
+    p0 = float(np.sqrt(1 + p[0] ** 2))
+    ph = torch.exp(1j * (p[0] * x - p0 * d["t_in"]))  # e^{-i(p0 t - p.x)} along x
+    u = O.u_spinor(np.array(p), 1)
+    total = 0.0
+    for c in range(4):
+        wave = (complex(u[c]) * ph).to(torch.complex128)
+        full = psi[c].view(256, 256, 256).to(torch.complex128) + wave.view(1, 1, 256)
+        total += float((full.abs() ** 2).sum()) * dx ** 3
+        del full
+    assert abs(total - L ** 3) <= 2e-5 * L ** 3, (total, L ** 3)
+    z = dict(base, field=("zero", (0.0,)))
+    out.zero_()
+    ctx.march_dev([swf.from_workload(z)], out, bg=0, prec=swf.C64)
+    assert float(out.abs().max()) == 0.0
