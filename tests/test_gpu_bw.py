@@ -106,3 +106,22 @@ def test_bw_graph_replay_matches_plain_launches():
         res.append(list(r[0].amp) + list(r[0].prob))
         ctx.close()
     assert res[0] == res[1]
+
+
+def test_full_size_instance_matches_stored_oracle(env):
+    """One instance of the Breit-Wheeler uneven-grid workload at full size (192^2, 2605 steps),
+    against oracle values written by tests/golden/make_full_size_reference.py, in complex128 and
+    in the workload's complex64."""
+    swf, ctx = env
+    from paper_2512_16889_gb300 import workloads as W
+    golden = json.load(open(os.path.join(GOLDEN, "bw_uneven_sample.json")))
+    d = W.bw_uneven()[golden["instance"]]
+    M = complex(*golden["M"])
+    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+        res, _ = ctx.solve([swf.from_workload(d)], swf.BREIT_WHEELER, prec)
+        got = [complex(res[0].amp[2 * j], res[0].amp[2 * j + 1]) for j in range(4)]
+        assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        for j in range(3):
+            ref = complex(*golden["terms"][j])
+            assert abs(got[j] - ref) <= tol * max(abs(ref), abs(M)), (prec, j)
+        assert abs(res[0].diag[0] - golden["norm_u"]) <= 10 * tol * golden["norm_u"]
