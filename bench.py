@@ -412,6 +412,46 @@ def run_surrogate_scan(args):
     return 0
 
 
+def run_cross_section(args):
+    """The paper's (2+1)D momentum cross sections (Sec. V, Eqs. 11-12): N(p_1, q_1) on a 100 x 100
+    grid through swf_pair_matrix (complex64 march, FP64 overlaps), for the single field
+    (--workload cross_section_single) or the double field (cross_section_double).  Reports
+    pairs/s and where the spectrum peaks."""
+    import numpy as np
+    import torch
+    from paper_2512_16889_gb300 import build, swf
+    from paper_2512_16889_gb300 import workloads as W
+    build.build()
+    kind = "single_e" if args.workload.endswith("single") else "double_e"
+    els, pos = W.paper_cross_section(kind)
+    E = [swf.from_workload(d) for d in els]
+    P = [swf.from_workload(d) for d in pos]
+    ctx = swf.Context(0)
+    ctx.pair_matrix(E[:2], P[:2], swf.C64)  # warm-up
+    times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mat = ctx.pair_matrix(E, P, swf.C64)
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    N = np.array([[mat[m][n].prob[0] for n in range(len(P))] for m in range(len(E))])
+    m, n = np.unravel_index(np.argmax(N), N.shape)
+    d = els[0]
+    line = {"metric": "full pair numbers N(m, n)/s", "value": N.size / t, "unit": "pairs/s", "n_gpus": 1,
+            "steps": len(times), "warmup": 1, "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": f"cross_section: {kind}, E0 = 1/4, omega = E0, "
+                                                         f"kappa_x = kappa_y = E0/2, 100 x 100 (p1, q1)",
+                                             "grid": list(d["n"]), "box": list(d["L"]), "window": [d["t_in"], d["t_out"]],
+                                             "n_steps": d["n_steps"], "precision": "complex64 march, FP64 overlaps"},
+            "peak": {"p1": els[m]["p"][0], "q1": pos[n]["q"][0], "N": float(N[m, n])},
+            "two_lines_max_rel_diff": float(np.max(np.abs(
+                np.array([[mat[i][j].prob[1] for j in range(len(P))] for i in range(len(E))]) - N)) / N.max())}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_pair_scan(args):
     """Times the all-pairs full pair number on one GPU: 128 electrons x 128 positrons of one
     field on the 256^2 grid (1000 steps, complex64 march, FP64 overlaps) through swf_pair_matrix:
@@ -551,6 +591,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "pair_scan":
         return run_pair_scan(args)
+    if args.workload in ("cross_section_single", "cross_section_double"):
+        return run_cross_section(args)
     if args.workload == "surrogate_scan":
         return run_surrogate_scan(args)
     if args.workload:

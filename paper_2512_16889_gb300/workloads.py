@@ -76,6 +76,32 @@ def pair_scan(n=256, L=40.0, n_steps=1000, t_window=20.0, n_p=8, E=0.3, omega=0.
     return els, pos
 
 
+def paper_cross_section(kind="single_e", n_p=100, h=0.1):
+    """The (2+1)D momentum cross sections of Sec. V (Eqs. 11-12): E0 = 1/4, omega = E0,
+    kappa_x = kappa_y = E0/2 (and Delta x = 1.75/kappa_x for the double field), p_2 = p_3 = q_2 =
+    q_3 = 0, spins s = r = +1, and an n_p x n_p grid of (p_1, q_1).  Box and window are readings
+    (the text gives neither): a 128 x 64 box at 0.5 spacing (the field's Gaussian is below
+    exp(-16) at its edge, also for the double field's peaks at +-14), the window where exp(-(omega
+    t)^2) falls below exp(-20), fixed step h.  The momenta are the box's modes p_1 = 2 pi k/128,
+    k = -n_p/2 .. n_p/2 - 1 (p_1 in [-2.45, 2.40] for n_p = 100), so that both lines of Eq. 8
+    agree on the grid.  Returns (electrons, positrons)."""
+    E0 = 0.25
+    kx = ky = E0 / 2
+    if kind == "single_e":
+        field = ("single_e", (E0, E0, kx, ky, 0.0))
+    else:
+        field = ("double_e", (E0, E0, kx, ky, 0.0, 1.75 / kx))
+    Lx, Ly = 128.0, 64.0
+    nx, ny = 256, 128
+    t_w = 4.0 / E0 + 2.0
+    n_steps = int(round(2 * t_w / h))
+    ps = 2 * np.pi / Lx * np.arange(-(n_p // 2), n_p - n_p // 2)
+    base = (field, (nx, ny, 1), (Lx, Ly, 1.0), -t_w, t_w, n_steps)
+    els = [_inst(*base, p=(float(p), 0.0, 0.0), s=1, q=(0.0, 0.0, 0.0), r=1) for p in ps]
+    pos = [_inst(*base, p=(0.0, 0.0, 0.0), s=1, q=(float(q), 0.0, 0.0), r=1) for q in ps]
+    return els, pos
+
+
 def bw_uneven(count=128, sizes=(192, 256, 320, 384), seed=7, h=0.05, a0=1.0, omega0=0.5, tau=10.0, w=8.0):
     L = 16.0 * math.pi
     ns = np.random.default_rng(seed).choice(list(sizes), count)
