@@ -478,10 +478,13 @@ def run_pair_scan(args):
     t = min(times)
     ctx.profile_read()
     ctx.profile_enable(True)
-    ctx.pair_matrix(E, P, swf.C64)
+    mat = ctx.pair_matrix(E, P, swf.C64)
     ctx.profile_enable(False)
     prof, _ = ctx.profile_read()
     n_pairs = len(E) * len(P)
+    import numpy as np
+    l2 = np.array([[r.prob[0] for r in row] for row in mat])
+    l1 = np.array([[r.prob[1] for r in row] for row in mat])
     su = marched * 256 * 256 * els[0]["n_steps"]  # site-updates actually marched
     line = {"metric": "full pair numbers N(m, n)/s", "value": n_pairs / t, "unit": "pairs/s", "n_gpus": 1,
             "steps": len(times), "warmup": 1, "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f32",
@@ -489,6 +492,7 @@ def run_pair_scan(args):
                                              "electrons": len(E), "positrons": len(P),
                                              "precision": "complex64 march, FP64 overlaps"},
             "site_updates_per_s": su / t, "fields": len(E) + len(P), "fields_marched": marched,
+            "max_N": float(l2.max()), "two_lines_max_rel_diff": float(np.max(np.abs(l1 - l2)) / l2.max()),
             "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -63,9 +63,11 @@ def schwinger_batched(n=256, L=40.0, n_steps=1000, t_window=20.0, n_p=8, omega=0
 
 def pair_scan(n=256, L=40.0, n_steps=1000, t_window=20.0, n_p=8, E=0.3, omega=0.5, lam=5.0):
     """A momentum scan in one field (the batched workload's grid and window at E = 0.3):
-    electrons (s, p) over an n_p x n_p momentum lattice in [-1, 1]^2 and both spins, and the
-    positrons (r, q = -p) of the same lattice, for the all-pairs full pair number."""
-    ps = np.linspace(-1.0, 1.0, n_p)
+    electrons (s, p) over an n_p x n_p lattice of grid momenta (every second mode, 2 pi k/L,
+    k = -8, -6, .., 6: p in [-1.26, 0.94]) and both spins, and the positrons (r, q = -p) of the
+    same lattice, for the all-pairs full pair number (grid momenta, so that both lines of Eq. 8
+    agree)."""
+    ps = 2 * np.pi / L * 2 * (np.arange(n_p) - n_p // 2)
     base = (("sauter_gauss", (E, omega, lam)), (n, n, 1), (L, L, 1.0), -t_window, t_window, n_steps)
     els, pos = [], []
     for px in ps:
