@@ -349,6 +349,61 @@ def dopri5_march(f, y0, t_out: float, t_in: float, n_steps: int, stage_hook=None
     return y, acc
 
 
+def dopri5_adaptive(f, y0, t_out: float, t_in: float, h0: float, rtol: float, atol: float, max_attempts: int):
+    """Dormand-Prince 5(4) with step-size control (the integrator Sec. II.A names: Dopri5 with
+    relative and absolute tolerances), from t_out down to t_in (h < 0), first-same-as-last.
+
+    Error of a step: e = h sum_i (b_i - b*_i) k_i (fifth- minus fourth-order solution); scaled
+    norm err = sqrt(mean(|e|^2 / (atol + rtol max(|y_n|, |y_n+1|))^2)) over all complex entries.
+    The step is accepted when err <= 1; the next step is h * min(10, max(0.2, 0.9 err^(-1/5)))
+    (the standard integral controller), never passing t_in.  Returns (y(t_in), accepted,
+    rejected).
+    """
+    c = [float(v) for v in DP_C]
+    a = [[float(v) for v in row] for row in DP_A]
+    db = [float(DP_B[j] - DP_BSTAR[j]) for j in range(7)]
+    y = y0.copy()
+    t = t_out
+    span = abs(t_in - t_out)
+    h = -abs(h0) if t_in < t_out else abs(h0)
+    k = [f(t, y)] + [None] * 6
+    accepted = rejected = 0
+    while abs(t_in - t) > 1e-12 * span:
+        if accepted + rejected >= max_attempts:
+            raise RuntimeError("adaptive march: too many attempts")
+        if abs(h) > abs(t_in - t):
+            h = t_in - t
+        for i in range(1, 7):
+            yi = y.copy()
+            for j in range(i):
+                if a[i][j] != 0.0:
+                    yi = yi + (h * a[i][j]) * k[j]
+            k[i] = f(t + c[i] * h, yi)
+        y_new = yi
+        e = h * sum(db[j] * k[j] for j in range(7) if db[j] != 0.0)
+        sc = atol + rtol * np.maximum(np.abs(y), np.abs(y_new))
+        err = float(np.sqrt(np.mean((np.abs(e) / sc) ** 2)))
+        fac = 10.0 if err == 0.0 else min(10.0, max(0.2, 0.9 * err ** -0.2))
+        if err <= 1.0:
+            t = t + h
+            y = y_new
+            k[0] = k[6]
+            accepted += 1
+        else:
+            rejected += 1
+        h = h * fac
+    return y, accepted, rejected
+
+
+def march_scattered_adaptive(fld: Field, grid: Grid, bg: Background, t_in, t_out, h0, rtol, atol,
+                             max_attempts=100000):
+    """psi_scat(t_in) of Eqs. 6-7 with the step-size-controlled march."""
+    h0f = h0_field(grid, bg.offset())
+    y0 = np.zeros((4,) + grid.n, dtype=complex)
+    return dopri5_adaptive(lambda t, y: rhs(fld, grid, bg, h0f, t, y), y0, t_out, t_in, h0, rtol, atol,
+                           max_attempts)
+
+
 def march_scattered(fld: Field, grid: Grid, bg: Background, t_in, t_out, n_steps):
     """psi_scat(t_in) for psi_scat(t_out) = 0 (Eq. 7), marched backward through Eq. 6."""
     h0 = h0_field(grid, bg.offset())

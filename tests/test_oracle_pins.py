@@ -424,3 +424,24 @@ def test_spectral_convergence_under_grid_refinement():
     errs = [np.max(np.abs(np.array(c_at(n)) - ref)) / np.max(np.abs(ref)) for n in (12, 18, 24, 36)]
     assert all(errs[i] > 10 * errs[i + 1] for i in range(3)), errs
     assert errs[-1] < 1e-9, errs
+
+
+def test_adaptive_dopri5_error_follows_the_tolerance():
+    """The step-size-controlled march: its global error against a converged fixed-step march
+    falls in proportion to the tolerance (Dormand-Prince 5(4) with the integral controller), a
+    too-large first step is rejected and retried, and A = 0 stays exactly zero in a few steps."""
+    fld = O.Field("sauter_gauss", (0.8, 0.6, 2.5))
+    grid = O.Grid((16, 16, 1), (12.0, 12.0, 1.0))
+    bg = O.Background("U", (0.3, -0.2, 0.0), 1)
+    ref = O.march_scattered(fld, grid, bg, -6.0, 6.0, 4000)
+    errs, steps = [], []
+    for rtol in (1e-4, 1e-6):
+        y, na, nr = O.march_scattered_adaptive(fld, grid, bg, -6.0, 6.0, 0.1, rtol, 1e-10)
+        errs.append(np.max(np.abs(y - ref)) / np.max(np.abs(ref)))
+        steps.append(na)
+    assert errs[0] < 20 * 1e-4 and errs[1] < 20 * 1e-6 and errs[1] < errs[0] / 50, errs
+    assert steps[1] > steps[0]
+    y, na, nr = O.march_scattered_adaptive(fld, grid, bg, -6.0, 6.0, 3.0, 1e-5, 1e-10)
+    assert nr > 0 and np.max(np.abs(y - ref)) / np.max(np.abs(ref)) < 2e-3
+    y0, na0, nr0 = O.march_scattered_adaptive(O.Field("zero"), grid, bg, -6.0, 6.0, 0.1, 1e-5, 1e-10)
+    assert np.all(y0 == 0) and na0 <= 4 and nr0 == 0
