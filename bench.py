@@ -525,6 +525,10 @@ def run_workload(args):
         raise SystemExit(f"unknown workload {name}")
     if args.limit:
         ds = ds[:args.limit]
+    if args.adaptive:
+        if process != swf.SCHWINGER:
+            raise SystemExit("--adaptive applies to Schwinger workloads")
+        ds = [dict(d, flags=tuple(d.get("flags", ())) + ("adaptive",)) for d in ds]
     if args.max_steps:
         for d in ds:
             if d["n_steps"] > args.max_steps:
@@ -548,12 +552,16 @@ def run_workload(args):
     ctx.solve(insts, process, prec)
     ctx.profile_enable(False)
     prof, _ = ctx.profile_read()
+    if args.adaptive:  # site-updates of the accepted steps (the last march's count for every field)
+        su = sum(int(np.prod(d["n"])) * ctx.march_stats()[0] * fields for d in ds)
     line = {"metric": METRIC, "value": su / t, "unit": UNIT, "n_gpus": 1, "steps": len(times), "warmup": 1,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f64" if prec == swf.C128 else "f32",
             "data": "synthetic", "config": {"workload": name, "instances": len(ds),
                                              "n_steps": ds[0]["n_steps"], "grids": sorted({d["n"] for d in ds}),
                                              "precision": "complex128" if prec == swf.C128 else "complex64"},
             "results_per_s": len(ds) / t, "site_updates_per_step": su,
+            "step_control": ({"rtol": 1e-5, "atol": 1e-10, "accepted_rejected": ctx.march_stats()}
+                             if args.adaptive else None),
             "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -588,6 +596,7 @@ def main():
     ap.add_argument("--workload", default=None, help="time another workload (see run_workload)")
     ap.add_argument("--limit", type=int, default=0, help="at most this many instances (--workload)")
     ap.add_argument("--max-steps", type=int, default=0, help="at most this many steps (--workload)")
+    ap.add_argument("--adaptive", action="store_true", help="step-size-controlled marches (--workload, Schwinger)")
     args = ap.parse_args()
     if args.small_march:
         return run_small_march(args)

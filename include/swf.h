@@ -98,6 +98,10 @@ typedef struct {
 
 #define SWF_WANT_SPECTRUM 1  /* Schwinger: |C(m,(r,q))|^2 for every grid positron q */
 #define SWF_WANT_FULL_N   2  /* Schwinger: march V too and return both lines of Eq. 8 */
+#define SWF_ADAPTIVE      4  /* Schwinger: step-size-controlled march (Sec. II.A: Dopri5 with relative and
+                                absolute tolerances, swf_set_tolerances); the first step is
+                                (t_in - t_out)/n_steps and at most 100 n_steps + 100 attempts are made
+                                (SWF_ENUMERIC beyond); pass kernels only */
 
 /* Per-instance scalar results (complex values as (re, im) pairs).
  * Schwinger: amp = {C(m,n), D(m,n), A(m,n), B(m,n)} for the listed positron n = (r, q);
@@ -190,6 +194,15 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
  * CTAs per SM (2 and 3 still fall back to the pass kernels where the fused kernel does not
  * apply). */
 swf_status swf_set_march_path(swf_ctx* ctx, int path);
+
+/* Tolerances of step-size-controlled marches (SWF_ADAPTIVE): a Dormand-Prince 5(4) step is
+ * accepted when the RMS over the field's complex entries of |e|/(atol + rtol max(|y_n|, |y_n+1|))
+ * is at most 1 (the largest over the fields of one call), e the difference of the fifth- and
+ * fourth-order solutions; the next step is h min(10, max(0.2, 0.9 err^(-1/5))).  Defaults: the
+ * paper's rtol = 1e-5, atol = 1e-10 (Sec. II.A). */
+swf_status swf_set_tolerances(swf_ctx* ctx, double rtol, double atol);
+/* Accepted and rejected steps of the context's last step-size-controlled march. */
+swf_status swf_march_stats(swf_ctx* ctx, long long* accepted, long long* rejected);
 
 /* Repeated marches.  on = 1 (default): within one call, a field whose march repeats another's
  * is marched once: the same field, window and background wave, or (with the z axis trivial,

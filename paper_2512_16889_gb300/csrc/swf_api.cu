@@ -338,9 +338,10 @@ struct GroupKey {
   double t_in, t_out;
   int n_steps;
   int full;
+  int adaptive = 0;
   bool operator<(const GroupKey& o) const {
-    return std::tie(n[0], n[1], n[2], L[0], L[1], L[2], t_in, t_out, n_steps, full) <
-           std::tie(o.n[0], o.n[1], o.n[2], o.L[0], o.L[1], o.L[2], o.t_in, o.t_out, o.n_steps, o.full);
+    return std::tie(n[0], n[1], n[2], L[0], L[1], L[2], t_in, t_out, n_steps, full, adaptive) <
+           std::tie(o.n[0], o.n[1], o.n[2], o.L[0], o.L[1], o.L[2], o.t_in, o.t_out, o.n_steps, o.full, o.adaptive);
   }
 };
 
@@ -357,6 +358,7 @@ static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* 
     k.t_out = in.grid.t_out;
     k.n_steps = in.grid.n_steps;
     k.full = (in.flags & SWF_WANT_FULL_N) ? 1 : 0;
+    k.adaptive = (in.flags & SWF_ADAPTIVE) ? 1 : 0;
     groups[k].push_back(i);
     if (in.flags & SWF_WANT_SPECTRUM) {
       spec_off[i] = off;
@@ -399,7 +401,8 @@ static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* 
     if ((s = ws_get(ctx, "solve.uq", (size_t)F * 64, &uq)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "solve.normU", (size_t)F * 8, &normU)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "solve.inst", sizeof(InstDev) * F, &pid)) != SWF_OK) return s;
-    if ((s = march_fields(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, F, fdU.data(), prec, psiU, st)) != SWF_OK)
+    if ((s = march_fields(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, F, fdU.data(), prec, psiU, st,
+                          kv.first.adaptive)) != SWF_OK)
       return s;
     if ((s = transform_at(ctx, g, F, prec, psiU, kq.data(), (double2*)uq, st)) != SWF_OK) return s;
     if ((s = field_norms(ctx, g, F, prec, psiU, (double*)normU, st)) != SWF_OK) return s;
@@ -423,7 +426,8 @@ static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* 
       if ((s = ws_get(ctx, "solve.specV", state * 16, &specV)) != SWF_OK) return s;
       if ((s = ws_get(ctx, "solve.vp", (size_t)F * 64, &vp)) != SWF_OK) return s;
       if ((s = ws_get(ctx, "solve.normV", (size_t)F * 8, &normV)) != SWF_OK) return s;
-      if ((s = march_fields(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, F, fdV.data(), prec, psiV, st)) != SWF_OK)
+      if ((s = march_fields(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, F, fdV.data(), prec, psiV, st,
+                            kv.first.adaptive)) != SWF_OK)
         return s;
       if ((s = transform_fields(ctx, g, F, prec, psiV, (double2*)specV, st)) != SWF_OK) return s;
       if ((s = transform_at(ctx, g, F, prec, psiV, kp.data(), (double2*)vp, st)) != SWF_OK) return s;
@@ -457,6 +461,10 @@ static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, s
     k.n_steps = in.grid.n_steps;
     k.full = 0;
     groups[k].push_back(i);
+    if (in.flags & SWF_ADAPTIVE) {
+      set_error("instance " + std::to_string(i) + ": step-size control is for Schwinger marches (fixed steps here)");
+      return SWF_EUNSUPPORTED;
+    }
     // the photon momentum must be a grid mode; along trivial axes momentum is conserved
     for (int a = 0; a < 3; ++a) {
       if (in.grid.n[a] > 1) {
@@ -621,6 +629,23 @@ swf_status swf_set_march_path(swf_ctx* ctx, int path) {
   return SWF_OK;
 }
 
+swf_status swf_set_tolerances(swf_ctx* ctx, double rtol, double atol) {
+  if (!ctx || !(rtol > 0.0) || !(atol > 0.0) || !std::isfinite(rtol) || !std::isfinite(atol)) {
+    set_error("swf_set_tolerances: need ctx and positive finite rtol, atol");
+    return SWF_EINVAL;
+  }
+  ctx->rtol = rtol;
+  ctx->atol = atol;
+  return SWF_OK;
+}
+
+swf_status swf_march_stats(swf_ctx* ctx, long long* accepted, long long* rejected) {
+  if (!ctx || !accepted || !rejected) { set_error("swf_march_stats: NULL argument"); return SWF_EINVAL; }
+  *accepted = ctx->last_accepted;
+  *rejected = ctx->last_rejected;
+  return SWF_OK;
+}
+
 swf_status swf_set_dedupe(swf_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) { set_error("swf_set_dedupe: ctx NULL or on not 0 or 1"); return SWF_EINVAL; }
   ctx->dedupe = on != 0;
@@ -694,8 +719,8 @@ swf_status swf_march_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst, int
   for (int i = 1; i < n_inst; ++i) {
     const swf_grid &a = inst[0].grid, &b = inst[i].grid;
     if (std::memcmp(a.n, b.n, sizeof a.n) || a.n_steps != b.n_steps || a.t_in != b.t_in || a.t_out != b.t_out ||
-        std::memcmp(a.L, b.L, sizeof a.L)) {
-      set_error("swf_march_dev: all instances must share the grid and time window");
+        std::memcmp(a.L, b.L, sizeof a.L) || ((inst[0].flags ^ inst[i].flags) & SWF_ADAPTIVE)) {
+      set_error("swf_march_dev: all instances must share the grid, time window and step control");
       return SWF_EINVAL;
     }
   }
@@ -705,7 +730,7 @@ swf_status swf_march_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst, int
   for (int i = 0; i < n_inst; ++i) fd[i] = make_field_desc(inst[i], bg);
   const GridDesc g = make_grid(inst[0].grid);
   s = march_fields(ctx, g, inst[0].grid.t_in, inst[0].grid.t_out, inst[0].grid.n_steps, n_inst, fd.data(), prec,
-                   psi_out_dev, st);
+                   psi_out_dev, st, (inst[0].flags & SWF_ADAPTIVE) ? 1 : 0);
   if (s != SWF_OK) return s;
   cudaError_t e = cudaStreamSynchronize(st);  // fd lives on this stack frame
   if (e != cudaSuccess) return cuda_status(e, "march synchronisation");

@@ -123,6 +123,8 @@ struct swf_ctx {
   bool use_fused = true;  // route eligible marches to the fused cluster kernel
   bool dedupe = true;     // march fields that repeat another (the other spin) once
   bool use_graphs = true; // replay pass-kernel march steps from CUDA graphs
+  double rtol = 1e-5, atol = 1e-10;  // step-size control (SWF_ADAPTIVE), the paper's tolerances
+  long long last_accepted = 0, last_rejected = 0;  // steps of the last controlled march
   long long fields_marched = 0;  // fields actually marched since the last profile read
   int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
 };
@@ -156,7 +158,10 @@ swf_status twiddles(swf_ctx* ctx, int n, int is_double, const void** ptr);
 // in the march precision [F][4][N].  fd_host: n_f descriptors.
 swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
                         int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
-                        cudaStream_t st);
+                        cudaStream_t st, int adaptive = 0);
+// Step-size-controlled march (first step h0, at most max_attempts attempts; tolerances from ctx)
+swf_status march_adaptive(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, double h0, int max_attempts,
+                          int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out, cudaStream_t st);
 // Breit-Wheeler: march U (fields 2i) and V (fields 2i+1) together and accumulate the appended
 // integral M(t) of Eq. 34 for (ss, bs, sb) into macc [n_inst][3] (M_finite = -M(t_in)).
 // photon_host: per instance k[3], eps[3].

@@ -52,6 +52,19 @@ struct StageArgs {
   const struct MarchClock* clk;  // march clock (graph replays), or null
   int ls;               // step within the replayed pair of steps (0 or 1)
   double c;             // Dormand-Prince node c_i of the stage
+  const struct StepControl* ctl;  // step-size-controlled march, or null (see march_adaptive)
+  cpx<R>* ynew;         // with ctl: the last stage writes the step's result here, not into y
+};
+
+// State of a step-size-controlled march, in device memory: the accepted time t and the step h
+// of the current attempt (the stage times are t + c_i h and the stage coefficients h a_ij), the
+// tolerances, counters and flags.  One thread of k_step_control updates it after every attempt.
+struct StepControl {
+  double t, h, t_in, span, rtol, atol;
+  int done;        // t_in reached, or the march failed: later attempts do nothing
+  int ok;          // the last attempt was accepted (its result and k_7 are copied in)
+  int failed;      // too many attempts or a non-finite error
+  int accepted, rejected, max_attempts;
 };
 
 // Device clock of a march whose steps are replayed from a CUDA graph: the stage time is
@@ -65,6 +78,7 @@ struct MarchClock {
 
 template <typename R>
 __device__ __forceinline__ double stage_time(const StageArgs<R>& A) {
+  if (A.ctl) return A.ctl->t + A.c * A.ctl->h;
   if (!A.clk) return A.t;
   const double tn = A.clk->t_out + (A.clk->step + A.ls) * A.clk->h;
   return tn + A.c * A.clk->h;
@@ -411,9 +425,12 @@ static const size_t kPassSmem = 72 * 1024;
 // (and the whole derivative when x is the only non-trivial axis).
 template <typename R>
 __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
+  if (A.ctl && A.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* buf2 = buf + 4 * rows * ld;
+  const double hscale = A.ctl ? A.ctl->h : 1.0;  // stage coefficients are a_ij (times h here) under control
+  cpx<R>* const yout = A.ynew ? A.ynew : A.y;
   __shared__ double s_ft[64];
   __shared__ cpx<R> s_tf;
   const int f = blockIdx.y;
@@ -457,13 +474,13 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
 #pragma unroll
       for (int q = 0; q < 6; ++q)
         if (q < A.nterm) {
-          const R co = (R)A.coef[q];
+          const R co = (R)(A.coef[q] * hscale);
 #pragma unroll
           for (int c = 0; c < 4; ++c) v[c] = v[c] + co * A.kin[q][gi + c * cs];
         }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        if (A.write_y) A.y[gi + c * cs] = v[c];
+        if (A.write_y) yout[gi + c * cs] = v[c];
         if (A.ystage) A.ystage[gi + c * cs] = v[c];
       }
       // local term Z = -i V (Y + psi_b), kept in the output slot until the last pass
@@ -530,6 +547,7 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
 template <typename R>
 __global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int lgtx, int ld, int do_fwd, int do_h0,
                                              int do_inv) {
+  if (A.ctl && A.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   const int f = blockIdx.y;
@@ -592,6 +610,7 @@ __global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int lgtx,
 // x lines: inverse x-FFT, k = (that) + Z.
 template <typename R>
 __global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) {
+  if (A.ctl && A.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* buf2 = buf + 4 * rows * ld;
@@ -1059,6 +1078,277 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
   return SWF_OK;
 }
 
+// ---------------------------------------------------------------- step-size control
+// Fifth- minus fourth-order weights b_i - b*_i of the Dormand-Prince pair (1980).
+static const double DP_DB[7] = {35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695,
+                                125.0 / 192 - 393.0 / 640, -2187.0 / 6784 + 92097.0 / 339200,
+                                11.0 / 84 - 187.0 / 2100, -1.0 / 40};
+
+struct ErrWeights {
+  double db[7];
+};
+
+// part[f][b] = sum over block b's entries of field f of (|e| / (atol + rtol max(|y|, |y_new|)))^2,
+// e = h sum_i (b_i - b*_i) k_i, in FP64 (fixed order inside the block).
+template <typename R>
+__global__ void __launch_bounds__(256) k_step_error(const cpx<R>* __restrict__ y, const cpx<R>* __restrict__ ynew,
+                                                    const cpx<R>* k0, const cpx<R>* k1, const cpx<R>* k2,
+                                                    const cpx<R>* k3, const cpx<R>* k4, const cpx<R>* k5,
+                                                    const cpx<R>* k6, ErrWeights W, const StepControl* ctl,
+                                                    size_t per_field, double* part) {
+  __shared__ double red[8];
+  if (ctl->done) return;
+  const int f = blockIdx.y;
+  const double h = ctl->h, rtol = ctl->rtol, atol = ctl->atol;
+  const cpx<R>* ks[7] = {k0, k1, k2, k3, k4, k5, k6};
+  double acc = 0.0;
+  const size_t off = (size_t)f * per_field;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per_field; i += (size_t)gridDim.x * blockDim.x) {
+    double ex = 0.0, ey = 0.0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      if (W.db[j] == 0.0) continue;
+      const cpx<R> kv = ks[j][off + i];
+      ex += W.db[j] * (double)kv.x;
+      ey += W.db[j] * (double)kv.y;
+    }
+    const cpx<R> a = y[off + i], b = ynew[off + i];
+    const double ya = sqrt((double)a.x * a.x + (double)a.y * a.y), yb = sqrt((double)b.x * b.x + (double)b.y * b.y);
+    const double sc = atol + rtol * fmax(ya, yb);
+    acc += h * h * (ex * ex + ey * ey) / (sc * sc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < 8; ++w) sum += red[w];
+    part[(size_t)f * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+// One thread: err = max over fields of the RMS scaled error; accept when err <= 1 (and finite);
+// next step h min(10, max(0.2, 0.9 err^(-1/5))), clamped so as not to pass t_in.
+__global__ void k_step_control(StepControl* ctl, const double* part, int nb, int F, double count) {
+  if (threadIdx.x != 0 || ctl->done) {
+    if (threadIdx.x == 0) ctl->ok = 0;
+    return;
+  }
+  double err = 0.0;
+  for (int f = 0; f < F; ++f) {
+    double sum = 0.0;
+    for (int b = 0; b < nb; ++b) sum += part[(size_t)f * nb + b];
+    err = fmax(err, sqrt(sum / count));
+  }
+  if (!(err == err) || isinf(err)) {  // non-finite: stop
+    ctl->ok = 0;
+    ctl->failed = 1;
+    ctl->done = 1;
+    return;
+  }
+  const double fac = err == 0.0 ? 10.0 : fmin(10.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+  if (err <= 1.0) {
+    ctl->t += ctl->h;
+    ctl->ok = 1;
+    ctl->accepted += 1;
+  } else {
+    ctl->ok = 0;
+    ctl->rejected += 1;
+  }
+  double h = ctl->h * fac;
+  const double rest = ctl->t_in - ctl->t;
+  if (fabs(rest) <= 1e-12 * ctl->span) {
+    ctl->done = 1;
+  } else if (fabs(h) > fabs(rest)) {
+    h = rest;
+  }
+  ctl->h = h;
+  if (!ctl->done && ctl->accepted + ctl->rejected >= ctl->max_attempts) {
+    ctl->failed = 1;
+    ctl->done = 1;
+  }
+}
+
+// After an accepted attempt: y <- y_new and k_1 <- k_7 (first same as last).
+template <typename R>
+__global__ void k_step_accept(const StepControl* ctl, cpx<R>* y, const cpx<R>* ynew, cpx<R>* k1, const cpx<R>* k7,
+                              size_t n) {
+  if (!ctl->ok) return;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    y[i] = ynew[i];
+    k1[i] = k7[i];
+  }
+}
+
+// Step-size-controlled march (Sec. II.A: Dopri5 with relative and absolute tolerances), from
+// t_out with first step h0 toward t_in.  Every attempt (six evaluations, the error norm, the
+// controller, the copy-in of an accepted step) is one CUDA graph replay; nothing is decided on
+// the host: after t_in (or a failure) the remaining replays of a chunk do nothing.  The host
+// reads the controller's state once per chunk of replays.
+template <typename R>
+static swf_status march_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, double h0,
+                                      int max_attempts, int F, const FieldDesc* fd_host, void* psi_out,
+                                      cudaStream_t st) {
+  StageArgs<R> A;
+  swf_status s = prepare_args<R>(ctx, g, F, fd_host, &A, "march", st);
+  if (s != SWF_OK) return s;
+  const size_t per_field = (size_t)4 * g.N;
+  const size_t state = (size_t)F * per_field * sizeof(cpx<R>);
+  void *py = nullptr, *pyn = nullptr, *pT = nullptr, *pk[7], *pctl = nullptr, *ppart = nullptr;
+  if ((s = ws_get(ctx, "march.y", state, &py)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.ynew", state, &pyn)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.T", state, &pT)) != SWF_OK) return s;
+  for (int i = 0; i < 7; ++i) {
+    char nm[32];
+    std::snprintf(nm, sizeof nm, "march.k%d", i);
+    if ((s = ws_get(ctx, nm, state, &pk[i])) != SWF_OK) return s;
+  }
+  const int nbe = (int)std::max<size_t>(1, std::min<size_t>((per_field + 4095) / 4096, 64));
+  if ((s = ws_get(ctx, "march.ctl", sizeof(StepControl), &pctl)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.err_part", sizeof(double) * (size_t)nbe * F, &ppart)) != SWF_OK) return s;
+  cudaError_t e = cudaMemsetAsync(py, 0, state, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset state");
+  StepControl c0{};
+  c0.t = t_out;
+  c0.h = (t_in < t_out) ? -std::fabs(h0) : std::fabs(h0);
+  if (std::fabs(c0.h) > std::fabs(t_in - t_out)) c0.h = t_in - t_out;
+  c0.t_in = t_in;
+  c0.span = std::fabs(t_in - t_out);
+  c0.rtol = ctx->rtol;
+  c0.atol = ctx->atol;
+  c0.max_attempts = max_attempts;
+  StepControl* ctl = (StepControl*)pctl;
+  e = cudaMemcpyAsync(ctl, &c0, sizeof(StepControl), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload step control");
+  A.y = (cpx<R>*)py;
+  A.T = (cpx<R>*)pT;
+  {
+    StageArgs<R> B = A;  // shapes by timing, before the slots hold anything
+    B.nterm = 6;
+    for (int q = 0; q < 6; ++q) {
+      B.kin[q] = (const cpx<R>*)pk[q + 1];
+      B.coef[q] = 0.0;
+    }
+    B.write_y = 0;
+    B.ystage = nullptr;
+    B.kout = (cpx<R>*)pk[0];
+    B.t = t_out;
+    if ((s = autotune_eval<R>(ctx, B, F, st)) != SWF_OK) return s;
+  }
+  // k_1 = f(t_out, 0)
+  A.nterm = 0;
+  A.write_y = 0;
+  A.kout = (cpx<R>*)pk[0];
+  A.t = t_out;
+  if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  A.ctl = ctl;
+  A.ynew = (cpx<R>*)pyn;
+  ErrWeights W;
+  for (int j = 0; j < 7; ++j) W.db[j] = DP_DB[j];
+  auto attempt = [&]() -> swf_status {
+    for (int i = 1; i < 7; ++i) {
+      int nt = 0;
+      for (int j = 0; j < i; ++j) {
+        if (DP_A[i][j] == 0.0) continue;
+        A.kin[nt] = (const cpx<R>*)pk[j];
+        A.coef[nt] = DP_A[i][j];  // times the device-held h in k_first
+        ++nt;
+      }
+      A.nterm = nt;
+      A.write_y = (i == 6);
+      A.kout = (cpx<R>*)pk[i];
+      A.c = DP_C[i];
+      swf_status r = launch_eval<R>(ctx, A, F, st);
+      if (r != SWF_OK) return r;
+    }
+    {
+      ProfScope ps(ctx, "k_step_error", st);
+      k_step_error<R><<<dim3(nbe, F), 256, 0, st>>>(
+          (const cpx<R>*)py, (const cpx<R>*)pyn, (const cpx<R>*)pk[0], (const cpx<R>*)pk[1], (const cpx<R>*)pk[2],
+          (const cpx<R>*)pk[3], (const cpx<R>*)pk[4], (const cpx<R>*)pk[5], (const cpx<R>*)pk[6], W, ctl, per_field,
+          (double*)ppart);
+    }
+    {
+      ProfScope ps(ctx, "k_step_control", st);
+      k_step_control<<<1, 32, 0, st>>>(ctl, (const double*)ppart, nbe, F, (double)per_field);
+    }
+    {
+      ProfScope ps(ctx, "k_step_accept", st);
+      const size_t n = (size_t)F * per_field;
+      k_step_accept<R><<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(
+          ctl, (cpx<R>*)py, (const cpx<R>*)pyn, (cpx<R>*)pk[0], (const cpx<R>*)pk[6], n);
+    }
+    return SWF_OK;
+  };
+  // chunks of attempts, as graph replays (kernel by kernel when timing is on)
+  bool graph = !ctx->prof.on && st != 0 && ctx->use_graphs;
+  cudaGraphExec_t exec = nullptr;
+  long long per_attempt = 0;
+  if (graph) {
+    const long long l0 = ctx->prof.launches;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      graph = false;
+    } else {
+      s = attempt();
+      cudaGraph_t gr = nullptr;
+      e = cudaStreamEndCapture(st, &gr);
+      per_attempt = ctx->prof.launches - l0;
+      ctx->prof.launches = l0;
+      if (s != SWF_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_status(e, "capture of the step attempt");
+      e = cudaGraphInstantiate(&exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return cuda_status(e, "instantiate the step attempt");
+    }
+  }
+  StepControl hc{};
+  int chunk = 8, attempts = 0;
+  while (true) {
+    for (int a = 0; a < chunk; ++a) {
+      if (graph) {
+        e = cudaGraphLaunch(exec, st);
+        ctx->prof.launches += per_attempt;
+        if (e != cudaSuccess) break;
+      } else if ((s = attempt()) != SWF_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        return s;
+      }
+    }
+    attempts += chunk;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(StepControl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || hc.done) break;
+    if (attempts > max_attempts + chunk) {  // the controller stops at max_attempts; this is a backstop
+      hc.failed = 1;
+      break;
+    }
+    chunk = std::min(chunk * 2, 64);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return cuda_status(e, "step-size-controlled march");
+  ctx->last_accepted = hc.accepted;
+  ctx->last_rejected = hc.rejected;
+  if (hc.failed) {
+    set_error("step-size-controlled march: no convergence (too many attempts or a non-finite error)");
+    return SWF_ENUMERIC;
+  }
+  e = cudaMemcpyAsync(psi_out, py, state, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "copy psi(t_in)");
+  return SWF_OK;
+}
+
+swf_status march_adaptive(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, double h0, int max_attempts,
+                          int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out, cudaStream_t st) {
+  if (prec == SWF_C64)
+    return march_adaptive_impl<float>(ctx, g, t_in, t_out, h0, max_attempts, n_f, fd_host, psi_out, st);
+  return march_adaptive_impl<double>(ctx, g, t_in, t_out, h0, max_attempts, n_f, fd_host, psi_out, st);
+}
+
 // psi_out[f] = psi_u[rep[f]] with the components {1, 2} times sgn[f] (+1 or -1).
 template <typename R>
 __global__ void k_expand_fields(const cpx<R>* __restrict__ psi_u, const int* __restrict__ rep,
@@ -1121,7 +1411,11 @@ static int dedupe_fields(const GridDesc& g, int n_f, const FieldDesc* fd, std::v
 }
 
 static swf_status march_unique(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
-                               const FieldDesc* fd_host, swf_precision prec, void* psi_out, cudaStream_t st) {
+                               const FieldDesc* fd_host, swf_precision prec, void* psi_out, cudaStream_t st,
+                               int adaptive) {
+  if (adaptive)  // first step (t_in - t_out)/n_steps, at most 100 n_steps + 100 attempts
+    return march_adaptive(ctx, g, t_in, t_out, (t_in - t_out) / n_steps, 100 * n_steps + 100, n_f, fd_host, prec,
+                          psi_out, st);
   if (ctx->use_fused && fused_applicable(g, n_f, fd_host, prec)) {
     swf_status s = march_fused(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
     if (s != SWF_EUNSUPPORTED) return s;
@@ -1133,18 +1427,18 @@ static swf_status march_unique(swf_ctx* ctx, const GridDesc& g, double t_in, dou
 
 swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
                         int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out,
-                        cudaStream_t st) {
+                        cudaStream_t st, int adaptive) {
   std::vector<int> rep, sgn;
   std::vector<FieldDesc> uniq;
   const int n_u = ctx->dedupe ? dedupe_fields(g, n_f, fd_host, rep, sgn, uniq) : n_f;
   ctx->fields_marched += n_u;
-  if (n_u == n_f) return march_unique(ctx, g, t_in, t_out, n_steps, n_f, fd_host, prec, psi_out, st);
+  if (n_u == n_f) return march_unique(ctx, g, t_in, t_out, n_steps, n_f, fd_host, prec, psi_out, st, adaptive);
   const size_t elem = prec == SWF_C64 ? 8 : 16;
   void *pu = nullptr, *ptab = nullptr;
   swf_status s = ws_get(ctx, "march.unique", (size_t)n_u * 4 * g.N * elem, &pu);
   if (s != SWF_OK) return s;
   if ((s = ws_get(ctx, "march.unique_map", sizeof(int) * 2 * (size_t)n_f, &ptab)) != SWF_OK) return s;
-  if ((s = march_unique(ctx, g, t_in, t_out, n_steps, n_u, uniq.data(), prec, pu, st)) != SWF_OK) return s;
+  if ((s = march_unique(ctx, g, t_in, t_out, n_steps, n_u, uniq.data(), prec, pu, st, adaptive)) != SWF_OK) return s;
   std::vector<int> tab(rep);
   tab.insert(tab.end(), sgn.begin(), sgn.end());
   cudaError_t e = cudaMemcpyAsync(ptab, tab.data(), sizeof(int) * 2 * (size_t)n_f, cudaMemcpyHostToDevice, st);

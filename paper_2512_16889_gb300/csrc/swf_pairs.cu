@@ -233,8 +233,9 @@ extern "C" swf_status swf_pair_matrix(swf_ctx* ctx, int n_e, const swf_instance*
   const swf_instance& i0 = electrons[0];
   for (int k = 0; k < n_e + n_p; ++k) {
     const swf_instance& in = k < n_e ? electrons[k] : positrons[k - n_e];
-    if (!pairs::same_grid(in.grid, i0.grid) || !pairs::same_field(in.field, i0.field)) {
-      set_error("swf_pair_matrix: every electron and positron must share the field, grid and time window");
+    if (!pairs::same_grid(in.grid, i0.grid) || !pairs::same_field(in.field, i0.field) ||
+        ((in.flags ^ i0.flags) & SWF_ADAPTIVE)) {
+      set_error("swf_pair_matrix: every electron and positron must share the field, grid, time window and step control");
       return SWF_EINVAL;
     }
     for (int a = 0; a < 3; ++a) {
@@ -285,8 +286,11 @@ extern "C" swf_status swf_pair_matrix(swf_ctx* ctx, int n_e, const swf_instance*
   if ((s = ws_get(ctx, "pairs.results", sizeof(swf_result) * (size_t)n_e * n_p, &pres)) != SWF_OK) return s;
   // one march per electron (U waves) and per positron (V waves), then their FP64 transforms
   const double t_in = i0.grid.t_in;
-  if ((s = march_fields(ctx, g, t_in, i0.grid.t_out, i0.grid.n_steps, n_e, fdU.data(), prec, psiU, st)) != SWF_OK) return s;
-  if ((s = march_fields(ctx, g, t_in, i0.grid.t_out, i0.grid.n_steps, n_p, fdV.data(), prec, psiV, st)) != SWF_OK) return s;
+  const int adaptive = (i0.flags & SWF_ADAPTIVE) ? 1 : 0;
+  if ((s = march_fields(ctx, g, t_in, i0.grid.t_out, i0.grid.n_steps, n_e, fdU.data(), prec, psiU, st, adaptive)) != SWF_OK)
+    return s;
+  if ((s = march_fields(ctx, g, t_in, i0.grid.t_out, i0.grid.n_steps, n_p, fdV.data(), prec, psiV, st, adaptive)) != SWF_OK)
+    return s;
   if ((s = transform_fields(ctx, g, n_e, prec, psiU, (double2*)specU, st)) != SWF_OK) return s;
   if ((s = transform_fields(ctx, g, n_p, prec, psiV, (double2*)specV, st)) != SWF_OK) return s;
   if ((s = field_norms(ctx, g, n_e, prec, psiU, (double*)normU, st)) != SWF_OK) return s;

@@ -20,7 +20,7 @@ STATUS_NAMES = ["SWF_OK", "SWF_EINVAL", "SWF_ENOMEM", "SWF_ECUDA", "SWF_ENUMERIC
 SCHWINGER, BREIT_WHEELER = 0, 1
 C128, C64 = 0, 1
 FIELD_ZERO, FIELD_SAUTER_GAUSS, FIELD_PULSE_GAUSS, FIELD_SINGLE_E, FIELD_DOUBLE_E = range(5)
-WANT_SPECTRUM, WANT_FULL_N = 1, 2
+WANT_SPECTRUM, WANT_FULL_N, ADAPTIVE = 1, 2, 4
 
 
 class Field(C.Structure):
@@ -47,6 +47,7 @@ class Result(C.Structure):
 EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_pair_matrix", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_set_dedupe", "swf_fields_marched",
+           "swf_set_tolerances", "swf_march_stats",
            "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
            "swf_mlp_get_params"]
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH):
     lib.swf_set_march_path.argtypes = [vp, ip]
     lib.swf_set_autotune.argtypes = [vp, ip]
     lib.swf_set_dedupe.argtypes = [vp, ip]
+    lib.swf_set_tolerances.argtypes = [vp, dp, dp]
+    lib.swf_march_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     lib.swf_fields_marched.argtypes = [vp, C.POINTER(C.c_longlong)]
     lib.swf_rhs_noalloc.argtypes = [inst_p, ip, ip, dp, vp, vp, vp]
     fp = C.POINTER(C.c_float)
@@ -173,6 +176,16 @@ class Context:
         """0 = automatic (fused cluster kernel where it applies), 1 = pass kernels only."""
         _check(_lib.swf_set_march_path(self._h, int(path)))
 
+    def set_tolerances(self, rtol, atol):
+        """Tolerances of step-size-controlled marches (flag "adaptive")."""
+        _check(_lib.swf_set_tolerances(self._h, float(rtol), float(atol)))
+
+    def march_stats(self):
+        """(accepted, rejected) steps of the last step-size-controlled march."""
+        a, r = C.c_longlong(), C.c_longlong()
+        _check(_lib.swf_march_stats(self._h, C.byref(a), C.byref(r)))
+        return a.value, r.value
+
     def set_dedupe(self, on: bool):
         """March repeated fields (the other spin of a z-spin-conserving field) once (True, default)."""
         _check(_lib.swf_set_dedupe(self._h, 1 if on else 0))
@@ -251,7 +264,7 @@ class Context:
 
 FIELD_CODES = {"zero": FIELD_ZERO, "sauter_gauss": FIELD_SAUTER_GAUSS, "pulse_gauss": FIELD_PULSE_GAUSS,
                "single_e": FIELD_SINGLE_E, "double_e": FIELD_DOUBLE_E}
-FLAG_CODES = {"spectrum": WANT_SPECTRUM, "full_n": WANT_FULL_N}
+FLAG_CODES = {"spectrum": WANT_SPECTRUM, "full_n": WANT_FULL_N, "adaptive": ADAPTIVE}
 
 
 def from_workload(d) -> Instance:

@@ -489,3 +489,51 @@ def test_full_3d_grid_conserves_the_norm_of_the_full_wave(env):
     out.zero_()
     ctx.march_dev([swf.from_workload(z)], out, bg=0, prec=swf.C64)
     assert float(out.abs().max()) == 0.0
+
+
+def test_step_size_controlled_march_matches_oracle(env):
+    """SWF_ADAPTIVE: the Dormand-Prince 5(4) pair with the integral step controller, decided on
+    the device (graph replays).  Against the oracle's controlled march (same tolerances, same first
+    step): same accepted/rejected counts and the same state to round-off in complex128; both
+    within the tolerance of a converged fixed-step march; a too-large first step is rejected;
+    graph replay and kernel-by-kernel launches give the same bits."""
+    torch, swf, _ = env
+    d0 = dict(field=("sauter_gauss", (0.8, 0.6, 2.5)), n=(16, 16, 1), L=(12.0, 12.0, 1.0), t_in=-6.0, t_out=6.0,
+              n_steps=120, p=(0.3, -0.2, 0.0), s=1, q=(-0.2, 0.1, 0.0), r=1, k=(0, 0, 0), eps=(0, 0, 0),
+              flags=("adaptive",))
+    grid, fld, bg = OA.grid(d0), OA.field(d0), OA.background(d0, 0)
+    ref_fixed = OA.to_gpu_layout(O.march_scattered(fld, grid, bg, -6.0, 6.0, 4000))
+    for n_steps in (120, 4):  # first step 0.1, and 3.0 (rejected at least once)
+        d = dict(d0, n_steps=n_steps)
+        y, na, nr = O.march_scattered_adaptive(fld, grid, bg, -6.0, 6.0, 12.0 / n_steps, 1e-5, 1e-10)
+        ref = OA.to_gpu_layout(y)
+        outs = []
+        for timed in (False, True):
+            ctx = swf.Context(0)
+            ctx.profile_enable(timed)
+            out = torch.zeros(2 * 4 * 256, dtype=torch.float64, device="cuda")
+            ctx.march_dev([swf.from_workload(d)], out, bg=0, prec=swf.C128)
+            torch.cuda.synchronize()
+            outs.append(out.cpu().numpy())
+            stats = ctx.march_stats()
+            ctx.close()
+        assert np.array_equal(outs[0], outs[1])
+        assert stats == (na, nr), (stats, na, nr)
+        got = to_complex(torch.from_numpy(outs[0])).reshape(ref.shape)
+        assert rel_state(got, ref) < 1e-9, rel_state(got, ref)
+        assert rel_state(got, ref_fixed) < 20 * 1e-5
+        if n_steps == 4:
+            assert nr > 0
+    # complex64: within the tolerance of the converged march
+    ctx = swf.Context(0)
+    out = torch.zeros(2 * 4 * 256, dtype=torch.float32, device="cuda")
+    ctx.march_dev([swf.from_workload(d0)], out, bg=0, prec=swf.C64)
+    got = to_complex(out).reshape(ref_fixed.shape)
+    assert rel_state(got, ref_fixed) < 20 * 1e-5
+    # tighter tolerance: more steps, smaller error
+    ctx.set_tolerances(1e-7, 1e-12)
+    out64 = torch.zeros(2 * 4 * 256, dtype=torch.float64, device="cuda")
+    ctx.march_dev([swf.from_workload(d0)], out64, bg=0, prec=swf.C128)
+    got = to_complex(out64).reshape(ref_fixed.shape)
+    assert rel_state(got, ref_fixed) < 20 * 1e-7 and ctx.march_stats()[0] > stats[0]
+    ctx.close()
