@@ -524,7 +524,7 @@ class Photon:
 
 
 def bw_integrand(grid, photon, bg_u, bg_v, t, psi_u, psi_v):
-    """dM_{a,b}/dt of Eq. 33's integrand: dx^d sum_x U_a^+ (alpha.eps) V_b e^{-ikx}.
+    """dM_{a,b}/dt of the finite-time terms (the integrand of Eq. 17): dx^d sum_x U_a^+ (alpha.eps) V_b e^{-ikx}.
 
     Returns the three terms (ss, bs, sb) as a complex array of length 3.
     """
@@ -542,12 +542,109 @@ def bw_integrand(grid, photon, bg_u, bg_v, t, psi_u, psi_v):
     return np.array([term(psi_u, psi_v), term(ub, psi_v), term(psi_u, vb)])
 
 
-def bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps):
-    """March (U_scat, V_scat) together with M appended (Eqs. 33-35).
+class PartialIntegrationTables:
+    """Time-independent pieces of the partial-integration integrand (Sec. IV, Eqs. 28-33).
 
-    The appended variable obeys dM/dt = M-dot(t), M(t_out) = 0, so the finite-time part of
-    Eq. 17 is M_finite = integral_{t_in}^{t_out} M-dot dt = -M(t_in).
-    Returns (U_scat(t_in), V_scat(t_in), M_finite[3]).
+    For every U grid mode kappa_u (index idx) the V mode is kappa_v = kappa_u - k (index
+    idx - shift, periodic, as in the past terms).  Holds the energy projectors of both modes
+    and the four denominators Omega = sigma E_u - sigma' E_v - k0.
+    """
+
+    def __init__(self, grid, photon, bg_u, bg_v):
+        k = np.asarray(photon.k, dtype=float)
+        self.shift = []
+        for a in range(3):
+            if grid.n[a] > 1:
+                m = k[a] * grid.L[a] / (2.0 * np.pi)
+                assert abs(m - round(m)) < 1e-9, "photon momentum must be a grid mode"
+                self.shift.append(int(round(m)))
+            else:
+                self.shift.append(0)
+        ku = np.stack(grid.modes(bg_u.offset()))
+        kv = np.stack(grid.modes(bg_v.offset()))
+        # V quantities moved onto the U mode they pair with: entry idx holds mode idx - shift
+        kv = np.roll(kv, self.shift, axis=(1, 2, 3))
+        self.eu = np.sqrt(1.0 + np.sum(ku * ku, axis=0))
+        self.ev = np.sqrt(1.0 + np.sum(kv * kv, axis=0))
+
+        def proj(kk, e, sign):
+            h = sum(ALPHA[a][:, :, None, None, None] * kk[a][None, None] for a in range(3)) + BETA[:, :, None, None, None]
+            return 0.5 * (ID4[:, :, None, None, None] + sign * h / e[None, None])
+
+        self.pu = {sg: proj(ku, self.eu, sg) for sg in (1, -1)}
+        self.pv = {sg: proj(kv, self.ev, sg) for sg in (1, -1)}
+        k0 = photon.k0()
+        self.omega = {(sg, sgp): sg * self.eu - sgp * self.ev - k0 for sg in (1, -1) for sgp in (1, -1)}
+
+    def on_u_modes(self, spec_v):
+        """A V spectrum re-indexed so that entry idx holds V~(kappa_u(idx) - k)."""
+        return np.roll(spec_v, self.shift, axis=(1, 2, 3))
+
+
+def bw_integrand_partial(fld, grid, photon, bg_u, bg_v, tabs, t, psi_u, psi_v):
+    """dM_{a,b}/dt of the partial-integration form (Eqs. 30-33) for (ss, bs, sb).
+
+    With the grid transform psi~(kappa) and the energy projectors P_sigma of Eq. 23, the split
+    parts of Eq. 29 are P_sigma psi~ e^{+i sigma E t} (free oscillation removed).  Their time
+    derivative is P_sigma (d/dt + i H0) psi~ = P_sigma F[-i V (psi_s + psi_b)] (Eq. 6), so
+    (i e^{i Omega t} / Omega) d/dt[...] of Eq. 33 becomes, after the phases cancel against
+    e^{i Omega t},
+        ss: (i e^{-i k0 t} / L^d) sum_kappa sum_{sigma,sigma'}
+            [(P_s dU~)^+ (alpha.eps) P_s' V~ + (P_s U~)^+ (alpha.eps) P_s' dV~] / Omega_{s s'}
+        bs: i e^{i (p0 - k0) t} sum_s' u^+ (alpha.eps) P_s'(p - k) dV~(p - k) / (p0 - s' E - k0)
+        sb: i e^{i (q0 - k0) t} sum_s (P_s(k - q) dU~(k - q))^+ (alpha.eps) v / (s E + q0 - k0)
+    with dU = -i V (U_scat + U_back), dV = -i V (V_scat + V_back) at time t.
+    """
+    k0 = photon.k0()
+    ae = photon.alpha_eps()
+    du = -1j * apply_v(fld, grid, t, psi_u + bg_u.values(grid, t))
+    dv = -1j * apply_v(fld, grid, t, psi_v + bg_v.values(grid, t))
+    su = transform_on_grid(psi_u, grid)
+    sdu = transform_on_grid(du, grid)
+    sv = tabs.on_u_modes(transform_on_grid(psi_v, grid))
+    sdv = tabs.on_u_modes(transform_on_grid(dv, grid))
+
+    def proj(P, x):
+        return np.einsum("ab...,b...->a...", P, x)
+
+    def form(x, y):
+        return np.einsum("a...,ab,b...->...", np.conj(x), ae, y)
+
+    ss = 0.0 + 0.0j
+    for sg in (1, -1):
+        pu, pdu = proj(tabs.pu[sg], su), proj(tabs.pu[sg], sdu)
+        for sgp in (1, -1):
+            pv, pdv = proj(tabs.pv[sgp], sv), proj(tabs.pv[sgp], sdv)
+            ss += np.sum((form(pdu, pv) + form(pu, pdv)) / tabs.omega[(sg, sgp)])
+    ss = 1j * np.exp(-1j * k0 * t) * ss / grid.volume
+    k = np.asarray(photon.k, dtype=float)
+    p = np.asarray(bg_u.p, dtype=float)
+    kv = p - k
+    dvk = transform_at(dv, grid, kv)
+    u = bg_u.spinor()
+    bs = 0.0 + 0.0j
+    for sgp in (1, -1):
+        bs += (np.conj(u) @ ae @ (energy_projector(kv, sgp) @ dvk)) / (energy(p) - sgp * energy(kv) - k0)
+    bs = 1j * np.exp(1j * (energy(p) - k0) * t) * bs
+    q = np.asarray(bg_v.p, dtype=float)
+    ku = k - q
+    duk = transform_at(du, grid, ku)
+    v = bg_v.spinor()
+    sb = 0.0 + 0.0j
+    for sg in (1, -1):
+        sb += (np.conj(energy_projector(ku, sg) @ duk) @ ae @ v) / (sg * energy(ku) + energy(q) - k0)
+    sb = 1j * np.exp(1j * (energy(q) - k0) * t) * sb
+    return np.array([ss, bs, sb])
+
+
+def bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps, form: int = 1):
+    """March (U_scat, V_scat) together with M appended (Eqs. 34-35).
+
+    The appended variable obeys dM/dt = M-dot(t), M(t_out) = 0, so its integral over the march
+    is -M(t_in).  form = 1: M-dot is the integrand of Eq. 17 (finite-time terms; the past terms
+    are added at t_in).  form = 2: M-dot is the partial-integration integrand of Eqs. 30-33,
+    which vanishes outside the field, so -M(t_in) is the whole amplitude.
+    Returns (U_scat(t_in), V_scat(t_in), -M(t_in)[3]).
     """
     h0u = h0_field(grid, bg_u.offset())
     h0v = h0_field(grid, bg_v.offset())
@@ -556,8 +653,14 @@ def bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps):
     def f(t, y):
         return np.stack([rhs(fld, grid, bg_u, h0u, t, y[0]), rhs(fld, grid, bg_v, h0v, t, y[1])])
 
-    def g(t, y):
-        return bw_integrand(grid, photon, bg_u, bg_v, t, y[0], y[1])
+    if form == 2:
+        tabs = PartialIntegrationTables(grid, photon, bg_u, bg_v)
+
+        def g(t, y):
+            return bw_integrand_partial(fld, grid, photon, bg_u, bg_v, tabs, t, y[0], y[1])
+    else:
+        def g(t, y):
+            return bw_integrand(grid, photon, bg_u, bg_v, t, y[0], y[1])
 
     y0 = np.zeros((2,) + shape, dtype=complex)
     y, m = dopri5_march(f, y0, t_out, t_in, n_steps, stage_hook=g)
@@ -630,10 +733,19 @@ def bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in):
     return np.array([ss, bs, sb])
 
 
-def bw_amplitude(fld, grid, p, s, q, r, photon, t_in, t_out, n_steps):
-    """M = M_ss + M_bs + M_sb (Eq. 13), each the sum of its finite (Eq. 17) and past part."""
+def bw_amplitude(fld, grid, p, s, q, r, photon, t_in, t_out, n_steps, form: int = 1):
+    """M = M_ss + M_bs + M_sb (Eq. 13).
+
+    form = 1: each term is the sum of its finite (Eq. 17) and past (Eqs. 25-27) part.
+    form = 2: each term is the time integral of the partial-integration integrand (Eqs. 30-33);
+    "past" is then zero.
+    """
     bg_u = Background("U", tuple(p), s)
     bg_v = Background("V", tuple(q), r)
+    if form == 2:
+        psi_u, psi_v, m = bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps, form=2)
+        return {"finite": m, "past": np.zeros(3, dtype=complex), "terms": m, "M": complex(np.sum(m)),
+                "psi_u": psi_u, "psi_v": psi_v}
     psi_u, psi_v, m_fin = bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps)
     m_past = bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in)
     return {"finite": m_fin, "past": m_past, "terms": m_fin + m_past,

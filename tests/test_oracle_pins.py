@@ -299,8 +299,34 @@ def test_bw_t_in_independence():
     assert abs(r1["M"] - r2["M"]) / abs(r1["M"]) < 2e-6, (r1["M"], r2["M"])
 
 
-def test_bw_spin_ratio_is_exact_in_1p1d():
-    """Eq. A81 for the (1+1)D example of Sec. IV (golden fixture): |M(r != s)|^2/|M(r = s)|^2 = p_2^2."""
+def test_bw_partial_integration_form_equals_past_finite_split():
+    """The two ways of Sec. IV to handle t < t_in give the same amplitude: the partial-integration
+    integrals of Eqs. 30-32 equal finite (Eq. 17) plus past (Eqs. 25-27) parts term by term, up to
+    the time quadrature, whose error falls at least as fast as h^5 (Dormand-Prince)."""
+    grid, fld, ph = _bw_setup_2d()
+    p, q = (0.25, -1.0, 0.0), (-0.25, -1.0, 0.0)
+    gaps = []
+    for n_steps in (100, 200):
+        r1 = O.bw_amplitude(fld, grid, p, 1, q, 1, ph, -9.0, 9.0, n_steps)
+        r2 = O.bw_amplitude(fld, grid, p, 1, q, 1, ph, -9.0, 9.0, n_steps, form=2)
+        assert np.all(r2["past"] == 0)
+        # the split between finite and past parts is O(1); the partial-integration terms match the sums
+        assert abs(r1["past"][0]) > 0.05 * abs(r1["M"])
+        gaps.append(np.max(np.abs(r1["terms"] - r2["terms"])) / abs(r1["M"]))
+    assert gaps[1] < 1e-6, gaps
+    assert gaps[0] / gaps[1] > 20.0, gaps
+
+
+def test_bw_partial_integration_zero_field_gives_zero():
+    grid, _, ph = _bw_setup_2d()
+    res = O.bw_amplitude(O.Field("zero"), grid, (0.25, -1.0, 0), 1, (-0.25, -1.0, 0), 1, ph, -3.0, 3.0, 20, form=2)
+    assert res["M"] == 0
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_bw_spin_ratio_is_exact_in_1p1d(form):
+    """Eq. A81 for the (1+1)D example of Sec. IV (golden fixture): |M(r != s)|^2/|M(r = s)|^2 = p_2^2,
+    with either treatment of the times before t_in."""
     with open(os.path.join(GOLDEN, "bw_spin_ratio_1p1d.json")) as fh:
         gold = json.load(fh)
     c = gold["case"]
@@ -317,7 +343,7 @@ def test_bw_spin_ratio_is_exact_in_1p1d():
     amps = {}
     for r in (1, -1):
         for s in (1, -1):
-            amps[(r, s)] = O.bw_amplitude(fld, grid, p, r, q, s, ph, -20.0, 20.0, 800)["M"]
+            amps[(r, s)] = O.bw_amplitude(fld, grid, p, r, q, s, ph, -20.0, 20.0, 800, form=form)["M"]
     diag = abs(amps[(1, 1)]) ** 2
     assert diag > 1e-12
     assert np.isclose(abs(amps[(-1, -1)]) ** 2, diag, rtol=1e-6)
