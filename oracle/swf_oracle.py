@@ -752,6 +752,74 @@ def bw_amplitude(fld, grid, p, s, q, r, photon, t_in, t_out, n_steps, form: int 
             "M": complex(np.sum(m_fin + m_past)), "psi_u": psi_u, "psi_v": psi_v}
 
 
+def bw_photon_scan(fld, grid, p, s, q, r, photons, t_in, t_out, n_steps):
+    """Amplitudes M(k_j, eps_j) for a list of plane-wave photons from one march of U and V.
+
+    The photon enters only the integrals of Eq. 14, not the Dirac equations for U and V (Sec. IV,
+    closing paragraphs), so the appended integral carries the finite-time integrands of every
+    photon and the past terms (Eqs. 25-27) are added per photon at t_in.
+    Returns a list of dicts like bw_amplitude's (without the wave functions).
+    """
+    bg_u = Background("U", tuple(p), s)
+    bg_v = Background("V", tuple(q), r)
+    h0u = h0_field(grid, bg_u.offset())
+    h0v = h0_field(grid, bg_v.offset())
+
+    def f(t, y):
+        return np.stack([rhs(fld, grid, bg_u, h0u, t, y[0]), rhs(fld, grid, bg_v, h0v, t, y[1])])
+
+    def g(t, y):
+        return np.concatenate([bw_integrand(grid, ph, bg_u, bg_v, t, y[0], y[1]) for ph in photons])
+
+    y0 = np.zeros((2, 4) + grid.n, dtype=complex)
+    y, m = dopri5_march(f, y0, t_out, t_in, n_steps, stage_hook=g)
+    out = []
+    for j, ph in enumerate(photons):
+        fin = -m[3 * j:3 * j + 3]
+        past = bw_past(grid, ph, bg_u, bg_v, y[0], y[1], t_in)
+        out.append({"finite": fin, "past": past, "terms": fin + past, "M": complex(np.sum(fin + past))})
+    return out
+
+
+def bw_packet_finite(fld, grid, p, s, q, r, photons, weights, t_in, t_out, n_steps):
+    """Finite-time terms (Eq. 17) for a photon wave packet: eps_mu e^{-ikx} replaced by the packet
+    f(t, x) = sum_j w_j eps_j e^{-i k_j x} (Sec. IV, closing paragraphs), integrated as one
+    space-time integral dx^d sum_x U_a^+ (alpha.f) V_b per stage.  Returns (ss, bs, sb)."""
+    bg_u = Background("U", tuple(p), s)
+    bg_v = Background("V", tuple(q), r)
+    h0u = h0_field(grid, bg_u.offset())
+    h0v = h0_field(grid, bg_v.offset())
+    X, Y, Z = grid.coords()
+
+    def packet(t):
+        fv = np.zeros((3,) + grid.n, dtype=complex)
+        for ph, w in zip(photons, weights):
+            k = np.asarray(ph.k, dtype=float)
+            kk = [k[a] if grid.n[a] > 1 else 0.0 for a in range(3)]
+            wave = w * np.exp(-1j * ph.k0() * t + 1j * (kk[0] * X + kk[1] * Y + kk[2] * Z))
+            for a in range(3):
+                fv[a] = fv[a] + ph.eps[a] * wave
+        return fv
+
+    def f(t, y):
+        return np.stack([rhs(fld, grid, bg_u, h0u, t, y[0]), rhs(fld, grid, bg_v, h0v, t, y[1])])
+
+    def g(t, y):
+        fv = packet(t)
+        ub = bg_u.values(grid, t)
+        vb = bg_v.values(grid, t)
+
+        def term(uu, vv):
+            av = sum(np.einsum("ab,b...->a...", ALPHA[a], vv) * fv[a][None] for a in range(3))
+            return grid.cell * np.sum(np.conj(uu) * av)
+
+        return np.array([term(y[0], y[1]), term(ub, y[1]), term(y[0], vb)])
+
+    y0 = np.zeros((2, 4) + grid.n, dtype=complex)
+    _, m = dopri5_march(f, y0, t_out, t_in, n_steps, stage_hook=g)
+    return -m
+
+
 # --------------------------------------------------------------------------------------------
 # Convenience drivers used by tests and by the CPU baseline
 # --------------------------------------------------------------------------------------------

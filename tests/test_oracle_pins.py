@@ -323,6 +323,48 @@ def test_bw_partial_integration_zero_field_gives_zero():
     assert res["M"] == 0
 
 
+def _photon_list(grid):
+    du = grid.kappa[0][1]
+    out = []
+    for k in ((0.0, -4 * du, 0.0), (du, -4 * du, 0.0), (-2 * du, -3 * du, 0.0)):
+        perp, par = O.polarisation_basis((1, 0, 0), k)
+        out.append(O.Photon(k, tuple(par)))
+        out.append(O.Photon(k, tuple(perp)))
+    return out
+
+
+def test_bw_photon_scan_equals_single_photon_solves():
+    """One march serves every photon (the photon enters only the integrals of Eq. 14): the scan's
+    amplitudes equal separate solves photon by photon."""
+    grid, fld, _ = _bw_setup_2d()
+    p, q = (0.25, -1.0, 0.0), (-0.25, -1.0, 0.0)
+    photons = _photon_list(grid)[::2]
+    scan = O.bw_photon_scan(fld, grid, p, 1, q, -1, photons, -6.0, 6.0, 80)
+    for ph, got in zip(photons, scan):
+        ref = O.bw_amplitude(fld, grid, p, 1, q, -1, ph, -6.0, 6.0, 80)
+        assert abs(got["M"]) > 1e-3
+        assert np.max(np.abs(got["terms"] - ref["terms"])) <= 1e-13 * abs(ref["M"])
+
+
+def test_bw_wave_packet_finite_term_is_one_space_time_integral():
+    """A photon wave packet sampled on grid momenta (Sec. IV, closing paragraphs): the finite-time
+    terms with eps e^{-ikx} replaced by the packet f(t, x) = sum_j w_j eps_j e^{-i k_j x} equal the
+    weighted sum of the plane-wave finite terms; and M is linear in the polarisation."""
+    grid, fld, _ = _bw_setup_2d()
+    p, q = (0.25, -1.0, 0.0), (-0.25, -1.0, 0.0)
+    photons = _photon_list(grid)
+    rng = np.random.default_rng(3)
+    w = rng.normal(size=len(photons)) + 1j * rng.normal(size=len(photons))
+    scan = O.bw_photon_scan(fld, grid, p, 1, q, 1, photons, -6.0, 6.0, 60)
+    direct = O.bw_packet_finite(fld, grid, p, 1, q, 1, photons, w, -6.0, 6.0, 60)
+    summed = sum(wj * r["finite"] for wj, r in zip(w, scan))
+    assert np.max(np.abs(direct - summed)) <= 1e-12 * np.max(np.abs(summed))
+    # photons 0 and 1 share k: their weighted sum is the photon with polarisation w0 eps0 + w1 eps1
+    mix = O.Photon(photons[0].k, tuple(w[0] * np.asarray(photons[0].eps) + w[1] * np.asarray(photons[1].eps)))
+    one = O.bw_amplitude(fld, grid, p, 1, q, 1, mix, -6.0, 6.0, 60)["M"]
+    assert abs(one - (w[0] * scan[0]["M"] + w[1] * scan[1]["M"])) <= 1e-12 * abs(one)
+
+
 @pytest.mark.parametrize("form", [1, 2])
 def test_bw_spin_ratio_is_exact_in_1p1d(form):
     """Eq. A81 for the (1+1)D example of Sec. IV (golden fixture): |M(r != s)|^2/|M(r = s)|^2 = p_2^2,
