@@ -499,6 +499,54 @@ def run_pair_scan(args):
     return 0
 
 
+def run_photon_scan(args):
+    """Times the Breit-Wheeler photon scan on one GPU: 64 photons for one pair of the uneven-grid
+    workload (192^2, 2605 steps, complex64) from one march of U and V (swf_bw_photons), against
+    the same 64 amplitudes as 64 instances of one batched solve (a march each)."""
+    import numpy as np
+    import torch
+    from paper_2512_16889_gb300 import build, swf
+    from paper_2512_16889_gb300 import workloads as W
+    build.build()
+    d, ks, es = W.bw_photon_scan()
+    if args.limit:
+        ks, es = ks[:args.limit], es[:args.limit]
+    inst = swf.from_workload(d)
+    n = len(ks)
+    w = np.exp(-0.5 * (np.array([k[0] for k in ks]) / 0.5) ** 2).astype(complex)  # a Gaussian packet in k_x
+    ctx = swf.Context(0)
+    ctx.bw_photons(inst, ks[:2], es[:2], swf.C64)  # warm-up
+    times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        amps, packet = ctx.bw_photons(inst, ks, es, swf.C64, weights=w)
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    ctx.profile_read()
+    ctx.profile_enable(True)
+    ctx.bw_photons(inst, ks, es, swf.C64, weights=w)
+    ctx.profile_enable(False)
+    prof, _ = ctx.profile_read()
+    insts = [swf.from_workload(dict(d, k=tuple(k), eps=tuple(e))) for k, e in zip(ks, es)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, _ = ctx.solve(insts, swf.BREIT_WHEELER, swf.C64)
+    t_sep = time.perf_counter() - t0
+    sep = np.array([complex(r.amp[6], r.amp[7]) for r in res])
+    line = {"metric": "Breit-Wheeler photon amplitudes/s", "value": n / t, "unit": "amplitudes/s", "n_gpus": 1,
+            "steps": len(times), "warmup": 1, "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "bw_photon_scan: one 192^2 pair of bw_uneven, 2605 steps",
+                                             "photons": n, "precision": "complex64 march, FP64 phases"},
+            "separate_solves_s": t_sep, "speedup_vs_separate": t_sep / t,
+            "max_abs_diff_vs_separate": float(np.max(np.abs(amps[:, 3] - sep))),
+            "packet_M": [float(packet[3].real), float(packet[3].imag)],
+            "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_workload(args):
     """Times another workload of the benchmark family on one GPU (not the headline line):
     schwinger_fp64_single (128^2, complex128, full pair number), schwinger_batched_fp64 (the
@@ -529,6 +577,10 @@ def run_workload(args):
         if process != swf.SCHWINGER:
             raise SystemExit("--adaptive applies to Schwinger workloads")
         ds = [dict(d, flags=tuple(d.get("flags", ())) + ("adaptive",)) for d in ds]
+    if args.bw_partial:
+        if process != swf.BREIT_WHEELER:
+            raise SystemExit("--bw-partial applies to Breit-Wheeler workloads")
+        ds = [dict(d, flags=tuple(d.get("flags", ())) + ("bw_partial",)) for d in ds]
     if args.max_steps:
         for d in ds:
             if d["n_steps"] > args.max_steps:
@@ -554,6 +606,14 @@ def run_workload(args):
     prof, _ = ctx.profile_read()
     if args.adaptive:  # site-updates of the accepted steps (the last march's count for every field)
         su = sum(int(np.prod(d["n"])) * ctx.march_stats()[0] * fields for d in ds)
+    forms = None
+    if args.bw_partial:  # the same instances with past + finite terms (untimed): the gap between the forms
+        ref = [swf.from_workload(dict(d, flags=())) for d in ds]
+        r1, _ = ctx.solve(ref, process, prec)
+        m1 = np.array([complex(x.amp[6], x.amp[7]) for x in r1])
+        m2 = np.array([complex(x.amp[6], x.amp[7]) for x in res])
+        forms = {"integrand": "partial integration (Eqs. 30-33)",
+                 "max_rel_gap_to_past_finite": float(np.max(np.abs(m2 - m1) / np.abs(m1)))}
     line = {"metric": METRIC, "value": su / t, "unit": UNIT, "n_gpus": 1, "steps": len(times), "warmup": 1,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "dtype": "f64" if prec == swf.C128 else "f32",
             "data": "synthetic", "config": {"workload": name, "instances": len(ds),
@@ -562,6 +622,7 @@ def run_workload(args):
             "results_per_s": len(ds) / t, "site_updates_per_step": su,
             "step_control": ({"rtol": 1e-5, "atol": 1e-10, "accepted_rejected": ctx.march_stats()}
                              if args.adaptive else None),
+            "bw_form": forms,
             "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -597,11 +658,15 @@ def main():
     ap.add_argument("--limit", type=int, default=0, help="at most this many instances (--workload)")
     ap.add_argument("--max-steps", type=int, default=0, help="at most this many steps (--workload)")
     ap.add_argument("--adaptive", action="store_true", help="step-size-controlled marches (--workload, Schwinger)")
+    ap.add_argument("--bw-partial", action="store_true",
+                    help="partial-integration form of the Breit-Wheeler terms (--workload bw_uneven)")
     args = ap.parse_args()
     if args.small_march:
         return run_small_march(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "bw_photon_scan":
+        return run_photon_scan(args)
     if args.workload == "pair_scan":
         return run_pair_scan(args)
     if args.workload in ("cross_section_single", "cross_section_double"):

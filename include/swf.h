@@ -102,6 +102,12 @@ typedef struct {
                                 absolute tolerances, swf_set_tolerances); the first step is
                                 (t_in - t_out)/n_steps and at most 100 n_steps + 100 attempts are made
                                 (SWF_ENUMERIC beyond); pass kernels only */
+#define SWF_BW_PARTIAL    8  /* Breit-Wheeler: integrate the partial-integration integrands of Sec. IV
+                                (Eqs. 30-33) during the march instead of adding the past terms of
+                                Eqs. 25-27 to the finite-time terms of Eq. 17; amp holds the same three
+                                terms and M.  Each weighted stage transforms the stage value and the
+                                source term -iV(psi_s + psi_b) of both waves on the grid (about twice
+                                the work of the default form) */
 
 /* Per-instance scalar results (complex values as (re, im) pairs).
  * Schwinger: amp = {C(m,n), D(m,n), A(m,n), B(m,n)} for the listed positron n = (r, q);
@@ -155,6 +161,22 @@ swf_status solve_swf_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf
  * diag = {||psi_U,m||^2, ||psi_V,n||^2}.  Synchronous; uses the context's stream and workspace. */
 swf_status swf_pair_matrix(swf_ctx* ctx, int n_e, const swf_instance* electrons, int n_p,
                            const swf_instance* positrons, swf_precision prec, swf_result* results);
+
+/* Breit-Wheeler photon scan (Sec. IV): the photon enters only the integrals of Eq. 14, not the
+ * Dirac equations for U and V, so one march of the instance's U and V (its p, s, q, r, field and
+ * grid; its own k and eps are not read) gives the amplitude M(k_j, eps_j) of every photon of a list,
+ * each with the past/finite split of Eqs. 17 and 25-27.  A photon wave packet sampled on grid
+ * momenta (Sec. IV, closing paragraphs) is, by linearity, sum_j w_j M(k_j, eps_j).
+ * k, eps: host [n_photons][3] (each k a grid mode along non-trivial axes, k = p + q along trivial
+ *         ones, k != 0; eps real, eps_mu = (0, eps)).
+ * weights: host [n_photons] complex (re, im) or NULL; packet_out: host 4 complex (8 doubles):
+ *         sum_j w_j (M_ss, M_bs, M_sb, M)_j, or NULL (needs weights).
+ * amp_out: host [n_photons][4] complex (8 doubles per photon): M_ss, M_bs, M_sb, M.
+ * Instances with SWF_ADAPTIVE or SWF_BW_PARTIAL give SWF_EUNSUPPORTED; invalid photons SWF_EINVAL
+ * (outputs untouched).  Synchronous; uses the context's stream and workspace. */
+swf_status swf_bw_photons(swf_ctx* ctx, const swf_instance* inst, int n_photons, const double* k,
+                          const double* eps, const double* weights, swf_precision prec,
+                          double* amp_out, double* packet_out);
 
 /* Lower-level: march n_inst instances' electron (bg = 0, background u_s(p) e^{-ipx}) or
  * positron (bg = 1, background v_r(q) e^{+iqx}) scattered wave from psi_s(t_out) = 0 to t_in

@@ -448,6 +448,33 @@ static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* 
   return SWF_OK;
 }
 
+// The photon momentum must be a grid mode along non-trivial axes (the V mode of the past terms is
+// the U mode minus k); along trivial axes momentum is conserved (p + q = k); k0 > 0.
+static swf_status check_bw_photon(const swf_instance& in, const double* k, const std::string& pre) {
+  for (int a = 0; a < 3; ++a) {
+    if (in.grid.n[a] > 1) {
+      const double m = k[a] * in.grid.L[a] / 6.283185307179586476925286766559;
+      if (std::fabs(m - std::round(m)) > 1e-6) {
+        set_error(pre + "the photon momentum must be a grid mode");
+        return SWF_EINVAL;
+      }
+    } else if (std::fabs(in.p[a] + in.q[a] - k[a]) > 1e-9) {
+      set_error(pre + "p + q must equal k along trivial axes");
+      return SWF_EINVAL;
+    }
+  }
+  if (!(std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]) > 0.0)) {
+    set_error(pre + "the photon momentum must be non-zero");
+    return SWF_EINVAL;
+  }
+  return SWF_OK;
+}
+
+static void photon_shift(const swf_instance& in, const double* k, int shift[3]) {
+  for (int a = 0; a < 3; ++a)
+    shift[a] = in.grid.n[a] > 1 ? (int)std::lround(k[a] * in.grid.L[a] / 6.283185307179586476925286766559) : 0;
+}
+
 // Breit-Wheeler (Sec. IV): U and V marched together per instance, then past terms and totals.
 static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf_precision prec,
                            swf_result* results_dev, cudaStream_t st) {
@@ -459,36 +486,21 @@ static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, s
     k.t_in = in.grid.t_in;
     k.t_out = in.grid.t_out;
     k.n_steps = in.grid.n_steps;
-    k.full = 0;
+    k.full = (in.flags & SWF_BW_PARTIAL) ? 1 : 0;  // the integrand form (Eq. 17 + past, or Eqs. 30-33)
     groups[k].push_back(i);
     if (in.flags & SWF_ADAPTIVE) {
       set_error("instance " + std::to_string(i) + ": step-size control is for Schwinger marches (fixed steps here)");
       return SWF_EUNSUPPORTED;
     }
-    // the photon momentum must be a grid mode; along trivial axes momentum is conserved
-    for (int a = 0; a < 3; ++a) {
-      if (in.grid.n[a] > 1) {
-        const double m = in.k[a] * in.grid.L[a] / 6.283185307179586476925286766559;
-        if (std::fabs(m - std::round(m)) > 1e-6) {
-          set_error("instance " + std::to_string(i) + ": the photon momentum must be a grid mode");
-          return SWF_EINVAL;
-        }
-      } else if (std::fabs(in.p[a] + in.q[a] - in.k[a]) > 1e-9) {
-        set_error("instance " + std::to_string(i) + ": p + q must equal k along trivial axes");
-        return SWF_EINVAL;
-      }
-    }
-    const double k0 = std::sqrt(in.k[0] * in.k[0] + in.k[1] * in.k[1] + in.k[2] * in.k[2]);
-    if (!(k0 > 0.0)) {
-      set_error("instance " + std::to_string(i) + ": the photon momentum must be non-zero");
-      return SWF_EINVAL;
-    }
+    swf_status c = check_bw_photon(in, in.k, "instance " + std::to_string(i) + ": ");
+    if (c != SWF_OK) return c;
   }
   const size_t elem = prec == SWF_C64 ? 8 : 16;
   swf_status s;
   for (auto& kv : groups) {
     const std::vector<int>& idx = kv.second;
     const int G = (int)idx.size();
+    const int form = kv.first.full ? 2 : 1;
     const swf_instance& i0 = inst[idx[0]];
     const GridDesc g = make_grid(i0.grid);
     std::vector<FieldDesc> fd(2 * G);
@@ -499,25 +511,35 @@ static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, s
       fd[2 * f] = make_field_desc(in, 0);
       fd[2 * f + 1] = make_field_desc(in, 1);
       int shift[3];
+      photon_shift(in, in.k, shift);
       for (int a = 0; a < 3; ++a) {
         photon[6 * f + a] = in.k[a];
         photon[6 * f + 3 + a] = in.eps[a];
-        shift[a] = in.grid.n[a] > 1 ? (int)std::lround(in.k[a] * in.grid.L[a] / 6.283185307179586476925286766559) : 0;
         kat[6 * f + a] = in.k[a] - in.q[a];      // U~ at k - q
         kat[6 * f + 3 + a] = in.p[a] - in.k[a];  // V~ at p - k
       }
-      bw_fill_inst(bw.data() + bw_inst_size() * f, in, idx[f], fd[2 * f], fd[2 * f + 1], shift);
+      bw_fill_inst(bw.data() + bw_inst_size() * f, in, idx[f], fd[2 * f], fd[2 * f + 1], shift, f);
     }
     const size_t state = (size_t)2 * G * 4 * g.N;
     void *psi, *spec, *tat, *macc, *norms;
     if ((s = ws_get(ctx, "bwsolve.psi", state * elem, &psi)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "bwsolve.spec", state * 16, &spec)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "bwsolve.tat", (size_t)2 * G * 64, &tat)) != SWF_OK) return s;
-    if ((s = ws_get(ctx, "bwsolve.macc", (size_t)G * 3 * 16, &macc)) != SWF_OK) return s;
+    if ((s = ws_get(ctx, "bwsolve.macc", (size_t)G * 9 * 16, &macc)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "bwsolve.norms", (size_t)2 * G * 8, &norms)) != SWF_OK) return s;
+    // kat holds, per wave, the momentum of its direct transform (U~ at k - q, V~ at p - k)
     if ((s = march_bw(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, G, fd.data(), photon.data(), prec, psi,
-                      (double2*)macc, st)) != SWF_OK)
+                      (double2*)macc, st, form, kat.data())) != SWF_OK)
       return s;
+    if (form == 2) {
+      if ((s = field_norms(ctx, g, 2 * G, prec, psi, (double*)norms, st)) != SWF_OK) return s;
+      if ((s = bw_finalize_partial(ctx, g, G, bw.data(), (const double2*)macc, (const double*)norms, results_dev,
+                                   st)) != SWF_OK)
+        return s;
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_status(e, "Breit-Wheeler group");
+      continue;
+    }
     if ((s = transform_fields(ctx, g, 2 * G, prec, psi, (double2*)spec, st)) != SWF_OK) return s;
     if ((s = transform_at(ctx, g, 2 * G, prec, psi, kat.data(), (double2*)tat, st)) != SWF_OK) return s;
     if ((s = field_norms(ctx, g, 2 * G, prec, psi, (double*)norms, st)) != SWF_OK) return s;
@@ -527,6 +549,62 @@ static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, s
     cudaError_t e = cudaStreamSynchronize(st);  // host tables above are temporaries
     if (e != cudaSuccess) return cuda_status(e, "Breit-Wheeler group");
   }
+  return SWF_OK;
+}
+
+// Photon scan (Sec. IV): one march of U and V, the amplitudes of n photons (k_j, eps_j), and their
+// weighted sum.  Host outputs; synchronous.
+static swf_status bw_photon_scan(swf_ctx* ctx, const swf_instance& in, int n, const double* k, const double* eps,
+                                 const double* weights, swf_precision prec, double* amp_out, double* packet_out) {
+  cudaStream_t st = ctx->stream;
+  const GridDesc g = make_grid(in.grid);
+  const FieldDesc fd[2] = {make_field_desc(in, 0), make_field_desc(in, 1)};
+  std::vector<double> photon(6 * (size_t)n), kat(6 * (size_t)n);
+  std::vector<unsigned char> bw(bw_inst_size() * (size_t)n);
+  for (int j = 0; j < n; ++j) {
+    swf_instance ij = in;
+    int shift[3];
+    for (int a = 0; a < 3; ++a) {
+      ij.k[a] = k[3 * j + a];
+      ij.eps[a] = eps[3 * j + a];
+      photon[6 * j + a] = ij.k[a];
+      photon[6 * j + 3 + a] = ij.eps[a];
+      kat[6 * j + a] = ij.k[a] - in.q[a];      // U~ at k_j - q
+      kat[6 * j + 3 + a] = in.p[a] - ij.k[a];  // V~ at p - k_j
+    }
+    photon_shift(in, ij.k, shift);
+    bw_fill_inst(bw.data() + bw_inst_size() * j, ij, j, fd[0], fd[1], shift, 0);
+  }
+  const size_t elem = prec == SWF_C64 ? 8 : 16;
+  void *psi, *spec, *tat, *macc, *norms, *res, *pk;
+  swf_status s;
+  if ((s = ws_get(ctx, "bwscan.psi", (size_t)2 * 4 * g.N * elem, &psi)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bwscan.spec", (size_t)2 * 4 * g.N * 16, &spec)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bwscan.tat", (size_t)n * 8 * 16, &tat)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bwscan.macc", (size_t)n * 3 * 16, &macc)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bwscan.norms", 2 * 8, &norms)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bwscan.results", sizeof(swf_result) * (size_t)n, &res)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bwscan.packet", 4 * 16, &pk)) != SWF_OK) return s;
+  if ((s = march_bw(ctx, g, in.grid.t_in, in.grid.t_out, in.grid.n_steps, 1, fd, photon.data(), prec, psi,
+                    (double2*)macc, st, 1, nullptr, n)) != SWF_OK)
+    return s;
+  if ((s = transform_fields(ctx, g, 2, prec, psi, (double2*)spec, st)) != SWF_OK) return s;
+  for (int j = 0; j < n; ++j)
+    if ((s = transform_at(ctx, g, 2, prec, psi, kat.data() + 6 * j, (double2*)tat + 8 * j, st)) != SWF_OK) return s;
+  if ((s = field_norms(ctx, g, 2, prec, psi, (double*)norms, st)) != SWF_OK) return s;
+  if ((s = bw_finalize(ctx, g, n, bw.data(), in.grid.t_in, (const double2*)spec, (const double2*)tat,
+                       (const double2*)macc, (const double*)norms, (swf_result*)res, st)) != SWF_OK)
+    return s;
+  if (packet_out && (s = bw_packet(ctx, n, (const swf_result*)res, weights, (double2*)pk, st)) != SWF_OK) return s;
+  std::vector<swf_result> host(n);
+  cudaError_t e = cudaMemcpyAsync(host.data(), res, sizeof(swf_result) * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_status(e, "copy photon-scan results");
+  if (packet_out && (e = cudaMemcpyAsync(packet_out, pk, 4 * 16, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_status(e, "copy packet amplitude");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "photon scan");
+  for (int j = 0; j < n; ++j)
+    for (int c = 0; c < 8; ++c) amp_out[8 * j + c] = host[j].amp[c];
   return SWF_OK;
 }
 
@@ -706,6 +784,33 @@ swf_status solve_swf(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf_pro
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_status(e, "stream synchronisation");
   return SWF_OK;
+}
+
+swf_status swf_bw_photons(swf_ctx* ctx, const swf_instance* inst, int n_photons, const double* k, const double* eps,
+                          const double* weights, swf_precision prec, double* amp_out, double* packet_out) {
+  if (!ctx) { set_error("ctx is NULL"); return SWF_EINVAL; }
+  swf_status s = validate(1, inst, SWF_BREIT_WHEELER, prec);
+  if (s != SWF_OK) return s;
+  if (n_photons < 1 || !k || !eps || !amp_out) {
+    set_error("need n_photons >= 1 and the k, eps and amp_out pointers");
+    return SWF_EINVAL;
+  }
+  if (packet_out && !weights) { set_error("packet_out needs weights"); return SWF_EINVAL; }
+  if (inst->flags & (SWF_ADAPTIVE | SWF_BW_PARTIAL)) {
+    set_error("photon scans march at fixed steps with the past/finite split of the amplitude");
+    return SWF_EUNSUPPORTED;
+  }
+  for (int j = 0; j < n_photons; ++j) {
+    const std::string pre = "photon " + std::to_string(j) + ": ";
+    if (!finite3(k + 3 * j) || !finite3(eps + 3 * j) ||
+        (weights && !(std::isfinite(weights[2 * j]) && std::isfinite(weights[2 * j + 1])))) {
+      set_error(pre + "momentum, polarisation and weight must be finite");
+      return SWF_EINVAL;
+    }
+    if ((s = check_bw_photon(*inst, k + 3 * j, pre)) != SWF_OK) return s;
+  }
+  cudaSetDevice(ctx->device);
+  return bw_photon_scan(ctx, *inst, n_photons, k, eps, weights, prec, amp_out, packet_out);
 }
 
 swf_status swf_march_dev(swf_ctx* ctx, int n_inst, const swf_instance* inst, int bg, swf_precision prec,

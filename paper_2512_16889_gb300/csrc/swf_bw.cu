@@ -1,6 +1,7 @@
-// Breit-Wheeler amplitude at t_in (Sec. IV): the analytic past terms of Eqs. 25-27 built with
-// the energy projectors of Eq. 23, added to the finite-time terms integrated during the march
-// (Eqs. 17, 33-35), in FP64.
+// Breit-Wheeler amplitude at t_in (Sec. IV), in FP64: the analytic past terms of Eqs. 25-27 built
+// with the energy projectors of Eq. 23, added to the finite-time terms integrated during the march
+// (Eqs. 17, 34-35); or the three terms of the partial-integration form (Eqs. 30-33) from the
+// accumulators of that march.
 #include "swf_internal.h"
 
 namespace swf {
@@ -44,12 +45,14 @@ struct BwInst {
   int s, r;
   int out;
   int shift[3];   // the photon momentum in grid modes per non-trivial axis
+  int src;        // the marched pair (U, V) of this amplitude: spectra and norms at index src
   double Ku[3], Kv[3];
 };
 
-// One block per instance.  U~ = spec[2i], V~ = spec[2i+1] (continuum-normalised transforms at
-// t_in); tat[2i] = U~(k - q) and tat[2i+1] = V~(p - k) by direct sums; macc = M(t_in) of the
-// appended integral; norms[2i], norms[2i+1] = ||U_scat||^2, ||V_scat||^2.
+// One block per amplitude i (an instance, or one photon of a photon scan).  With c = bi[i].src:
+// U~ = spec[2c], V~ = spec[2c+1] (continuum-normalised transforms at t_in); tat[2i] = U~(k - q)
+// and tat[2i+1] = V~(p - k) by direct sums; macc = M(t_in) of the appended integral; norms[2c],
+// norms[2c+1] = ||U_scat||^2, ||V_scat||^2.
 __global__ void __launch_bounds__(256) k_bw_finalize(const BwInst* bi, GridDesc g, double t_in,
                                                      const cpx<double>* spec, const cpx<double>* tat,
                                                      const cpx<double>* macc, const double* norms,
@@ -58,8 +61,8 @@ __global__ void __launch_bounds__(256) k_bw_finalize(const BwInst* bi, GridDesc 
   const int inst = blockIdx.x;
   const BwInst& I = bi[inst];
   const double k0 = sqrt(I.k[0] * I.k[0] + I.k[1] * I.k[1] + I.k[2] * I.k[2]);
-  const cpx<double>* su = spec + (size_t)(2 * inst) * 4 * g.N;
-  const cpx<double>* sv = spec + (size_t)(2 * inst + 1) * 4 * g.N;
+  const cpx<double>* su = spec + (size_t)(2 * I.src) * 4 * g.N;
+  const cpx<double>* sv = spec + (size_t)(2 * I.src + 1) * 4 * g.N;
   // scat, scat: sum over U modes kappa, V mode kappa - k (periodic), both energy signs each
   cpx<double> acc = mk<double>(0, 0);
   for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
@@ -157,8 +160,8 @@ __global__ void __launch_bounds__(256) k_bw_finalize(const BwInst* bi, GridDesc 
   o.amp[6] = M.x; o.amp[7] = M.y;
   o.prob[0] = M.x * M.x + M.y * M.y;
   o.prob[1] = 0.0;
-  o.diag[0] = norms[2 * inst];
-  o.diag[1] = norms[2 * inst + 1];
+  o.diag[0] = norms[2 * I.src];
+  o.diag[1] = norms[2 * I.src + 1];
 }
 
 swf_status bw_finalize(swf_ctx* ctx, const GridDesc& g, int n_inst, const void* bw_host, double t_in,
@@ -179,10 +182,128 @@ swf_status bw_finalize(swf_ctx* ctx, const GridDesc& g, int n_inst, const void* 
   return SWF_OK;
 }
 
+// Partial-integration form (Eqs. 30-33): one thread per instance turns the march's accumulators
+// macc[inst] = (mode sum of the ss integrand, D_U[4], D_V[4]) into the three terms.  With the
+// march's weights w_i = h b_i (h < 0) every term is M = -sum_i w_i M-dot(t_i):
+//   M_ss = -i dx^{2d} e^{i k.x0} / L^d * (mode sum)            (x0: the grid origin)
+//   M_bs = -i dx^d sum_s' u^+ (alpha.eps) P_s'(p - k) D_V / (p0 - s' E(p - k) - k0)
+//   M_sb = -i dx^d D_U^+ sum_s P_s(k - q) (alpha.eps) v / (s E(k - q) + q0 - k0)
+__global__ void k_bw_finalize_partial(const BwInst* bi, GridDesc g, const cpx<double>* macc, const double* norms,
+                                      swf_result* res) {
+  if (threadIdx.x != 0) return;
+  const int inst = blockIdx.x;
+  const BwInst& I = bi[inst];
+  const cpx<double>* m = macc + 9 * inst;
+  const double k0 = sqrt(I.k[0] * I.k[0] + I.k[1] * I.k[1] + I.k[2] * I.k[2]);
+  double vol = 1.0, kx0 = 0.0;
+  for (int a = 0; a < 3; ++a)
+    if (g.n[a] > 1) {
+      vol *= g.L[a];
+      kx0 += I.k[a] * g.x0[a];
+    }
+  const double cell = g.dx[0] * g.dx[1] * g.dx[2];
+  double sn, cs;
+  sincos(kx0, &sn, &cs);
+  const cpx<double> t_ss = mul_mi((cell * cell / vol) * (mk<double>(cs, sn) * m[0]));
+  // back, scat
+  double sp[8];
+  spinor_uv(I.p, I.s, false, sp);
+  cpx<double> ub[4], dv[4], pv[4], apv[4];
+  for (int a = 0; a < 4; ++a) {
+    ub[a] = mk<double>(sp[2 * a], sp[2 * a + 1]);
+    dv[a] = m[5 + a];
+  }
+  double kv[3];
+  for (int a = 0; a < 3; ++a) kv[a] = I.p[a] - I.k[a];
+  const double p0 = energy3(I.p), Ekv = energy3(kv);
+  cpx<double> bs = mk<double>(0, 0);
+  for (int sgp = -1; sgp <= 1; sgp += 2) {
+    proj_d(kv, sgp, dv, pv);
+    alpha_eps_d(I.eps, pv, apv);
+    cpx<double> d = mk<double>(0, 0);
+    for (int a = 0; a < 4; ++a) d = d + cdot(ub[a], apv[a]);
+    bs = bs + (1.0 / (p0 - sgp * Ekv - k0)) * d;
+  }
+  const cpx<double> t_bs = mul_mi(cell * bs);
+  // scat, back
+  spinor_uv(I.q, I.r, true, sp);
+  cpx<double> vb[4], avb[4], pw[4], wsb[4];
+  for (int a = 0; a < 4; ++a) {
+    vb[a] = mk<double>(sp[2 * a], sp[2 * a + 1]);
+    wsb[a] = mk<double>(0, 0);
+  }
+  alpha_eps_d(I.eps, vb, avb);
+  double ku[3];
+  for (int a = 0; a < 3; ++a) ku[a] = I.k[a] - I.q[a];
+  const double q0 = energy3(I.q), Eku = energy3(ku);
+  for (int sg = -1; sg <= 1; sg += 2) {
+    proj_d(ku, sg, avb, pw);
+    for (int a = 0; a < 4; ++a) wsb[a] = wsb[a] + (1.0 / (sg * Eku + q0 - k0)) * pw[a];
+  }
+  cpx<double> sb = mk<double>(0, 0);
+  for (int a = 0; a < 4; ++a) sb = sb + cdot(m[1 + a], wsb[a]);
+  const cpx<double> t_sb = mul_mi(cell * sb);
+  const cpx<double> M = t_ss + t_bs + t_sb;
+  swf_result& o = res[I.out];
+  o.amp[0] = t_ss.x; o.amp[1] = t_ss.y;
+  o.amp[2] = t_bs.x; o.amp[3] = t_bs.y;
+  o.amp[4] = t_sb.x; o.amp[5] = t_sb.y;
+  o.amp[6] = M.x; o.amp[7] = M.y;
+  o.prob[0] = M.x * M.x + M.y * M.y;
+  o.prob[1] = 0.0;
+  o.diag[0] = norms[2 * I.src];
+  o.diag[1] = norms[2 * I.src + 1];
+}
+
+swf_status bw_finalize_partial(swf_ctx* ctx, const GridDesc& g, int n_inst, const void* bw_host,
+                               const double2* macc, const double* norms, swf_result* results, cudaStream_t st) {
+  void* pb;
+  swf_status s = ws_get(ctx, "bw.inst", sizeof(BwInst) * n_inst, &pb);
+  if (s != SWF_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(pb, bw_host, sizeof(BwInst) * n_inst, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload Breit-Wheeler table");
+  {
+    ProfScope ps(ctx, "k_bw_finalize_partial", st);
+    k_bw_finalize_partial<<<n_inst, 32, 0, st>>>((const BwInst*)pb, g, (const cpx<double>*)macc, norms, results);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "Breit-Wheeler finalize (partial integration)");
+  return SWF_OK;
+}
+
+// Photon wave packet sampled on grid momenta (Sec. IV, closing paragraphs): by linearity in the
+// photon wave function its amplitude is sum_j w_j M(k_j, eps_j).  One thread adds the n amplitudes
+// (per term and in total) in order.
+__global__ void k_bw_packet(const swf_result* res, int n, const double* w, cpx<double>* out) {
+  if (threadIdx.x != 0) return;
+  cpx<double> acc[4] = {mk<double>(0, 0), mk<double>(0, 0), mk<double>(0, 0), mk<double>(0, 0)};
+  for (int j = 0; j < n; ++j) {
+    const cpx<double> wj = mk<double>(w[2 * j], w[2 * j + 1]);
+    for (int c = 0; c < 4; ++c) acc[c] = acc[c] + wj * mk<double>(res[j].amp[2 * c], res[j].amp[2 * c + 1]);
+  }
+  for (int c = 0; c < 4; ++c) out[c] = acc[c];
+}
+
+swf_status bw_packet(swf_ctx* ctx, int n, const swf_result* results, const double* weights_host, double2* out,
+                     cudaStream_t st) {
+  void* pw;
+  swf_status s = ws_get(ctx, "bw.packet_w", sizeof(double) * 2 * (size_t)n, &pw);
+  if (s != SWF_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(pw, weights_host, sizeof(double) * 2 * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload packet weights");
+  {
+    ProfScope ps(ctx, "k_bw_packet", st);
+    k_bw_packet<<<1, 32, 0, st>>>(results, n, (const double*)pw, (cpx<double>*)out);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "photon packet sum");
+  return SWF_OK;
+}
+
 size_t bw_inst_size() { return sizeof(BwInst); }
 
 void bw_fill_inst(void* dst, const swf_instance& in, int out, const FieldDesc& fu, const FieldDesc& fv,
-                  const int shift[3]) {
+                  const int shift[3], int src) {
   BwInst b;
   for (int a = 0; a < 3; ++a) {
     b.p[a] = in.p[a];
@@ -196,6 +317,7 @@ void bw_fill_inst(void* dst, const swf_instance& in, int out, const FieldDesc& f
   b.s = in.s;
   b.r = in.r;
   b.out = out;
+  b.src = src;
   *reinterpret_cast<BwInst*>(dst) = b;
 }
 

@@ -163,19 +163,31 @@ swf_status march_fields(swf_ctx* ctx, const GridDesc& g, double t_in, double t_o
 swf_status march_adaptive(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, double h0, int max_attempts,
                           int n_f, const FieldDesc* fd_host, swf_precision prec, void* psi_out, cudaStream_t st);
 // Breit-Wheeler: march U (fields 2i) and V (fields 2i+1) together and accumulate the appended
-// integral M(t) of Eq. 34 for (ss, bs, sb) into macc [n_inst][3] (M_finite = -M(t_in)).
-// photon_host: per instance k[3], eps[3].
+// integral M(t) of Eq. 34.  photon_host: per instance k[3], eps[3].
+// form 1: the integrand of Eq. 17 for (ss, bs, sb) into macc [n_inst][3] (M_finite = -M(t_in)).
+// form 2: the partial-integration integrand of Eqs. 30-33 into macc [n_inst][9]: the mode sum of
+//   the ss term, then the time-weighted direct transforms D_U[4] of -iV(U_scat + U_back) at
+//   k - q and D_V[4] of -iV(V_scat + V_back) at p - k (wave_k_host: per wave the momentum of its
+//   direct transform, 3 doubles; bw_finalize_partial turns these into amplitudes).
 swf_status march_bw(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_inst,
                     const FieldDesc* fd_host, const double* photon_host, swf_precision prec, void* psi_out,
-                    double2* macc, cudaStream_t st);
+                    double2* macc, cudaStream_t st, int form = 1, const double* wave_k_host = nullptr,
+                    int n_ph = 1);
+// (n_ph photons per instance, form 1 only: photon_host and macc then hold n_inst * n_ph entries,
+// photon j of instance i at i n_ph + j; the marched waves are shared by the photons.)
 
 // Breit-Wheeler past terms and totals (swf_bw.cu).
 size_t bw_inst_size();
 void bw_fill_inst(void* dst, const swf_instance& in, int out, const FieldDesc& fu, const FieldDesc& fv,
-                  const int shift[3]);
+                  const int shift[3], int src);
 swf_status bw_finalize(swf_ctx* ctx, const GridDesc& g, int n_inst, const void* bw_host, double t_in,
                        const double2* spec, const double2* tat, const double2* macc, const double* norms,
                        swf_result* results, cudaStream_t st);
+// sum_j w_j amp_j of n results (4 complex: the three terms and M); weights_host [n] complex.
+swf_status bw_packet(swf_ctx* ctx, int n, const swf_result* results, const double* weights_host, double2* out,
+                     cudaStream_t st);
+swf_status bw_finalize_partial(swf_ctx* ctx, const GridDesc& g, int n_inst, const void* bw_host,
+                               const double2* macc, const double* norms, swf_result* results, cudaStream_t st);
 
 // ---- fused cluster march (swf_fused.cu)
 bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_precision prec);

@@ -12,6 +12,9 @@
 // Gauge field and background are analytic and evaluated on the fly from per-field 1D tables
 // (every field kind is a product of a time factor and one factor per axis).
 #include <algorithm>
+#include <cmath>
+#include <map>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 
@@ -54,6 +57,8 @@ struct StageArgs {
   double c;             // Dormand-Prince node c_i of the stage
   const struct StepControl* ctl;  // step-size-controlled march, or null (see march_adaptive)
   cpx<R>* ynew;         // with ctl: the last stage writes the step's result here, not into y
+  cpx<R>* yspec;        // optional: receives the grid transform of the stage value (written by the
+                        // y or z pass that applies H0, before it does)
 };
 
 // State of a step-size-controlled march, in device memory: the accepted time t and the step h
@@ -575,6 +580,19 @@ __global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int lgtx,
   __syncthreads();
   cpx<R>* res = buf;
   if (do_fwd) res = fft_pp<R>(res, buf2, ld, 4 * TX, A.plan[axis], false, A.tw[axis]);
+  if (do_h0 && A.yspec) {
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int m = e >> lgtx;
+      const int t = e & (TX - 1);
+      const int x = xt * TX + t;
+      if (x < nx) {
+        const size_t gi = fo + base + m * stride + x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) A.yspec[gi + c * cs] = res[(c * TX + t) * ld + pad32(m)];
+      }
+    }
+    __syncthreads();
+  }
   if (do_h0) {
     const FieldDesc* F = A.fd + f;
     const R sc = (R)(1.0 / (double)N);
@@ -1585,29 +1603,43 @@ __global__ void k_photon_tables(const double* photon, GridDesc g, int n_inst, cp
   }
 }
 
-// Per instance, step and stage (Dormand-Prince nodes c_i): the background time phases of U and V
-// at t = t_out + (step + c_i) h and the quadrature factor w_i dx^d e^{-i k0 t} of the M-dot
-// integral, with w_i = h b_{i+1} for i = 2..5 and h b_1 (of the next step) for the last stage,
-// 0 elsewhere.  FP64, computed once per march so that the integrand kernel needs none.
-__global__ void k_bw_phase_table(const FieldDesc* fd, const double* photon, int n_inst, int n_steps, double t_out,
-                                 double h, double cell, cpx<double>* tab) {
+// Per instance, step and stage (Dormand-Prince nodes c_i) at t = t_out + (step + c_i) h, with the
+// quadrature weight w_i = h b_{i+1} for i = 2..5 and h b_1 (of the next step) for the last stage,
+// 0 elsewhere.  form 1: the background time phases of U and V and w_i dx^d e^{-i k0 t} (the
+// integrand of Eq. 17 vanishes at the first stage, psi_s(t_out) = 0).  form 2 (Eqs. 30-33):
+// w_i e^{-i(q0 - k0)t} and w_i e^{i(p0 - k0)t} for the direct transforms of the U and V waves
+// and w_i e^{-i k0 t} for the mode sum; the first stage of the march carries h b_1 (the source
+// term is not zero there).  FP64, computed once per march so that the integrand kernels need none.
+__global__ void k_bw_phase_table(const FieldDesc* fd, const double* photon, int n_pi, int n_ph, int n_steps,
+                                 double t_out, double h, double cell, int form, cpx<double>* tab) {
   const double DPc[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
   const double DPb[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
-  const long total = (long)n_inst * n_steps * 7;
+  const long total = (long)n_pi * n_steps * 7;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-    const int inst = (int)(e / (7L * n_steps));
+    const int pi = (int)(e / (7L * n_steps));  // photon-instance; its waves are those of instance pi / n_ph
+    const int inst = pi / n_ph;
     const int step = (int)((e / 7) % n_steps), i = (int)(e % 7);
     const double t = t_out + (step + DPc[i]) * h;
-    const double w = (i >= 2 && i <= 5) ? h * DPb[i] : (i == 6 && step + 1 < n_steps ? h * DPb[0] : 0.0);
+    double w = (i >= 2 && i <= 5) ? h * DPb[i] : (i == 6 && step + 1 < n_steps ? h * DPb[0] : 0.0);
+    if (form == 2 && i == 0 && step == 0) w = h * DPb[0];
     double sn, cs;
     const FieldDesc& FU = fd[2 * inst];
     const FieldDesc& FV = fd[2 * inst + 1];
+    const double k0 = sqrt(photon[6 * pi] * photon[6 * pi] + photon[6 * pi + 1] * photon[6 * pi + 1] +
+                           photon[6 * pi + 2] * photon[6 * pi + 2]);
+    if (form == 2) {
+      sincos(-(FV.e0 - k0) * t, &sn, &cs);
+      tab[3 * e] = mk<double>(w * cs, w * sn);
+      sincos((FU.e0 - k0) * t, &sn, &cs);
+      tab[3 * e + 1] = mk<double>(w * cs, w * sn);
+      sincos(-k0 * t, &sn, &cs);
+      tab[3 * e + 2] = mk<double>(w * cs, w * sn);
+      continue;
+    }
     sincos(FU.tsign * FU.e0 * t, &sn, &cs);
     tab[3 * e] = mk<double>(cs, sn);
     sincos(FV.tsign * FV.e0 * t, &sn, &cs);
     tab[3 * e + 1] = mk<double>(cs, sn);
-    const double k0 = sqrt(photon[6 * inst] * photon[6 * inst] + photon[6 * inst + 1] * photon[6 * inst + 1] +
-                           photon[6 * inst + 2] * photon[6 * inst + 2]);
     sincos(-k0 * t, &sn, &cs);
     tab[3 * e + 2] = mk<double>(w * cell * cs, w * cell * sn);
   }
@@ -1623,28 +1655,30 @@ __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o
   o[3] = e[0] * v[0] + e[1] * mul_i(v[0]) - e[2] * v[1];
 }
 
-// The three integrands of Eq. 33, dx^d sum_x U_a^+ (alpha.eps) V_b exp(-ikx), for (ss, bs, sb)
-// at the stage values, integrated with weight w (= h b_i).  Block (b, inst) sums the sites
-// j = b*256 + threadIdx.x (stride gridDim.x*256) of instance inst and adds w dx^d e^{-i k0 t}
-// (from the phase table) times its sum to its own accumulator acc[inst][b][3] (FP64; no other block touches it, so
+// The three integrands of Eq. 17, dx^d sum_x U_a^+ (alpha.eps) V_b exp(-ikx), for (ss, bs, sb)
+// at the stage values, integrated with weight w (= h b_i).  Block (b, pi) sums the sites
+// j = b*256 + threadIdx.x (stride gridDim.x*256) of photon-instance pi (photon pi % n_ph of
+// instance pi / n_ph: several photons share one march) and adds w dx^d e^{-i k0 t}
+// (from the phase table) times its sum to its own accumulator acc[pi][b][3] (FP64; no other block touches it, so
 // the march's sum is deterministic); k_mdot_final adds the accumulators in a fixed order.
 template <typename R>
 __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const cpx<R>* gcplx, const cpx<R>* kph,
                                               const double* photon, GridDesc g, const cpx<double>* __restrict__ ptab,
                                               const MarchClock* clk, int ls, int stage, int tab_stride,
-                                              cpx<double>* acc) {
+                                              int n_ph, cpx<double>* acc) {
   const long tab_row = (long)(clk->step + ls) * 7 + stage;
   __shared__ cpx<double> red[8][3];
-  const int inst = blockIdx.y;
+  const int pi = blockIdx.y;  // photon-instance: photon pi % n_ph of instance pi / n_ph
+  const int inst = pi / n_ph;
   const int nt = g.n[0] + g.n[1] + g.n[2];
   const cpx<R>* tu = gcplx + (size_t)(2 * inst) * (nt + 4);
   const cpx<R>* tv = gcplx + (size_t)(2 * inst + 1) * (nt + 4);
-  const cpx<R>* kp = kph + (size_t)inst * nt;
-  // this instance's row of the phase table: U and V time phases, quadrature factor
-  const cpx<double>* trow = ptab + 3 * (tab_row + (long)inst * tab_stride);
+  const cpx<R>* kp = kph + (size_t)pi * nt;
+  // this photon-instance's row of the phase table: U and V time phases, quadrature factor
+  const cpx<double>* trow = ptab + 3 * (tab_row + (long)pi * tab_stride);
   const cpx<R> tfu = cvt<R>(trow[0]), tfv = cvt<R>(trow[1]);
   R eps[3];
-  for (int a = 0; a < 3; ++a) eps[a] = (R)photon[6 * inst + 3 + a];
+  for (int a = 0; a < 3; ++a) eps[a] = (R)photon[6 * pi + 3 + a];
   const cpx<R>* U = ys + (size_t)(2 * inst) * 4 * g.N;
   const cpx<R>* V = ys + (size_t)(2 * inst + 1) * 4 * g.N;
   // per-thread sums in the march precision (a few sites each), then FP64 across threads
@@ -1694,7 +1728,7 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   if (threadIdx.x < 3) {
     cpx<double> sacc = mk<double>(0, 0);
     for (int wi = 0; wi < 8; ++wi) sacc = sacc + red[wi][threadIdx.x];
-    cpx<double>& a = acc[((size_t)inst * gridDim.x + blockIdx.x) * 3 + threadIdx.x];
+    cpx<double>& a = acc[((size_t)pi * gridDim.x + blockIdx.x) * 3 + threadIdx.x];
     a = a + trow[2] * sacc;
   }
 }
@@ -1714,11 +1748,508 @@ __global__ void __launch_bounds__(96) k_mdot_final(const cpx<double>* __restrict
   if (lane == 0) macc[3 * inst + q] = sacc;
 }
 
+// ---------------------------------------------------------------- partial-integration form (Sec. IV, Eqs. 28-33)
+// The integrand of Eq. 33 and its analogues for (back, scat) and (scat, back), written with the grid
+// transform psi~(kappa) and the energy projectors P_sigma of Eq. 23.  The time derivative of the split
+// parts P_sigma psi~ e^{i sigma E t} is P_sigma F[Z] with Z = -i V (psi_s + psi_b) (Eq. 6), so per
+// stage the march needs F[psi_s] and F[Z] of both waves on every grid mode (ss) and F[Z] at one
+// off-grid momentum per wave (bs: V wave at p - k, sb: U wave at k - q).
+
+// Per wave and axis: exp(-i kappa_a x_a) on the grid coordinates (trivial axes: 1), kappa = the wave's
+// direct-transform momentum (3 doubles per wave).
+template <typename R>
+__global__ void k_f2_dtables(const double* wave_k, GridDesc g, int n_waves, cpx<R>* dph) {
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_waves * nt; i += gridDim.x * blockDim.x) {
+    const int wv = i / nt;
+    int j = i % nt, axis = 0;
+    while (j >= g.n[axis]) { j -= g.n[axis]; ++axis; }
+    const double xc = g.n[axis] > 1 ? g.x0[axis] + j * g.dx[axis] : 0.0;
+    double sn, cs;
+    sincos(-wave_k[3 * wv + axis] * xc, &sn, &cs);
+    dph[i] = mk<R>((R)cs, (R)sn);
+  }
+}
+
+// Parameters of one mode-sum table: the photon's mode shift per axis, the fixed momenta of U and V
+// along trivial axes, and k0.
+struct F2Table {
+  int shift[3];
+  int pad;
+  double Ku[3], Kv[3], k0;
+};
+
+// Per table and U grid mode j (V mode j - shift, periodic): rho / Omega_{sigma sigma'} for
+// (sigma, sigma') = (+,+), (+,-), (-,+), (-,-), Omega = sigma E_u - sigma' E_v - k0, in FP64 and
+// rounded once.  rho = exp(i (kappa_u - kappa_v - k).x0) = +-1 is the origin phase that the wrapped
+// V mode leaves after exp(i k.x0) is taken out (-1 only for an odd axis length).
+template <typename R>
+__global__ void k_f2_omega_table(const F2Table* tabs, GridDesc g, int n_tab, R* omt) {
+  const long total = (long)n_tab * g.N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const F2Table& T = tabs[e / g.N];
+    const int j = (int)(e % g.N);
+    const int id[3] = {j % g.n[0], (j / g.n[0]) % g.n[1], j / (g.n[0] * g.n[1])};
+    double ku[3], kv[3];
+    int odd = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int jv = ((id[a] - T.shift[a]) % g.n[a] + g.n[a]) % g.n[a];
+      ku[a] = kappa_of(id[a], g.n[a], g.L[a], T.Ku[a]);
+      kv[a] = kappa_of(jv, g.n[a], g.L[a], T.Kv[a]);
+      if (g.n[a] > 1 && (g.n[a] & 1)) {
+        // integer wrap count of (f(id) - f(jv) - shift) / n along this axis
+        const long fu = id[a] < (g.n[a] + 1) / 2 ? id[a] : id[a] - g.n[a];
+        const long fv = jv < (g.n[a] + 1) / 2 ? jv : jv - g.n[a];
+        const long wr = (fu - fv - T.shift[a]) / g.n[a];
+        odd ^= (int)(wr & 1);
+      }
+    }
+    const double eu = energy3(ku), ev = energy3(kv);
+    const double rho = odd ? -1.0 : 1.0;
+    R* o = omt + 4 * e;
+    o[0] = (R)(rho / (eu - ev - T.k0));
+    o[1] = (R)(rho / (eu + ev - T.k0));
+    o[2] = (R)(rho / (-eu - ev - T.k0));
+    o[3] = (R)(rho / (-eu + ev - T.k0));
+  }
+}
+
+// x lines of `rows` grid rows of wave f = 2 inst + (0: U, 1: V) at a weighted stage:
+// Z = -i V (Y + psi_b) of the stage value Y (from ys; the local term of the right-hand side,
+// evaluated as in k_first) x-transformed into Zspec[f], and with do_y also Y into Yspec[f] (grids
+// without a y or z pass; otherwise the right-hand side's pass writes the transform of Y); and
+// the block's part of sum_x exp(-i kappa.x) Z(x) (the wave's direct transform), which
+// trow[w] (w_i and its time phase) times adds to the block's own FP64 accumulators
+// dpart[f][block][4] (no other block touches them: the sum is deterministic).
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_f2_x(StageArgs<R> A, const cpx<R>* __restrict__ ys, cpx<R>* __restrict__ Yspec,
+                                              cpx<R>* __restrict__ Zspec, int do_y, const cpx<R>* __restrict__ dph,
+                                              const cpx<double>* __restrict__ ptab, int tab_stride, int stage,
+                                              cpx<double>* dpart, int rows, int ld) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* buf2 = buf + 4 * rows * ld;
+  __shared__ double s_ft[64];
+  __shared__ cpx<R> s_tf;
+  __shared__ cpx<double> red[8][4];
+  const int f = blockIdx.y;
+  const int inst = f >> 1, w = f & 1;
+  const int row0 = blockIdx.x * rows;
+  const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
+  const int N = A.g.N;
+  const size_t fo = (size_t)f * 4 * N;
+  const size_t cs = (size_t)N;
+  const FieldDesc* F = A.fd + f;
+  const double tst = stage_time(A);
+  for (int j = threadIdx.x; j < rows; j += blockDim.x) {
+    const int iy = (row0 + j) % ny;
+    const double yc = ny > 1 ? A.g.x0[1] + iy * A.g.dx[1] : 0.0;
+    s_ft[j] = field_time_factor(*F, tst, yc);
+  }
+  if (threadIdx.x == 0) {
+    double sn, c;
+    sincos(F->tsign * F->e0 * tst, &sn, &c);
+    s_tf = mk<R>((R)c, (R)sn);
+  }
+  __syncthreads();
+  const int nt = nx + ny + nz;
+  const R* gx = A.greal + (size_t)f * nt;
+  const R* gy = gx + nx;
+  const R* gz = gy + ny;
+  const cpx<R>* ex = A.gcplx + (size_t)f * (nt + 4);
+  const cpx<R>* ey = ex + nx;
+  const cpx<R>* ez = ey + ny;
+  const cpx<R>* wsp = ez + nz;
+  const cpx<R>* dx = dph + (size_t)f * nt;
+  const int acomp = F->acomp;
+  const int per = rows * nx;
+  cpx<R>* sy = Yspec + fo;
+  cpx<R>* sz = Zspec + fo;
+  cpx<R> dsum[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) dsum[c] = mk<R>(0, 0);
+  for (int part = do_y ? 0 : 1; part < 2; ++part) {
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int j = e / nx;
+      const int x = e - j * nx;
+      const int row = row0 + j;
+      cpx<R> v[4];
+      if (row < A.nrows) {
+        const size_t gi = fo + (size_t)row * nx + x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = ys[gi + c * cs];
+        if (part == 1) {
+          const int iy = row % ny, iz = row / ny;
+          const R a = (R)s_ft[j] * gx[x] * gy[iy] * gz[iz];
+          const cpx<R> ph = s_tf * ex[x] * ey[iy] * ez[iz];
+          cpx<R> phi[4], vz[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) phi[c] = v[c] + wsp[c] * ph;
+          apply_v<R>(acomp, a, phi, vz);
+          const cpx<R> dp = dx[x] * dx[nx + iy] * dx[nx + ny + iz];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            v[c] = mul_mi(vz[c]);
+            dsum[c] = dsum[c] + v[c] * dp;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = mk<R>(0, 0);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) buf[(c * rows + j) * ld + pad32(x)] = v[c];
+    }
+    __syncthreads();
+    cpx<R>* res = fft_pp<R>(buf, buf2, ld, 4 * rows, A.plan[0], false, A.tw[0]);
+    cpx<R>* dst = part == 0 ? sy : sz;
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int j = e / nx;
+      const int x = e - j * nx;
+      const int row = row0 + j;
+      if (row < A.nrows) {
+        const size_t gi = (size_t)row * nx + x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dst[gi + c * cs] = res[(c * rows + j) * ld + pad32(x)];
+      }
+    }
+    __syncthreads();
+  }
+  // block sum of the direct transform (FP64 across threads)
+  cpx<double> ds[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    ds[c] = cvt<double>(dsum[c]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      ds[c].x += __shfl_down_sync(0xffffffffu, ds[c].x, off);
+      ds[c].y += __shfl_down_sync(0xffffffffu, ds[c].y, off);
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[threadIdx.x >> 5][c] = ds[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const long tab_row = (long)(A.clk->step + A.ls) * 7 + stage;
+    const cpx<double> wt = ptab[3 * (tab_row + (long)inst * tab_stride) + w];
+    cpx<double> sacc = mk<double>(0, 0);
+    for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) sacc = sacc + red[wi][threadIdx.x];
+    cpx<double>& a = dpart[((size_t)f * gridDim.x + blockIdx.x) * 4 + threadIdx.x];
+    a = a + wt * sacc;
+  }
+}
+
+// o = P_+(kappa) x = (x + H0(kappa) x / E) / 2, the positive-energy part (evolves as e^{-iEt}).
+template <typename R>
+__device__ __forceinline__ void proj_plus(const R* kk, R inv_e, const cpx<R>* x, cpx<R>* o) {
+  cpx<R> hx[4];
+  alpha_eps<R>(kk, x, hx);
+  const R hh = (R)0.5 * inv_e;
+  o[0] = (R)0.5 * x[0] + hh * (hx[0] + x[0]);
+  o[1] = (R)0.5 * x[1] + hh * (hx[1] + x[1]);
+  o[2] = (R)0.5 * x[2] + hh * (hx[2] - x[2]);
+  o[3] = (R)0.5 * x[3] + hh * (hx[3] - x[3]);
+}
+
+// sum_a conj(x_a) (alpha.eps y)_a
+template <typename R>
+__device__ __forceinline__ cpx<R> form_ae(const cpx<R>* x, const cpx<R>* aey) {
+  cpx<R> d = cdot(x[0], aey[0]);
+#pragma unroll
+  for (int a = 1; a < 4; ++a) d = d + cdot(x[a], aey[a]);
+  return d;
+}
+
+// The mode sum of the (scat, scat) integrand at one weighted stage, on the raw transforms Yspec, Zspec
+// of the waves (no cell factor, no origin phase):
+//   sum_j sum_{sigma,sigma'} rho/Omega [ (P_s Zu~)^+ (alpha.eps) P_s' Yv~ + (P_s Yu~)^+ (alpha.eps) P_s' Zv~ ]
+// with U quantities at mode j and V quantities at mode j - shift.  Block (b, inst) adds trow[2]
+// (w_i e^{-i k0 t}) times its part to its own accumulator sspart[inst][b].
+// f2i per instance: shift[3], table index.
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_f2_ss(const cpx<R>* __restrict__ Yspec, const cpx<R>* __restrict__ Zspec,
+                                               GridDesc g, const FieldDesc* fd,
+                                               const double* photon, const int* __restrict__ f2i,
+                                               const R* __restrict__ omt, const cpx<double>* __restrict__ ptab,
+                                               const MarchClock* clk, int ls, int stage, int tab_stride,
+                                               cpx<double>* sspart) {
+  __shared__ cpx<double> red[8];
+  const int inst = blockIdx.y;
+  const int N = g.N;
+  const int shift[3] = {f2i[4 * inst], f2i[4 * inst + 1], f2i[4 * inst + 2]};
+  const R* om = omt + (size_t)f2i[4 * inst + 3] * 4 * N;
+  const FieldDesc& FU = fd[2 * inst];
+  const FieldDesc& FV = fd[2 * inst + 1];
+  R eps[3];
+  for (int a = 0; a < 3; ++a) eps[a] = (R)photon[6 * inst + 3 + a];
+  const cpx<R>* Yu = Yspec + (size_t)(2 * inst) * 4 * N;
+  const cpx<R>* Yv = Yu + (size_t)4 * N;
+  const cpx<R>* Zu = Zspec + (size_t)(2 * inst) * 4 * N;
+  const cpx<R>* Zv = Zu + (size_t)4 * N;
+  // mode spacing 2 pi / L per axis (the mode index times it is kappa; trivial axes: fixed K)
+  R du[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) du[a] = (R)(6.283185307179586476925286766559 / g.L[a]);
+  cpx<R> tacc = mk<R>(0, 0);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    const int id[3] = {j % g.n[0], (j / g.n[0]) % g.n[1], j / (g.n[0] * g.n[1])};
+    int jv[3];
+    R ku[3], kv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int n = g.n[a];
+      jv[a] = id[a] - shift[a];
+      if (jv[a] < 0) jv[a] += n;
+      if (jv[a] >= n) jv[a] -= n;
+      const int fu = id[a] < (n + 1) / 2 ? id[a] : id[a] - n;
+      const int fv = jv[a] < (n + 1) / 2 ? jv[a] : jv[a] - n;
+      ku[a] = n > 1 ? du[a] * (R)fu : (R)FU.K[a];
+      kv[a] = n > 1 ? du[a] * (R)fv : (R)FV.K[a];
+    }
+    const int j2 = (jv[2] * g.n[1] + jv[1]) * g.n[0] + jv[0];
+    const R ieu = (R)1 / sqrt((R)1 + ku[0] * ku[0] + ku[1] * ku[1] + ku[2] * ku[2]);
+    const R iev = (R)1 / sqrt((R)1 + kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+    cpx<R> y[4], z[4], ap[4], am[4], dap[4], dam[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      y[c] = Yu[(size_t)c * N + j];
+      z[c] = Zu[(size_t)c * N + j];
+    }
+    proj_plus<R>(ku, ieu, y, ap);
+    proj_plus<R>(ku, ieu, z, dap);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      am[c] = y[c] - ap[c];
+      dam[c] = z[c] - dap[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      y[c] = Yv[(size_t)c * N + j2];
+      z[c] = Zv[(size_t)c * N + j2];
+    }
+    cpx<R> bp[4], bm[4], dbp[4], dbm[4], t1[4], t2[4];
+    proj_plus<R>(kv, iev, y, t1);
+    proj_plus<R>(kv, iev, z, t2);
+    alpha_eps<R>(eps, t1, bp);
+    alpha_eps<R>(eps, t2, dbp);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      t1[c] = y[c] - t1[c];
+      t2[c] = z[c] - t2[c];
+    }
+    alpha_eps<R>(eps, t1, bm);
+    alpha_eps<R>(eps, t2, dbm);
+    const R* o = om + 4 * (size_t)j;
+    const R opp = o[0], opm = o[1], omp = o[2], omm = o[3];
+    tacc = tacc + opp * (form_ae<R>(dap, bp) + form_ae<R>(ap, dbp));
+    tacc = tacc + opm * (form_ae<R>(dap, bm) + form_ae<R>(ap, dbm));
+    tacc = tacc + omp * (form_ae<R>(dam, bp) + form_ae<R>(am, dbp));
+    tacc = tacc + omm * (form_ae<R>(dam, bm) + form_ae<R>(am, dbm));
+  }
+  cpx<double> s = cvt<double>(tacc);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s.x += __shfl_down_sync(0xffffffffu, s.x, off);
+    s.y += __shfl_down_sync(0xffffffffu, s.y, off);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const long tab_row = (long)(clk->step + ls) * 7 + stage;
+    const cpx<double> wt = ptab[3 * (tab_row + (long)inst * tab_stride) + 2];
+    cpx<double> sacc = mk<double>(0, 0);
+    for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) sacc = sacc + red[wi];
+    cpx<double>& a = sspart[(size_t)inst * gridDim.x + blockIdx.x];
+    a = a + wt * sacc;
+  }
+}
+
+// macc[inst] = (ss, D_U[4], D_V[4]): warp 0 sums the mode-sum accumulators of the instance, warps
+// 1-4 the U wave's direct transform components, warps 5-8 the V wave's, each in a fixed order.
+__global__ void __launch_bounds__(288) k_f2_final(const cpx<double>* __restrict__ sspart, int nbs,
+                                                  const cpx<double>* __restrict__ dpart, int nbx,
+                                                  cpx<double>* macc) {
+  const int inst = blockIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cpx<double> sacc = mk<double>(0, 0);
+  if (q == 0) {
+    for (int b = lane; b < nbs; b += 32) sacc = sacc + sspart[(size_t)inst * nbs + b];
+  } else {
+    const int wv = 2 * inst + (q - 1) / 4, c = (q - 1) % 4;
+    for (int b = lane; b < nbx; b += 32) sacc = sacc + dpart[((size_t)wv * nbx + b) * 4 + c];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sacc.x += __shfl_down_sync(0xffffffffu, sacc.x, off);
+    sacc.y += __shfl_down_sync(0xffffffffu, sacc.y, off);
+  }
+  if (lane == 0) macc[9 * inst + q] = sacc;
+}
+
+// Buffers and launch shapes of the partial-integration integrand.
+template <typename R>
+struct F2Plan {
+  cpx<R>* Yspec = nullptr;   // [2 n_inst][4][N]: transforms of the stage values Y of both waves
+  cpx<R>* Zspec = nullptr;   // [2 n_inst][4][N]: transforms of Z = -i V (Y + psi_b)
+  int has_mid = 0;           // a y or z pass exists (it writes Yspec)
+  cpx<R>* dph = nullptr;     // [2 n_inst][nx + ny + nz]: direct-transform phases per wave
+  int* f2i = nullptr;        // [n_inst][4]: photon mode shift, table index
+  R* omt = nullptr;          // [tables][N][4]: rho / Omega
+  cpx<double>* dpart = nullptr;   // [2 n_inst][nbx][4]
+  cpx<double>* sspart = nullptr;  // [n_inst][nbs]
+  int n_inst = 0, nbx = 0, nbs = 0, rows = 0, ld = 0, xthr = 256;
+  size_t smem_x = 0;
+};
+
+template <typename R>
+static swf_status f2_prepare(swf_ctx* ctx, const GridDesc& g, int n_inst, const FieldDesc* fd_host,
+                             const double* photon_host, const double* wave_k_host, const StageArgs<R>& A,
+                             F2Plan<R>* p, cudaStream_t st) {
+  static bool attr_done[64] = {false};
+  const int dv = dev_slot();
+  cudaError_t e;
+  if (!attr_done[dv]) {
+    e = cudaFuncSetAttribute(k_f2_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+    if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_f2_x)");
+    attr_done[dv] = true;
+  }
+  const int nx = g.n[0];
+  const int nrows = g.n[1] * g.n[2];
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  p->n_inst = n_inst;
+  // rows per block and block size of the right-hand side's x passes (tuned by timing if enabled)
+  const int xv = tune_lookup(ctx, tune_key('x', (int)sizeof(cpx<R>), nx, nrows, 0, 2 * n_inst),
+                             4 * x_rows<R>(nx, nrows, 2 * n_inst));
+  p->rows = xv >> 2;
+  p->xthr = (xv & 3) ? kThreads / 2 : kThreads;
+  if (p->rows < 1) {
+    set_error("partial-integration integrand: an x line does not fit shared memory");
+    return SWF_EUNSUPPORTED;
+  }
+  p->ld = padded_len(nx);
+  p->smem_x = (size_t)2 * 4 * p->rows * p->ld * sizeof(cpx<R>);
+  p->nbx = (nrows + p->rows - 1) / p->rows;
+  // one mode per thread where the grid allows (the gathers of the V modes are latency-bound)
+  p->nbs = std::max(1, std::min((g.N + 255) / 256, (32 * sm_count() + n_inst - 1) / n_inst));
+  // mode-sum tables, shared by instances with the same photon shift, trivial-axis momenta and k0
+  std::vector<int> info(4 * (size_t)n_inst);
+  std::vector<F2Table> tabs;
+  std::map<std::vector<double>, int> seen;
+  for (int i = 0; i < n_inst; ++i) {
+    F2Table T;
+    std::memset(&T, 0, sizeof T);
+    const double* k = photon_host + 6 * i;
+    for (int a = 0; a < 3; ++a) {
+      T.shift[a] = g.n[a] > 1 ? (int)std::lround(k[a] * g.L[a] / 6.283185307179586476925286766559) : 0;
+      T.Ku[a] = fd_host[2 * i].K[a];
+      T.Kv[a] = fd_host[2 * i + 1].K[a];
+    }
+    T.k0 = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+    const std::vector<double> key = {(double)T.shift[0], (double)T.shift[1], (double)T.shift[2], T.Ku[0], T.Ku[1],
+                                     T.Ku[2], T.Kv[0], T.Kv[1], T.Kv[2], T.k0};
+    auto it = seen.find(key);
+    int id;
+    if (it == seen.end()) {
+      id = (int)tabs.size();
+      seen[key] = id;
+      tabs.push_back(T);
+    } else {
+      id = it->second;
+    }
+    for (int a = 0; a < 3; ++a) info[4 * i + a] = T.shift[a];
+    info[4 * i + 3] = id;
+  }
+  const int n_tab = (int)tabs.size();
+  constexpr size_t esz = sizeof(cpx<R>);
+  void *pY, *pZ, *pdph, *pinfo, *ptabs, *pomt, *pdp, *pss, *pwk;
+  swf_status s;
+  if ((s = ws_get(ctx, "bw2.yspec", (size_t)2 * n_inst * 4 * g.N * esz, &pY)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw2.zspec", (size_t)2 * n_inst * 4 * g.N * esz, &pZ)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw2.dph", (size_t)2 * n_inst * nt * esz, &pdph)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw2.wavek", sizeof(double) * 6 * (size_t)n_inst, &pwk)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw2.info", sizeof(int) * 4 * (size_t)n_inst, &pinfo)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw2.tabs", sizeof(F2Table) * (size_t)n_tab, &ptabs)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw2.omega", sizeof(R) * 4 * (size_t)n_tab * g.N, &pomt)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw2.dpart", sizeof(cpx<double>) * 4 * (size_t)2 * n_inst * p->nbx, &pdp)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw2.sspart", sizeof(cpx<double>) * (size_t)n_inst * p->nbs, &pss)) != SWF_OK) return s;
+  p->Yspec = (cpx<R>*)pY;
+  p->Zspec = (cpx<R>*)pZ;
+  p->has_mid = (g.n[1] > 1 || g.n[2] > 1) ? 1 : 0;
+  p->dph = (cpx<R>*)pdph;
+  p->f2i = (int*)pinfo;
+  p->omt = (R*)pomt;
+  p->dpart = (cpx<double>*)pdp;
+  p->sspart = (cpx<double>*)pss;
+  if ((e = cudaMemcpyAsync(pwk, wave_k_host, sizeof(double) * 6 * n_inst, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(pinfo, info.data(), sizeof(int) * info.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ptabs, tabs.data(), sizeof(F2Table) * tabs.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_status(e, "upload partial-integration tables");
+  if ((e = cudaMemsetAsync(pdp, 0, sizeof(cpx<double>) * 4 * (size_t)2 * n_inst * p->nbx, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(pss, 0, sizeof(cpx<double>) * (size_t)n_inst * p->nbs, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(pY, 0, (size_t)2 * n_inst * 4 * g.N * esz, st)) != cudaSuccess)
+    return cuda_status(e, "memset partial-integration accumulators");
+  {
+    ProfScope ps(ctx, "k_f2_dtables", st);
+    k_f2_dtables<R><<<(2 * n_inst * nt + 127) / 128, 128, 0, st>>>((const double*)pwk, g, 2 * n_inst, p->dph);
+  }
+  {
+    const long total = (long)n_tab * g.N;
+    ProfScope ps(ctx, "k_f2_omega_table", st);
+    k_f2_omega_table<R><<<(int)std::min((total + 255) / 256, 8192L), 256, 0, st>>>((const F2Table*)ptabs, g, n_tab,
+                                                                                   p->omt);
+  }
+  (void)A;
+  // the host tables above are temporaries
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "partial-integration tables");
+  return SWF_OK;
+}
+
+// One evaluation of the partial-integration integrand at stage `stage` of step (clock step + ls), on
+// the stage values ys of all waves: x transforms with Z and the direct transforms, forward y (and
+// z) transforms of the spectra, then the mode sum.
+template <typename R>
+static swf_status f2_integrand(swf_ctx* ctx, const StageArgs<R>& A, const F2Plan<R>& p, const cpx<R>* ys,
+                               const double* photon_dev, const cpx<double>* ptab, int tab_stride, int ls, int stage,
+                               cudaStream_t st) {
+  const GridDesc& g = A.g;
+  const int G = p.n_inst;
+  StageArgs<R> B = A;
+  B.ls = ls;
+  B.c = DP_C[stage];
+  {
+    ProfScope ps(ctx, "k_f2_x", st);
+    k_f2_x<R><<<dim3(p.nbx, 2 * G), p.xthr, p.smem_x, st>>>(B, ys, p.Yspec, p.Zspec, p.has_mid ? 0 : 1, p.dph,
+                                                             ptab, tab_stride, stage, p.dpart, p.rows, p.ld);
+  }
+  StageArgs<R> C = A;
+  C.T = p.Zspec;
+  C.yspec = nullptr;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  for (int axis = 1; axis <= 2; ++axis) {
+    if (g.n[axis] <= 1) continue;
+    const int other = axis == 1 ? nz : ny;
+    const MidShape ms = mid_shape<R>(g.n[axis], nx, (long)other * 2 * G);
+    const int ntx = (nx + (1 << ms.lgtx) - 1) >> ms.lgtx;
+    ProfScope ps(ctx, "k_mid", st);
+    k_mid<R><<<dim3(ntx * other, 2 * G), kThreads, ms.smem, st>>>(C, axis, ms.lgtx, ms.ld, 1, 0, 0);
+  }
+  {
+    ProfScope ps(ctx, "k_f2_ss", st);
+    k_f2_ss<R><<<dim3(p.nbs, G), kThreads, 0, st>>>(p.Yspec, p.Zspec, g, A.fd, photon_dev, p.f2i, p.omt, ptab, A.clk,
+                                                    ls, stage, tab_stride, p.sspart);
+  }
+  return SWF_OK;
+}
+
 template <typename R>
 static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_inst,
                                 const FieldDesc* fd_host, const double* photon_host, void* psi_out, double2* macc,
-                                cudaStream_t st) {
+                                cudaStream_t st, int form, const double* wave_k_host, int n_ph) {
   const int F = 2 * n_inst;
+  const int NP = n_inst * n_ph;  // photon-instances: photon j of instance i is i n_ph + j
   StageArgs<R> A;
   swf_status s = prepare_args<R>(ctx, g, F, fd_host, &A, "bw", st);
   if (s != SWF_OK) return s;
@@ -1733,31 +2264,31 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
     std::snprintf(nm, sizeof nm, "march.k%d", i);
     if ((s = ws_get(ctx, nm, state, &pk[i])) != SWF_OK) return s;
   }
-  if ((s = ws_get(ctx, "bw.photon", sizeof(double) * 6 * n_inst, &pph)) != SWF_OK) return s;
-  if ((s = ws_get(ctx, "bw.kph", sizeof(cpx<R>) * n_inst * nt, &pkph)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.photon", sizeof(double) * 6 * NP, &pph)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.kph", sizeof(cpx<R>) * NP * nt, &pkph)) != SWF_OK) return s;
   // blocks per instance of the M-dot reduction: about four waves of the GPU in total, at least
   // 1024 sites per block
   const int nb = std::max(1, std::min((g.N + 1023) / 1024, (4 * sm_count() + n_inst - 1) / n_inst));
   void* ptab;
-  if ((s = ws_get(ctx, "bw.phase_table", sizeof(cpx<double>) * 3 * 7 * (size_t)n_steps * n_inst, &ptab)) != SWF_OK)
+  if ((s = ws_get(ctx, "bw.phase_table", sizeof(cpx<double>) * 3 * 7 * (size_t)n_steps * NP, &ptab)) != SWF_OK)
     return s;
   void* ppart;
-  if ((s = ws_get(ctx, "bw.mpart", sizeof(cpx<double>) * 3 * (size_t)nb * n_inst, &ppart)) != SWF_OK) return s;
-  cudaError_t e = cudaMemcpyAsync(pph, photon_host, sizeof(double) * 6 * n_inst, cudaMemcpyHostToDevice, st);
+  if ((s = ws_get(ctx, "bw.mpart", sizeof(cpx<double>) * 3 * (size_t)nb * NP, &ppart)) != SWF_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(pph, photon_host, sizeof(double) * 6 * NP, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "upload photon table");
   {
     ProfScope ps(ctx, "k_photon_tables", st);
-    k_photon_tables<R><<<(n_inst * nt + 127) / 128, 128, 0, st>>>((const double*)pph, g, n_inst, (cpx<R>*)pkph);
+    k_photon_tables<R><<<(NP * nt + 127) / 128, 128, 0, st>>>((const double*)pph, g, NP, (cpx<R>*)pkph);
   }
   {
-    const long total = (long)n_inst * n_steps * 7;
+    const long total = (long)NP * n_steps * 7;
     ProfScope ps(ctx, "k_bw_phase_table", st);
     k_bw_phase_table<<<(int)std::min((total + 127) / 128, 4096L), 128, 0, st>>>(
-        A.fd, (const double*)pph, n_inst, n_steps, t_out, (t_in - t_out) / n_steps, g.dx[0] * g.dx[1] * g.dx[2],
-        (cpx<double>*)ptab);
+        A.fd, (const double*)pph, NP, n_ph, n_steps, t_out, (t_in - t_out) / n_steps, g.dx[0] * g.dx[1] * g.dx[2],
+        form, (cpx<double>*)ptab);
   }
   if ((e = cudaMemsetAsync(py, 0, state, st)) != cudaSuccess) return cuda_status(e, "memset state");
-  if ((e = cudaMemsetAsync(ppart, 0, sizeof(cpx<double>) * 3 * (size_t)nb * n_inst, st)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ppart, 0, sizeof(cpx<double>) * 3 * (size_t)nb * NP, st)) != cudaSuccess)
     return cuda_status(e, "memset M accumulators");
   A.y = (cpx<R>*)py;
   A.T = (cpx<R>*)pT;
@@ -1774,6 +2305,9 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
     B.t = t_out;
     if ((s = autotune_eval<R>(ctx, B, F, st)) != SWF_OK) return s;
   }
+  F2Plan<R> p2;  // after the tuning: the integrand's x pass takes the tuned shape of the x passes
+  if (form == 2 && (s = f2_prepare<R>(ctx, g, n_inst, fd_host, photon_host, wave_k_host, A, &p2, st)) != SWF_OK)
+    return s;
   int slot[7] = {0, 1, 2, 3, 4, 5, 6};
   const double h = (t_in - t_out) / n_steps;
   void* pclk = nullptr;
@@ -1786,8 +2320,12 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   A.kout = (cpx<R>*)pk[slot[0]];
   A.ls = 0;
   A.c = 0.0;
-  A.ystage = nullptr;  // M-dot vanishes at psi_s(t_out) = 0
+  A.ystage = nullptr;  // the integrand of Eq. 17 vanishes at psi_s(t_out) = 0
   if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  // the partial-integration integrand does not (its source term is V psi_b): stage value y = 0
+  if (form == 2 && (s = f2_integrand<R>(ctx, A, p2, (const cpx<R>*)py, (const double*)pph, (const cpx<double>*)ptab,
+                                        7 * n_steps, 0, 0, st)) != SWF_OK)
+    return s;
   auto step = [&](int ls) -> swf_status {
     for (int i = 1; i < 7; ++i) {
       int ntm = 0;
@@ -1807,13 +2345,18 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
       // step launches the same kernels)
       const bool weighted = i >= 2;
       A.ystage = weighted ? (cpx<R>*)pys : nullptr;
+      A.yspec = (weighted && form == 2) ? p2.Yspec : nullptr;  // the y or z pass writes F[Y] (if there is one)
       swf_status r = launch_eval<R>(ctx, A, F, st);
       if (r != SWF_OK) return r;
-      if (weighted) {
+      if (weighted && form == 2) {
+        if ((r = f2_integrand<R>(ctx, A, p2, (const cpx<R>*)pys, (const double*)pph, (const cpx<double>*)ptab,
+                                 7 * n_steps, ls, i, st)) != SWF_OK)
+          return r;
+      } else if (weighted) {
         ProfScope ps(ctx, "k_mdot", st);
-        k_mdot<R><<<dim3(nb, n_inst), 256, 0, st>>>((const cpx<R>*)pys, A.gcplx, (const cpx<R>*)pkph,
-                                                    (const double*)pph, g, (const cpx<double>*)ptab, clk, ls, i,
-                                                    7 * n_steps, (cpx<double>*)ppart);
+        k_mdot<R><<<dim3(nb, NP), 256, 0, st>>>((const cpx<R>*)pys, A.gcplx, (const cpx<R>*)pkph,
+                                                (const double*)pph, g, (const cpx<double>*)ptab, clk, ls, i,
+                                                7 * n_steps, n_ph, (cpx<double>*)ppart);
       }
     }
     std::swap(slot[0], slot[6]);
@@ -1825,9 +2368,12 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   });
   if (s != SWF_OK) return s;
   if (n_steps % 2 && (s = step(0)) != SWF_OK) return s;
-  {
+  if (form == 2) {
+    ProfScope ps(ctx, "k_f2_final", st);
+    k_f2_final<<<n_inst, 288, 0, st>>>(p2.sspart, p2.nbs, p2.dpart, p2.nbx, (cpx<double>*)macc);
+  } else {
     ProfScope ps(ctx, "k_mdot_final", st);
-    k_mdot_final<<<n_inst, 96, 0, st>>>((const cpx<double>*)ppart, nb, (cpx<double>*)macc);
+    k_mdot_final<<<NP, 96, 0, st>>>((const cpx<double>*)ppart, nb, (cpx<double>*)macc);
   }
   e = cudaMemcpyAsync(psi_out, py, state, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "copy psi(t_in)");
@@ -1838,10 +2384,20 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
 
 swf_status march_bw(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_inst,
                     const FieldDesc* fd_host, const double* photon_host, swf_precision prec, void* psi_out,
-                    double2* macc, cudaStream_t st) {
+                    double2* macc, cudaStream_t st, int form, const double* wave_k_host, int n_ph) {
+  if (form == 2 && (!wave_k_host || n_ph != 1)) {
+    set_error("march_bw: the partial-integration form needs the direct-transform momenta and one photon per instance");
+    return SWF_EINVAL;
+  }
+  if (n_ph < 1) {
+    set_error("march_bw: at least one photon per instance");
+    return SWF_EINVAL;
+  }
   if (prec == SWF_C64)
-    return march_bw_impl<float>(ctx, g, t_in, t_out, n_steps, n_inst, fd_host, photon_host, psi_out, macc, st);
-  return march_bw_impl<double>(ctx, g, t_in, t_out, n_steps, n_inst, fd_host, photon_host, psi_out, macc, st);
+    return march_bw_impl<float>(ctx, g, t_in, t_out, n_steps, n_inst, fd_host, photon_host, psi_out, macc, st, form,
+                                wave_k_host, n_ph);
+  return march_bw_impl<double>(ctx, g, t_in, t_out, n_steps, n_inst, fd_host, photon_host, psi_out, macc, st, form,
+                               wave_k_host, n_ph);
 }
 
 }  // namespace swf

@@ -20,7 +20,7 @@ STATUS_NAMES = ["SWF_OK", "SWF_EINVAL", "SWF_ENOMEM", "SWF_ECUDA", "SWF_ENUMERIC
 SCHWINGER, BREIT_WHEELER = 0, 1
 C128, C64 = 0, 1
 FIELD_ZERO, FIELD_SAUTER_GAUSS, FIELD_PULSE_GAUSS, FIELD_SINGLE_E, FIELD_DOUBLE_E = range(5)
-WANT_SPECTRUM, WANT_FULL_N, ADAPTIVE = 1, 2, 4
+WANT_SPECTRUM, WANT_FULL_N, ADAPTIVE, BW_PARTIAL = 1, 2, 4, 8
 
 
 class Field(C.Structure):
@@ -44,7 +44,8 @@ class Result(C.Structure):
     _fields_ = [("amp", C.c_double * 8), ("prob", C.c_double * 2), ("diag", C.c_double * 2)]
 
 
-EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_pair_matrix", "swf_march_dev",
+EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_swf_dev", "swf_pair_matrix",
+           "swf_bw_photons", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_set_dedupe", "swf_fields_marched",
            "swf_set_tolerances", "swf_march_stats",
@@ -236,6 +237,31 @@ class Context:
         n_p = len(positrons)
         return [[res[m * n_p + n] for n in range(n_p)] for m in range(len(electrons))]
 
+    def bw_photons(self, instance, k, eps, prec=C64, weights=None):
+        """swf_bw_photons: Breit-Wheeler amplitudes of n photons from one march of the instance's U
+        and V.  k, eps: (n, 3) arrays; weights: optional (n,) complex.  Returns (amps, packet):
+        amps (n, 4) complex (M_ss, M_bs, M_sb, M) and packet (4,) complex = sum_j w_j amps[j], or
+        None without weights."""
+        k = np.ascontiguousarray(np.asarray(k, dtype=np.float64).reshape(-1, 3))
+        eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(-1, 3))
+        n = k.shape[0]
+        if eps.shape[0] != n:
+            raise ValueError("k and eps must list the same photons")
+        arr = instance_array([instance])
+        amps = np.zeros((n, 8), dtype=np.float64)
+        dp = C.POINTER(C.c_double)
+        wbuf, pbuf = None, None
+        if weights is not None:
+            w = np.asarray(weights, dtype=np.complex128).reshape(n)
+            wbuf = np.ascontiguousarray(np.stack([w.real, w.imag], axis=1))
+            pbuf = np.zeros(8, dtype=np.float64)
+        _check(_lib.swf_bw_photons(self._h, arr, n, k.ctypes.data_as(dp), eps.ctypes.data_as(dp),
+                                   wbuf.ctypes.data_as(dp) if wbuf is not None else None, prec,
+                                   amps.ctypes.data_as(dp), pbuf.ctypes.data_as(dp) if pbuf is not None else None))
+        out = amps[:, 0::2] + 1j * amps[:, 1::2]
+        packet = (pbuf[0::2] + 1j * pbuf[1::2]) if pbuf is not None else None
+        return out, packet
+
     # -- device buffers (torch tensors), asynchronous on `stream`
     def solve_dev(self, instances, results_dev, spectrum_dev=None, process=SCHWINGER, prec=C64, stream=None,
                   arr=None):
@@ -264,7 +290,7 @@ class Context:
 
 FIELD_CODES = {"zero": FIELD_ZERO, "sauter_gauss": FIELD_SAUTER_GAUSS, "pulse_gauss": FIELD_PULSE_GAUSS,
                "single_e": FIELD_SINGLE_E, "double_e": FIELD_DOUBLE_E}
-FLAG_CODES = {"spectrum": WANT_SPECTRUM, "full_n": WANT_FULL_N, "adaptive": ADAPTIVE}
+FLAG_CODES = {"spectrum": WANT_SPECTRUM, "full_n": WANT_FULL_N, "adaptive": ADAPTIVE, "bw_partial": BW_PARTIAL}
 
 
 def from_workload(d) -> Instance:

@@ -17,6 +17,8 @@ Workloads (shapes follow the paper's runs: 128^2 (x, y) grids with momentum scan
   a0 = 1, omega0 = 0.5, tau = 10, w = 8, photon k = (0, -2, 0), 128 pairs p = (P, -1, 0),
   q = (-P, -1, 0), P in linspace(-1.5, 1.5, 128), parallel polarisation, grids n^2 with n drawn
   from {192, 256, 320, 384} by default_rng(7), box 16 pi, t_out = -t_in = 8 pi + 4 tau, h ~ 0.05.
+* ``bw_photon_scan``: one pair of ``bw_uneven`` (192^2) with 64 photons k = (2 pi m/L, -2, 0),
+  m = -16 .. 15, parallel and perpendicular polarisation each.
 * ``schwinger_3d``: (3+1)D 256^3 grid, box 48, E = 0.3, omega = 0.4, lambda = 6, [-25, 25] in
   2000 steps, 16 electrons p = (p_x, 0, 0), p_x in linspace(-1, 1, 16), s = +1.
 * ``surrogate_samples``: field parameters and momenta for the surrogate's training set,
@@ -113,6 +115,24 @@ def bw_uneven(count=128, sizes=(192, 256, 320, 384), seed=7, h=0.05, a0=1.0, ome
     return [_inst(("pulse_gauss", (a0, omega0, tau, w, 0.0)), (int(ns[i]), int(ns[i]), 1), (L, L, 1.0),
                   -t_out, t_out, n_steps, p=(Ps[i], -1.0, 0.0), s=1, q=(-Ps[i], -1.0, 0.0), r=1,
                   k=(0.0, -2.0, 0.0), eps=(-1.0, 0.0, 0.0)) for i in range(count)]
+
+
+def bw_photon_scan(m_range=16):
+    """One pair of the uneven-grid Breit-Wheeler workload (the first on a 192^2 grid) and a list of
+    photons k = (2 pi m / L, -2, 0), m = -m_range .. m_range - 1, each with the polarisations
+    transverse to k in the plane of k and x (parallel: (-2, -k_x, 0)/|.|) and along -z
+    (perpendicular).  Returns (instance, k [n][3], eps [n][3])."""
+    ds = bw_uneven()
+    d = next(x for x in ds if x["n"][0] == 192)
+    ks, es = [], []
+    for m in range(-m_range, m_range):
+        kx = 2.0 * math.pi * m / d["L"][0]
+        k = (kx, -2.0, 0.0)
+        nrm = math.sqrt(4.0 + kx * kx)
+        for e in ((-2.0 / nrm, -kx / nrm, 0.0), (0.0, 0.0, -1.0)):
+            ks.append(k)
+            es.append(e)
+    return d, ks, es
 
 
 def schwinger_3d(n=256, L=48.0, n_steps=2000, t_window=25.0, count=16):

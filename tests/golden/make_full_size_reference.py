@@ -6,12 +6,14 @@
 * single FP64 Schwinger (128^2, 1000 steps): the full pair number (both lines of Eq. 8 and the
   amplitudes C, D, A, B) for r = +1 and -1, and C-spectrum samples -> schwinger_fp64_single.json;
 * Breit-Wheeler uneven grids: the amplitude terms of one instance of the smallest grid (192^2,
-  2605 steps) -> bw_uneven_sample.json.
+  2605 steps) -> bw_uneven_sample.json; the same instance in the partial-integration form of
+  Sec. IV (Eqs. 30-33) -> bw_uneven_partial_sample.json.
 The GPU tests compare the library's solves of the same instances against these values.
 
     python tests/golden/make_full_size_reference.py [instance ...]     # batched Schwinger
     python tests/golden/make_full_size_reference.py --single
     python tests/golden/make_full_size_reference.py --bw
+    python tests/golden/make_full_size_reference.py --bw-partial
 """
 import json
 import os
@@ -70,7 +72,7 @@ def single_fp64():
     json.dump(out, open(os.path.join(os.path.dirname(OUT), "schwinger_fp64_single.json"), "w"), indent=1)
 
 
-def bw_sample():
+def bw_sample(form=1):
     """Amplitude terms of the first 192^2 instance of the Breit-Wheeler uneven-grid workload."""
     ds = W.bw_uneven()
     i = next(j for j, d in enumerate(ds) if d["n"][0] == 192)
@@ -78,13 +80,16 @@ def bw_sample():
     g = OA.grid(d)
     t0 = time.time()
     ph = O.Photon(tuple(d["k"]), tuple(d["eps"]))
-    ref = O.bw_amplitude(OA.field(d), g, d["p"], d["s"], d["q"], d["r"], ph, d["t_in"], d["t_out"], d["n_steps"])
-    out = {"citation": "oracle/swf_oracle.py on paper_2512_16889_gb300.workloads.bw_uneven()",
+    ref = O.bw_amplitude(OA.field(d), g, d["p"], d["s"], d["q"], d["r"], ph, d["t_in"], d["t_out"], d["n_steps"],
+                         form=form)
+    name = "bw_uneven_sample.json" if form == 1 else "bw_uneven_partial_sample.json"
+    out = {"citation": "oracle/swf_oracle.py on paper_2512_16889_gb300.workloads.bw_uneven()"
+                       + ("" if form == 1 else ", partial-integration form (Sec. IV, Eqs. 30-33)"),
            "instance": i, "n": list(d["n"]), "n_steps": d["n_steps"],
            "terms": [[complex(v).real, complex(v).imag] for v in ref["terms"]], "M": [ref["M"].real, ref["M"].imag],
            "norm_u": float(O.inner(ref["psi_u"], ref["psi_u"], g).real),
            "norm_v": float(O.inner(ref["psi_v"], ref["psi_v"], g).real), "seconds": time.time() - t0}
-    json.dump(out, open(os.path.join(os.path.dirname(OUT), "bw_uneven_sample.json"), "w"), indent=1)
+    json.dump(out, open(os.path.join(os.path.dirname(OUT), name), "w"), indent=1)
 
 
 if __name__ == "__main__":
@@ -93,6 +98,9 @@ if __name__ == "__main__":
         sys.exit(0)
     if sys.argv[1:] == ["--bw"]:
         bw_sample()
+        sys.exit(0)
+    if sys.argv[1:] == ["--bw-partial"]:
+        bw_sample(form=2)
         sys.exit(0)
     which = [int(v) for v in sys.argv[1:]] or [0, 77]
     data = {"citation": "oracle/swf_oracle.py on paper_2512_16889_gb300.workloads.schwinger_batched()",

@@ -20,21 +20,61 @@ def env():
     ctx.close()
 
 
-def _bw_inst(swf, fld_kind, prm, n, L, t_in, t_out, n_steps, p, s, q, r, k, eps):
+def _bw_inst(swf, fld_kind, prm, n, L, t_in, t_out, n_steps, p, s, q, r, k, eps, flags=0):
     code = swf.FIELD_CODES[fld_kind]
-    return swf.make_instance(code, prm, n, L, t_in, t_out, n_steps, p=p, s=s, q=q, r=r, k=k, eps=eps)
+    return swf.make_instance(code, prm, n, L, t_in, t_out, n_steps, p=p, s=s, q=q, r=r, k=k, eps=eps, flags=flags)
 
 
 CASE2D = dict(fld=("sauter_gauss", (1.0, 0.7, 2.0)), n=(16, 16, 1), L=(8 * np.pi, 8 * np.pi, 1.0), t_in=-9.0,
               t_out=9.0, n_steps=450, p=(0.25, -1.0, 0.0), q=(-0.25, -1.0, 0.0), k=(0.0, -2.0, 0.0))
 
 
-def _oracle(c, s, r):
+def _oracle(c, s, r, form=1):
     fld = O.Field(*c["fld"])
     grid = O.Grid(c["n"], c["L"])
     perp, par = O.polarisation_basis((1, 0, 0), c["k"])
     ph = O.Photon(c["k"], tuple(par))
-    return O.bw_amplitude(fld, grid, c["p"], s, c["q"], r, ph, c["t_in"], c["t_out"], c["n_steps"]), par
+    return O.bw_amplitude(fld, grid, c["p"], s, c["q"], r, ph, c["t_in"], c["t_out"], c["n_steps"], form=form), par
+
+
+def _amps(res):
+    return [complex(res.amp[2 * j], res.amp[2 * j + 1]) for j in range(4)]
+
+
+@pytest.mark.parametrize("spins", [(1, 1), (-1, 1)])
+def test_bw_partial_integration_form_matches_oracle_2d(env, spins):
+    """The partial-integration form (Eqs. 30-33) on the GPU against the oracle's, term by term."""
+    swf, ctx = env
+    s, r = spins
+    ref, par = _oracle(CASE2D, s, r, form=2)
+    c = CASE2D
+    inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], s, c["q"], r,
+                    c["k"], par, flags=swf.BW_PARTIAL)
+    M = ref["M"]
+    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+        res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
+        got = _amps(res[0])
+        assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        for j in range(3):
+            assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
+
+
+def test_bw_both_forms_in_one_call_agree(env):
+    """Instances of both forms in one call are solved in separate groups; on the GPU the two forms
+    agree term by term to the time-quadrature gap (Sec. IV: both handle t < t_in exactly)."""
+    swf, ctx = env
+    c = CASE2D
+    perp, par = O.polarisation_basis((1, 0, 0), c["k"])
+    insts = [_bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], 1, c["q"], 1,
+                      c["k"], par, flags=f) for f in (0, swf.BW_PARTIAL, 0)]
+    res, _ = ctx.solve(insts, swf.BREIT_WHEELER, swf.C128)
+    a1, a2, a3 = _amps(res[0]), _amps(res[1]), _amps(res[2])
+    assert a1 == a3
+    M = a1[3]
+    for j in range(4):
+        assert abs(a1[j] - a2[j]) <= 1e-6 * abs(M), (j, a1[j], a2[j])
+    single, _ = ctx.solve([insts[1]], swf.BREIT_WHEELER, swf.C128)
+    assert _amps(single[0]) == a2
 
 
 @pytest.mark.parametrize("spins", [(1, 1), (1, -1)])
@@ -55,8 +95,9 @@ def test_bw_amplitude_matches_oracle_2d(env, spins):
         assert abs(res[0].prob[0] - abs(M) ** 2) <= 2 * tol * abs(M) ** 2
 
 
-def test_bw_exact_spin_ratio_1p1d_on_gpu(env):
-    """Eq. A81 on the (1+1)D example of Sec. IV, computed by the CUDA path."""
+@pytest.mark.parametrize("partial", [False, True])
+def test_bw_exact_spin_ratio_1p1d_on_gpu(env, partial):
+    """Eq. A81 on the (1+1)D example of Sec. IV, computed by the CUDA path (either integrand form)."""
     swf, ctx = env
     gold = json.load(open(os.path.join(GOLDEN, "bw_spin_ratio_1p1d.json")))
     c = gold["case"]
@@ -66,7 +107,8 @@ def test_bw_exact_spin_ratio_1p1d_on_gpu(env):
     k = (0.0, c["k2"], 0.0)
     perp, par = O.polarisation_basis((1, 0, 0), k)
     insts = [_bw_inst(swf, "single_e", (c["E0"], c["omega"], c["kappa_x"], 0.0, 0.0), (n, 1, 1), (L, 1.0, 1.0),
-                      -20.0, 20.0, 800, (P, rho, 0.0), rs[0], (-P, rho, 0.0), rs[1], k, par)
+                      -20.0, 20.0, 800, (P, rho, 0.0), rs[0], (-P, rho, 0.0), rs[1], k, par,
+                      flags=swf.BW_PARTIAL if partial else 0)
              for rs in ((1, 1), (1, -1), (-1, 1), (-1, -1))]
     res, _ = ctx.solve(insts, swf.BREIT_WHEELER, swf.C128)
     prob = [res[i].prob[0] for i in range(4)]
@@ -90,14 +132,16 @@ def test_bw_zero_field_and_validation(env):
     assert ei.value.status == swf.SWF_EINVAL and "grid mode" in str(ei.value)
 
 
-def test_bw_graph_replay_matches_plain_launches():
+@pytest.mark.parametrize("partial", [False, True])
+def test_bw_graph_replay_matches_plain_launches(partial):
     """The Breit-Wheeler march replayed from CUDA graphs gives the same amplitudes as kernel-by-
-    kernel launches (kernel timing on), for an odd step count."""
+    kernel launches (kernel timing on), for an odd step count, in both integrand forms."""
     from paper_2512_16889_gb300 import build, swf
     build.build()
     c = CASE2D
     perp, par = O.polarisation_basis((1, 0, 0), c["k"])
-    inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], 451, c["p"], 1, c["q"], 1, c["k"], par)
+    inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], 451, c["p"], 1, c["q"], 1, c["k"], par,
+                    flags=swf.BW_PARTIAL if partial else 0)
     res = []
     for timed in (False, True):
         ctx = swf.Context(0)
@@ -125,3 +169,81 @@ def test_full_size_instance_matches_stored_oracle(env):
             ref = complex(*golden["terms"][j])
             assert abs(got[j] - ref) <= tol * max(abs(ref), abs(M)), (prec, j)
         assert abs(res[0].diag[0] - golden["norm_u"]) <= 10 * tol * golden["norm_u"]
+
+
+def test_full_size_partial_integration_form_matches_stored_oracle(env):
+    """The same full-size instance in the partial-integration form (Eqs. 30-33), against the oracle's
+    values of that form (written by tests/golden/make_full_size_reference.py --bw-partial)."""
+    swf, ctx = env
+    from paper_2512_16889_gb300 import workloads as W
+    golden = json.load(open(os.path.join(GOLDEN, "bw_uneven_partial_sample.json")))
+    d = W.bw_uneven()[golden["instance"]]
+    M = complex(*golden["M"])
+    inst = swf.from_workload(d)
+    inst.flags = swf.BW_PARTIAL
+    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+        res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
+        got = _amps(res[0])
+        assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        for j in range(3):
+            ref = complex(*golden["terms"][j])
+            assert abs(got[j] - ref) <= tol * max(abs(ref), abs(M)), (prec, j)
+
+
+def _scan_photons():
+    du = 2 * np.pi / CASE2D["L"][0]
+    ks, es = [], []
+    for k in ((0.0, -2.0, 0.0), (du, -2.0, 0.0), (-2 * du, -1.75, 0.0)):
+        perp, par = O.polarisation_basis((1, 0, 0), k)
+        for e in (par, perp):
+            ks.append(k)
+            es.append(tuple(e))
+    return np.array(ks), np.array(es)
+
+
+def test_bw_photon_scan_matches_oracle(env):
+    """Six photons from one march (Sec. IV: the photon enters only the integrals of Eq. 14), and
+    their wave-packet sum, against the oracle's photon scan."""
+    swf, ctx = env
+    c = dict(CASE2D, n_steps=300)
+    ks, es = _scan_photons()
+    photons = [O.Photon(tuple(k), tuple(e)) for k, e in zip(ks, es)]
+    ref = O.bw_photon_scan(O.Field(*c["fld"]), O.Grid(c["n"], c["L"]), c["p"], 1, c["q"], -1, photons,
+                           c["t_in"], c["t_out"], c["n_steps"])
+    rng = np.random.default_rng(11)
+    w = rng.normal(size=len(photons)) + 1j * rng.normal(size=len(photons))
+    inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], 1, c["q"], -1,
+                    ks[0], es[0])
+    pk_ref = sum(wj * np.append(r["terms"], r["M"]) for wj, r in zip(w, ref))
+    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+        amps, packet = ctx.bw_photons(inst, ks, es, prec, weights=w)
+        for j, r in enumerate(ref):
+            M = r["M"]
+            assert abs(amps[j, 3] - M) <= tol * abs(M), (prec, j, amps[j, 3], M)
+            for t in range(3):
+                assert abs(amps[j, t] - r["terms"][t]) <= tol * max(abs(r["terms"][t]), abs(M)), (prec, j, t)
+        scale = np.max(np.abs([r["M"] for r in ref])) * np.sum(np.abs(w))
+        assert np.max(np.abs(packet - pk_ref)) <= tol * scale, (prec, packet, pk_ref)
+
+
+def test_bw_photon_scan_equals_solves_bitwise(env):
+    """Each photon of a scan gives the same bits as a solve of that photon alone (shared march,
+    same reductions), and invalid scans are refused."""
+    swf, ctx = env
+    c = dict(CASE2D, n_steps=120)
+    ks, es = _scan_photons()
+    insts = [_bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], 1, c["q"], 1, k, e)
+             for k, e in zip(ks, es)]
+    amps, packet = ctx.bw_photons(insts[0], ks, es, swf.C64)
+    assert packet is None
+    res, _ = ctx.solve(insts, swf.BREIT_WHEELER, swf.C64)
+    for j in range(len(insts)):
+        assert list(amps[j]) == _amps(res[j]), j
+    with pytest.raises(swf.SwfError) as ei:
+        ctx.bw_photons(insts[0], [(0.0, -2.05, 0.0)], [(1.0, 0.0, 0.0)], swf.C64)
+    assert ei.value.status == swf.SWF_EINVAL and "grid mode" in str(ei.value)
+    bad = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], 1, c["q"], 1, ks[0],
+                   es[0], flags=swf.BW_PARTIAL)
+    with pytest.raises(swf.SwfError) as ei:
+        ctx.bw_photons(bad, ks, es, swf.C64)
+    assert ei.value.status == swf.SWF_EUNSUPPORTED
