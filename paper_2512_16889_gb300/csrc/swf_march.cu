@@ -1645,6 +1645,19 @@ __global__ void k_bw_phase_table(const FieldDesc* fd, const double* photon, int 
   }
 }
 
+// Sum over the 32 lanes of a warp in the march precision (lane 0 holds it); the integrand kernels
+// add the warps' sums of a block in FP64.  FP64 is scarce on GB300: a shuffle tree in FP64 per
+// block and value cost more than the integrand itself.
+template <typename R>
+__device__ __forceinline__ cpx<R> warp_sum(cpx<R> v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
 // (alpha . eps) v for a real polarisation eps (Dirac representation).
 template <typename R>
 __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o) {
@@ -1661,37 +1674,48 @@ __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o
 // instance pi / n_ph: several photons share one march) and adds w dx^d e^{-i k0 t}
 // (from the phase table) times its sum to its own accumulator acc[pi][b][3] (FP64; no other block touches it, so
 // the march's sum is deterministic); k_mdot_final adds the accumulators in a fixed order.
-template <typename R>
+template <typename R, int NPH>
 __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const cpx<R>* gcplx, const cpx<R>* kph,
                                               const double* photon, GridDesc g, const cpx<double>* __restrict__ ptab,
                                               const MarchClock* clk, int ls, int stage, int tab_stride,
                                               int n_ph, cpx<double>* acc) {
   const long tab_row = (long)(clk->step + ls) * 7 + stage;
-  __shared__ cpx<double> red[8][3];
-  const int pi = blockIdx.y;  // photon-instance: photon pi % n_ph of instance pi / n_ph
-  const int inst = pi / n_ph;
+  __shared__ cpx<double> red[8][3 * NPH];
+  // block row: instance inst, photons j0 .. j0 + nj - 1 (photon-instances pi0 + jj); U and V are
+  // loaded once per site for the NPH photons of the block
+  const int nchunk = (n_ph + NPH - 1) / NPH;
+  const int inst = blockIdx.y / nchunk;
+  const int j0 = (blockIdx.y % nchunk) * NPH;
+  const int nj = min(NPH, n_ph - j0);
+  const int pi0 = inst * n_ph + j0;
   const int nt = g.n[0] + g.n[1] + g.n[2];
   const cpx<R>* tu = gcplx + (size_t)(2 * inst) * (nt + 4);
   const cpx<R>* tv = gcplx + (size_t)(2 * inst + 1) * (nt + 4);
-  const cpx<R>* kp = kph + (size_t)pi * nt;
-  // this photon-instance's row of the phase table: U and V time phases, quadrature factor
-  const cpx<double>* trow = ptab + 3 * (tab_row + (long)pi * tab_stride);
-  const cpx<R> tfu = cvt<R>(trow[0]), tfv = cvt<R>(trow[1]);
-  R eps[3];
-  for (int a = 0; a < 3; ++a) eps[a] = (R)photon[6 * pi + 3 + a];
+  // the U and V time phases are the same in every photon's row of the phase table
+  const cpx<double>* trow0 = ptab + 3 * (tab_row + (long)pi0 * tab_stride);
+  const cpx<R> tfu = cvt<R>(trow0[0]), tfv = cvt<R>(trow0[1]);
+  R eps[NPH][3];
+  const cpx<R>* kp[NPH];
+#pragma unroll
+  for (int jj = 0; jj < NPH; ++jj) {
+    const int pj = pi0 + min(jj, nj - 1);  // a partial last chunk repeats its last photon (not stored)
+    kp[jj] = kph + (size_t)pj * nt;
+    for (int a = 0; a < 3; ++a) eps[jj][a] = (R)photon[6 * pj + 3 + a];
+  }
   const cpx<R>* U = ys + (size_t)(2 * inst) * 4 * g.N;
   const cpx<R>* V = ys + (size_t)(2 * inst + 1) * 4 * g.N;
-  // per-thread sums in the march precision (a few sites each), then FP64 across threads
-  cpx<R> tss = mk<R>(0, 0), tbs = mk<R>(0, 0), tsb = mk<R>(0, 0);
-#pragma unroll 2
+  // per-thread sums in the march precision (a few sites each), the warp tree in it too, FP64 across warps
+  cpx<R> tss[NPH], tbs[NPH], tsb[NPH];
+#pragma unroll
+  for (int jj = 0; jj < NPH; ++jj) tss[jj] = tbs[jj] = tsb[jj] = mk<R>(0, 0);
+#pragma unroll(NPH == 1 ? 2 : 1)
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.N; j += gridDim.x * blockDim.x) {
     const int ix = j % g.n[0];
     const int iy = (j / g.n[0]) % g.n[1];
     const int iz = j / (g.n[0] * g.n[1]);
-    cpx<R> u[4], v[4], ub[4], vb[4], av[4], avb[4];
+    cpx<R> u[4], v[4], ub[4], vb[4];
     const cpx<R> phu = tfu * tu[ix] * tu[g.n[0] + iy] * tu[g.n[0] + g.n[1] + iz];
     const cpx<R> phv = tfv * tv[ix] * tv[g.n[0] + iy] * tv[g.n[0] + g.n[1] + iz];
-    const cpx<R> ph = kp[ix] * kp[g.n[0] + iy] * kp[g.n[0] + g.n[1] + iz];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       u[a] = U[(size_t)a * g.N + j];
@@ -1699,36 +1723,40 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
       ub[a] = tu[nt + a] * phu;
       vb[a] = tv[nt + a] * phv;
     }
-    alpha_eps<R>(eps, v, av);
-    alpha_eps<R>(eps, vb, avb);
-    cpx<R> ss = mk<R>(0, 0), bs = mk<R>(0, 0), sb = mk<R>(0, 0);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      ss = ss + cdot(u[a], av[a]);
-      bs = bs + cdot(ub[a], av[a]);
-      sb = sb + cdot(u[a], avb[a]);
+    for (int jj = 0; jj < NPH; ++jj) {
+      const cpx<R> ph = kp[jj][ix] * kp[jj][g.n[0] + iy] * kp[jj][g.n[0] + g.n[1] + iz];
+      cpx<R> av[4], avb[4];
+      alpha_eps<R>(eps[jj], v, av);
+      alpha_eps<R>(eps[jj], vb, avb);
+      cpx<R> ss = mk<R>(0, 0), bs = mk<R>(0, 0), sb = mk<R>(0, 0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ss = ss + cdot(u[a], av[a]);
+        bs = bs + cdot(ub[a], av[a]);
+        sb = sb + cdot(u[a], avb[a]);
+      }
+      tss[jj] = tss[jj] + ss * ph;
+      tbs[jj] = tbs[jj] + bs * ph;
+      tsb[jj] = tsb[jj] + sb * ph;
     }
-    tss = tss + ss * ph;
-    tbs = tbs + bs * ph;
-    tsb = tsb + sb * ph;
   }
-  cpx<double> ass = cvt<double>(tss), abs_ = cvt<double>(tbs), asb = cvt<double>(tsb);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    ass.x += __shfl_down_sync(0xffffffffu, ass.x, off); ass.y += __shfl_down_sync(0xffffffffu, ass.y, off);
-    abs_.x += __shfl_down_sync(0xffffffffu, abs_.x, off); abs_.y += __shfl_down_sync(0xffffffffu, abs_.y, off);
-    asb.x += __shfl_down_sync(0xffffffffu, asb.x, off); asb.y += __shfl_down_sync(0xffffffffu, asb.y, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5][0] = ass;
-    red[threadIdx.x >> 5][1] = abs_;
-    red[threadIdx.x >> 5][2] = asb;
+  for (int jj = 0; jj < NPH; ++jj) {
+    const cpx<R> ass = warp_sum<R>(tss[jj]), abs_ = warp_sum<R>(tbs[jj]), asb = warp_sum<R>(tsb[jj]);
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5][3 * jj] = cvt<double>(ass);
+      red[threadIdx.x >> 5][3 * jj + 1] = cvt<double>(abs_);
+      red[threadIdx.x >> 5][3 * jj + 2] = cvt<double>(asb);
+    }
   }
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < 3 * nj) {
+    const int jj = threadIdx.x / 3, q = threadIdx.x % 3;
     cpx<double> sacc = mk<double>(0, 0);
     for (int wi = 0; wi < 8; ++wi) sacc = sacc + red[wi][threadIdx.x];
-    cpx<double>& a = acc[((size_t)pi * gridDim.x + blockIdx.x) * 3 + threadIdx.x];
+    const cpx<double>* trow = ptab + 3 * (tab_row + (long)(pi0 + jj) * tab_stride);
+    cpx<double>& a = acc[((size_t)(pi0 + jj) * gridDim.x + blockIdx.x) * 3 + q];
     a = a + trow[2] * sacc;
   }
 }
@@ -1915,20 +1943,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_f2_x(StageArgs<
     }
     __syncthreads();
   }
-  // block sum of the direct transform (FP64 across threads)
-  cpx<double> ds[4];
+  // block sum of the direct transform (warp trees in the march precision, FP64 across warps)
+  cpx<R> ds[4];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    ds[c] = cvt<double>(dsum[c]);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      ds[c].x += __shfl_down_sync(0xffffffffu, ds[c].x, off);
-      ds[c].y += __shfl_down_sync(0xffffffffu, ds[c].y, off);
-    }
-  }
+  for (int c = 0; c < 4; ++c) ds[c] = warp_sum<R>(dsum[c]);
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) red[threadIdx.x >> 5][c] = ds[c];
+    for (int c = 0; c < 4; ++c) red[threadIdx.x >> 5][c] = cvt<double>(ds[c]);
   }
   __syncthreads();
   if (threadIdx.x < 4) {
@@ -2048,13 +2069,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_f2_ss(const cpx
     tacc = tacc + omp * (form_ae<R>(dam, bp) + form_ae<R>(am, dbp));
     tacc = tacc + omm * (form_ae<R>(dam, bm) + form_ae<R>(am, dbm));
   }
-  cpx<double> s = cvt<double>(tacc);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    s.x += __shfl_down_sync(0xffffffffu, s.x, off);
-    s.y += __shfl_down_sync(0xffffffffu, s.y, off);
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  const cpx<R> s = warp_sum<R>(tacc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cvt<double>(s);
   __syncthreads();
   if (threadIdx.x == 0) {
     const long tab_row = (long)(clk->step + ls) * 7 + stage;
@@ -2119,11 +2135,10 @@ static swf_status f2_prepare(swf_ctx* ctx, const GridDesc& g, int n_inst, const 
   const int nrows = g.n[1] * g.n[2];
   const int nt = g.n[0] + g.n[1] + g.n[2];
   p->n_inst = n_inst;
-  // rows per block and block size of the right-hand side's x passes (tuned by timing if enabled)
-  const int xv = tune_lookup(ctx, tune_key('x', (int)sizeof(cpx<R>), nx, nrows, 0, 2 * n_inst),
-                             4 * x_rows<R>(nx, nrows, 2 * n_inst));
-  p->rows = xv >> 2;
-  p->xthr = (xv & 3) ? kThreads / 2 : kThreads;
+  // a fixed shape (not the tuned one of the right-hand side's x passes): the block's rows and
+  // threads decide the order of the direct-transform sums, which must not depend on timing
+  p->rows = x_rows<R>(nx, nrows, 2 * n_inst);
+  p->xthr = kThreads;
   if (p->rows < 1) {
     set_error("partial-integration integrand: an x line does not fit shared memory");
     return SWF_EUNSUPPORTED;
@@ -2267,7 +2282,11 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   if ((s = ws_get(ctx, "bw.photon", sizeof(double) * 6 * NP, &pph)) != SWF_OK) return s;
   if ((s = ws_get(ctx, "bw.kph", sizeof(cpx<R>) * NP * nt, &pkph)) != SWF_OK) return s;
   // blocks per instance of the M-dot reduction: about four waves of the GPU in total, at least
-  // 1024 sites per block
+  // 1024 sites per block (the same split for every photon count, so a photon of a scan sums
+  // exactly as a solve of that photon alone); photons per block: 1, or 4 (8 in complex64) for
+  // scans, which then read U and V once per site for the block's photons
+  const int nph_blk = n_ph == 1 ? 1 : (sizeof(R) == 4 && n_ph > 4 ? 8 : 4);
+  const int nchunk = (n_ph + nph_blk - 1) / nph_blk;
   const int nb = std::max(1, std::min((g.N + 1023) / 1024, (4 * sm_count() + n_inst - 1) / n_inst));
   void* ptab;
   if ((s = ws_get(ctx, "bw.phase_table", sizeof(cpx<double>) * 3 * 7 * (size_t)n_steps * NP, &ptab)) != SWF_OK)
@@ -2305,7 +2324,7 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
     B.t = t_out;
     if ((s = autotune_eval<R>(ctx, B, F, st)) != SWF_OK) return s;
   }
-  F2Plan<R> p2;  // after the tuning: the integrand's x pass takes the tuned shape of the x passes
+  F2Plan<R> p2;
   if (form == 2 && (s = f2_prepare<R>(ctx, g, n_inst, fd_host, photon_host, wave_k_host, A, &p2, st)) != SWF_OK)
     return s;
   int slot[7] = {0, 1, 2, 3, 4, 5, 6};
@@ -2354,9 +2373,20 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
           return r;
       } else if (weighted) {
         ProfScope ps(ctx, "k_mdot", st);
-        k_mdot<R><<<dim3(nb, NP), 256, 0, st>>>((const cpx<R>*)pys, A.gcplx, (const cpx<R>*)pkph,
-                                                (const double*)pph, g, (const cpx<double>*)ptab, clk, ls, i,
-                                                7 * n_steps, n_ph, (cpx<double>*)ppart);
+        const cpx<R>* ysc = (const cpx<R>*)pys;
+        const cpx<R>* kpc = (const cpx<R>*)pkph;
+        const cpx<double>* tb = (const cpx<double>*)ptab;
+        cpx<double>* pa = (cpx<double>*)ppart;
+        const dim3 grid(nb, n_inst * nchunk);
+        if (nph_blk == 1)
+          k_mdot<R, 1><<<grid, 256, 0, st>>>(ysc, A.gcplx, kpc, (const double*)pph, g, tb, clk, ls, i, 7 * n_steps,
+                                             n_ph, pa);
+        else if (nph_blk == 4)
+          k_mdot<R, 4><<<grid, 256, 0, st>>>(ysc, A.gcplx, kpc, (const double*)pph, g, tb, clk, ls, i, 7 * n_steps,
+                                             n_ph, pa);
+        else
+          k_mdot<R, 8><<<grid, 256, 0, st>>>(ysc, A.gcplx, kpc, (const double*)pph, g, tb, clk, ls, i, 7 * n_steps,
+                                             n_ph, pa);
       }
     }
     std::swap(slot[0], slot[6]);

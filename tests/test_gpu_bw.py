@@ -228,7 +228,7 @@ def test_bw_photon_scan_matches_oracle(env):
 
 def test_bw_photon_scan_equals_solves_bitwise(env):
     """Each photon of a scan gives the same bits as a solve of that photon alone (shared march,
-    same reductions), and invalid scans are refused."""
+    the same split of the integrand sums), and invalid scans are refused."""
     swf, ctx = env
     c = dict(CASE2D, n_steps=120)
     ks, es = _scan_photons()
