@@ -211,10 +211,11 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
                             long long* launches, int* n_entries, long long* total_launches);
 
 /* March path selection: 0 = automatic (the fused cluster kernel for (2+1)D 256 x 256
- * complex64 marches that keep the z-spin sectors apart, the pass kernels otherwise),
- * 1 = pass kernels only, 2 = fused kernel with one CTA per SM, 3 = fused kernel with two
- * CTAs per SM (2 and 3 still fall back to the pass kernels where the fused kernel does not
- * apply). */
+ * complex64 marches that keep the z-spin sectors apart, the pass kernels otherwise; a large
+ * fused march gives some of its fields to the pass kernels, run concurrently on the SMs that the
+ * 16-CTA clusters leave free), 1 = pass kernels only, 2 = fused kernel with one CTA per SM for
+ * every field, 3 = fused kernel with two CTAs per SM (2 and 3 still fall back to the pass kernels
+ * where the fused kernel does not apply). */
 swf_status swf_set_march_path(swf_ctx* ctx, int path);
 
 /* Tolerances of step-size-controlled marches (SWF_ADAPTIVE): a Dormand-Prince 5(4) step is
@@ -236,6 +237,8 @@ swf_status swf_set_dedupe(swf_ctx* ctx, int on);
 /* Fields (U or V waves) actually marched by this context since its creation (a diagnostic of
  * the library; the paper has no counterpart). */
 swf_status swf_fields_marched(swf_ctx* ctx, long long* count);
+/* Of those, the fields marched by the fused cluster kernel (the rest ran on the pass kernels). */
+swf_status swf_fields_fused(swf_ctx* ctx, long long* count);
 
 /* Launch shapes of the pass kernels (rows per block of the x passes, tile width of the y and z
  * passes, 256 or 128 threads per block).  on = 1 (default): the first march of each grid

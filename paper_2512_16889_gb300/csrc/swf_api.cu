@@ -654,6 +654,12 @@ swf_status swf_destroy(swf_ctx* ctx) {
   for (auto& kv : ctx->ws.bufs) cudaFree(kv.second.first);
   for (auto& kv : ctx->tw.tables) cudaFree(kv.second);
   for (auto ev : ctx->prof.pool) cudaEventDestroy(ev);
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    for (auto ev : ctx->aux_ev)
+      if (ev) cudaEventDestroy(ev);
+    cudaStreamDestroy(ctx->aux);
+  }
   cudaStreamDestroy(ctx->stream);
   delete ctx;
   return SWF_OK;
@@ -703,7 +709,8 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
 swf_status swf_set_march_path(swf_ctx* ctx, int path) {
   if (!ctx || path < 0 || path > 3) { set_error("swf_set_march_path: ctx NULL or path not in 0..3"); return SWF_EINVAL; }
   ctx->use_fused = path != 1;
-  if (path >= 2) ctx->fused_variant = path - 1;
+  ctx->sm_split = path == 0;
+  ctx->fused_variant = path >= 2 ? path - 1 : 1;
   return SWF_OK;
 }
 
@@ -733,6 +740,12 @@ swf_status swf_set_dedupe(swf_ctx* ctx, int on) {
 swf_status swf_fields_marched(swf_ctx* ctx, long long* count) {
   if (!ctx || !count) { set_error("swf_fields_marched: NULL argument"); return SWF_EINVAL; }
   *count = ctx->fields_marched;
+  return SWF_OK;
+}
+
+swf_status swf_fields_fused(swf_ctx* ctx, long long* count) {
+  if (!ctx || !count) { set_error("swf_fields_fused: NULL argument"); return SWF_EINVAL; }
+  *count = ctx->fields_fused;
   return SWF_OK;
 }
 

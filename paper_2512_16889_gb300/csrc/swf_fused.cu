@@ -1010,6 +1010,65 @@ bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_preci
 
 static int g_fused_clusters[64][2];  // per device and variant: resident clusters + 1 (0: not set up)
 
+// Kernel attributes and the number of clusters that can be resident at once (cached per device).
+static swf_status fused_setup(int var, cudaStream_t st) {
+  using namespace fused;
+  void (*kern)(Args) = var ? k_fused2 : k_fused;
+  const int nthr = var ? v2::NT2 : NT;
+  const int smem = var ? v2::SMEM2 : SMEM;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return cuda_status(e, "cluster size attribute");
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_status(e, "shared memory attribute");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.blockDim = dim3(nthr, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = CL;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  int ncl = 0;
+  e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+  if (e != cudaSuccess) return cuda_status(e, "cudaOccupancyMaxActiveClusters");
+  g_fused_clusters[dev_slot()][var] = (ncl > 0 ? ncl : 0) + 1;
+  return SWF_OK;
+}
+
+int fused_resident_clusters(swf_ctx* ctx) {
+  const int var = ctx->fused_variant == 2 ? 1 : 0;
+  if (g_fused_clusters[dev_slot()][var] == 0 && fused_setup(var, ctx->stream) != SWF_OK) return 0;
+  return g_fused_clusters[dev_slot()][var] - 1;
+}
+
+// The fused kernel's 16-CTA clusters (one CTA per SM) fit once per GPC, so some SMs stay idle
+// (on GB300: 7 clusters on 112 of 152 SMs).  Moving some fields to the pass kernels, run
+// concurrently on those SMs, shortens the march when they finish within the fused kernel's
+// time.  With R = ceil(2 n_f / ncl) rounds of sectors per cluster, removing r rounds leaves
+// n_1 = floor((R - r) ncl / 2) fields to the clusters and n_2 = n_f - n_1 to the pass kernels,
+// which take about alpha n_2 rounds' time on the free SMs: alpha = 2.0 measured with 40 free SMs
+// on (2+1)D 256^2 complex64 marches (16 fields on the free SMs took as long as 32 fused rounds),
+// scaled by 40 / (free SMs).  The largest r with alpha n_2 <= R - r is taken.
+int fused_split_count(int n_f, int ncl, int n_sm) {
+  const int free_sm = n_sm - fused::CL * ncl;
+  if (ncl < 1 || free_sm < 16 || n_f < 16) return 0;
+  const double alpha = 2.0 * 40.0 / free_sm;
+  const int R = (2 * n_f + ncl - 1) / ncl;
+  int best = 0;
+  for (int r = 1; r < R; ++r) {
+    const int n1 = ((R - r) * ncl) / 2;
+    const int n2 = n_f - n1;
+    if (n2 <= 0) continue;
+    if (alpha * n2 > (double)(R - r)) break;
+    best = n2;
+  }
+  return best;
+}
+
 swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
                        const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
   using namespace fused;
@@ -1035,20 +1094,12 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
   };
   int* ncl_slot = &g_fused_clusters[dev_slot()][var];
   if (*ncl_slot == 0) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return cuda_status(e, "cluster size attribute");
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return cuda_status(e, "shared memory attribute");
-    cudaLaunchAttribute at;
-    cudaLaunchConfig_t cfg = config(1, &at);
-    int ncl = 0;
-    e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
-    if (e != cudaSuccess) return cuda_status(e, "cudaOccupancyMaxActiveClusters");
-    if (ncl < 1) {
-      set_error("the fused march kernel cannot be resident on this device");
-      return SWF_EUNSUPPORTED;
-    }
-    *ncl_slot = ncl + 1;
+    swf_status s0 = fused_setup(var, st);
+    if (s0 != SWF_OK) return s0;
+  }
+  if (*ncl_slot < 2) {
+    set_error("the fused march kernel cannot be resident on this device");
+    return SWF_EUNSUPPORTED;
   }
   const int n_sec = 2 * n_f;
   const int ncl = *ncl_slot - 1 < n_sec ? *ncl_slot - 1 : n_sec;
@@ -1067,6 +1118,8 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
   if (e != cudaSuccess) return cuda_status(e, "upload field descriptors");
   e = cudaMemcpyAsync(psec, sec.data(), sizeof(Sector) * n_sec, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "upload sector table");
+  e = cudaStreamSynchronize(st);  // the sector table is a host temporary; the march itself runs on
+  if (e != cudaSuccess) return cuda_status(e, "upload sector table");  // after this call returns
   void* ptab;
   if ((s = ws_get(ctx, "fused.ttab", (size_t)n_f * n_steps * 7 * sizeof(float4), &ptab)) != SWF_OK) return s;
   {
@@ -1095,8 +1148,7 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
     e = cudaLaunchKernelEx(&cfg, kern, A);
   }
   if (e != cudaSuccess) return cuda_status(e, "launch fused march");
-  e = cudaStreamSynchronize(st);  // the sector table above is a host temporary
-  if (e != cudaSuccess) return cuda_status(e, "fused march");
+  ctx->fields_fused += n_f;
   return SWF_OK;
 }
 

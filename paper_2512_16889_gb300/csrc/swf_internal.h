@@ -125,8 +125,12 @@ struct swf_ctx {
   bool use_graphs = true; // replay pass-kernel march steps from CUDA graphs
   double rtol = 1e-5, atol = 1e-10;  // step-size control (SWF_ADAPTIVE), the paper's tolerances
   long long last_accepted = 0, last_rejected = 0;  // steps of the last controlled march
-  long long fields_marched = 0;  // fields actually marched since the last profile read
+  long long fields_marched = 0;  // fields actually marched since the context's creation
+  long long fields_fused = 0;    // of those, fields marched by the fused cluster kernel
   int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
+  bool sm_split = true;   // automatic path: pass kernels on the SMs the fused clusters leave free
+  cudaStream_t aux = nullptr;            // stream of that concurrent pass-kernel march (lazy)
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
 };
 
 namespace swf {
@@ -194,6 +198,12 @@ bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_preci
 swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
                        const FieldDesc* fd_host, void* psi_out, cudaStream_t st);
 int fused_clusters();
+// Clusters of the fused kernel resident at once on this device (sets the kernel up on first use);
+// 0 if it cannot be resident.
+int fused_resident_clusters(swf_ctx* ctx);
+// Fields of an n_f-field fused march to give to the pass kernels running concurrently on the SMs
+// that the 16-CTA clusters leave free (0: no split).
+int fused_split_count(int n_f, int ncl, int n_sm);
 swf_status rhs_eval(swf_ctx* ctx, const GridDesc& g, const FieldDesc& fd, swf_precision prec,
                     double t, const void* psi, void* out, cudaStream_t st);
 // The same evaluation with all workspace taken from caller-provided device scratch.

@@ -425,6 +425,10 @@ __device__ cpx<R>* fft_pp(cpx<R>* a, cpx<R>* b, int ld, int nlines, const RadixP
 // Shared memory of every pass kernel: two line buffers (the FFT works out of place) within
 // kPassSmem, so that three blocks of 256 threads fit an SM.
 static const size_t kPassSmem = 72 * 1024;
+// The tuner may also try wider shapes (more rows per x block, wider y/z tiles) up to this much
+// shared memory per block (one or two blocks per SM): wider y/z tiles read longer contiguous
+// runs of each line and give every FFT pass more butterflies per barrier.
+static const size_t kPassSmemTune = 200 * 1024;
 
 // x lines of `rows` grid rows (4 components each): stage combine, local term, forward x-FFT
 // (and the whole derivative when x is the only non-trivial axis).
@@ -732,11 +736,11 @@ static size_t mid_smem(int n_a, int lg) {
   return (size_t)2 * 4 * (1 << lg) * mid_stride<R>(n_a, lg) * sizeof(cpx<R>);
 }
 
-// widest tile that fits (TX <= nx as well)
+// widest tile that fits `cap` bytes of shared memory (TX <= nx as well)
 template <typename R>
-static int mid_max_lg(int n_a, int nx) {
+static int mid_max_lg(int n_a, int nx, size_t cap = kPassSmem) {
   int lg = 4;
-  while (lg > 0 && ((1 << lg) > nx || mid_smem<R>(n_a, lg) > kPassSmem)) --lg;
+  while (lg > 0 && ((1 << lg) > nx || mid_smem<R>(n_a, lg) > cap)) --lg;
   return lg;
 }
 
@@ -776,11 +780,11 @@ static swf_status set_smem_attrs() {
   const int dv = dev_slot();
   if (done[dv]) return SWF_OK;
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_first<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+  e = cudaFuncSetAttribute(k_first<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_first)");
-  e = cudaFuncSetAttribute(k_mid<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+  e = cudaFuncSetAttribute(k_mid<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_mid)");
-  e = cudaFuncSetAttribute(k_last<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+  e = cudaFuncSetAttribute(k_last<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last)");
   done[dv] = true;
   return SWF_OK;
@@ -870,7 +874,7 @@ static swf_status autotune_eval(swf_ctx* ctx, const StageArgs<R>& B, int F, cuda
   const std::string xkey = tune_key('x', esz, nx, B.nrows, 0, F);
   if (!ctx->tune.best.count(xkey)) {
     const size_t line = (size_t)2 * 4 * padded_len(nx) * esz;
-    int rmax = (int)(kPassSmem / line);
+    int rmax = (int)(kPassSmemTune / line);
     rmax = std::min(std::min(rmax, 64), B.nrows);
     int best = 4 * x_rows<R>(nx, B.nrows, F);
     float tbest = 3.4e38f;
@@ -905,7 +909,7 @@ static swf_status autotune_eval(swf_ctx* ctx, const StageArgs<R>& B, int F, cuda
       if (ctx->tune.best.count(key)) continue;
       int best = 4 * mid_shape<R>(n_a, nx, (long)other * F).lgtx;
       float tbest = 3.4e38f;
-      for (int lg = mid_max_lg<R>(n_a, nx); lg >= 0 && status == SWF_OK; --lg) {
+      for (int lg = mid_max_lg<R>(n_a, nx, kPassSmemTune); lg >= 0 && status == SWF_OK; --lg) {
         for (int half = 0; half < 2 && status == SWF_OK; ++half) {
           const MidShape ms = mid_shape_lg<R>(n_a, lg);
           const int ntx = (nx + (1 << lg) - 1) >> lg;
@@ -1428,6 +1432,35 @@ static int dedupe_fields(const GridDesc& g, int n_f, const FieldDesc* fd, std::v
   return (int)uniq.size();
 }
 
+// The fused kernel on the first n_f - n2 fields (stream st) and, concurrently, the pass kernels
+// on the last n2 fields (the context's auxiliary stream), which take the SMs that the fused
+// kernel's clusters leave free.  The auxiliary stream starts after the work already queued on
+// st and st continues after both.  complex64 only (the fused kernel's precision).
+static swf_status march_split(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
+                              int n2, const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
+  cudaError_t e;
+  if (!ctx->aux) {
+    if ((e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_status(e, "auxiliary stream");
+    for (int i = 0; i < 2; ++i)
+      if ((e = cudaEventCreateWithFlags(&ctx->aux_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_status(e, "auxiliary stream events");
+  }
+  const int n1 = n_f - n2;
+  if ((e = cudaEventRecord(ctx->aux_ev[0], st)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(ctx->aux, ctx->aux_ev[0], 0)) != cudaSuccess)
+    return cuda_status(e, "order the auxiliary stream");
+  swf_status s = march_fused(ctx, g, t_in, t_out, n_steps, n1, fd_host, psi_out, st);
+  if (s != SWF_OK) return s;
+  cpx<float>* out2 = (cpx<float>*)psi_out + (size_t)n1 * 4 * g.N;
+  s = march_impl<float>(ctx, g, t_in, t_out, n_steps, n2, fd_host + n1, out2, ctx->aux);
+  if (s != SWF_OK) return s;
+  if ((e = cudaEventRecord(ctx->aux_ev[1], ctx->aux)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st, ctx->aux_ev[1], 0)) != cudaSuccess)
+    return cuda_status(e, "join the auxiliary stream");
+  return SWF_OK;
+}
+
 static swf_status march_unique(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
                                const FieldDesc* fd_host, swf_precision prec, void* psi_out, cudaStream_t st,
                                int adaptive) {
@@ -1435,6 +1468,10 @@ static swf_status march_unique(swf_ctx* ctx, const GridDesc& g, double t_in, dou
     return march_adaptive(ctx, g, t_in, t_out, (t_in - t_out) / n_steps, 100 * n_steps + 100, n_f, fd_host, prec,
                           psi_out, st);
   if (ctx->use_fused && fused_applicable(g, n_f, fd_host, prec)) {
+    const int n2 = (ctx->sm_split && ctx->fused_variant == 1)
+                       ? fused_split_count(n_f, fused_resident_clusters(ctx), sm_count())
+                       : 0;
+    if (n2 > 0) return march_split(ctx, g, t_in, t_out, n_steps, n_f, n2, fd_host, psi_out, st);
     swf_status s = march_fused(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);
     if (s != SWF_EUNSUPPORTED) return s;
     ctx->use_fused = false;  // the cluster shape cannot be resident here: pass kernels from now on

@@ -48,6 +48,7 @@ EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_sw
            "swf_bw_photons", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_set_dedupe", "swf_fields_marched",
+           "swf_fields_fused",
            "swf_set_tolerances", "swf_march_stats",
            "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_set_tolerances.argtypes = [vp, dp, dp]
     lib.swf_march_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     lib.swf_fields_marched.argtypes = [vp, C.POINTER(C.c_longlong)]
+    lib.swf_fields_fused.argtypes = [vp, C.POINTER(C.c_longlong)]
     lib.swf_rhs_noalloc.argtypes = [inst_p, ip, ip, dp, vp, vp, vp]
     fp = C.POINTER(C.c_float)
     lib.swf_mlp_param_count.argtypes = []
@@ -194,6 +196,12 @@ class Context:
     def fields_marched(self):
         n = C.c_longlong()
         _check(_lib.swf_fields_marched(self._h, C.byref(n)))
+        return n.value
+
+    def fields_fused(self):
+        """Fields marched by the fused cluster kernel since the context's creation."""
+        n = C.c_longlong()
+        _check(_lib.swf_fields_fused(self._h, C.byref(n)))
         return n.value
 
     def set_autotune(self, on: bool):

@@ -264,6 +264,34 @@ def test_fused_matches_pass_kernels_and_positron_waves(env):
             assert rel_state(ga[i], gb[i]) < 1e-5, (bg, i, rel_state(ga[i], gb[i]))
 
 
+def test_split_march_is_fused_plus_pass_kernels(env):
+    """A large fused march gives its last fields to the pass kernels, run concurrently on the SMs
+    the 16-CTA clusters leave free: the result is bit for bit the fused-only march on the first
+    fields and the pass-kernel march on the rest."""
+    torch, swf, _ = env
+    base = _fused_cases(n_steps=12)[0]
+    ds = [dict(base, p=(0.05 * (i % 8) - 0.2, 0.04 * (i // 8) - 0.1, 0.0), s=1 if i % 3 else -1) for i in range(32)]
+    insts = [swf.from_workload(d) for d in ds]
+    N = 256 * 256
+    outs, fused = {}, {}
+    for path in (0, 1, 2):
+        ctx = swf.Context(0)
+        ctx.set_dedupe(False)
+        ctx.set_march_path(path)
+        out = torch.zeros(len(ds) * 8 * N, dtype=torch.float32, device="cuda")
+        f0 = ctx.fields_fused()
+        ctx.march_dev(insts, out, bg=0, prec=swf.C64)
+        torch.cuda.synchronize()
+        fused[path] = ctx.fields_fused() - f0
+        outs[path] = out.cpu().numpy().reshape(len(ds), -1)
+        ctx.close()
+    n1 = fused[0]
+    assert fused[2] == len(ds) and fused[1] == 0 and 0 < n1 < len(ds), fused
+    assert np.array_equal(outs[0][:n1], outs[2][:n1])
+    assert np.array_equal(outs[0][n1:], outs[1][n1:])
+    assert np.max(np.abs(outs[0][n1:])) > 0
+
+
 def test_full_size_workload_matches_stored_oracle_samples(env):
     """The benchmark's own solve (128 instances, 256^2, 1000 steps, complex64, fused kernel)
     against FP64 oracle values stored by tests/golden/make_full_size_reference.py."""
