@@ -239,6 +239,12 @@ swf_status swf_set_dedupe(swf_ctx* ctx, int on);
 swf_status swf_fields_marched(swf_ctx* ctx, long long* count);
 /* Of those, the fields marched by the fused cluster kernel (the rest ran on the pass kernels). */
 swf_status swf_fields_fused(swf_ctx* ctx, long long* count);
+/* The split of an n_fields fused march (path 0) between the fused kernel and the pass kernels run
+ * concurrently on the SMs its clusters leave free, for `clusters` resident 16-CTA clusters on a
+ * device of `sms` SMs: *pass_fields receives the number of fields (the last ones) given to the
+ * pass kernels, 0 for no split.  Host-only (no device needed); SWF_EINVAL for negative counts or
+ * a NULL pointer. */
+swf_status swf_plan_split(int n_fields, int clusters, int sms, int* pass_fields);
 
 /* Launch shapes of the pass kernels (rows per block of the x passes, tile width of the y and z
  * passes, 256 or 128 threads per block).  on = 1 (default): the first march of each grid

@@ -743,6 +743,15 @@ swf_status swf_fields_marched(swf_ctx* ctx, long long* count) {
   return SWF_OK;
 }
 
+swf_status swf_plan_split(int n_fields, int clusters, int sms, int* pass_fields) {
+  if (!pass_fields || n_fields < 0 || clusters < 0 || sms < 0) {
+    set_error("swf_plan_split: negative count or NULL pointer");
+    return SWF_EINVAL;
+  }
+  *pass_fields = fused_split_count(n_fields, clusters, sms);
+  return SWF_OK;
+}
+
 swf_status swf_fields_fused(swf_ctx* ctx, long long* count) {
   if (!ctx || !count) { set_error("swf_fields_fused: NULL argument"); return SWF_EINVAL; }
   *count = ctx->fields_fused;

@@ -48,7 +48,7 @@ EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_sw
            "swf_bw_photons", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_set_dedupe", "swf_fields_marched",
-           "swf_fields_fused",
+           "swf_fields_fused", "swf_plan_split",
            "swf_set_tolerances", "swf_march_stats",
            "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_march_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     lib.swf_fields_marched.argtypes = [vp, C.POINTER(C.c_longlong)]
     lib.swf_fields_fused.argtypes = [vp, C.POINTER(C.c_longlong)]
+    lib.swf_plan_split.argtypes = [ip, ip, ip, C.POINTER(C.c_int)]
     lib.swf_rhs_noalloc.argtypes = [inst_p, ip, ip, dp, vp, vp, vp]
     fp = C.POINTER(C.c_float)
     lib.swf_mlp_param_count.argtypes = []
@@ -299,6 +300,14 @@ class Context:
 FIELD_CODES = {"zero": FIELD_ZERO, "sauter_gauss": FIELD_SAUTER_GAUSS, "pulse_gauss": FIELD_PULSE_GAUSS,
                "single_e": FIELD_SINGLE_E, "double_e": FIELD_DOUBLE_E}
 FLAG_CODES = {"spectrum": WANT_SPECTRUM, "full_n": WANT_FULL_N, "adaptive": ADAPTIVE, "bw_partial": BW_PARTIAL}
+
+
+def plan_split(n_fields, clusters, sms):
+    """swf_plan_split: fields of a fused march given to the pass kernels on the free SMs."""
+    load_library()
+    out = C.c_int()
+    _check(_lib.swf_plan_split(int(n_fields), int(clusters), int(sms), C.byref(out)))
+    return out.value
 
 
 def from_workload(d) -> Instance:

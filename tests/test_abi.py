@@ -79,3 +79,26 @@ def test_errors_without_device(lib):
     assert lib.solve_swf(None, 1, arr, 0, 1, res, None) == swf.SWF_EINVAL
     assert b"ctx is NULL" in lib.swf_last_error()
     assert lib.swf_destroy(None) == swf.SWF_OK
+
+
+def test_split_plan_of_fused_marches(lib):
+    """Host logic of the fused/pass split: the benchmark's 128 fields on GB300's 152 SMs and 7
+    resident 16-CTA clusters give 16 fields to the pass kernels; the fused part always ends in
+    fewer sector rounds than the whole, and the pass part stays within the time model."""
+    from paper_2512_16889_gb300 import swf
+    assert swf.plan_split(128, 7, 152) == 16
+    assert swf.plan_split(14, 7, 152) == 0      # too few fields
+    assert swf.plan_split(128, 9, 152) == 0     # too few free SMs
+    assert swf.plan_split(128, 0, 152) == 0
+    for n in range(16, 400):
+        n2 = swf.plan_split(n, 7, 152)
+        if n2 == 0:
+            continue
+        n1 = n - n2
+        rounds_all = -(-2 * n // 7)
+        rounds_fused = -(-2 * n1 // 7)
+        assert 0 < n2 < n and rounds_fused < rounds_all, n
+        assert 2.0 * n2 <= rounds_fused + 1e-12, n
+    with pytest.raises(swf.SwfError) as ei:
+        swf.plan_split(-1, 7, 152)
+    assert ei.value.status == swf.SWF_EINVAL
