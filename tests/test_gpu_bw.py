@@ -247,3 +247,35 @@ def test_bw_photon_scan_equals_solves_bitwise(env):
     with pytest.raises(swf.SwfError) as ei:
         ctx.bw_photons(bad, ks, es, swf.C64)
     assert ei.value.status == swf.SWF_EUNSUPPORTED
+
+
+EDGE_CASES = {
+    # (3+1)D: every axis non-trivial, the photon a grid mode along x and y
+    "3d": dict(fld=("sauter_gauss", (0.9, 0.7, 1.5)), n=(8, 6, 6), L=(6.0, 5.0, 5.0), t_in=-4.0, t_out=4.0,
+               n_steps=80, p=(0.3, 0.2, -0.1), q=(-0.2, 0.1, 0.3), k=(2 * np.pi / 6.0, 4 * np.pi / 5.0, 0.0)),
+    # an odd axis length (15 = 3 x 5): V modes that wrap around the grid carry the sign of the
+    # grid origin's phase
+    "odd": dict(fld=("sauter_gauss", (1.0, 0.7, 2.0)), n=(15, 12, 1), L=(7.5, 6.0, 1.0), t_in=-6.0, t_out=6.0,
+                n_steps=150, p=(0.3, -0.5, 0.0), q=(-0.2, -0.5, 0.0), k=(6 * np.pi / 7.5, -2 * np.pi / 6.0, 0.0)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(EDGE_CASES))
+@pytest.mark.parametrize("partial", [False, True])
+def test_bw_edge_grids_match_oracle(env, case, partial):
+    """Both integrand forms on a (3+1)D grid and on an odd axis length, against the oracle."""
+    swf, ctx = env
+    c = EDGE_CASES[case]
+    perp, par = O.polarisation_basis((0, 0, 1), c["k"])
+    ph = O.Photon(c["k"], tuple(par))
+    ref = O.bw_amplitude(O.Field(*c["fld"]), O.Grid(c["n"], c["L"]), c["p"], 1, c["q"], -1, ph, c["t_in"],
+                         c["t_out"], c["n_steps"], form=2 if partial else 1)
+    inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], 1, c["q"], -1,
+                    c["k"], par, flags=swf.BW_PARTIAL if partial else 0)
+    M = ref["M"]
+    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+        res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
+        got = _amps(res[0])
+        assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        for j in range(3):
+            assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
