@@ -2158,7 +2158,7 @@ struct F2Plan {
 
 template <typename R>
 static swf_status f2_prepare(swf_ctx* ctx, const GridDesc& g, int n_inst, const FieldDesc* fd_host,
-                             const double* photon_host, const double* wave_k_host, const StageArgs<R>& A,
+                             const double* photon_host, const double* wave_k_host,
                              F2Plan<R>* p, cudaStream_t st) {
   static bool attr_done[64] = {false};
   const int dv = dev_slot();
@@ -2252,7 +2252,6 @@ static swf_status f2_prepare(swf_ctx* ctx, const GridDesc& g, int n_inst, const 
     k_f2_omega_table<R><<<(int)std::min((total + 255) / 256, 8192L), 256, 0, st>>>((const F2Table*)ptabs, g, n_tab,
                                                                                    p->omt);
   }
-  (void)A;
   // the host tables above are temporaries
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "partial-integration tables");
@@ -2362,7 +2361,7 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
     if ((s = autotune_eval<R>(ctx, B, F, st)) != SWF_OK) return s;
   }
   F2Plan<R> p2;
-  if (form == 2 && (s = f2_prepare<R>(ctx, g, n_inst, fd_host, photon_host, wave_k_host, A, &p2, st)) != SWF_OK)
+  if (form == 2 && (s = f2_prepare<R>(ctx, g, n_inst, fd_host, photon_host, wave_k_host, &p2, st)) != SWF_OK)
     return s;
   int slot[7] = {0, 1, 2, 3, 4, 5, 6};
   const double h = (t_in - t_out) / n_steps;
