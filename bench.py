@@ -480,7 +480,9 @@ def run_pair_scan(args):
     E = [swf.from_workload(d) for d in els]
     P = [swf.from_workload(d) for d in pos]
     ctx = swf.Context(0)
-    ctx.pair_matrix(E[:2], P[:2], swf.C64)  # warm-up
+    # warm-up: the same scan at two steps (workspace, launch-shape tuning, first launches)
+    ctx.pair_matrix([swf.from_workload(dict(d, n_steps=2)) for d in els],
+                    [swf.from_workload(dict(d, n_steps=2)) for d in pos], swf.C64)
     times = []
     m0 = ctx.fields_marched()
     for _ in range(max(1, args.steps)):

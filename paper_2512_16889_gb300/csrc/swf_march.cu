@@ -1432,6 +1432,33 @@ static int dedupe_fields(const GridDesc& g, int n_f, const FieldDesc* fd, std::v
   return (int)uniq.size();
 }
 
+// Sizes the pass-kernel march's workspace for F fields (the buffers prepare_args and march_impl
+// take) without touching the device: growing a workspace buffer frees the old one, which waits
+// for the whole device, so march_split does it before the fused kernel starts.
+template <typename R>
+static swf_status reserve_march(swf_ctx* ctx, const GridDesc& g, int F) {
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  const size_t state = (size_t)F * 4 * g.N * sizeof(cpx<R>);
+  void* p = nullptr;
+  swf_status s;
+  if ((s = ws_get(ctx, "march.fd", sizeof(FieldDesc) * F, &p)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.greal", sizeof(R) * F * nt, &p)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.gcplx", sizeof(cpx<R>) * F * (nt + 4), &p)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.y", state, &p)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.T", state, &p)) != SWF_OK) return s;
+  for (int i = 0; i < 7; ++i) {
+    char nm[32];
+    std::snprintf(nm, sizeof nm, "march.k%d", i);
+    if ((s = ws_get(ctx, nm, state, &p)) != SWF_OK) return s;
+  }
+  if ((s = ws_get(ctx, "march.clock", sizeof(MarchClock), &p)) != SWF_OK) return s;
+  for (int a = 0; a < 3; ++a) {
+    const void* tw = nullptr;
+    if ((s = twiddles(ctx, g.n[a], Prec<R>::is_double, &tw)) != SWF_OK) return s;
+  }
+  return SWF_OK;
+}
+
 // The fused kernel on the first n_f - n2 fields (stream st) and, concurrently, the pass kernels
 // on the last n2 fields (the context's auxiliary stream), which take the SMs that the fused
 // kernel's clusters leave free.  The auxiliary stream starts after the work already queued on
@@ -1447,10 +1474,12 @@ static swf_status march_split(swf_ctx* ctx, const GridDesc& g, double t_in, doub
         return cuda_status(e, "auxiliary stream events");
   }
   const int n1 = n_f - n2;
+  swf_status s = reserve_march<float>(ctx, g, n2);
+  if (s != SWF_OK) return s;
   if ((e = cudaEventRecord(ctx->aux_ev[0], st)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(ctx->aux, ctx->aux_ev[0], 0)) != cudaSuccess)
     return cuda_status(e, "order the auxiliary stream");
-  swf_status s = march_fused(ctx, g, t_in, t_out, n_steps, n1, fd_host, psi_out, st);
+  s = march_fused(ctx, g, t_in, t_out, n_steps, n1, fd_host, psi_out, st);
   if (s != SWF_OK) return s;
   cpx<float>* out2 = (cpx<float>*)psi_out + (size_t)n1 * 4 * g.N;
   s = march_impl<float>(ctx, g, t_in, t_out, n_steps, n2, fd_host + n1, out2, ctx->aux);
