@@ -349,15 +349,18 @@ def dopri5_march(f, y0, t_out: float, t_in: float, n_steps: int, stage_hook=None
     return y, acc
 
 
-def dopri5_adaptive(f, y0, t_out: float, t_in: float, h0: float, rtol: float, atol: float, max_attempts: int):
+def dopri5_adaptive(f, y0, t_out: float, t_in: float, h0: float, rtol: float, atol: float, max_attempts: int,
+                    stage_hook=None, fields_axis0: bool = False):
     """Dormand-Prince 5(4) with step-size control (the integrator Sec. II.A names: Dopri5 with
     relative and absolute tolerances), from t_out down to t_in (h < 0), first-same-as-last.
 
     Error of a step: e = h sum_i (b_i - b*_i) k_i (fifth- minus fourth-order solution); scaled
-    norm err = sqrt(mean(|e|^2 / (atol + rtol max(|y_n|, |y_n+1|))^2)) over all complex entries.
+    norm err = sqrt(mean(|e|^2 / (atol + rtol max(|y_n|, |y_n+1|))^2)) over all complex entries
+    (with fields_axis0: over each field y[f] separately, err the largest of them).
     The step is accepted when err <= 1; the next step is h * min(10, max(0.2, 0.9 err^(-1/5)))
     (the standard integral controller), never passing t_in.  Returns (y(t_in), accepted,
-    rejected).
+    rejected), and with ``stage_hook(t_i, Y_i)`` also the appended quadrature variable, integrated
+    with the weights b_i over the accepted steps (Eq. 35's Y = (psi, M) form).
     """
     c = [float(v) for v in DP_C]
     a = [[float(v) for v in row] for row in DP_A]
@@ -366,7 +369,10 @@ def dopri5_adaptive(f, y0, t_out: float, t_in: float, h0: float, rtol: float, at
     t = t_out
     span = abs(t_in - t_out)
     h = -abs(h0) if t_in < t_out else abs(h0)
+    b = [float(v) for v in DP_B]
     k = [f(t, y)] + [None] * 6
+    g = [stage_hook(t, y) if stage_hook else 0.0] + [0.0] * 6
+    acc = 0.0
     accepted = rejected = 0
     while abs(t_in - t) > 1e-12 * span:
         if accepted + rejected >= max_attempts:
@@ -379,12 +385,21 @@ def dopri5_adaptive(f, y0, t_out: float, t_in: float, h0: float, rtol: float, at
                 if a[i][j] != 0.0:
                     yi = yi + (h * a[i][j]) * k[j]
             k[i] = f(t + c[i] * h, yi)
+            if stage_hook is not None:
+                g[i] = stage_hook(t + c[i] * h, yi)
         y_new = yi
         e = h * sum(db[j] * k[j] for j in range(7) if db[j] != 0.0)
         sc = atol + rtol * np.maximum(np.abs(y), np.abs(y_new))
-        err = float(np.sqrt(np.mean((np.abs(e) / sc) ** 2)))
+        q = (np.abs(e) / sc) ** 2
+        if fields_axis0:
+            err = float(max(np.sqrt(np.mean(q[fi])) for fi in range(q.shape[0])))
+        else:
+            err = float(np.sqrt(np.mean(q)))
         fac = 10.0 if err == 0.0 else min(10.0, max(0.2, 0.9 * err ** -0.2))
         if err <= 1.0:
+            if stage_hook is not None:
+                acc = acc + h * sum(b[j] * g[j] for j in range(7))
+                g[0] = g[6]
             t = t + h
             y = y_new
             k[0] = k[6]
@@ -392,6 +407,8 @@ def dopri5_adaptive(f, y0, t_out: float, t_in: float, h0: float, rtol: float, at
         else:
             rejected += 1
         h = h * fac
+    if stage_hook is not None:
+        return y, accepted, rejected, acc
     return y, accepted, rejected
 
 
@@ -667,6 +684,26 @@ def bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps, form: int = 1)
     return y[0], y[1], -m
 
 
+def bw_march_adaptive(fld, grid, bg_u, bg_v, photon, t_in, t_out, h0, rtol, atol, max_attempts=100000):
+    """bw_march with the step-size-controlled Dormand-Prince march: one step for both waves, the
+    error norm the larger of the U and V fields' (the appended integral is left out of it: three
+    numbers against 8 n^d), the integrand of Eq. 17 integrated over the accepted steps.
+    Returns (U_scat(t_in), V_scat(t_in), M_finite[3], accepted, rejected)."""
+    h0u = h0_field(grid, bg_u.offset())
+    h0v = h0_field(grid, bg_v.offset())
+
+    def f(t, y):
+        return np.stack([rhs(fld, grid, bg_u, h0u, t, y[0]), rhs(fld, grid, bg_v, h0v, t, y[1])])
+
+    def g(t, y):
+        return bw_integrand(grid, photon, bg_u, bg_v, t, y[0], y[1])
+
+    y0 = np.zeros((2, 4) + grid.n, dtype=complex)
+    y, acc_n, rej_n, m = dopri5_adaptive(f, y0, t_out, t_in, h0, rtol, atol, max_attempts, stage_hook=g,
+                                         fields_axis0=True)
+    return y[0], y[1], -m, acc_n, rej_n
+
+
 def bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in):
     """Analytic t < t_in parts of Eqs. 25-27 with the energy projectors of Eq. 23.
 
@@ -733,15 +770,24 @@ def bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in):
     return np.array([ss, bs, sb])
 
 
-def bw_amplitude(fld, grid, p, s, q, r, photon, t_in, t_out, n_steps, form: int = 1):
+def bw_amplitude(fld, grid, p, s, q, r, photon, t_in, t_out, n_steps, form: int = 1, adaptive=None):
     """M = M_ss + M_bs + M_sb (Eq. 13).
 
     form = 1: each term is the sum of its finite (Eq. 17) and past (Eqs. 25-27) part.
     form = 2: each term is the time integral of the partial-integration integrand (Eqs. 30-33);
     "past" is then zero.
+    adaptive = (rtol, atol) (form 1): the step-size-controlled march, first step
+    (t_in - t_out)/n_steps; the result then also holds "accepted" and "rejected".
     """
     bg_u = Background("U", tuple(p), s)
     bg_v = Background("V", tuple(q), r)
+    if adaptive is not None:
+        rtol, atol = adaptive
+        psi_u, psi_v, m_fin, acc_n, rej_n = bw_march_adaptive(fld, grid, bg_u, bg_v, photon, t_in, t_out,
+                                                              (t_in - t_out) / n_steps, rtol, atol)
+        m_past = bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in)
+        return {"finite": m_fin, "past": m_past, "terms": m_fin + m_past, "M": complex(np.sum(m_fin + m_past)),
+                "psi_u": psi_u, "psi_v": psi_v, "accepted": acc_n, "rejected": rej_n}
     if form == 2:
         psi_u, psi_v, m = bw_march(fld, grid, bg_u, bg_v, photon, t_in, t_out, n_steps, form=2)
         return {"finite": m, "past": np.zeros(3, dtype=complex), "terms": m, "M": complex(np.sum(m)),

@@ -317,6 +317,21 @@ def test_bw_partial_integration_form_equals_past_finite_split():
     assert gaps[0] / gaps[1] > 20.0, gaps
 
 
+def test_bw_step_size_controlled_march_converges_to_the_fixed_step_amplitude():
+    """Breit-Wheeler with the paper's step-size-controlled Dopri5 (Sec. II.A) and M appended
+    (Eq. 35): the amplitude approaches the fine fixed-step one as the tolerances tighten."""
+    grid, fld, ph = _bw_setup_2d()
+    p, q = (0.25, -1.0, 0.0), (-0.25, -1.0, 0.0)
+    ref = O.bw_amplitude(fld, grid, p, 1, q, 1, ph, -9.0, 9.0, 800)["M"]
+    gaps, steps = [], []
+    for tol in ((1e-5, 1e-10), (1e-7, 1e-12)):
+        r = O.bw_amplitude(fld, grid, p, 1, q, 1, ph, -9.0, 9.0, 50, adaptive=tol)
+        gaps.append(abs(r["M"] - ref) / abs(ref))
+        steps.append(r["accepted"])
+    assert gaps[0] < 1e-5 and gaps[1] < gaps[0] / 20, gaps
+    assert steps[1] > steps[0] > 50, steps
+
+
 def test_bw_partial_integration_zero_field_gives_zero():
     grid, _, ph = _bw_setup_2d()
     res = O.bw_amplitude(O.Field("zero"), grid, (0.25, -1.0, 0), 1, (-0.25, -1.0, 0), 1, ph, -3.0, 3.0, 20, form=2)
