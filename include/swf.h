@@ -98,10 +98,13 @@ typedef struct {
 
 #define SWF_WANT_SPECTRUM 1  /* Schwinger: |C(m,(r,q))|^2 for every grid positron q */
 #define SWF_WANT_FULL_N   2  /* Schwinger: march V too and return both lines of Eq. 8 */
-#define SWF_ADAPTIVE      4  /* Schwinger: step-size-controlled march (Sec. II.A: Dopri5 with relative and
+#define SWF_ADAPTIVE      4  /* step-size-controlled march (Sec. II.A: Dopri5 with relative and
                                 absolute tolerances, swf_set_tolerances); the first step is
                                 (t_in - t_out)/n_steps and at most 100 n_steps + 100 attempts are made
-                                (SWF_ENUMERIC beyond); pass kernels only */
+                                (SWF_ENUMERIC beyond); pass kernels only.  Breit-Wheeler: U and V share
+                                the controller (the larger of their error norms decides), the
+                                integrand of Eq. 17 is integrated over the accepted steps (Eq. 35);
+                                not with SWF_BW_PARTIAL (SWF_EUNSUPPORTED) */
 #define SWF_BW_PARTIAL    8  /* Breit-Wheeler: integrate the partial-integration integrands of Sec. IV
                                 (Eqs. 30-33) during the march instead of adding the past terms of
                                 Eqs. 25-27 to the finite-time terms of Eq. 17; amp holds the same three

@@ -487,9 +487,11 @@ static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, s
     k.t_out = in.grid.t_out;
     k.n_steps = in.grid.n_steps;
     k.full = (in.flags & SWF_BW_PARTIAL) ? 1 : 0;  // the integrand form (Eq. 17 + past, or Eqs. 30-33)
+    k.adaptive = (in.flags & SWF_ADAPTIVE) ? 1 : 0;
     groups[k].push_back(i);
-    if (in.flags & SWF_ADAPTIVE) {
-      set_error("instance " + std::to_string(i) + ": step-size control is for Schwinger marches (fixed steps here)");
+    if ((in.flags & SWF_ADAPTIVE) && (in.flags & SWF_BW_PARTIAL)) {
+      set_error("instance " + std::to_string(i) +
+                ": the partial-integration form marches at fixed steps (step-size control is for the past/finite split)");
       return SWF_EUNSUPPORTED;
     }
     swf_status c = check_bw_photon(in, in.k, "instance " + std::to_string(i) + ": ");
@@ -528,9 +530,16 @@ static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, s
     if ((s = ws_get(ctx, "bwsolve.macc", (size_t)G * 9 * 16, &macc)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "bwsolve.norms", (size_t)2 * G * 8, &norms)) != SWF_OK) return s;
     // kat holds, per wave, the momentum of its direct transform (U~ at k - q, V~ at p - k)
-    if ((s = march_bw(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, G, fd.data(), photon.data(), prec, psi,
-                      (double2*)macc, st, form, kat.data())) != SWF_OK)
+    if (kv.first.adaptive) {
+      // first step (t_in - t_out)/n_steps, at most 100 n_steps + 100 attempts (as for Schwinger marches)
+      const double h0 = (i0.grid.t_in - i0.grid.t_out) / i0.grid.n_steps;
+      if ((s = march_bw_adaptive(ctx, g, i0.grid.t_in, i0.grid.t_out, h0, 100 * i0.grid.n_steps + 100, G, fd.data(),
+                                 photon.data(), prec, psi, (double2*)macc, st)) != SWF_OK)
+        return s;
+    } else if ((s = march_bw(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, G, fd.data(), photon.data(), prec,
+                             psi, (double2*)macc, st, form, kat.data())) != SWF_OK) {
       return s;
+    }
     if (form == 2) {
       if ((s = field_norms(ctx, g, 2 * G, prec, psi, (double*)norms, st)) != SWF_OK) return s;
       if ((s = bw_finalize_partial(ctx, g, G, bw.data(), (const double2*)macc, (const double*)norms, results_dev,

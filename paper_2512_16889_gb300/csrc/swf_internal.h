@@ -177,6 +177,11 @@ swf_status march_bw(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, 
                     const FieldDesc* fd_host, const double* photon_host, swf_precision prec, void* psi_out,
                     double2* macc, cudaStream_t st, int form = 1, const double* wave_k_host = nullptr,
                     int n_ph = 1);
+// The same march (form 1, one photon per instance) with step-size control (first step h0, at most
+// max_attempts attempts; tolerances from ctx); macc [n_inst][3].
+swf_status march_bw_adaptive(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, double h0, int max_attempts,
+                             int n_inst, const FieldDesc* fd_host, const double* photon_host, swf_precision prec,
+                             void* psi_out, double2* macc, cudaStream_t st);
 // (n_ph photons per instance, form 1 only: photon_host and macc then hold n_inst * n_ph entries,
 // photon j of instance i at i n_ph + j; the marched waves are shared by the photons.)
 

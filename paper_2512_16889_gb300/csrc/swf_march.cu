@@ -1208,6 +1208,67 @@ __global__ void k_step_accept(const StepControl* ctl, cpx<R>* y, const cpx<R>* y
 // controller, the copy-in of an accepted step) is one CUDA graph replay; nothing is decided on
 // the host: after t_in (or a failure) the remaining replays of a chunk do nothing.  The host
 // reads the controller's state once per chunk of replays.
+// Runs step attempts recorded by `attempt` (launches only, on st) until the controller in ctl
+// reports t_in reached or a failure: chunks of 8, 16, .. 64 attempts as CUDA-graph replays
+// (kernel by kernel when timing is on), the controller's state read once per chunk into *out.
+template <typename Att>
+static swf_status run_attempts(swf_ctx* ctx, cudaStream_t st, int max_attempts, const StepControl* ctl,
+                               Att&& attempt, StepControl* out) {
+  swf_status s = SWF_OK;
+  cudaError_t e = cudaSuccess;
+  bool graph = !ctx->prof.on && st != 0 && ctx->use_graphs;
+  cudaGraphExec_t exec = nullptr;
+  long long per_attempt = 0;
+  if (graph) {
+    const long long l0 = ctx->prof.launches;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      graph = false;
+    } else {
+      s = attempt();
+      cudaGraph_t gr = nullptr;
+      e = cudaStreamEndCapture(st, &gr);
+      per_attempt = ctx->prof.launches - l0;
+      ctx->prof.launches = l0;
+      if (s != SWF_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_status(e, "capture of the step attempt");
+      e = cudaGraphInstantiate(&exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return cuda_status(e, "instantiate the step attempt");
+    }
+  }
+  StepControl hc{};
+  int chunk = 8, attempts = 0;
+  while (true) {
+    for (int a = 0; a < chunk; ++a) {
+      if (graph) {
+        e = cudaGraphLaunch(exec, st);
+        ctx->prof.launches += per_attempt;
+        if (e != cudaSuccess) break;
+      } else if ((s = attempt()) != SWF_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        return s;
+      }
+    }
+    attempts += chunk;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(StepControl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || hc.done) break;
+    if (attempts > max_attempts + chunk) {  // the controller stops at max_attempts; this is a backstop
+      hc.failed = 1;
+      break;
+    }
+    chunk = std::min(chunk * 2, 64);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return cuda_status(e, "step-size-controlled march");
+  *out = hc;
+  return SWF_OK;
+}
+
 template <typename R>
 static swf_status march_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, double h0,
                                       int max_attempts, int F, const FieldDesc* fd_host, void* psi_out,
@@ -1303,56 +1364,8 @@ static swf_status march_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double t_
     }
     return SWF_OK;
   };
-  // chunks of attempts, as graph replays (kernel by kernel when timing is on)
-  bool graph = !ctx->prof.on && st != 0 && ctx->use_graphs;
-  cudaGraphExec_t exec = nullptr;
-  long long per_attempt = 0;
-  if (graph) {
-    const long long l0 = ctx->prof.launches;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      cudaGetLastError();
-      graph = false;
-    } else {
-      s = attempt();
-      cudaGraph_t gr = nullptr;
-      e = cudaStreamEndCapture(st, &gr);
-      per_attempt = ctx->prof.launches - l0;
-      ctx->prof.launches = l0;
-      if (s != SWF_OK) {
-        if (gr) cudaGraphDestroy(gr);
-        return s;
-      }
-      if (e != cudaSuccess) return cuda_status(e, "capture of the step attempt");
-      e = cudaGraphInstantiate(&exec, gr, 0);
-      cudaGraphDestroy(gr);
-      if (e != cudaSuccess) return cuda_status(e, "instantiate the step attempt");
-    }
-  }
   StepControl hc{};
-  int chunk = 8, attempts = 0;
-  while (true) {
-    for (int a = 0; a < chunk; ++a) {
-      if (graph) {
-        e = cudaGraphLaunch(exec, st);
-        ctx->prof.launches += per_attempt;
-        if (e != cudaSuccess) break;
-      } else if ((s = attempt()) != SWF_OK) {
-        if (exec) cudaGraphExecDestroy(exec);
-        return s;
-      }
-    }
-    attempts += chunk;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(StepControl), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess || hc.done) break;
-    if (attempts > max_attempts + chunk) {  // the controller stops at max_attempts; this is a backstop
-      hc.failed = 1;
-      break;
-    }
-    chunk = std::min(chunk * 2, 64);
-  }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (e != cudaSuccess) return cuda_status(e, "step-size-controlled march");
+  if ((s = run_attempts(ctx, st, max_attempts, ctl, attempt, &hc)) != SWF_OK) return s;
   ctx->last_accepted = hc.accepted;
   ctx->last_rejected = hc.rejected;
   if (hc.failed) {
@@ -2493,6 +2506,213 @@ swf_status march_bw(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, 
                                 wave_k_host, n_ph);
   return march_bw_impl<double>(ctx, g, t_in, t_out, n_steps, n_inst, fd_host, photon_host, psi_out, macc, st, form,
                                wave_k_host, n_ph);
+}
+
+// ---------------------------------------------------------------- step-size-controlled Breit-Wheeler march
+// Per attempt and photon-instance: the stage rows of the integrand's phase table from the
+// controller's t and h (stage i at t + c_i h): the U and V background time phases and the
+// quadrature factor h b_{i+1} dx^d e^{-i k0 t} (stage 0 is the accepted state y_n, stage 6 the
+// new state, whose weight b_7 is zero).  rows [inst][7][3].
+__global__ void k_bw_attempt_rows(const FieldDesc* fd, const double* photon, const StepControl* ctl, double cell,
+                                  cpx<double>* rows) {
+  const int inst = blockIdx.x, i = threadIdx.x;
+  if (i >= 7 || ctl->done) return;
+  const double DPc[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
+  const double DPb[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
+  const double t = ctl->t + DPc[i] * ctl->h;
+  const double w = ctl->h * DPb[i];
+  const FieldDesc& FU = fd[2 * inst];
+  const FieldDesc& FV = fd[2 * inst + 1];
+  const double* k = photon + 6 * inst;
+  const double k0 = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+  double sn, cs;
+  cpx<double>* r = rows + 3 * (7 * (size_t)inst + i);
+  sincos(FU.tsign * FU.e0 * t, &sn, &cs);
+  r[0] = mk<double>(cs, sn);
+  sincos(FV.tsign * FV.e0 * t, &sn, &cs);
+  r[1] = mk<double>(cs, sn);
+  sincos(-k0 * t, &sn, &cs);
+  r[2] = mk<double>(w * cell * cs, w * cell * sn);
+}
+
+// After an accepted attempt: the attempt's integrand sums join the march's.
+__global__ void k_mdot_commit(const StepControl* ctl, const cpx<double>* __restrict__ tryacc, cpx<double>* acc,
+                              size_t n) {
+  if (!ctl->ok) return;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc[i] = acc[i] + tryacc[i];
+}
+
+// The Breit-Wheeler march (U and V of every instance, the integrand of Eq. 17 appended) with
+// step-size control: one controller for all 2 n_inst waves (the error norm is the largest of
+// theirs), each attempt one graph replay as in march_adaptive_impl.  The integrand is summed per
+// attempt and committed only when the step is accepted.  macc [n_inst][3] as march_bw's form 1.
+template <typename R>
+static swf_status march_bw_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, double h0,
+                                         int max_attempts, int n_inst, const FieldDesc* fd_host,
+                                         const double* photon_host, void* psi_out, double2* macc, cudaStream_t st) {
+  const int F = 2 * n_inst;
+  StageArgs<R> A;
+  swf_status s = prepare_args<R>(ctx, g, F, fd_host, &A, "bw", st);
+  if (s != SWF_OK) return s;
+  const size_t per_field = (size_t)4 * g.N;
+  const size_t state = (size_t)F * per_field * sizeof(cpx<R>);
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  void *py, *pyn, *pT, *pys, *pk[7], *pctl, *ppart, *pph, *pkph, *prow, *pacc, *ptry, *pclk;
+  if ((s = ws_get(ctx, "march.y", state, &py)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.ynew", state, &pyn)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.T", state, &pT)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.ystage", state, &pys)) != SWF_OK) return s;
+  for (int i = 0; i < 7; ++i) {
+    char nm[32];
+    std::snprintf(nm, sizeof nm, "march.k%d", i);
+    if ((s = ws_get(ctx, nm, state, &pk[i])) != SWF_OK) return s;
+  }
+  const int nbe = (int)std::max<size_t>(1, std::min<size_t>((per_field + 4095) / 4096, 64));
+  const int nb = std::max(1, std::min((g.N + 1023) / 1024, (4 * sm_count() + n_inst - 1) / n_inst));
+  const size_t nacc = (size_t)3 * nb * n_inst;
+  if ((s = ws_get(ctx, "march.ctl", sizeof(StepControl), &pctl)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "march.err_part", sizeof(double) * (size_t)nbe * F, &ppart)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.photon", sizeof(double) * 6 * n_inst, &pph)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.kph", sizeof(cpx<R>) * n_inst * nt, &pkph)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.arows", sizeof(cpx<double>) * 3 * 7 * (size_t)n_inst, &prow)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.mpart", sizeof(cpx<double>) * nacc, &pacc)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.mtry", sizeof(cpx<double>) * nacc, &ptry)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "bw.aclock", sizeof(MarchClock), &pclk)) != SWF_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(pph, photon_host, sizeof(double) * 6 * n_inst, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload photon table");
+  {
+    ProfScope ps(ctx, "k_photon_tables", st);
+    k_photon_tables<R><<<(n_inst * nt + 127) / 128, 128, 0, st>>>((const double*)pph, g, n_inst, (cpx<R>*)pkph);
+  }
+  // k_mdot reads its phase row at (clock step + ls) * 7 + stage: a clock at step 0 and a row
+  // stride of 7 select the attempt's rows
+  MarchClock* clk = (MarchClock*)pclk;
+  k_clock_set<<<1, 1, 0, st>>>(clk, t_out, 0.0);
+  if ((e = cudaMemsetAsync(py, 0, state, st)) != cudaSuccess) return cuda_status(e, "memset state");
+  if ((e = cudaMemsetAsync(pacc, 0, sizeof(cpx<double>) * nacc, st)) != cudaSuccess)
+    return cuda_status(e, "memset M accumulators");
+  StepControl c0{};
+  c0.t = t_out;
+  c0.h = (t_in < t_out) ? -std::fabs(h0) : std::fabs(h0);
+  if (std::fabs(c0.h) > std::fabs(t_in - t_out)) c0.h = t_in - t_out;
+  c0.t_in = t_in;
+  c0.span = std::fabs(t_in - t_out);
+  c0.rtol = ctx->rtol;
+  c0.atol = ctx->atol;
+  c0.max_attempts = max_attempts;
+  StepControl* ctl = (StepControl*)pctl;
+  e = cudaMemcpyAsync(ctl, &c0, sizeof(StepControl), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "upload step control");
+  A.y = (cpx<R>*)py;
+  A.T = (cpx<R>*)pT;
+  {
+    StageArgs<R> B = A;  // shapes by timing, before the slots hold anything
+    B.nterm = 6;
+    for (int q = 0; q < 6; ++q) {
+      B.kin[q] = (const cpx<R>*)pk[q + 1];
+      B.coef[q] = 0.0;
+    }
+    B.write_y = 0;
+    B.ystage = nullptr;
+    B.kout = (cpx<R>*)pk[0];
+    B.t = t_out;
+    if ((s = autotune_eval<R>(ctx, B, F, st)) != SWF_OK) return s;
+  }
+  // k_1 = f(t_out, 0)
+  A.nterm = 0;
+  A.write_y = 0;
+  A.kout = (cpx<R>*)pk[0];
+  A.t = t_out;
+  if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  A.ctl = ctl;
+  A.ynew = (cpx<R>*)pyn;
+  ErrWeights W;
+  for (int j = 0; j < 7; ++j) W.db[j] = DP_DB[j];
+  const double cell = g.dx[0] * g.dx[1] * g.dx[2];
+  auto mdot = [&](const void* ys, int stage) {
+    ProfScope ps(ctx, "k_mdot", st);
+    k_mdot<R, 1><<<dim3(nb, n_inst), 256, 0, st>>>((const cpx<R>*)ys, A.gcplx, (const cpx<R>*)pkph,
+                                                   (const double*)pph, g, (const cpx<double>*)prow, clk, 0, stage,
+                                                   7, 1, (cpx<double>*)ptry);
+  };
+  auto attempt = [&]() -> swf_status {
+    cudaError_t e1 = cudaMemsetAsync(ptry, 0, sizeof(cpx<double>) * nacc, st);
+    if (e1 != cudaSuccess) return cuda_status(e1, "memset attempt sums");
+    {
+      ProfScope ps(ctx, "k_bw_attempt_rows", st);
+      k_bw_attempt_rows<<<n_inst, 32, 0, st>>>(A.fd, (const double*)pph, ctl, cell, (cpx<double>*)prow);
+    }
+    mdot(py, 0);  // stage 1 of the step: the accepted state
+    for (int i = 1; i < 7; ++i) {
+      int ntm = 0;
+      for (int j = 0; j < i; ++j) {
+        if (DP_A[i][j] == 0.0) continue;
+        A.kin[ntm] = (const cpx<R>*)pk[j];
+        A.coef[ntm] = DP_A[i][j];  // times the device-held h in k_first
+        ++ntm;
+      }
+      A.nterm = ntm;
+      A.write_y = (i == 6);
+      A.kout = (cpx<R>*)pk[i];
+      A.c = DP_C[i];
+      const bool weighted = i >= 2 && i <= 5;  // b_2 = b_7 = 0
+      A.ystage = weighted ? (cpx<R>*)pys : nullptr;
+      swf_status r = launch_eval<R>(ctx, A, F, st);
+      if (r != SWF_OK) return r;
+      if (weighted) mdot(pys, i);
+    }
+    {
+      ProfScope ps(ctx, "k_step_error", st);
+      k_step_error<R><<<dim3(nbe, F), 256, 0, st>>>(
+          (const cpx<R>*)py, (const cpx<R>*)pyn, (const cpx<R>*)pk[0], (const cpx<R>*)pk[1], (const cpx<R>*)pk[2],
+          (const cpx<R>*)pk[3], (const cpx<R>*)pk[4], (const cpx<R>*)pk[5], (const cpx<R>*)pk[6], W, ctl, per_field,
+          (double*)ppart);
+    }
+    {
+      ProfScope ps(ctx, "k_step_control", st);
+      k_step_control<<<1, 32, 0, st>>>(ctl, (const double*)ppart, nbe, F, (double)per_field);
+    }
+    {
+      ProfScope ps(ctx, "k_step_accept", st);
+      const size_t n = (size_t)F * per_field;
+      k_step_accept<R><<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(
+          ctl, (cpx<R>*)py, (const cpx<R>*)pyn, (cpx<R>*)pk[0], (const cpx<R>*)pk[6], n);
+    }
+    {
+      ProfScope ps(ctx, "k_mdot_commit", st);
+      k_mdot_commit<<<(unsigned)std::min<size_t>((nacc + 255) / 256, 1024), 256, 0, st>>>(
+          ctl, (const cpx<double>*)ptry, (cpx<double>*)pacc, nacc);
+    }
+    return SWF_OK;
+  };
+  StepControl hc{};
+  if ((s = run_attempts(ctx, st, max_attempts, ctl, attempt, &hc)) != SWF_OK) return s;
+  ctx->last_accepted = hc.accepted;
+  ctx->last_rejected = hc.rejected;
+  if (hc.failed) {
+    set_error("step-size-controlled march: no convergence (too many attempts or a non-finite error)");
+    return SWF_ENUMERIC;
+  }
+  {
+    ProfScope ps(ctx, "k_mdot_final", st);
+    k_mdot_final<<<n_inst, 96, 0, st>>>((const cpx<double>*)pacc, nb, (cpx<double>*)macc);
+  }
+  e = cudaMemcpyAsync(psi_out, py, state, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e, "copy psi(t_in)");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "Breit-Wheeler march kernels");
+  return SWF_OK;
+}
+
+swf_status march_bw_adaptive(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, double h0, int max_attempts,
+                             int n_inst, const FieldDesc* fd_host, const double* photon_host, swf_precision prec,
+                             void* psi_out, double2* macc, cudaStream_t st) {
+  if (prec == SWF_C64)
+    return march_bw_adaptive_impl<float>(ctx, g, t_in, t_out, h0, max_attempts, n_inst, fd_host, photon_host,
+                                         psi_out, macc, st);
+  return march_bw_adaptive_impl<double>(ctx, g, t_in, t_out, h0, max_attempts, n_inst, fd_host, photon_host,
+                                        psi_out, macc, st);
 }
 
 }  // namespace swf

@@ -279,3 +279,31 @@ def test_bw_edge_grids_match_oracle(env, case, partial):
         assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
         for j in range(3):
             assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
+
+
+def test_bw_step_size_controlled_march_matches_oracle(env):
+    """Breit-Wheeler with the paper's step-size control (Sec. II.A, rtol 1e-5, atol 1e-10) and
+    the integral appended (Eq. 35): the same accepted and rejected steps and amplitude as the
+    oracle's controlled march in complex128; complex64 within its tolerance."""
+    swf, ctx = env
+    c = CASE2D
+    perp, par = O.polarisation_basis((1, 0, 0), c["k"])
+    ph = O.Photon(c["k"], tuple(par))
+    ref = O.bw_amplitude(O.Field(*c["fld"]), O.Grid(c["n"], c["L"]), c["p"], 1, c["q"], 1, ph, c["t_in"],
+                         c["t_out"], 50, adaptive=(1e-5, 1e-10))
+    inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], 50, c["p"], 1, c["q"], 1, c["k"], par,
+                    flags=swf.ADAPTIVE)
+    M = ref["M"]
+    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+        res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
+        got = _amps(res[0])
+        if prec == swf.C128:
+            assert ctx.march_stats() == (ref["accepted"], ref["rejected"])
+        assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        for j in range(3):
+            assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
+    bad = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], 50, c["p"], 1, c["q"], 1, c["k"], par,
+                   flags=swf.ADAPTIVE | swf.BW_PARTIAL)
+    with pytest.raises(swf.SwfError) as ei:
+        ctx.solve([bad], swf.BREIT_WHEELER, swf.C64)
+    assert ei.value.status == swf.SWF_EUNSUPPORTED
