@@ -589,9 +589,9 @@ def run_workload(args):
         raise SystemExit(f"unknown workload {name}")
     if args.limit:
         ds = ds[:args.limit]
+    if args.adaptive and args.bw_partial:
+        raise SystemExit("--adaptive and --bw-partial do not combine (the partial-integration form uses fixed steps)")
     if args.adaptive:
-        if process != swf.SCHWINGER:
-            raise SystemExit("--adaptive applies to Schwinger workloads")
         ds = [dict(d, flags=tuple(d.get("flags", ())) + ("adaptive",)) for d in ds]
     if args.bw_partial:
         if process != swf.BREIT_WHEELER:
@@ -607,9 +607,10 @@ def run_workload(args):
     fields = 2 if process == swf.BREIT_WHEELER else (2 if name == "schwinger_fp64_single" else 1)
     su = sum(int(np.prod(d["n"])) * d["n_steps"] * fields for d in ds)
     ctx = swf.Context(0)
-    # warm-up: the same instances at two steps (plans, launch-shape tuning per grid group and
+    # warm-up: the same instances at two fixed steps (plans, launch-shape tuning per grid group and
     # first launches happen here, not in the timed solves)
-    ctx.solve([swf.from_workload(dict(d, n_steps=2)) for d in ds], process, prec)
+    ctx.solve([swf.from_workload(dict(d, n_steps=2, flags=tuple(f for f in d.get("flags", ()) if f != "adaptive")))
+               for d in ds], process, prec)
     times = []
     for _ in range(max(1, args.steps)):
         torch.cuda.synchronize()
@@ -675,7 +676,7 @@ def main():
     ap.add_argument("--workload", default=None, help="time another workload (see run_workload)")
     ap.add_argument("--limit", type=int, default=0, help="at most this many instances (--workload)")
     ap.add_argument("--max-steps", type=int, default=0, help="at most this many steps (--workload)")
-    ap.add_argument("--adaptive", action="store_true", help="step-size-controlled marches (--workload, Schwinger)")
+    ap.add_argument("--adaptive", action="store_true", help="step-size-controlled marches (--workload)")
     ap.add_argument("--bw-partial", action="store_true",
                     help="partial-integration form of the Breit-Wheeler terms (--workload bw_uneven)")
     args = ap.parse_args()
