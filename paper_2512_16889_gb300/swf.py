@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH):
     lib.solve_swf.argtypes = [vp, ip, inst_p, ip, ip, res_p, dbl_p]
     lib.solve_swf_dev.argtypes = [vp, ip, inst_p, ip, ip, vp, vp, vp]
     lib.swf_pair_matrix.argtypes = [vp, ip, inst_p, ip, inst_p, ip, res_p]
+    dptr = C.POINTER(C.c_double)
+    lib.swf_bw_photons.argtypes = [vp, inst_p, ip, dptr, dptr, dptr, ip, dptr, dptr]
     lib.swf_march_dev.argtypes = [vp, ip, inst_p, ip, ip, vp, vp]
     lib.swf_rhs_dev.argtypes = [vp, inst_p, ip, ip, dp, vp, vp, vp]
     lib.swf_spectrum_dev.argtypes = [vp, ip, inst_p, ip, vp, vp, vp, vp]
