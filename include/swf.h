@@ -48,7 +48,7 @@ typedef enum {
   SWF_ECUDA = 3,        /* a CUDA runtime call failed */
   SWF_ENUMERIC = 4,     /* a non-finite value appeared in the march */
   SWF_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
-  SWF_EUNSUPPORTED = 6  /* valid request outside what this build implements */
+  SWF_EUNSUPPORTED = 6  /* valid request outside what the library implements */
 } swf_status;
 
 typedef enum { SWF_SCHWINGER = 0, SWF_BREIT_WHEELER = 1 } swf_process;

@@ -21,7 +21,7 @@ multidimensional background fields"):
 * App. A.5, Eqs. A44-A45: spinor basis u_s(p), v_s(p), R_s;  App. A.6, Eq. A58: photon
   polarisation basis.
 
-Conventions (the readings are listed in the design doc):
+Conventions (readings where the paper leaves a choice open):
 * metric (+,-,-,-); A_mu covariant; Dirac representation of the gamma matrices;
   alpha^k = gamma^0 gamma^k, beta = gamma^0.
 * Hamiltonian form of Eq. 6:  d psi_s/dt = -i [ H0 psi_s + V (psi_s + psi_b) ],

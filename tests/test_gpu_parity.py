@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerances (derived in the design doc):
+Tolerances (from the arithmetic of the two paths):
 * complex128 path: same scheme and steps as the oracle, only the summation order differs ->
   1e-10 relative (state: max|diff| / max|ref|; scalars: |diff| / |ref|).
 * complex64 march: single-precision rounding accumulated over the march -> 1e-4 relative on
@@ -163,7 +163,7 @@ def test_c64_spectrum_within_tolerance(env):
     ref = np.transpose(np.abs(O.c_spectrum(pu, grid, d["t_in"])) ** 2, (0, 3, 2, 1)).ravel()
     bins = binned_rel_errors(spec, ref)
     print("c64 |C|^2 max rel error per decade below the maximum:", bins)
-    # 1e-4 relative holds for |C|^2 >= 1e-2 of the spectrum maximum (the floor stated in the design doc)
+    # 1e-4 relative holds for |C|^2 >= 1e-2 of the spectrum maximum (below it, the absolute floor)
     assert max(v for k, v in bins.items() if k >= -2) < 1e-4, bins
     # below the floor the error is an absolute single-precision noise floor of the whole wave
     assert np.max(np.abs(spec - ref)) < 5e-6 * ref.max()
