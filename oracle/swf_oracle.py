@@ -563,8 +563,10 @@ class PartialIntegrationTables:
     """Time-independent pieces of the partial-integration integrand (Sec. IV, Eqs. 28-33).
 
     For every U grid mode kappa_u (index idx) the V mode is kappa_v = kappa_u - k (index
-    idx - shift, periodic, as in the past terms).  Holds the energy projectors of both modes
-    and the four denominators Omega = sigma E_u - sigma' E_v - k0.
+    idx - shift, periodic, as in the past terms).  Holds the energy projectors of both modes,
+    the four denominators Omega = sigma E_u - sigma' E_v - k0 and the factor
+    e^{i(kappa_v + k - kappa_u).x0} that the grid sum of the pair's plane waves carries (1 unless
+    the V mode wrapped around the grid, then -1 on an odd axis length).
     """
 
     def __init__(self, grid, photon, bg_u, bg_v):
@@ -592,6 +594,9 @@ class PartialIntegrationTables:
         self.pv = {sg: proj(kv, self.ev, sg) for sg in (1, -1)}
         k0 = photon.k0()
         self.omega = {(sg, sgp): sg * self.eu - sgp * self.ev - k0 for sg in (1, -1) for sgp in (1, -1)}
+        X0 = [grid.x[a][0] if grid.n[a] > 1 else 0.0 for a in range(3)]
+        kk = [k[a] if grid.n[a] > 1 else 0.0 for a in range(3)]
+        self.wrap = np.exp(1j * sum((kv[a] + kk[a] - ku[a]) * X0[a] for a in range(3)))
 
     def on_u_modes(self, spec_v):
         """A V spectrum re-indexed so that entry idx holds V~(kappa_u(idx) - k)."""
@@ -632,7 +637,7 @@ def bw_integrand_partial(fld, grid, photon, bg_u, bg_v, tabs, t, psi_u, psi_v):
         pu, pdu = proj(tabs.pu[sg], su), proj(tabs.pu[sg], sdu)
         for sgp in (1, -1):
             pv, pdv = proj(tabs.pv[sgp], sv), proj(tabs.pv[sgp], sdv)
-            ss += np.sum((form(pdu, pv) + form(pu, pdv)) / tabs.omega[(sg, sgp)])
+            ss += np.sum(tabs.wrap * (form(pdu, pv) + form(pu, pdv)) / tabs.omega[(sg, sgp)])
     ss = 1j * np.exp(-1j * k0 * t) * ss / grid.volume
     k = np.asarray(photon.k, dtype=float)
     p = np.asarray(bg_u.p, dtype=float)
@@ -731,6 +736,7 @@ def bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in):
         else:
             shift.append(0)
     ss = 0.0 + 0.0j
+    x0 = [grid.x[a][0] for a in range(3)]
     for idx in np.ndindex(*grid.n):
         jdx = tuple((idx[a] - shift[a]) % grid.n[a] for a in range(3))  # mode kappa - k
         ku = np.array([KXu[idx], KYu[idx], KZu[idx]])
@@ -738,12 +744,15 @@ def bw_past(grid, photon, bg_u, bg_v, psi_u, psi_v, t_in):
         eu, ev = energy(ku), energy(kv)
         uu = su[(slice(None),) + idx]
         vv = sv[(slice(None),) + jdx]
+        # the grid sum of e^{i(kappa_v + k - kappa_u).x} over N points is N e^{i(kappa_v + k - kappa_u).x0}:
+        # 1 unless the V mode wrapped around the grid (then -1 on an odd axis length)
+        wrap = np.exp(1j * sum((kv[a] + k[a] - ku[a]) * x0[a] for a in range(3) if grid.n[a] > 1))
         for sg in (+1, -1):
             pu = energy_projector(ku, sg) @ uu
             for sgp in (+1, -1):
                 pv = energy_projector(kv, sgp) @ vv
                 om = sg * eu - sgp * ev - k0
-                ss += (np.conj(pu) @ ae @ pv) / (1j * om)
+                ss += wrap * (np.conj(pu) @ ae @ pv) / (1j * om)
     ss = ss * np.exp(-1j * k0 * t_in) / grid.volume
     # back, scat: U_back = u(p) e^{-i p0 t} in mode p, so V_scat is needed at mode p - k
     p = np.asarray(bg_u.p, dtype=float)

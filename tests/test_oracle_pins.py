@@ -332,6 +332,26 @@ def test_bw_step_size_controlled_march_converges_to_the_fixed_step_amplitude():
     assert steps[1] > steps[0] > 50, steps
 
 
+def test_bw_forms_agree_on_an_odd_axis_length():
+    """On a grid with an odd axis length a V mode that wraps around the grid pairs with its U mode
+    through the grid sum of their plane waves, N e^{i(kappa_v + k - kappa_u).x0} = -N: with that
+    factor in the mode sums the past/finite split and the partial-integration form are again the
+    same number (for grid momenta), up to the time quadrature."""
+    grid = O.Grid((15, 12, 1), (7.5, 6.0, 1.0))
+    fld = O.Field("sauter_gauss", (1.0, 0.7, 2.0))
+    ux, uy = 2 * np.pi / 7.5, 2 * np.pi / 6.0
+    k = (3 * ux, -uy, 0.0)
+    perp, par = O.polarisation_basis((0, 0, 1), k)
+    ph = O.Photon(k, tuple(par))
+    p, q = (ux, -2 * uy, 0.0), (-2 * ux, -uy, 0.0)
+    gaps = []
+    for n_steps in (200, 400):
+        r1 = O.bw_amplitude(fld, grid, p, 1, q, -1, ph, -10.0, 10.0, n_steps)
+        r2 = O.bw_amplitude(fld, grid, p, 1, q, -1, ph, -10.0, 10.0, n_steps, form=2)
+        gaps.append(np.max(np.abs(r1["terms"] - r2["terms"])) / abs(r1["terms"][0]))
+    assert gaps[1] < 1e-7 and gaps[0] / gaps[1] > 20.0, gaps
+
+
 def test_bw_partial_integration_zero_field_gives_zero():
     grid, _, ph = _bw_setup_2d()
     res = O.bw_amplitude(O.Field("zero"), grid, (0.25, -1.0, 0), 1, (-0.25, -1.0, 0), 1, ph, -3.0, 3.0, 20, form=2)
