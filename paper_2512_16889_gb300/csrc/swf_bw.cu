@@ -78,6 +78,17 @@ __global__ void __launch_bounds__(256) k_bw_finalize(const BwInst* bi, GridDesc 
       kv[a] = g.n[a] > 1 ? mode_kappa(jv[a], g.n[a], g.L[a]) : I.Kv[a];
     }
     const int j2 = (jv[2] * g.n[1] + jv[1]) * g.n[0] + jv[0];
+    // the grid sum of the pair's plane waves, N e^{i(kappa_v + k - kappa_u).x0}: -1 for a V mode
+    // that wrapped around an odd axis length (an odd number of times), 1 otherwise
+    int odd = 0;
+    for (int a = 0; a < 3; ++a) {
+      if (g.n[a] > 1 && (g.n[a] & 1)) {
+        const long fu = id[a] < (g.n[a] + 1) / 2 ? id[a] : id[a] - g.n[a];
+        const long fv = jv[a] < (g.n[a] + 1) / 2 ? jv[a] : jv[a] - g.n[a];
+        odd ^= (int)(((fu - fv - I.shift[a]) / g.n[a]) & 1);
+      }
+    }
+    const double wrap = odd ? -1.0 : 1.0;
     cpx<double> u[4], v[4];
     for (int a = 0; a < 4; ++a) {
       u[a] = su[(size_t)a * g.N + j];
@@ -94,7 +105,7 @@ __global__ void __launch_bounds__(256) k_bw_finalize(const BwInst* bi, GridDesc 
         alpha_eps_d(I.eps, pv, apv);
         cpx<double> d = mk<double>(0, 0);
         for (int a = 0; a < 4; ++a) d = d + cdot(pu[a], apv[a]);
-        acc = acc + div_i(d, sg * Eu - sgp * Ev - k0);
+        acc = acc + div_i(wrap * d, sg * Eu - sgp * Ev - k0);
       }
     }
   }

@@ -1886,10 +1886,11 @@ struct F2Table {
   double Ku[3], Kv[3], k0;
 };
 
-// Per table and U grid mode j (V mode j - shift, periodic): rho / Omega_{sigma sigma'} for
+// Per table and U grid mode j (V mode j - shift, periodic): 1 / Omega_{sigma sigma'} for
 // (sigma, sigma') = (+,+), (+,-), (-,+), (-,-), Omega = sigma E_u - sigma' E_v - k0, in FP64 and
-// rounded once.  rho = exp(i (kappa_u - kappa_v - k).x0) = +-1 is the origin phase that the wrapped
-// V mode leaves after exp(i k.x0) is taken out (-1 only for an odd axis length).
+// rounded once.  (On the raw transforms the pair's grid-sum factor e^{i(kappa_v + k - kappa_u).x0}
+// and the two origin phases combine into e^{i k.x0} for every pair, wrapped or not; the finalize
+// kernel applies it.)
 template <typename R>
 __global__ void k_f2_omega_table(const F2Table* tabs, GridDesc g, int n_tab, R* omt) {
   const long total = (long)n_tab * g.N;
@@ -1898,26 +1899,17 @@ __global__ void k_f2_omega_table(const F2Table* tabs, GridDesc g, int n_tab, R* 
     const int j = (int)(e % g.N);
     const int id[3] = {j % g.n[0], (j / g.n[0]) % g.n[1], j / (g.n[0] * g.n[1])};
     double ku[3], kv[3];
-    int odd = 0;
     for (int a = 0; a < 3; ++a) {
       const int jv = ((id[a] - T.shift[a]) % g.n[a] + g.n[a]) % g.n[a];
       ku[a] = kappa_of(id[a], g.n[a], g.L[a], T.Ku[a]);
       kv[a] = kappa_of(jv, g.n[a], g.L[a], T.Kv[a]);
-      if (g.n[a] > 1 && (g.n[a] & 1)) {
-        // integer wrap count of (f(id) - f(jv) - shift) / n along this axis
-        const long fu = id[a] < (g.n[a] + 1) / 2 ? id[a] : id[a] - g.n[a];
-        const long fv = jv < (g.n[a] + 1) / 2 ? jv : jv - g.n[a];
-        const long wr = (fu - fv - T.shift[a]) / g.n[a];
-        odd ^= (int)(wr & 1);
-      }
     }
     const double eu = energy3(ku), ev = energy3(kv);
-    const double rho = odd ? -1.0 : 1.0;
     R* o = omt + 4 * e;
-    o[0] = (R)(rho / (eu - ev - T.k0));
-    o[1] = (R)(rho / (eu + ev - T.k0));
-    o[2] = (R)(rho / (-eu - ev - T.k0));
-    o[3] = (R)(rho / (-eu + ev - T.k0));
+    o[0] = (R)(1.0 / (eu - ev - T.k0));
+    o[1] = (R)(1.0 / (eu + ev - T.k0));
+    o[2] = (R)(1.0 / (-eu - ev - T.k0));
+    o[3] = (R)(1.0 / (-eu + ev - T.k0));
   }
 }
 
@@ -2064,7 +2056,7 @@ __device__ __forceinline__ cpx<R> form_ae(const cpx<R>* x, const cpx<R>* aey) {
 
 // The mode sum of the (scat, scat) integrand at one weighted stage, on the raw transforms Yspec, Zspec
 // of the waves (no cell factor, no origin phase):
-//   sum_j sum_{sigma,sigma'} rho/Omega [ (P_s Zu~)^+ (alpha.eps) P_s' Yv~ + (P_s Yu~)^+ (alpha.eps) P_s' Zv~ ]
+//   sum_j sum_{sigma,sigma'} 1/Omega [ (P_s Zu~)^+ (alpha.eps) P_s' Yv~ + (P_s Yu~)^+ (alpha.eps) P_s' Zv~ ]
 // with U quantities at mode j and V quantities at mode j - shift.  Block (b, inst) adds trow[2]
 // (w_i e^{-i k0 t}) times its part to its own accumulator sspart[inst][b].
 // f2i per instance: shift[3], table index.
