@@ -42,3 +42,19 @@ def test_two_ranks_take_the_slowest_time_and_sum_the_work():
     for rank, ms_max, value in got:
         assert ms_max == 1500.0
         assert value == pytest.approx(2 * 100 * 3 / 1.5)
+
+
+def test_reference_arm_prints_its_line():
+    """bench.py --impl reference times the FP64 oracle on the host cores and prints one JSON line
+    with the arm's metric, cpu_baseline and an e2e record without device copies."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "site-updates/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
