@@ -2293,8 +2293,9 @@ static swf_status f2_prepare(swf_ctx* ctx, const GridDesc& g, int n_inst, const 
 }
 
 // One evaluation of the partial-integration integrand at stage `stage` of step (clock step + ls), on
-// the stage values ys of all waves: x transforms with Z and the direct transforms, forward y (and
-// z) transforms of the spectra, then the mode sum.
+// the stage values ys of all waves: the x transform of Z (and of Y on grids without a y or z pass;
+// otherwise the right-hand side's pass has written F[Y]) with the direct transforms, the forward y
+// (and z) transforms of Z, then the mode sum.
 template <typename R>
 static swf_status f2_integrand(swf_ctx* ctx, const StageArgs<R>& A, const F2Plan<R>& p, const cpx<R>* ys,
                                const double* photon_dev, const cpx<double>* ptab, int tab_stride, int ls, int stage,
