@@ -259,21 +259,21 @@ swf_status swf_plan_split(int n_fields, int clusters, int sms, int* pass_fields)
 swf_status swf_set_autotune(swf_ctx* ctx, int on);
 
 /* Allocation-free variant of swf_rhs_dev (the paper has no counterpart: this is a service of
- * the library).  Some callers cannot call cudaMalloc: code that runs while a stream is being
- * captured into a CUDA graph (an allocation is not captured, and cudaFree synchronises the
- * device), latency-critical loops that cannot absorb that synchronisation, and host
- * applications that own all device memory.  This entry point allocates nothing: it needs no
- * context and takes its workspace from one fixed device array of about 4.1 MiB that every GPU
- * loading the library holds until the process exits.  The caller passes inputs and outputs
- * exactly as for swf_rhs_dev; the evaluation runs on the current CUDA device, on `stream`
- * (NULL = the default stream), asynchronously.
+ * the library).  Some callers cannot call cudaMalloc: host applications that own all device
+ * memory and hand it out from a pool of their own, and latency-critical loops that cannot
+ * absorb the device-wide synchronisation that cudaFree brings.  This entry point allocates
+ * nothing: it needs no context and takes its workspace from one fixed device array of about
+ * 4.1 MiB that every GPU loading the library holds until the process exits.  The caller passes
+ * inputs and outputs exactly as for swf_rhs_dev; the evaluation runs on the current CUDA
+ * device, on `stream` (NULL = the default stream), asynchronously.
  * Limit: grids of at most 65536 points (for example 256 x 256 or 64 x 64 x 16) in either
  * precision; larger grids return SWF_EINVAL with a message.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture begins.  All calls on a device share the array and
- * it keeps the last call's contents (every value a call reads is written earlier by the same
- * call), so calls that overlap on the GPU -- on different streams or from different host
- * threads -- race on it and must be serialised by the caller. */
+ * The first call on a device (and the first after the device's context was reset) looks up
+ * the array's device address (cudaGetSymbolAddress) and sets the kernels' shared-memory limits;
+ * make that first call before any stream capture begins.  All calls on a device share the
+ * array and it keeps the last call's contents (every value a call reads is written earlier by
+ * the same call), so calls that overlap on the GPU -- on different streams or from different
+ * host threads -- race on it and must be serialised by the caller. */
 swf_status swf_rhs_noalloc(const swf_instance* inst, int bg, swf_precision prec, double t,
                            const void* psi_dev, void* out_dev, void* stream);
 

@@ -11,6 +11,7 @@
 //   last pass (x lines):   inverse x-FFT and k = (that) + Z.
 // Gauge field and background are analytic and evaluated on the fly from per-field 1D tables
 // (every field kind is a product of a time factor and one factor per axis).
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -776,9 +777,10 @@ static int tune_lookup(swf_ctx* ctx, const std::string& key, int fallback) {
 
 template <typename R>
 static swf_status set_smem_attrs() {
-  static bool done[64] = {false};
+  // per device; several host threads may arrive at once, and setting the attributes twice is harmless
+  static std::atomic<bool> done[64];
   const int dv = dev_slot();
-  if (done[dv]) return SWF_OK;
+  if (done[dv].load(std::memory_order_acquire)) return SWF_OK;
   cudaError_t e;
   e = cudaFuncSetAttribute(k_first<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_first)");
@@ -786,7 +788,7 @@ static swf_status set_smem_attrs() {
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_mid)");
   e = cudaFuncSetAttribute(k_last<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last)");
-  done[dv] = true;
+  done[dv].store(true, std::memory_order_release);
   return SWF_OK;
 }
 
@@ -1598,6 +1600,10 @@ __global__ void k_twiddles_into(cpx<R>* tw, int n) {
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Stores a field descriptor passed by value (kernel parameters are copied at launch, so no host
+// memory is referenced once the launch returns).
+__global__ void k_store_field_desc(FieldDesc fd, FieldDesc* dst) { *dst = fd; }
+
 size_t rhs_scratch_bytes(const GridDesc& g, swf_precision prec) {
   const size_t e = prec == SWF_C64 ? 8 : 16, r = prec == SWF_C64 ? 4 : 8;
   const size_t nt = g.n[0] + g.n[1] + g.n[2];
@@ -1637,8 +1643,7 @@ static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, doubl
     k_twiddles_into<R><<<(g.n[a] + 127) / 128, 128, 0, st>>>(tw, g.n[a]);
     A.tw[a] = tw;
   }
-  cudaError_t e = cudaMemcpyAsync(dfd, &fd, sizeof(FieldDesc), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_status(e, "upload field descriptor");
+  k_store_field_desc<<<1, 1, 0, st>>>(fd, dfd);
   k_tables<R><<<dim3((nt + 4 + 127) / 128, 1), 128, 0, st>>>(dfd, g, greal, gcplx);
   A.fd = dfd;
   A.greal = greal;
@@ -1649,7 +1654,7 @@ static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, doubl
   A.t = t;
   s = launch_eval<R>(nullptr, A, 1, st);
   if (s != SWF_OK) return s;
-  e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "rhs kernels");
   return SWF_OK;
 }

@@ -148,12 +148,37 @@ def _stream_ptr(stream):
     return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
+def _check_state_tensors(instance, psi, out, prec):
+    """Checks the device tensors of a right-hand-side call before their pointers are passed on:
+    the real dtype of the precision, at least 2 x 4 x N values each (N grid points), contiguous,
+    both on one CUDA device.  Returns that device."""
+    import torch
+    real = torch.float64 if prec == C128 else torch.float32
+    need = 8 * int(np.prod([instance.grid.n[a] for a in range(3)]))
+    for name, t in (("psi", psi), ("out", out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != real:
+            raise ValueError(f"{name} has dtype {t.dtype}; precision {'C128' if prec == C128 else 'C64'} needs {real}")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} values; the grid needs {need}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if psi.device != out.device:
+        raise ValueError(f"psi is on {psi.device} and out on {out.device}")
+    return psi.device
+
+
 def rhs_noalloc(instance, t, psi, out, bg=0, prec=C64, stream=None):
-    """swf_rhs_noalloc: one right-hand-side evaluation without any device allocation (see swf.h)."""
+    """swf_rhs_noalloc: one right-hand-side evaluation without any device allocation (see swf.h),
+    on the tensors' device."""
+    import torch
     load_library()
+    dev = _check_state_tensors(instance, psi, out, prec)
     arr = instance_array([instance])
-    _check(_lib.swf_rhs_noalloc(arr, bg, prec, float(t), C.c_void_p(psi.data_ptr()), C.c_void_p(out.data_ptr()),
-                                _stream_ptr(stream)))
+    with torch.cuda.device(dev):
+        _check(_lib.swf_rhs_noalloc(arr, bg, prec, float(t), C.c_void_p(psi.data_ptr()),
+                                    C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
 
 
 class Context:
@@ -161,6 +186,7 @@ class Context:
 
     def __init__(self, device: int = 0):
         load_library()
+        self.device = int(device)
         self._h = C.c_void_p()
         _check(_lib.swf_create(C.byref(self._h), int(device)))
 
@@ -287,6 +313,9 @@ class Context:
                                   _stream_ptr(stream)))
 
     def rhs_dev(self, instance, t, psi, out, bg=0, prec=C64, stream=None):
+        dev = _check_state_tensors(instance, psi, out, prec)
+        if dev.index != self.device:
+            raise ValueError(f"the tensors are on {dev}; this context runs on cuda:{self.device}")
         arr = instance_array([instance])
         _check(_lib.swf_rhs_dev(self._h, arr, bg, prec, float(t), C.c_void_p(psi.data_ptr()),
                                 C.c_void_p(out.data_ptr()), _stream_ptr(stream)))

@@ -5,12 +5,16 @@
   ||psi_scat(t_in)||^2 -> schwinger_batched_samples.json;
 * single FP64 Schwinger (128^2, 1000 steps): the full pair number (both lines of Eq. 8 and the
   amplitudes C, D, A, B) for r = +1 and -1, and C-spectrum samples -> schwinger_fp64_single.json;
+* batched Schwinger, whole spectra: for selected instances every C-spectrum entry at or above
+  1e-24 of the spectrum's maximum (the range where the complex64 and FP64 marches are compared
+  decade by decade) -> schwinger_batched_spectrum_<i>.json;
 * Breit-Wheeler uneven grids: the amplitude terms of one instance of the smallest grid (192^2,
   2605 steps) -> bw_uneven_sample.json; the same instance in the partial-integration form of
   Sec. IV (Eqs. 30-33) -> bw_uneven_partial_sample.json.
 The GPU tests compare the library's solves of the same instances against these values.
 
     python tests/golden/make_full_size_reference.py [instance ...]     # batched Schwinger
+    python tests/golden/make_full_size_reference.py --spectrum <instance>
     python tests/golden/make_full_size_reference.py --single
     python tests/golden/make_full_size_reference.py --bw
     python tests/golden/make_full_size_reference.py --bw-partial
@@ -45,6 +49,23 @@ def sample(i):
     return {"instance": i, "modes": [int(v) for v in idx], "prob": [float(prob[v]) for v in idx],
             "norm": float(O.inner(psi, psi, g).real), "max_prob": float(prob.max()),
             "seconds": time.time() - t0}
+
+
+def whole_spectrum(i, floor=1e-24):
+    """Every C-spectrum entry of instance i with |C|^2 >= floor * max, and the instance's norm."""
+    d = W.schwinger_batched()[i]
+    g = OA.grid(d)
+    t0 = time.time()
+    psi = O.march_scattered(OA.field(d), g, OA.background(d, 0), d["t_in"], d["t_out"], d["n_steps"])
+    C = O.c_spectrum(psi, g, d["t_in"])
+    prob = np.transpose(np.abs(C) ** 2, (0, 3, 2, 1)).ravel()  # library layout [r][z][y][x]
+    keep = np.nonzero(prob >= floor * prob.max())[0]
+    out = {"citation": "oracle/swf_oracle.py on paper_2512_16889_gb300.workloads.schwinger_batched()",
+           "instance": i, "floor": floor, "size": int(prob.size), "max_prob": float(prob.max()),
+           "modes": [int(v) for v in keep], "prob": [float(prob[v]) for v in keep],
+           "norm": float(O.inner(psi, psi, g).real), "seconds": time.time() - t0}
+    name = f"schwinger_batched_spectrum_{i}.json"
+    json.dump(out, open(os.path.join(os.path.dirname(OUT), name), "w"))
 
 
 def single_fp64():
@@ -95,6 +116,9 @@ def bw_sample(form=1):
 if __name__ == "__main__":
     if sys.argv[1:] == ["--single"]:
         single_fp64()
+        sys.exit(0)
+    if sys.argv[1:2] == ["--spectrum"]:
+        whole_spectrum(int(sys.argv[2]))
         sys.exit(0)
     if sys.argv[1:] == ["--bw"]:
         bw_sample()

@@ -102,3 +102,39 @@ def test_split_plan_of_fused_marches(lib):
     with pytest.raises(swf.SwfError) as ei:
         swf.plan_split(-1, 7, 152)
     assert ei.value.status == swf.SWF_EINVAL
+
+
+def test_rhs_wrappers_check_their_tensors_before_any_call(monkeypatch):
+    """The right-hand-side wrappers refuse tensors that would make the kernels read or write out
+    of bounds (wrong dtype for the precision, too few values, not contiguous) before a pointer
+    reaches the library; the checks need no GPU."""
+    import torch
+    from paper_2512_16889_gb300 import swf
+    d = dict(field=("sauter_gauss", (0.8, 0.6, 2.5)), n=(8, 4, 1), L=(8.0, 4.0, 1.0), t_in=-1.0, t_out=1.0,
+             n_steps=2, p=(0.0, 0.0, 0.0), s=1, q=(0.0, 0.0, 0.0), r=1, k=(0, 0, 0), eps=(0, 0, 0), flags=())
+    inst = swf.from_workload(d)
+    cpu = torch.zeros(8 * 32, dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        swf._check_state_tensors(inst, cpu, cpu, swf.C64)
+
+    class FakeCuda:  # the attributes the check reads, without a device
+        def __init__(self, dtype, numel, contiguous=True, device="cuda:0"):
+            self.dtype, self._n, self._c, self.device, self.is_cuda = dtype, numel, contiguous, torch.device(device), True
+
+        def numel(self):
+            return self._n
+
+        def is_contiguous(self):
+            return self._c
+
+    monkeypatch.setattr(torch, "Tensor", FakeCuda)  # the wrapper's isinstance check
+    ok = FakeCuda(torch.float32, 8 * 32)
+    assert swf._check_state_tensors(inst, ok, ok, swf.C64) == torch.device("cuda:0")
+    with pytest.raises(ValueError, match="dtype"):
+        swf._check_state_tensors(inst, ok, ok, swf.C128)
+    with pytest.raises(ValueError, match="the grid needs 256"):
+        swf._check_state_tensors(inst, FakeCuda(torch.float32, 255), ok, swf.C64)
+    with pytest.raises(ValueError, match="contiguous"):
+        swf._check_state_tensors(inst, ok, FakeCuda(torch.float32, 256, contiguous=False), swf.C64)
+    with pytest.raises(ValueError, match="cuda:1"):
+        swf._check_state_tensors(inst, ok, FakeCuda(torch.float32, 256, device="cuda:1"), swf.C64)

@@ -10,6 +10,20 @@ from oracle import swf_oracle as O
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
+# Tolerances: complex128 runs the oracle's scheme and steps (only the summation order differs):
+# 1e-10 relative on M and on each term (measured: 1e-15 on the small grids, 4e-13 on the full-size
+# instance).  complex64: 5e-5 relative on M and the terms, so that |M|^2 is within 1e-4 (measured:
+# at most 9e-7 on the small grids, 6e-6 at full size).
+
+
+def _precs(swf):
+    return ((swf.C128, 1e-10), (swf.C64, 5e-5))
+
+
+def _check_prob(prob, M, tol):
+    """|M|^2 within 2 tol relative (1e-4 for complex64, 2e-10 for complex128)."""
+    assert abs(prob - abs(M) ** 2) <= 2 * tol * abs(M) ** 2, (prob, abs(M) ** 2)
+
 
 @pytest.fixture(scope="module")
 def env():
@@ -51,10 +65,11 @@ def test_bw_partial_integration_form_matches_oracle_2d(env, spins):
     inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], s, c["q"], r,
                     c["k"], par, flags=swf.BW_PARTIAL)
     M = ref["M"]
-    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+    for prec, tol in _precs(swf):
         res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
         got = _amps(res[0])
         assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        _check_prob(res[0].prob[0], M, tol)
         for j in range(3):
             assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
 
@@ -85,14 +100,14 @@ def test_bw_amplitude_matches_oracle_2d(env, spins):
     c = CASE2D
     inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], s, c["q"], r,
                     c["k"], par)
-    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+    for prec, tol in _precs(swf):
         res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
         got = [complex(res[0].amp[2 * j], res[0].amp[2 * j + 1]) for j in range(4)]
         M = ref["M"]
         assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        _check_prob(res[0].prob[0], M, tol)
         for j in range(3):  # each of ss, bs, sb (finite + past)
             assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
-        assert abs(res[0].prob[0] - abs(M) ** 2) <= 2 * tol * abs(M) ** 2
 
 
 @pytest.mark.parametrize("partial", [False, True])
@@ -161,10 +176,11 @@ def test_full_size_instance_matches_stored_oracle(env):
     golden = json.load(open(os.path.join(GOLDEN, "bw_uneven_sample.json")))
     d = W.bw_uneven()[golden["instance"]]
     M = complex(*golden["M"])
-    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+    for prec, tol in _precs(swf):
         res, _ = ctx.solve([swf.from_workload(d)], swf.BREIT_WHEELER, prec)
         got = [complex(res[0].amp[2 * j], res[0].amp[2 * j + 1]) for j in range(4)]
         assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        _check_prob(res[0].prob[0], M, tol)
         for j in range(3):
             ref = complex(*golden["terms"][j])
             assert abs(got[j] - ref) <= tol * max(abs(ref), abs(M)), (prec, j)
@@ -181,10 +197,11 @@ def test_full_size_partial_integration_form_matches_stored_oracle(env):
     M = complex(*golden["M"])
     inst = swf.from_workload(d)
     inst.flags = swf.BW_PARTIAL
-    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+    for prec, tol in _precs(swf):
         res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
         got = _amps(res[0])
         assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        _check_prob(res[0].prob[0], M, tol)
         for j in range(3):
             ref = complex(*golden["terms"][j])
             assert abs(got[j] - ref) <= tol * max(abs(ref), abs(M)), (prec, j)
@@ -215,7 +232,7 @@ def test_bw_photon_scan_matches_oracle(env):
     inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], 1, c["q"], -1,
                     ks[0], es[0])
     pk_ref = sum(wj * np.append(r["terms"], r["M"]) for wj, r in zip(w, ref))
-    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+    for prec, tol in _precs(swf):
         amps, packet = ctx.bw_photons(inst, ks, es, prec, weights=w)
         for j, r in enumerate(ref):
             M = r["M"]
@@ -273,10 +290,11 @@ def test_bw_edge_grids_match_oracle(env, case, partial):
     inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], c["n_steps"], c["p"], 1, c["q"], -1,
                     c["k"], par, flags=swf.BW_PARTIAL if partial else 0)
     M = ref["M"]
-    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+    for prec, tol in _precs(swf):
         res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
         got = _amps(res[0])
         assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        _check_prob(res[0].prob[0], M, tol)
         for j in range(3):
             assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
 
@@ -294,12 +312,13 @@ def test_bw_step_size_controlled_march_matches_oracle(env):
     inst = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], 50, c["p"], 1, c["q"], 1, c["k"], par,
                     flags=swf.ADAPTIVE)
     M = ref["M"]
-    for prec, tol in ((swf.C128, 1e-9), (swf.C64, 2e-4)):
+    for prec, tol in _precs(swf):
         res, _ = ctx.solve([inst], swf.BREIT_WHEELER, prec)
         got = _amps(res[0])
         if prec == swf.C128:
             assert ctx.march_stats() == (ref["accepted"], ref["rejected"])
         assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
+        _check_prob(res[0].prob[0], M, tol)
         for j in range(3):
             assert abs(got[j] - ref["terms"][j]) <= tol * max(abs(ref["terms"][j]), abs(M)), (prec, j)
     bad = _bw_inst(swf, *c["fld"], c["n"], c["L"], c["t_in"], c["t_out"], 50, c["p"], 1, c["q"], 1, c["k"], par,

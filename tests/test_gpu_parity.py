@@ -4,7 +4,8 @@ Tolerances (from the arithmetic of the two paths):
 * complex128 path: same scheme and steps as the oracle, only the summation order differs ->
   1e-10 relative (state: max|diff| / max|ref|; scalars: |diff| / |ref|).
 * complex64 march: single-precision rounding accumulated over the march -> 1e-4 relative on
-  |C|^2 for modes above a floor of 1e-6 of the spectrum maximum, 2e-5 relative on the state.
+  |C|^2 for entries at or above 1e-2 of the spectrum maximum (below, an absolute noise floor of
+  the single-precision march), 2e-5 relative on the state.
 """
 import numpy as np
 import pytest
@@ -136,9 +137,9 @@ def test_solve_full_pair_number_matches_oracle(env):
         r = res[i]
         for j, key in enumerate(("C", "D", "A", "B")):
             got = complex(r.amp[2 * j], r.amp[2 * j + 1])
-            assert abs(got - ref[key]) <= 1e-9 * max(abs(ref[key]), 1e-300), (key, got, ref[key])
-        assert abs(r.prob[0] - ref["N_line2"]) <= 1e-9 * ref["N_line2"]
-        assert abs(r.prob[1] - ref["N_line1"]) <= 1e-9 * ref["N_line1"]
+            assert abs(got - ref[key]) <= 1e-10 * max(abs(ref[key]), abs(ref["C"] + ref["D"])), (key, got, ref[key])
+        assert abs(r.prob[0] - ref["N_line2"]) <= 1e-10 * ref["N_line2"]
+        assert abs(r.prob[1] - ref["N_line1"]) <= 1e-10 * ref["N_line1"]
         assert abs(r.diag[0] - O.inner(pu, pu, grid).real) <= 1e-10 * r.diag[0]
         n = int(np.prod(d["n"]))
         C = O.c_spectrum(pu, grid, d["t_in"])
@@ -315,6 +316,48 @@ def test_full_size_workload_matches_stored_oracle_samples(env):
         assert abs(res[i].diag[0] - smp["norm"]) < 1e-5 * smp["norm"]
 
 
+@pytest.mark.parametrize("inst", [0, 77])
+def test_full_size_spectrum_by_decade_against_the_oracle(env, inst):
+    """Whole C-spectra of two instances of the batched workload at full size (256^2, 1000 steps)
+    against the oracle's (every entry at or above 1e-24 of the maximum, stored by
+    tests/golden/make_full_size_reference.py --spectrum), decade by decade.  What the accuracy
+    counts of the benchmark line rest on:
+    * complex128 (the plain FP64 march): 1e-10 relative on every entry >= 1e-7 of the maximum
+      and 1e-4 on every entry >= 1e-19 of it (measured: 5e-11 and 6e-5 at those floors); below,
+      FP64 rounding of the march sets the error (the probabilities fall far below the state's
+      rounding level);
+    * complex64 on the fused kernel and on the pass kernels: 1e-4 relative on every entry
+      >= 1e-2 of the maximum (measured: at most 8e-5); the benchmark line reports, decade by
+      decade, how many entries below that still meet 1e-4.
+    Entries the oracle puts below 1e-24 of the maximum stay below 1e-7 of it on the GPU."""
+    import json
+    import os
+    torch, swf, _ = env
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", f"schwinger_batched_spectrum_{inst}.json")))
+    modes, ref, mx = np.array(g["modes"]), np.array(g["prob"]), g["max_prob"]
+    d = W.schwinger_batched()[inst]
+    rows = {}
+    for prec, path, name in ((swf.C128, 0, "c128"), (swf.C64, 0, "c64 fused"), (swf.C64, 1, "c64 pass")):
+        ctx = swf.Context(0)
+        ctx.set_march_path(path)
+        res, spec = ctx.solve([swf.from_workload(d)], swf.SCHWINGER, prec)
+        ctx.close()
+        rel = np.abs(spec[modes] - ref) / ref
+        rest = np.ones(spec.size, bool)
+        rest[modes] = False
+        assert spec[rest].max() <= 1e-7 * mx, (name, spec[rest].max() / mx)
+        if prec == swf.C128:
+            assert rel[ref >= 1e-7 * mx].max() <= 1e-10, rel[ref >= 1e-7 * mx].max()
+            assert rel[ref >= 1e-19 * mx].max() <= 1e-4, rel[ref >= 1e-19 * mx].max()
+            assert abs(res[0].diag[0] - g["norm"]) <= 1e-10 * g["norm"]
+        else:
+            assert rel[ref >= 1e-2 * mx].max() <= 1e-4, (name, rel[ref >= 1e-2 * mx].max())
+            assert abs(res[0].diag[0] - g["norm"]) <= 1e-5 * g["norm"]
+        dec = np.floor(np.log10(ref / mx))
+        rows[name] = {int(k): round(float(np.mean(rel[dec == k] <= 1e-4)), 3) for k in range(0, -25, -4)}
+    print("fraction within 1e-4 per decade below the maximum:", rows)
+
+
 def test_tuned_launch_shapes_give_bitwise_identical_marches(env):
     """The pass kernels' launch shapes (chosen by timing, or by the fixed rule) decide only which
     lines a block transforms: marches agree bit for bit (x-only, 2D, 3D; both precisions)."""
@@ -364,9 +407,9 @@ def test_pair_matrix_matches_oracle_and_pair_path(env):
             r = mat[m][n]
             for j, key in enumerate(("C", "D", "A", "B")):
                 got = complex(r.amp[2 * j], r.amp[2 * j + 1])
-                assert abs(got - ref[key]) <= 1e-9 * max(abs(ref[key]), 1e-300), (m, n, key, got, ref[key])
-            assert abs(r.prob[0] - ref["N_line2"]) <= 1e-9 * ref["N_line2"]
-            assert abs(r.prob[1] - ref["N_line1"]) <= 1e-9 * ref["N_line1"]
+                assert abs(got - ref[key]) <= 1e-10 * max(abs(ref[key]), abs(ref["C"] + ref["D"])), (m, n, key, got, ref[key])
+            assert abs(r.prob[0] - ref["N_line2"]) <= 1e-10 * ref["N_line2"]
+            assert abs(r.prob[1] - ref["N_line1"]) <= 1e-10 * ref["N_line1"]
     # the same pairs through solve_swf with SWF_WANT_FULL_N: same marches, other summation order
     for prec, tol in ((swf.C128, 1e-11), (swf.C64, 1e-6)):
         mat = ctx.pair_matrix([swf.from_workload(d) for d in els], [swf.from_workload(d) for d in pos], prec)
@@ -476,8 +519,8 @@ def test_single_fp64_workload_matches_stored_oracle(env):
         for j, key in enumerate(("C", "D", "A", "B")):
             got = complex(r.amp[2 * j], r.amp[2 * j + 1])
             assert abs(got - complex(*pr[key])) <= 1e-10 * scale, (pr["r"], key)
-        assert abs(r.prob[0] - pr["N_line2"]) <= 1e-9 * n_scale
-        assert abs(r.prob[1] - pr["N_line1"]) <= 1e-9 * n_scale
+        assert abs(r.prob[0] - pr["N_line2"]) <= 1e-10 * n_scale
+        assert abs(r.prob[1] - pr["N_line1"]) <= 1e-10 * n_scale
         assert abs(r.diag[0] - golden["norm_u"]) <= 1e-10 * golden["norm_u"]
         assert abs(r.diag[1] - pr["norm_v"]) <= 1e-10 * pr["norm_v"]
     modes = np.array(golden["spectrum_modes"])
@@ -548,7 +591,7 @@ def test_step_size_controlled_march_matches_oracle(env):
         assert np.array_equal(outs[0], outs[1])
         assert stats == (na, nr), (stats, na, nr)
         got = to_complex(torch.from_numpy(outs[0])).reshape(ref.shape)
-        assert rel_state(got, ref) < 1e-9, rel_state(got, ref)
+        assert rel_state(got, ref) < 1e-10, rel_state(got, ref)
         assert rel_state(got, ref_fixed) < 20 * 1e-5
         if n_steps == 4:
             assert nr > 0

@@ -16,8 +16,13 @@ def _table(n, seed):
 
 
 def test_forward_and_gradients_match_oracle():
+    """Forward (tensor-memory inference kernel), loss and gradients (training kernels) against the
+    plain FP64 network (oracle bf=False, pinned by finite differences), element by element within
+    6 standard deviations of the probabilistic BF16 error model of tests/bf16_bounds.py (about
+    0.7 % of mu); and, as a secondary check, against the oracle's BF16-rounding network."""
     import torch
     from paper_2512_16889_gb300 import build, surrogate as S, swf
+    from tests import bf16_bounds as BB
     build.build()
     t = _table(192, seed=11)
     X = S.features(t)
@@ -30,15 +35,23 @@ def test_forward_and_gradients_match_oracle():
     out = torch.zeros(len(X), 2, dtype=torch.float32, device="cuda")
     sur.forward(Xd, out)  # 192 rows: one full tile of 128 and a ragged one
     sur.status()
-    mu_ref, lv_ref = _heads(M.forward(p0.astype(float), X.astype(float), norm.astype(float), bf=True)[0], norm)
-    got = out.cpu().numpy()
-    assert np.max(np.abs(got[:, 0] - mu_ref)) <= 1e-2 * max(1.0, np.max(np.abs(mu_ref)))
-    assert np.max(np.abs(got[:, 1] - lv_ref)) <= 1e-2 * max(1.0, np.max(np.abs(lv_ref)))
+    pf, Xf, yf, nf = p0.astype(float), X.astype(float), y.astype(float), norm.astype(float)
+    mu64, lv64, smu, slv = BB.head_sigma(pf, Xf, nf)
+    got = out.cpu().numpy().astype(float)
+    assert np.all(np.abs(got[:, 0] - mu64) <= BB.K * smu), np.max(np.abs(got[:, 0] - mu64) / smu)
+    assert np.all(np.abs(got[:, 1] - lv64) <= BB.K * slv), np.max(np.abs(got[:, 1] - lv64) / slv)
     grad = torch.zeros(swf.Surrogate.param_count(), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     sur.gradients(Xd, yd, grad, loss)
-    ref_loss, ref_g = M.loss_and_grad(p0.astype(float), X.astype(float), y.astype(float), norm.astype(float), bf=True)
+    loss64, g64, sl, sg = BB.loss_grad_sigma(pf, Xf, yf, nf)
     g = grad.cpu().numpy().astype(float)
+    assert abs(loss.item() - loss64) <= BB.K * sl, (loss.item(), loss64, sl)
+    assert np.all(np.abs(g - g64) <= BB.K * sg), np.max(np.abs(g - g64) / sg)
+    # secondary: the oracle's network with the kernels' BF16 rounding points
+    mu_ref, lv_ref = _heads(M.forward(pf, Xf, nf, bf=True)[0], norm)
+    assert np.max(np.abs(got[:, 0] - mu_ref)) <= 1e-2 * max(1.0, np.max(np.abs(mu_ref)))
+    assert np.max(np.abs(got[:, 1] - lv_ref)) <= 1e-2 * max(1.0, np.max(np.abs(lv_ref)))
+    ref_loss, ref_g = M.loss_and_grad(pf, Xf, yf, nf, bf=True)
     assert abs(loss.item() - ref_loss) <= 1e-3 * abs(ref_loss)
     # the inference kernel (tensor memory) and the training path's forward give the same loss
     r = (y - norm[12]) * norm[13] - (got[:, 0] - norm[12]) * norm[13]
@@ -80,6 +93,10 @@ def test_inference_tiles_match_oracle(n_rows):
     assert np.all(np.isfinite(got))
     rows = np.unique(np.concatenate([np.arange(min(n_rows, 64)), np.arange(max(0, n_rows - 64), n_rows),
                                      np.random.default_rng(1).integers(0, n_rows, 256)]))
+    from tests import bf16_bounds as BB
+    mu64, lv64, smu, slv = BB.head_sigma(p0.astype(float), X[rows].astype(float), norm.astype(float))
+    assert np.all(np.abs(got[rows, 0] - mu64) <= BB.K * smu), np.max(np.abs(got[rows, 0] - mu64) / smu)
+    assert np.all(np.abs(got[rows, 1] - lv64) <= BB.K * slv), np.max(np.abs(got[rows, 1] - lv64) / slv)
     mu_ref, lv_ref = _heads(M.forward(p0.astype(float), X[rows].astype(float), norm.astype(float), bf=True)[0], norm)
     assert np.max(np.abs(got[rows, 0] - mu_ref)) <= 1e-2 * max(1.0, np.max(np.abs(mu_ref)))
     assert np.max(np.abs(got[rows, 1] - lv_ref)) <= 1e-2 * max(1.0, np.max(np.abs(lv_ref)))

@@ -42,3 +42,36 @@ def test_loss_gradient_matches_finite_differences():
         e[i] = 1e-6
         num = (M.loss_and_grad(p + e, x, y, NORM, bf=False)[0] - M.loss_and_grad(p - e, x, y, NORM, bf=False)[0]) / 2e-6
         assert abs(num - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, num, g[i])
+
+
+def test_bf16_error_model_covers_the_oracles_bf16_arithmetic():
+    """The probabilistic BF16 error model (tests/bf16_bounds.py) that sets the GPU tolerances,
+    checked against one realisation of BF16 arithmetic, the oracle's bf=True network: its
+    outputs, loss and every gradient element lie within 6 model standard deviations of the
+    plain FP64 network (measured: at most 2.6 sigma forward, 1.7 sigma for the gradients)."""
+    from tests import bf16_bounds as BB
+    from paper_2512_16889_gb300 import surrogate as S, workloads as W
+    t = W.surrogate_samples(192, seed=11)
+    X = S.features(t).astype(float)
+    y = -12.0 + 3.0 * np.tanh(X[:, 0] * 5 - 1.0) + 0.5 * X[:, 3] * X[:, 4]
+    norm = S.normalisation(X.astype(np.float32), y.astype(np.float32)).astype(float)
+    p = S.init_params(seed=3).astype(float)
+    mu, lv, smu, slv = BB.head_sigma(p, X, norm)
+    mir = M.forward(p, X, norm, bf=True)[0]
+    ys = norm[13]
+    assert np.all(np.abs(mir[:, 0] / ys + norm[12] - mu) <= BB.K * smu)
+    assert np.all(np.abs(mir[:, 1] - 2 * np.log(ys) - lv) <= BB.K * slv)
+    assert np.max(BB.K * smu / np.abs(mu)) < 1e-2  # the tolerance is below 1 % of the output
+    loss, g, sl, sg = BB.loss_grad_sigma(p, X, y, norm)
+    ml, mg = M.loss_and_grad(p, X, y, norm, bf=True)
+    assert abs(ml - loss) <= BB.K * sl
+    assert np.all(np.abs(mg - g) <= BB.K * sg)
+    # the tolerance is not vacuous: scaling any one weight matrix by 1.03 moves some output by
+    # more than 6 sigma (9 to 17 sigma, depending on the layer)
+    off = 0
+    for i, o in zip(M.DIN, M.DOUT):
+        q = p.copy()
+        q[off:off + i * o] *= 1.03
+        out_q = M.forward(q, X, norm, bf=False)[0]
+        assert np.any(np.abs(out_q[:, 0] / ys + norm[12] - mu) > BB.K * smu), off
+        off += i * o + o

@@ -352,6 +352,29 @@ def test_bw_forms_agree_on_an_odd_axis_length():
     assert gaps[1] < 1e-7 and gaps[0] / gaps[1] > 20.0, gaps
 
 
+def test_bw_t_in_independence_on_an_odd_axis_length():
+    """Eq. 24 on a 15 x 12 grid, where V modes that wrap around the grid carry the factor
+    N e^{i(kappa_v + k - kappa_u).x0} = -N in the scat-scat mode sum of Eq. 25.  The finite part
+    (Eq. 17, an x-space integral without mode pairing) and the past part must still add up to an
+    amplitude that does not depend on t_in.  Moving t_in from -12 to -15 shifts the finite parts
+    by O(|M|) while the sum moves by 1e-7 |M| (the field's tail, sech^2(0.7 t) ~ 2e-7 at |t| = 12);
+    with the wrap factor set to 1 the ss term moves by 7.7e-5 |M|, so this pins the factor against
+    the x-space integral, independently of the partial-integration form."""
+    grid = O.Grid((15, 12, 1), (7.5, 6.0, 1.0))
+    fld = O.Field("sauter_gauss", (1.0, 0.7, 2.0))
+    ux, uy = 2 * np.pi / 7.5, 2 * np.pi / 6.0
+    k = (3 * ux, -uy, 0.0)
+    perp, par = O.polarisation_basis((0, 0, 1), k)
+    ph = O.Photon(k, tuple(par))
+    p, q = (ux, -2 * uy, 0.0), (-2 * ux, -uy, 0.0)
+    r1 = O.bw_amplitude(fld, grid, p, 1, q, -1, ph, -12.0, 12.0, 600)
+    r2 = O.bw_amplitude(fld, grid, p, 1, q, -1, ph, -15.0, 12.0, 675)
+    M = abs(r1["M"])
+    assert M > 1e-3
+    assert abs(r1["finite"][0] - r2["finite"][0]) > 1.0 * M
+    assert np.max(np.abs(r1["terms"] - r2["terms"])) < 1e-6 * M, (r1["terms"], r2["terms"])
+
+
 def test_bw_partial_integration_zero_field_gives_zero():
     grid, _, ph = _bw_setup_2d()
     res = O.bw_amplitude(O.Field("zero"), grid, (0.25, -1.0, 0), 1, (-0.25, -1.0, 0), 1, ph, -3.0, 3.0, 20, form=2)

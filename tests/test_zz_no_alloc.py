@@ -1,8 +1,8 @@
 """The allocation-free right-hand side (swf_rhs_noalloc) against swf_rhs_dev.
 
-swf_rhs_noalloc serves callers that cannot allocate device memory (for example code running
-during CUDA-graph stream capture); it takes its workspace from a fixed device array instead of
-a context.  This file is collected last so that a failure here never hides another test.
+swf_rhs_noalloc serves callers that cannot allocate device memory (host applications that own
+all device memory through a pool of their own, loops that cannot absorb cudaFree's device-wide
+synchronisation); it takes its workspace from a fixed device array instead of a context.  This file is collected last so that a failure here never hides another test.
 """
 import numpy as np
 import pytest
@@ -54,8 +54,8 @@ def test_rhs_noalloc_rejects_grids_beyond_its_scratch():
     build.build()
     d = dict(field=("sauter_gauss", (0.3, 0.5, 5.0)), n=(512, 256, 1), L=(40.0, 40.0, 1.0), t_in=-1.0, t_out=1.0,
              n_steps=1, p=(0.0, 0.0, 0.0), s=1, q=(0.0, 0.0, 0.0), r=1, k=(0, 0, 0), eps=(0, 0, 0), flags=())
-    x = torch.zeros(16, dtype=torch.float32, device="cuda")
-    y = torch.zeros(16, dtype=torch.float32, device="cuda")
+    x = torch.zeros(8 * 512 * 256, dtype=torch.float32, device="cuda")  # the grid's full size: the
+    y = torch.zeros_like(x)                                              # library's own check answers
     with pytest.raises(swf.SwfError) as ei:
         swf.rhs_noalloc(swf.from_workload(d), 0.0, x, y, prec=swf.C64)
     assert ei.value.status == swf.SWF_EINVAL and "exceeds the fixed scratch" in str(ei.value)
