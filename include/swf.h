@@ -237,6 +237,17 @@ swf_status swf_march_stats(swf_ctx* ctx, long long* accepted, long long* rejecte
  * -1, 1) R_+ and every operator of Eq. 6 keeps {0, 3} and {1, 2} apart; App. A.5 Eq. A44).
  * on = 0 marches every field.  Results agree either way (up to the sign of zeros). */
 swf_status swf_set_dedupe(swf_ctx* ctx, int on);
+
+/* Batching of uneven grids (Sec. II.A: many instances marched at once).  Instance groups of one
+ * call that sit on different grids but share the time grid (t_out, t_in, step count) and the
+ * non-trivial axes, and that run on the pass kernels at fixed steps (Schwinger, and
+ * Breit-Wheeler with the integrand of Eq. 17), can be marched together, up to eight groups at a
+ * time: one launch per pass serves all of them, persistent blocks taking (group, block) work
+ * items from a device counter, largest grids first, and one CUDA graph replays their step
+ * pairs.  Each group's results are bitwise those of marching it alone.
+ * mode = 1 (default): together when the groups hold fewer than 4 Mi fields x grid points (above
+ * that each group fills the GPU alone); 2: always together; 0: one group after another. */
+swf_status swf_set_multi_grid(swf_ctx* ctx, int mode);
 /* Fields (U or V waves) actually marched by this context since its creation (a diagnostic of
  * the library; the paper has no counterpart). */
 swf_status swf_fields_marched(swf_ctx* ctx, long long* count);

@@ -345,6 +345,74 @@ struct GroupKey {
   }
 };
 
+// In the automatic mode a set of groups is marched together when all of them hold fewer fields x
+// grid points than this (per evaluation): above it every group fills the GPU by itself and one
+// launch sequence per group was as fast (Breit-Wheeler on the uneven grids, 300 steps: grouped
+// +5 % at 8 instances, 2 per grid size; level at 16; -3 % at 32).
+constexpr double kMultiAutoSites = 4.0 * 1024 * 1024;
+
+// Time grid and non-trivial axes: groups that agree on these can be marched together.
+struct MultiKey {
+  double t_in, t_out;
+  int n_steps, ny_on, nz_on;
+  bool operator<(const MultiKey& o) const {
+    return std::tie(t_in, t_out, n_steps, ny_on, nz_on) < std::tie(o.t_in, o.t_out, o.n_steps, o.ny_on, o.nz_on);
+  }
+};
+
+// Marches, in multi-grid marches, the fields of every fixed-step Schwinger group that runs on the
+// pass kernels and shares its time grid and non-trivial axes with another such group (at most
+// eight groups per march).  premarched[group] = device buffer [F_U (+ F_V)][4][N] of the group's
+// psi(t_in): the U fields, then (full pair number) the V fields.
+static swf_status premarch_schwinger(swf_ctx* ctx, const swf_instance* inst,
+                                     const std::map<GroupKey, std::vector<int>>& groups, swf_precision prec,
+                                     std::map<const GroupKey*, void*>& premarched, cudaStream_t st) {
+  if (!ctx->multi_grid) return SWF_OK;
+  const size_t elem = prec == SWF_C64 ? 8 : 16;
+  std::map<MultiKey, std::vector<const GroupKey*>> sets;
+  std::map<const GroupKey*, std::vector<FieldDesc>> fds;
+  for (auto& kv : groups) {
+    if (kv.first.adaptive) continue;
+    const std::vector<int>& idx = kv.second;
+    const swf_instance& i0 = inst[idx[0]];
+    const GridDesc g = make_grid(i0.grid);
+    std::vector<FieldDesc> fd;
+    for (int f : idx) fd.push_back(make_field_desc(inst[f], 0));
+    if (ctx->use_fused && fused_applicable(g, (int)fd.size(), fd.data(), prec)) continue;
+    if (kv.first.full) {
+      for (int f : idx) fd.push_back(make_field_desc(inst[f], 1));
+      if (ctx->use_fused && fused_applicable(g, (int)idx.size(), fd.data() + idx.size(), prec)) continue;
+    }
+    sets[MultiKey{i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, g.n[1] > 1, g.n[2] > 1}].push_back(&kv.first);
+    fds[&kv.first] = std::move(fd);
+  }
+  swf_status s;
+  int buf = 0;
+  for (auto& kv : sets) {
+    const std::vector<const GroupKey*>& list = kv.second;
+    for (size_t b = 0; b + 1 < list.size(); b += 8) {
+      const size_t e = std::min(list.size(), b + 8);
+      double sites = 0.0;
+      for (size_t i = b; i < e; ++i) sites += (double)fds[list[i]].size() * make_grid(inst[groups.at(*list[i])[0]].grid).N;
+      if (ctx->multi_grid == 1 && sites >= kMultiAutoSites) continue;
+      std::vector<MultiGroup> mg;
+      for (size_t i = b; i < e; ++i) {
+        const GroupKey* k = list[i];
+        const std::vector<FieldDesc>& fd = fds[k];
+        const GridDesc g = make_grid(inst[groups.at(*k)[0]].grid);
+        void* out = nullptr;
+        if ((s = ws_get(ctx, "solve.multi" + std::to_string(buf++), fd.size() * 4 * (size_t)g.N * elem, &out)) != SWF_OK)
+          return s;
+        mg.push_back(MultiGroup{g, (int)fd.size(), fd.data(), out, nullptr, nullptr});
+        premarched[k] = out;
+      }
+      if ((s = march_fields_multi(ctx, mg, kv.first.t_in, kv.first.t_out, kv.first.n_steps, prec, st)) != SWF_OK)
+        return s;
+    }
+  }
+  return SWF_OK;
+}
+
 static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf_precision prec,
                                   swf_result* results_dev, double* spectrum_dev, cudaStream_t st) {
   std::map<GroupKey, std::vector<int>> groups;
@@ -367,12 +435,17 @@ static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* 
   }
   const size_t elem = prec == SWF_C64 ? 8 : 16;
   swf_status s;
+  // groups on the pass kernels that share a time grid and their non-trivial axes: every march
+  // of those groups (U, and V for the full pair number) in one multi-grid march
+  std::map<const GroupKey*, void*> premarched;
+  if ((s = premarch_schwinger(ctx, inst, groups, prec, premarched, st)) != SWF_OK) return s;
   for (auto& kv : groups) {
     const std::vector<int>& idx = kv.second;
     const int F = (int)idx.size();
     const swf_instance& i0 = inst[idx[0]];
     const GridDesc g = make_grid(i0.grid);
     const bool full = kv.first.full != 0;
+    auto pre = premarched.find(&kv.first);
     std::vector<FieldDesc> fdU(F), fdV(F);
     std::vector<InstDev> idv(F);
     std::vector<double> kq(3 * F), kp(3 * F);
@@ -401,9 +474,12 @@ static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* 
     if ((s = ws_get(ctx, "solve.uq", (size_t)F * 64, &uq)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "solve.normU", (size_t)F * 8, &normU)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "solve.inst", sizeof(InstDev) * F, &pid)) != SWF_OK) return s;
-    if ((s = march_fields(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, F, fdU.data(), prec, psiU, st,
-                          kv.first.adaptive)) != SWF_OK)
+    if (pre != premarched.end()) {
+      psiU = pre->second;  // U fields, then (full) V fields
+    } else if ((s = march_fields(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, F, fdU.data(), prec, psiU, st,
+                                 kv.first.adaptive)) != SWF_OK) {
       return s;
+    }
     if ((s = transform_at(ctx, g, F, prec, psiU, kq.data(), (double2*)uq, st)) != SWF_OK) return s;
     if ((s = field_norms(ctx, g, F, prec, psiU, (double*)normU, st)) != SWF_OK) return s;
     if (any_spec || full)
@@ -422,13 +498,17 @@ static swf_status solve_schwinger(swf_ctx* ctx, int n_inst, const swf_instance* 
     }
     void *psiV = nullptr, *specV = nullptr, *vp = nullptr, *normV = nullptr;
     if (full) {
-      if ((s = ws_get(ctx, "solve.psiV", state * elem, &psiV)) != SWF_OK) return s;
       if ((s = ws_get(ctx, "solve.specV", state * 16, &specV)) != SWF_OK) return s;
       if ((s = ws_get(ctx, "solve.vp", (size_t)F * 64, &vp)) != SWF_OK) return s;
       if ((s = ws_get(ctx, "solve.normV", (size_t)F * 8, &normV)) != SWF_OK) return s;
-      if ((s = march_fields(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, F, fdV.data(), prec, psiV, st,
-                            kv.first.adaptive)) != SWF_OK)
-        return s;
+      if (pre != premarched.end()) {
+        psiV = (unsigned char*)pre->second + state * elem;
+      } else {
+        if ((s = ws_get(ctx, "solve.psiV", state * elem, &psiV)) != SWF_OK) return s;
+        if ((s = march_fields(ctx, g, i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, F, fdV.data(), prec, psiV, st,
+                              kv.first.adaptive)) != SWF_OK)
+          return s;
+      }
       if ((s = transform_fields(ctx, g, F, prec, psiV, (double2*)specV, st)) != SWF_OK) return s;
       if ((s = transform_at(ctx, g, F, prec, psiV, kp.data(), (double2*)vp, st)) != SWF_OK) return s;
       if ((s = field_norms(ctx, g, F, prec, psiV, (double*)normV, st)) != SWF_OK) return s;
@@ -475,6 +555,65 @@ static void photon_shift(const swf_instance& in, const double* k, int shift[3]) 
     shift[a] = in.grid.n[a] > 1 ? (int)std::lround(k[a] * in.grid.L[a] / 6.283185307179586476925286766559) : 0;
 }
 
+// Marches, in multi-grid marches, every fixed-step Breit-Wheeler group of the past/finite form
+// (Eq. 17) that shares its time grid and non-trivial axes with another such group (at most eight
+// groups per march).  premarched[group] = (psi(t_in) [2G][4][N], the integrals of Eq. 17 [G][3]).
+static swf_status premarch_bw(swf_ctx* ctx, const swf_instance* inst, const std::map<GroupKey, std::vector<int>>& groups,
+                              swf_precision prec, std::map<const GroupKey*, std::pair<void*, void*>>& premarched,
+                              cudaStream_t st) {
+  if (!ctx->multi_grid) return SWF_OK;
+  const size_t elem = prec == SWF_C64 ? 8 : 16;
+  std::map<MultiKey, std::vector<const GroupKey*>> sets;
+  for (auto& kv : groups) {
+    if (kv.first.adaptive || kv.first.full) continue;
+    const swf_instance& i0 = inst[kv.second[0]];
+    sets[MultiKey{i0.grid.t_in, i0.grid.t_out, i0.grid.n_steps, i0.grid.n[1] > 1, i0.grid.n[2] > 1}].push_back(
+        &kv.first);
+  }
+  swf_status s;
+  int buf = 0;
+  for (auto& kv : sets) {
+    const std::vector<const GroupKey*>& list = kv.second;
+    for (size_t b = 0; b + 1 < list.size(); b += 8) {
+      const size_t e = std::min(list.size(), b + 8);
+      double sites = 0.0;  // U and V of every instance
+      for (size_t i = b; i < e; ++i)
+        sites += 2.0 * groups.at(*list[i]).size() * make_grid(inst[groups.at(*list[i])[0]].grid).N;
+      if (ctx->multi_grid == 1 && sites >= kMultiAutoSites) continue;
+      std::vector<std::vector<FieldDesc>> fds(e - b);
+      std::vector<std::vector<double>> photons(e - b);
+      std::vector<MultiGroup> mg;
+      for (size_t i = b; i < e; ++i) {
+        const std::vector<int>& idx = groups.at(*list[i]);
+        const int G = (int)idx.size();
+        const GridDesc g = make_grid(inst[idx[0]].grid);
+        std::vector<FieldDesc>& fd = fds[i - b];
+        std::vector<double>& ph = photons[i - b];
+        fd.resize(2 * G);
+        ph.resize(6 * G);
+        for (int f = 0; f < G; ++f) {
+          const swf_instance& in = inst[idx[f]];
+          fd[2 * f] = make_field_desc(in, 0);
+          fd[2 * f + 1] = make_field_desc(in, 1);
+          for (int a = 0; a < 3; ++a) {
+            ph[6 * f + a] = in.k[a];
+            ph[6 * f + 3 + a] = in.eps[a];
+          }
+        }
+        void *psi = nullptr, *macc = nullptr;
+        const std::string tag = "bwsolve.multi" + std::to_string(buf++);
+        if ((s = ws_get(ctx, tag + ".psi", (size_t)2 * G * 4 * g.N * elem, &psi)) != SWF_OK) return s;
+        if ((s = ws_get(ctx, tag + ".macc", (size_t)G * 9 * 16, &macc)) != SWF_OK) return s;
+        mg.push_back(MultiGroup{g, 2 * G, fd.data(), psi, ph.data(), (double2*)macc});
+        premarched[list[i]] = {psi, macc};
+      }
+      if ((s = march_multi(ctx, mg, kv.first.t_in, kv.first.t_out, kv.first.n_steps, prec, 1, st)) != SWF_OK)
+        return s;
+    }
+  }
+  return SWF_OK;
+}
+
 // Breit-Wheeler (Sec. IV): U and V marched together per instance, then past terms and totals.
 static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, swf_precision prec,
                            swf_result* results_dev, cudaStream_t st) {
@@ -499,10 +638,15 @@ static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, s
   }
   const size_t elem = prec == SWF_C64 ? 8 : 16;
   swf_status s;
+  // fixed-step groups of the past/finite form that share a time grid and their non-trivial axes:
+  // marched together (U, V and the integrals of Eq. 17) in multi-grid marches
+  std::map<const GroupKey*, std::pair<void*, void*>> premarched;
+  if ((s = premarch_bw(ctx, inst, groups, prec, premarched, st)) != SWF_OK) return s;
   for (auto& kv : groups) {
     const std::vector<int>& idx = kv.second;
     const int G = (int)idx.size();
     const int form = kv.first.full ? 2 : 1;
+    auto pre = premarched.find(&kv.first);
     const swf_instance& i0 = inst[idx[0]];
     const GridDesc g = make_grid(i0.grid);
     std::vector<FieldDesc> fd(2 * G);
@@ -524,13 +668,20 @@ static swf_status solve_bw(swf_ctx* ctx, int n_inst, const swf_instance* inst, s
     }
     const size_t state = (size_t)2 * G * 4 * g.N;
     void *psi, *spec, *tat, *macc, *norms;
-    if ((s = ws_get(ctx, "bwsolve.psi", state * elem, &psi)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "bwsolve.spec", state * 16, &spec)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "bwsolve.tat", (size_t)2 * G * 64, &tat)) != SWF_OK) return s;
-    if ((s = ws_get(ctx, "bwsolve.macc", (size_t)G * 9 * 16, &macc)) != SWF_OK) return s;
     if ((s = ws_get(ctx, "bwsolve.norms", (size_t)2 * G * 8, &norms)) != SWF_OK) return s;
+    if (pre != premarched.end()) {
+      psi = pre->second.first;
+      macc = pre->second.second;
+    } else {
+      if ((s = ws_get(ctx, "bwsolve.psi", state * elem, &psi)) != SWF_OK) return s;
+      if ((s = ws_get(ctx, "bwsolve.macc", (size_t)G * 9 * 16, &macc)) != SWF_OK) return s;
+    }
     // kat holds, per wave, the momentum of its direct transform (U~ at k - q, V~ at p - k)
-    if (kv.first.adaptive) {
+    if (pre != premarched.end()) {
+      // marched with the other groups of its time grid
+    } else if (kv.first.adaptive) {
       // first step (t_in - t_out)/n_steps, at most 100 n_steps + 100 attempts (as for Schwinger marches)
       const double h0 = (i0.grid.t_in - i0.grid.t_out) / i0.grid.n_steps;
       if ((s = march_bw_adaptive(ctx, g, i0.grid.t_in, i0.grid.t_out, h0, 100 * i0.grid.n_steps + 100, G, fd.data(),
@@ -743,6 +894,12 @@ swf_status swf_march_stats(swf_ctx* ctx, long long* accepted, long long* rejecte
 swf_status swf_set_dedupe(swf_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) { set_error("swf_set_dedupe: ctx NULL or on not 0 or 1"); return SWF_EINVAL; }
   ctx->dedupe = on != 0;
+  return SWF_OK;
+}
+
+swf_status swf_set_multi_grid(swf_ctx* ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 2) { set_error("swf_set_multi_grid: ctx NULL or mode not 0, 1 or 2"); return SWF_EINVAL; }
+  ctx->multi_grid = mode;
   return SWF_OK;
 }
 

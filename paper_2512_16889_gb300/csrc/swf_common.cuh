@@ -27,6 +27,29 @@ template <typename R> __host__ __device__ __forceinline__ cpx<R> mul_mi(cpx<R> a
 template <typename R> __host__ __device__ __forceinline__ cpx<R> cdot(cpx<R> a, cpx<R> b) {
   return mk<R>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
+// Complex arithmetic with every rounding fixed: built from the _rn intrinsics, which the compiler
+// neither fuses into multiply-adds nor reorders.  Code that several kernels inline and whose
+// results must agree bit for bit between them (the Breit-Wheeler integrand of single-photon,
+// photon-scan and multi-grid launches) uses these instead of the operators above.
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename R> __device__ __forceinline__ cpx<R> xadd(cpx<R> a, cpx<R> b) {
+  return mk<R>(rn_add(a.x, b.x), rn_add(a.y, b.y));
+}
+template <typename R> __device__ __forceinline__ cpx<R> xmul(cpx<R> a, cpx<R> b) {
+  return mk<R>(rn_fma(a.x, b.x, -rn_mul(a.y, b.y)), rn_fma(a.x, b.y, rn_mul(a.y, b.x)));
+}
+template <typename R> __device__ __forceinline__ cpx<R> xscale(R s, cpx<R> a) {
+  return mk<R>(rn_mul(s, a.x), rn_mul(s, a.y));
+}
+// conj(a) b
+template <typename R> __device__ __forceinline__ cpx<R> xcdot(cpx<R> a, cpx<R> b) {
+  return mk<R>(rn_fma(a.x, b.x, rn_mul(a.y, b.y)), rn_fma(a.x, b.y, -rn_mul(a.y, b.x)));
+}
 template <typename Rto, typename Rfrom> __host__ __device__ __forceinline__ cpx<Rto> cvt(cpx<Rfrom> a) {
   return mk<Rto>((Rto)a.x, (Rto)a.y);
 }

@@ -127,6 +127,8 @@ struct swf_ctx {
   long long last_accepted = 0, last_rejected = 0;  // steps of the last controlled march
   long long fields_marched = 0;  // fields actually marched since the context's creation
   long long fields_fused = 0;    // of those, fields marched by the fused cluster kernel
+  int multi_grid = 1;            // grid groups sharing a time grid in one launch sequence: 0 never, 1 auto, 2 always
+  long long multi_marches = 0;   // multi-grid marches run since the context's creation
   int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
   bool sm_split = true;   // automatic path: pass kernels on the SMs the fused clusters leave free
   cudaStream_t aux = nullptr;            // stream of that concurrent pass-kernel march (lazy)
@@ -197,6 +199,26 @@ swf_status bw_packet(swf_ctx* ctx, int n, const swf_result* results, const doubl
                      cudaStream_t st);
 swf_status bw_finalize_partial(swf_ctx* ctx, const GridDesc& g, int n_inst, const void* bw_host,
                                const double2* macc, const double* norms, swf_result* results, cudaStream_t st);
+
+// Multi-grid march: groups of fields on different grids sharing one time grid, marched by one
+// launch per pass for all groups (persistent blocks on a device work queue) and one CUDA graph
+// per step pair.  Each group's result is bitwise that of marching it alone.
+struct MultiGroup {
+  GridDesc g;
+  int F;                  // fields (Breit-Wheeler: 2 per instance, U then V)
+  const FieldDesc* fd;    // host, F descriptors
+  void* psi_out;          // device, psi(t_in) [F][4][N] in the march precision
+  const double* photon;   // Breit-Wheeler: host, per instance k[3], eps[3]; else null
+  double2* macc;          // Breit-Wheeler: device, per instance the three integrals of Eq. 17
+};
+// Groups may be combined when they have the same non-trivial axes (2D with 2D, 3D with 3D).
+bool multi_compatible(const GridDesc& a, const GridDesc& b);
+// bw = 1: Breit-Wheeler (form 1, one photon per instance) with the integrand of Eq. 17.
+swf_status march_multi(swf_ctx* ctx, const std::vector<MultiGroup>& groups, double t_in, double t_out, int n_steps,
+                       swf_precision prec, int bw, cudaStream_t st);
+// Plain marches of several groups, with the spin reuse of march_fields within each group.
+swf_status march_fields_multi(swf_ctx* ctx, const std::vector<MultiGroup>& groups, double t_in, double t_out,
+                              int n_steps, swf_precision prec, cudaStream_t st);
 
 // ---- fused cluster march (swf_fused.cu)
 bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_precision prec);

@@ -11,6 +11,7 @@
 //   last pass (x lines):   inverse x-FFT and k = (that) + Z.
 // Gauge field and background are analytic and evaluated on the fly from per-field 1D tables
 // (every field kind is a product of a time factor and one factor per axis).
+#include <array>
 #include <atomic>
 #include <algorithm>
 #include <cmath>
@@ -433,8 +434,9 @@ static const size_t kPassSmemTune = 200 * 1024;
 
 // x lines of `rows` grid rows (4 components each): stage combine, local term, forward x-FFT
 // (and the whole derivative when x is the only non-trivial axis).
+// Block (bx, f) of the pass: rows bx*rows .. of field f.
 template <typename R>
-__global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
+__device__ __forceinline__ void first_body(const StageArgs<R>& A, int bx, int f, int rows, int ld, int only_x) {
   if (A.ctl && A.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -443,8 +445,7 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
   cpx<R>* const yout = A.ynew ? A.ynew : A.y;
   __shared__ double s_ft[64];
   __shared__ cpx<R> s_tf;
-  const int f = blockIdx.y;
-  const int row0 = blockIdx.x * rows;
+  const int row0 = bx * rows;
   const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
   const int N = A.g.N;
   const size_t fo = (size_t)f * 4 * N;
@@ -551,24 +552,29 @@ __global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld,
   }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
+  first_body<R>(A, blockIdx.x, blockIdx.y, rows, ld, only_x);
+}
+
 // Lines along axis 1 (y) or 2 (z) of a tile of TX = 2^lgtx consecutive x columns: forward FFT,
 // -i H0(kappa)/N, inverse FFT, as selected.  The tile sits in shared memory as 4 TX lines of
 // stride ld (chosen so that the transposing loads and stores of a warp spread over the banks).
+// Block (bx, f): tile bx of field f.
 template <typename R>
-__global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int lgtx, int ld, int do_fwd, int do_h0,
-                                             int do_inv) {
+__device__ __forceinline__ void mid_body(const StageArgs<R>& A, int bx, int f, int axis, int lgtx, int ld, int do_fwd,
+                                         int do_h0, int do_inv) {
   if (A.ctl && A.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
-  const int f = blockIdx.y;
   const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
   const int N = A.g.N;
   const int na = A.g.n[axis];
   const int TX = 1 << lgtx;
   cpx<R>* buf2 = buf + 4 * TX * ld;
   const int ntx = (nx + TX - 1) >> lgtx;
-  const int xt = blockIdx.x % ntx;
-  const int o = blockIdx.x / ntx;  // z index (axis 1) or y index (axis 2)
+  const int xt = bx % ntx;
+  const int o = bx / ntx;  // z index (axis 1) or y index (axis 2)
   const size_t base = axis == 1 ? (size_t)o * nx * ny : (size_t)o * nx;
   const size_t stride = axis == 1 ? (size_t)nx : (size_t)nx * ny;
   const size_t fo = (size_t)f * 4 * N;
@@ -630,15 +636,20 @@ __global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int lgtx,
   }
 }
 
-// x lines: inverse x-FFT, k = (that) + Z.
 template <typename R>
-__global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) {
+__global__ void __launch_bounds__(256) k_mid(StageArgs<R> A, int axis, int lgtx, int ld, int do_fwd, int do_h0,
+                                             int do_inv) {
+  mid_body<R>(A, blockIdx.x, blockIdx.y, axis, lgtx, ld, do_fwd, do_h0, do_inv);
+}
+
+// x lines: inverse x-FFT, k = (that) + Z.  Block (bx, f): rows bx*rows .. of field f.
+template <typename R>
+__device__ __forceinline__ void last_body(const StageArgs<R>& A, int bx, int f, int rows, int ld) {
   if (A.ctl && A.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* buf2 = buf + 4 * rows * ld;
-  const int f = blockIdx.y;
-  const int row0 = blockIdx.x * rows;
+  const int row0 = bx * rows;
   const int nx = A.g.n[0];
   const int N = A.g.N;
   const size_t fo = (size_t)f * 4 * N;
@@ -665,6 +676,11 @@ __global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) 
       for (int c = 0; c < 4; ++c) A.kout[gi + c * cs] = A.kout[gi + c * cs] + res[(c * rows + j) * ld + pad32(x)];
     }
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) {
+  last_body<R>(A, blockIdx.x, blockIdx.y, rows, ld);
 }
 
 // ---------------------------------------------------------------- host side
@@ -1742,14 +1758,16 @@ __device__ __forceinline__ cpx<R> warp_sum(cpx<R> v) {
   return v;
 }
 
-// (alpha . eps) v for a real polarisation eps (Dirac representation).
+// (alpha . eps) v for a real polarisation eps (Dirac representation), every rounding fixed (the
+// integrand must give the same bits in every launch variant).
 template <typename R>
 __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o) {
   // sigma.eps (u0, u1) = (ez u0 + ex u1 - i ey u1, ex u0 + i ey u0 - ez u1)
-  o[0] = e[2] * v[2] + e[0] * v[3] + e[1] * mul_mi(v[3]);
-  o[1] = e[0] * v[2] + e[1] * mul_i(v[2]) - e[2] * v[3];
-  o[2] = e[2] * v[0] + e[0] * v[1] + e[1] * mul_mi(v[1]);
-  o[3] = e[0] * v[0] + e[1] * mul_i(v[0]) - e[2] * v[1];
+  const R mz = -e[2];
+  o[0] = xadd(xadd(xscale(e[2], v[2]), xscale(e[0], v[3])), xscale(e[1], mul_mi(v[3])));
+  o[1] = xadd(xadd(xscale(e[0], v[2]), xscale(e[1], mul_i(v[2]))), xscale(mz, v[3]));
+  o[2] = xadd(xadd(xscale(e[2], v[0]), xscale(e[0], v[1])), xscale(e[1], mul_mi(v[1])));
+  o[3] = xadd(xadd(xscale(e[0], v[0]), xscale(e[1], mul_i(v[0]))), xscale(mz, v[1]));
 }
 
 // The three integrands of Eq. 17, dx^d sum_x U_a^+ (alpha.eps) V_b exp(-ikx), for (ss, bs, sb)
@@ -1758,18 +1776,20 @@ __device__ __forceinline__ void alpha_eps(const R* e, const cpx<R>* v, cpx<R>* o
 // instance pi / n_ph: several photons share one march) and adds w dx^d e^{-i k0 t}
 // (from the phase table) times its sum to its own accumulator acc[pi][b][3] (FP64; no other block touches it, so
 // the march's sum is deterministic); k_mdot_final adds the accumulators in a fixed order.
+// Block (bx, by) of a launch with nbx blocks per row.
 template <typename R, int NPH>
-__global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const cpx<R>* gcplx, const cpx<R>* kph,
-                                              const double* photon, GridDesc g, const cpx<double>* __restrict__ ptab,
-                                              const MarchClock* clk, int ls, int stage, int tab_stride,
-                                              int n_ph, cpx<double>* acc) {
+__device__ __forceinline__ void mdot_body(const cpx<R>* __restrict__ ys, const cpx<R>* gcplx, const cpx<R>* kph,
+                                          const double* photon, const GridDesc& g,
+                                          const cpx<double>* __restrict__ ptab, const MarchClock* clk, int ls,
+                                          int stage, int tab_stride, int n_ph, cpx<double>* acc, int bx, int by,
+                                          int nbx) {
   const long tab_row = (long)(clk->step + ls) * 7 + stage;
   __shared__ cpx<double> red[8][3 * NPH];
   // block row: instance inst, photons j0 .. j0 + nj - 1 (photon-instances pi0 + jj); U and V are
   // loaded once per site for the NPH photons of the block
   const int nchunk = (n_ph + NPH - 1) / NPH;
-  const int inst = blockIdx.y / nchunk;
-  const int j0 = (blockIdx.y % nchunk) * NPH;
+  const int inst = by / nchunk;
+  const int j0 = (by % nchunk) * NPH;
   const int nj = min(NPH, n_ph - j0);
   const int pi0 = inst * n_ph + j0;
   const int nt = g.n[0] + g.n[1] + g.n[2];
@@ -1793,36 +1813,36 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
 #pragma unroll
   for (int jj = 0; jj < NPH; ++jj) tss[jj] = tbs[jj] = tsb[jj] = mk<R>(0, 0);
 #pragma unroll(NPH == 1 ? 2 : 1)
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.N; j += gridDim.x * blockDim.x) {
+  for (int j = bx * blockDim.x + threadIdx.x; j < g.N; j += nbx * blockDim.x) {
     const int ix = j % g.n[0];
     const int iy = (j / g.n[0]) % g.n[1];
     const int iz = j / (g.n[0] * g.n[1]);
     cpx<R> u[4], v[4], ub[4], vb[4];
-    const cpx<R> phu = tfu * tu[ix] * tu[g.n[0] + iy] * tu[g.n[0] + g.n[1] + iz];
-    const cpx<R> phv = tfv * tv[ix] * tv[g.n[0] + iy] * tv[g.n[0] + g.n[1] + iz];
+    const cpx<R> phu = xmul(xmul(xmul(tfu, tu[ix]), tu[g.n[0] + iy]), tu[g.n[0] + g.n[1] + iz]);
+    const cpx<R> phv = xmul(xmul(xmul(tfv, tv[ix]), tv[g.n[0] + iy]), tv[g.n[0] + g.n[1] + iz]);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       u[a] = U[(size_t)a * g.N + j];
       v[a] = V[(size_t)a * g.N + j];
-      ub[a] = tu[nt + a] * phu;
-      vb[a] = tv[nt + a] * phv;
+      ub[a] = xmul(tu[nt + a], phu);
+      vb[a] = xmul(tv[nt + a], phv);
     }
 #pragma unroll
     for (int jj = 0; jj < NPH; ++jj) {
-      const cpx<R> ph = kp[jj][ix] * kp[jj][g.n[0] + iy] * kp[jj][g.n[0] + g.n[1] + iz];
+      const cpx<R> ph = xmul(xmul(kp[jj][ix], kp[jj][g.n[0] + iy]), kp[jj][g.n[0] + g.n[1] + iz]);
       cpx<R> av[4], avb[4];
       alpha_eps<R>(eps[jj], v, av);
       alpha_eps<R>(eps[jj], vb, avb);
       cpx<R> ss = mk<R>(0, 0), bs = mk<R>(0, 0), sb = mk<R>(0, 0);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        ss = ss + cdot(u[a], av[a]);
-        bs = bs + cdot(ub[a], av[a]);
-        sb = sb + cdot(u[a], avb[a]);
+        ss = xadd(ss, xcdot(u[a], av[a]));
+        bs = xadd(bs, xcdot(ub[a], av[a]));
+        sb = xadd(sb, xcdot(u[a], avb[a]));
       }
-      tss[jj] = tss[jj] + ss * ph;
-      tbs[jj] = tbs[jj] + bs * ph;
-      tsb[jj] = tsb[jj] + sb * ph;
+      tss[jj] = xadd(tss[jj], xmul(ss, ph));
+      tbs[jj] = xadd(tbs[jj], xmul(bs, ph));
+      tsb[jj] = xadd(tsb[jj], xmul(sb, ph));
     }
   }
 #pragma unroll
@@ -1838,11 +1858,20 @@ __global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, con
   if (threadIdx.x < 3 * nj) {
     const int jj = threadIdx.x / 3, q = threadIdx.x % 3;
     cpx<double> sacc = mk<double>(0, 0);
-    for (int wi = 0; wi < 8; ++wi) sacc = sacc + red[wi][threadIdx.x];
+    for (int wi = 0; wi < 8; ++wi) sacc = xadd(sacc, red[wi][threadIdx.x]);
     const cpx<double>* trow = ptab + 3 * (tab_row + (long)(pi0 + jj) * tab_stride);
-    cpx<double>& a = acc[((size_t)(pi0 + jj) * gridDim.x + blockIdx.x) * 3 + q];
-    a = a + trow[2] * sacc;
+    cpx<double>& a = acc[((size_t)(pi0 + jj) * nbx + bx) * 3 + q];
+    a = xadd(a, xmul(trow[2], sacc));
   }
+}
+
+template <typename R, int NPH>
+__global__ void __launch_bounds__(256) k_mdot(const cpx<R>* __restrict__ ys, const cpx<R>* gcplx, const cpx<R>* kph,
+                                              const double* photon, GridDesc g, const cpx<double>* __restrict__ ptab,
+                                              const MarchClock* clk, int ls, int stage, int tab_stride,
+                                              int n_ph, cpx<double>* acc) {
+  mdot_body<R, NPH>(ys, gcplx, kph, photon, g, ptab, clk, ls, stage, tab_stride, n_ph, acc, blockIdx.x, blockIdx.y,
+                    gridDim.x);
 }
 
 // macc[inst][q] = sum_b acc[inst][b][q]: warp q of block inst adds the accumulators
@@ -2711,6 +2740,499 @@ swf_status march_bw_adaptive(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
                                          psi_out, macc, st);
   return march_bw_adaptive_impl<double>(ctx, g, t_in, t_out, h0, max_attempts, n_inst, fd_host, photon_host,
                                         psi_out, macc, st);
+}
+
+// ---------------------------------------------------------------- multi-grid march (batching of uneven grids)
+// Groups of fields on different grids that share one time grid (t_out, t_in, steps) are marched by
+// one launch per pass for all groups: persistent blocks (as many as fit the SMs at once) take work
+// items -- one item is one block of one group's pass -- from a device counter, the largest grids'
+// items first, and run the single-group kernels' per-block code on them.  A group's lines are
+// therefore transformed with exactly the arithmetic of marching that group alone (bitwise the same
+// result); the launch only decides which SM does which block, and the whole multi-grid step pair
+// is one CUDA graph.  The per-group arguments of every evaluation of the step pair sit in device
+// tables, uploaded once before the graph is captured (the slots rotate with period two).
+
+constexpr int kMaxMultiGroups = 8;
+
+struct MultiPlan {
+  int items;                       // work items of the launch
+  int first[kMaxMultiGroups + 1];  // first item of queue position q (largest grids first)
+  int gid[kMaxMultiGroups];        // table index of the group at queue position q
+  int gx[kMaxMultiGroups];         // blocks per field of that group in this pass
+  int shape[kMaxMultiGroups];      // rows per block (x passes) or log2 of the tile width (y, z passes)
+  int ld[kMaxMultiGroups];         // padded line stride
+};
+
+// Breit-Wheeler integrand arguments of one group (one photon per instance).
+template <typename R>
+struct MdotArgs {
+  const cpx<R>* ys;
+  const cpx<R>* gcplx;
+  const cpx<R>* kph;
+  const double* photon;
+  const cpx<double>* ptab;
+  cpx<double>* acc;
+  GridDesc g;
+  int tab_stride;
+  int nb;  // blocks per instance (the split of the single-group march)
+};
+
+// Persistent loop over the work items of a grouped launch: body(args, bx, by, shape, ld) with the
+// item's group arguments copied into shared memory.
+template <typename Args, typename Body>
+__device__ __forceinline__ void multi_loop(const Args* __restrict__ tab, const MultiPlan& P, int* counter,
+                                           Body&& body) {
+  __shared__ __align__(16) Args sA;
+  __shared__ MultiPlan sP;
+  __shared__ int s_item;
+  if (threadIdx.x == 0) sP = P;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= sP.items) break;
+    int q = 0;
+    while (q + 1 < kMaxMultiGroups && item >= sP.first[q + 1]) ++q;
+    if (q != cur) {
+      const int* src = reinterpret_cast<const int*>(tab + sP.gid[q]);
+      int* dst = reinterpret_cast<int*>(&sA);
+      for (int i = threadIdx.x; i < (int)(sizeof(Args) / sizeof(int)); i += blockDim.x) dst[i] = __ldg(src + i);
+      __syncthreads();
+      cur = q;
+    }
+    const int local = item - sP.first[q];
+    body(sA, local % sP.gx[q], local / sP.gx[q], sP.shape[q], sP.ld[q]);
+    __syncthreads();  // shared memory and s_item are reused by the next item
+  }
+}
+
+// The per-group arguments come from shared memory instead of the constant bank, which costs the
+// kernels registers; the bounds keep them at the occupancy of the single-group kernels (a few
+// bytes of spills in complex64, about a hundred in complex128).
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_first_multi(const StageArgs<R>* __restrict__ tab, MultiPlan P, int only_x,
+                                                     int* counter) {
+  multi_loop(tab, P, counter, [&](const StageArgs<R>& A, int bx, int f, int rows, int ld) {
+    first_body<R>(A, bx, f, rows, ld, only_x);
+  });
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_mid_multi(const StageArgs<R>* __restrict__ tab, MultiPlan P, int axis,
+                                                   int do_fwd, int do_h0, int do_inv, int* counter) {
+  multi_loop(tab, P, counter, [&](const StageArgs<R>& A, int bx, int f, int lgtx, int ld) {
+    mid_body<R>(A, bx, f, axis, lgtx, ld, do_fwd, do_h0, do_inv);
+  });
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_last_multi(const StageArgs<R>* __restrict__ tab, MultiPlan P, int* counter) {
+  multi_loop(tab, P, counter, [&](const StageArgs<R>& A, int bx, int f, int rows, int ld) {
+    last_body<R>(A, bx, f, rows, ld);
+  });
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_mdot_multi(const MdotArgs<R>* __restrict__ tab, MultiPlan P,
+                                                    const MarchClock* clk, int ls, int stage, int* counter) {
+  multi_loop(tab, P, counter, [&](const MdotArgs<R>& M, int bx, int by, int, int) {
+    mdot_body<R, 1>(M.ys, M.gcplx, M.kph, M.photon, M.g, M.ptab, clk, ls, stage, M.tab_stride, 1, M.acc, bx, by,
+                    M.nb);
+  });
+}
+
+template <typename R>
+static swf_status set_multi_attrs() {
+  static std::atomic<bool> done[64];
+  const int dv = dev_slot();
+  if (done[dv].load(std::memory_order_acquire)) return SWF_OK;
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_first_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
+  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_first_multi)");
+  e = cudaFuncSetAttribute(k_mid_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
+  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_mid_multi)");
+  e = cudaFuncSetAttribute(k_last_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
+  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last_multi)");
+  done[dv].store(true, std::memory_order_release);
+  return SWF_OK;
+}
+
+// Blocks of a persistent grouped launch: as many as can be resident at once (at most one per item).
+template <typename K>
+static int persistent_blocks(K kernel, size_t smem, int items, int threads = kThreads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return std::max(1, std::min(items, per_sm * sm_count()));
+}
+
+// Queue positions of the groups: largest grids first (their items take longest).
+static std::vector<int> multi_order(const std::vector<MultiGroup>& G) {
+  std::vector<int> ord(G.size());
+  for (size_t i = 0; i < G.size(); ++i) ord[i] = (int)i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return G[a].g.N > G[b].g.N; });
+  return ord;
+}
+
+static MultiPlan make_plan(const std::vector<int>& ord, const std::vector<int>& gx, const std::vector<int>& per,
+                           const std::vector<int>& shape, const std::vector<int>& ld) {
+  MultiPlan P;
+  std::memset(&P, 0, sizeof(P));
+  int acc = 0;
+  for (int q = 0; q < kMaxMultiGroups; ++q) {
+    P.first[q] = acc;
+    if (q < (int)ord.size()) {
+      const int gi = ord[q];
+      P.gid[q] = gi;
+      P.gx[q] = gx[gi];
+      P.shape[q] = shape[gi];
+      P.ld[q] = ld[gi];
+      acc += gx[gi] * per[gi];
+    }
+  }
+  P.first[kMaxMultiGroups] = acc;
+  P.items = acc;
+  return P;
+}
+
+template <typename R>
+static swf_status march_multi_impl(swf_ctx* ctx, const std::vector<MultiGroup>& G, double t_in, double t_out,
+                                   int n_steps, int bw, cudaStream_t st) {
+  const int ng = (int)G.size();
+  constexpr int esz = (int)sizeof(cpx<R>);
+  swf_status s = set_multi_attrs<R>();
+  if (s != SWF_OK) return s;
+  const int ny0 = G[0].g.n[1], nz0 = G[0].g.n[2];
+  const bool only_x = (ny0 == 1 && nz0 == 1);
+  std::vector<StageArgs<R>> base(ng);
+  std::vector<void*> pk(7 * (size_t)ng), pys(ng, nullptr), ppart(ng, nullptr);
+  std::vector<MdotArgs<R>> mdot(ng);
+  std::vector<int> nb(ng, 1);
+  const double h = (t_in - t_out) / n_steps;
+  cudaError_t e;
+  for (int gi = 0; gi < ng; ++gi) {
+    const MultiGroup& M = G[gi];
+    const GridDesc& g = M.g;
+    const int F = M.F;
+    const std::string tag = "mg" + std::to_string(gi);
+    if ((s = prepare_args<R>(ctx, g, F, M.fd, &base[gi], tag.c_str(), st)) != SWF_OK) return s;
+    const size_t state = (size_t)F * 4 * g.N * esz;
+    void *py = nullptr, *pT = nullptr;
+    if ((s = ws_get(ctx, tag + ".y", state, &py)) != SWF_OK) return s;
+    if ((s = ws_get(ctx, tag + ".T", state, &pT)) != SWF_OK) return s;
+    for (int i = 0; i < 7; ++i)
+      if ((s = ws_get(ctx, tag + ".k" + std::to_string(i), state, &pk[7 * gi + i])) != SWF_OK) return s;
+    if ((e = cudaMemsetAsync(py, 0, state, st)) != cudaSuccess) return cuda_status(e, "memset state");
+    base[gi].y = (cpx<R>*)py;
+    base[gi].T = (cpx<R>*)pT;
+    if (bw) {
+      const int n_inst = F / 2;
+      const int nt = g.n[0] + g.n[1] + g.n[2];
+      void *pph = nullptr, *pkph = nullptr, *ptab = nullptr;
+      if ((s = ws_get(ctx, tag + ".ystage", state, &pys[gi])) != SWF_OK) return s;
+      if ((s = ws_get(ctx, tag + ".photon", sizeof(double) * 6 * n_inst, &pph)) != SWF_OK) return s;
+      if ((s = ws_get(ctx, tag + ".kph", sizeof(cpx<R>) * n_inst * nt, &pkph)) != SWF_OK) return s;
+      // the same split of the integrand sums as the single-group march of this group
+      nb[gi] = std::max(1, std::min((g.N + 1023) / 1024, (4 * sm_count() + n_inst - 1) / n_inst));
+      if ((s = ws_get(ctx, tag + ".ptab", sizeof(cpx<double>) * 3 * 7 * (size_t)n_steps * n_inst, &ptab)) != SWF_OK)
+        return s;
+      if ((s = ws_get(ctx, tag + ".mpart", sizeof(cpx<double>) * 3 * (size_t)nb[gi] * n_inst, &ppart[gi])) != SWF_OK)
+        return s;
+      if ((e = cudaMemcpyAsync(pph, M.photon, sizeof(double) * 6 * n_inst, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_status(e, "upload photon table");
+      {
+        ProfScope ps(ctx, "k_photon_tables", st);
+        k_photon_tables<R><<<(n_inst * nt + 127) / 128, 128, 0, st>>>((const double*)pph, g, n_inst, (cpx<R>*)pkph);
+      }
+      {
+        const long total = (long)n_inst * n_steps * 7;
+        ProfScope ps(ctx, "k_bw_phase_table", st);
+        k_bw_phase_table<<<(int)std::min((total + 127) / 128, 4096L), 128, 0, st>>>(
+            base[gi].fd, (const double*)pph, n_inst, 1, n_steps, t_out, h, g.dx[0] * g.dx[1] * g.dx[2], 1,
+            (cpx<double>*)ptab);
+      }
+      if ((e = cudaMemsetAsync(ppart[gi], 0, sizeof(cpx<double>) * 3 * (size_t)nb[gi] * n_inst, st)) != cudaSuccess)
+        return cuda_status(e, "memset M accumulators");
+      mdot[gi] = MdotArgs<R>{(const cpx<R>*)pys[gi], base[gi].gcplx, (const cpx<R>*)pkph, (const double*)pph,
+                             (const cpx<double>*)ptab, (cpx<double>*)ppart[gi], g, 7 * n_steps, nb[gi]};
+    }
+    {  // launch shapes of this group by timing (as for a single-group march)
+      StageArgs<R> B = base[gi];
+      B.nterm = 6;
+      for (int q = 0; q < 6; ++q) {
+        B.kin[q] = (const cpx<R>*)pk[7 * gi + q + 1];
+        B.coef[q] = 0.0;
+      }
+      B.write_y = 0;
+      B.ystage = nullptr;
+      B.kout = (cpx<R>*)pk[7 * gi];
+      B.t = t_out;
+      if ((s = autotune_eval<R>(ctx, B, F, st)) != SWF_OK) return s;
+    }
+  }
+  // Per-pass plans.  The lead group (the largest grid, first in the queue) keeps its tuned shape
+  // and thread count; it fixes the launch's shared memory per block, and every other group takes
+  // the largest shape that fits that budget (more rows, or wider tiles, for smaller grids), so that
+  // its blocks do not reserve shared memory they leave unused.
+  const std::vector<int> ord = multi_order(G);
+  const int lead = ord[0];
+  std::vector<int> fper(ng), xg(ng), xrows(ng), xld(ng);
+  int xthr = kThreads;
+  size_t xsmem = 0;
+  {
+    const GridDesc& g = G[lead].g;
+    const int nrows = g.n[1] * g.n[2];
+    const int xv = tune_lookup(ctx, tune_key('x', esz, g.n[0], nrows, 0, G[lead].F),
+                               4 * x_rows<R>(g.n[0], nrows, G[lead].F));
+    xthr = (xv & 3) ? kThreads / 2 : kThreads;
+    xsmem = (size_t)2 * 4 * std::max(1, xv >> 2) * padded_len(g.n[0]) * esz;
+  }
+  for (int gi = 0; gi < ng; ++gi) {
+    const GridDesc& g = G[gi].g;
+    fper[gi] = G[gi].F;
+    const int nrows = g.n[1] * g.n[2];
+    xld[gi] = padded_len(g.n[0]);
+    const size_t line = (size_t)2 * 4 * xld[gi] * esz;
+    xrows[gi] = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(xsmem / line, 64), nrows));
+    xg[gi] = (nrows + xrows[gi] - 1) / xrows[gi];
+    xsmem = std::max(xsmem, (size_t)xrows[gi] * line);
+  }
+  const MultiPlan px = make_plan(ord, xg, fper, xrows, xld);
+  struct MidPass { int axis, fwd, h0, inv; MultiPlan plan; size_t smem; int blocks, threads; };
+  std::vector<MidPass> mids;
+  if (!only_x) {
+    std::vector<std::array<int, 4>> combos;
+    if (ny0 > 1 && nz0 > 1) combos = {{1, 1, 0, 0}, {2, 1, 1, 1}, {1, 0, 0, 1}};
+    else combos = {{ny0 > 1 ? 1 : 2, 1, 1, 1}};
+    for (const auto& cb : combos) {
+      const int axis = cb[0];
+      auto tuned = [&](int gi) {
+        const GridDesc& g = G[gi].g;
+        const int other = axis == 1 ? g.n[2] : g.n[1];
+        const int lg_h = mid_shape<R>(g.n[axis], g.n[0], (long)other * G[gi].F).lgtx;
+        return tune_lookup(ctx, tune_key('m', esz, axis * 8 + cb[1] * 4 + cb[2] * 2 + cb[3], g.n[axis], g.n[0],
+                                         (long)other * G[gi].F), 4 * lg_h);
+      };
+      const int mv_lead = tuned(lead);
+      const size_t budget = mid_shape_lg<R>(G[lead].g.n[axis], mv_lead >> 2).smem;
+      std::vector<int> mg(ng), lg(ng), ld(ng);
+      size_t sm = 0;
+      for (int gi = 0; gi < ng; ++gi) {
+        const GridDesc& g = G[gi].g;
+        const int other = axis == 1 ? g.n[2] : g.n[1];
+        int l = gi == lead ? (mv_lead >> 2) : mid_max_lg<R>(g.n[axis], g.n[0], budget);
+        const MidShape ms = mid_shape_lg<R>(g.n[axis], l);
+        lg[gi] = ms.lgtx;
+        ld[gi] = ms.ld;
+        mg[gi] = ((g.n[0] + (1 << ms.lgtx) - 1) >> ms.lgtx) * other;
+        sm = std::max(sm, ms.smem);
+      }
+      MidPass mp{axis, cb[1], cb[2], cb[3], make_plan(ord, mg, fper, lg, ld), sm, 0,
+                 (mv_lead & 3) ? kThreads / 2 : kThreads};
+      mp.blocks = persistent_blocks(k_mid_multi<R>, sm, mp.plan.items, mp.threads);
+      mids.push_back(mp);
+    }
+  }
+  const int xfb = persistent_blocks(k_first_multi<R>, xsmem, px.items, xthr);
+  const int xlb = persistent_blocks(k_last_multi<R>, xsmem, px.items, xthr);
+  MultiPlan pd;
+  int dblocks = 0;
+  if (bw) {
+    std::vector<int> ones(ng, 1), zero(ng, 0), ninst(ng);
+    for (int gi = 0; gi < ng; ++gi) ninst[gi] = G[gi].F / 2;
+    pd = make_plan(ord, nb, ninst, zero, zero);
+    dblocks = persistent_blocks(k_mdot_multi<R>, 0, pd.items);
+  }
+  // argument tables of every evaluation of a step pair: entry 0 the first evaluation k_1 = f(t_out, 0),
+  // then (ls, stage) for ls = 0, 1 and stages 1..6, with the slot rotation of the single-group march
+  const int n_ev = 1 + 12;
+  std::vector<StageArgs<R>> tab((size_t)n_ev * ng);
+  std::vector<std::array<int, 7>> slot(ng);
+  for (int gi = 0; gi < ng; ++gi) {
+    for (int i = 0; i < 7; ++i) slot[gi][i] = i;
+    StageArgs<R> A = base[gi];
+    A.nterm = 0;
+    A.write_y = 0;
+    A.kout = (cpx<R>*)pk[7 * gi + slot[gi][0]];
+    A.ls = 0;
+    A.c = 0.0;
+    A.ystage = nullptr;
+    A.t = t_out;
+    tab[gi] = A;
+  }
+  void* pclk = nullptr;
+  if ((s = ws_get(ctx, "mg.clock", sizeof(MarchClock), &pclk)) != SWF_OK) return s;
+  MarchClock* clk = (MarchClock*)pclk;
+  for (int ls = 0; ls < 2; ++ls) {
+    for (int i = 1; i < 7; ++i) {
+      for (int gi = 0; gi < ng; ++gi) {
+        StageArgs<R> A = base[gi];
+        int nt = 0;
+        for (int j = 0; j < i; ++j) {
+          if (DP_A[i][j] == 0.0) continue;
+          A.kin[nt] = (const cpx<R>*)pk[7 * gi + slot[gi][j]];
+          A.coef[nt] = h * DP_A[i][j];
+          ++nt;
+        }
+        A.nterm = nt;
+        A.write_y = (i == 6);
+        A.kout = (cpx<R>*)pk[7 * gi + slot[gi][i]];
+        A.ls = ls;
+        A.c = DP_C[i];
+        A.clk = clk;
+        A.ystage = (bw && i >= 2) ? (cpx<R>*)pys[gi] : nullptr;
+        tab[(size_t)(1 + 6 * ls + (i - 1)) * ng + gi] = A;
+      }
+    }
+    for (int gi = 0; gi < ng; ++gi) std::swap(slot[gi][0], slot[gi][6]);
+  }
+  void *ptabs = nullptr, *pmd = nullptr, *pcnt = nullptr;
+  if ((s = ws_get(ctx, "mg.tables", sizeof(StageArgs<R>) * tab.size(), &ptabs)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "mg.counters", sizeof(int) * 64, &pcnt)) != SWF_OK) return s;
+  if ((e = cudaMemcpyAsync(ptabs, tab.data(), sizeof(StageArgs<R>) * tab.size(), cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return cuda_status(e, "upload multi-grid tables");
+  if (bw) {
+    if ((s = ws_get(ctx, "mg.mdot", sizeof(MdotArgs<R>) * ng, &pmd)) != SWF_OK) return s;
+    if ((e = cudaMemcpyAsync(pmd, mdot.data(), sizeof(MdotArgs<R>) * ng, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_status(e, "upload multi-grid integrand table");
+  }
+  const StageArgs<R>* dtab = (const StageArgs<R>*)ptabs;
+  int* cnt = (int*)pcnt;
+  int ci = 0;  // next counter of the recorded sequence
+  auto eval = [&](int ev) {
+    const StageArgs<R>* t = dtab + (size_t)ev * ng;
+    {
+      ProfScope ps(ctx, "k_first_multi", st);
+      k_first_multi<R><<<xfb, xthr, xsmem, st>>>(t, px, only_x ? 1 : 0, cnt + ci++);
+    }
+    if (only_x) return;
+    for (const MidPass& mp : mids) {
+      ProfScope ps(ctx, "k_mid_multi", st);
+      k_mid_multi<R><<<mp.blocks, mp.threads, mp.smem, st>>>(t, mp.plan, mp.axis, mp.fwd, mp.h0, mp.inv, cnt + ci++);
+    }
+    ProfScope ps(ctx, "k_last_multi", st);
+    k_last_multi<R><<<xlb, xthr, xsmem, st>>>(t, px, cnt + ci++);
+  };
+  auto step = [&](int ls) {
+    for (int i = 1; i < 7; ++i) {
+      eval(1 + 6 * ls + (i - 1));
+      if (bw && i >= 2) {
+        ProfScope ps(ctx, "k_mdot_multi", st);
+        k_mdot_multi<R><<<dblocks, kThreads, 0, st>>>((const MdotArgs<R>*)pmd, pd, clk, ls, i, cnt + ci++);
+      }
+    }
+  };
+  const int per_pair = 2 * 6 * (2 + (int)mids.size() + (bw ? 1 : 0));
+  if (per_pair > 64) {
+    set_error("multi-grid march: too many launches per step pair");
+    return SWF_EUNSUPPORTED;
+  }
+  k_clock_set<<<1, 1, 0, st>>>(clk, t_out, h);
+  if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * 64, st)) != cudaSuccess) return cuda_status(e, "reset work queues");
+  ci = 0;
+  eval(0);  // k_1 = f(t_out, 0) (the integrand of Eq. 17 vanishes at psi_s(t_out) = 0)
+  auto pair = [&]() -> swf_status {
+    cudaError_t r = cudaMemsetAsync(cnt, 0, sizeof(int) * 64, st);
+    if (r != cudaSuccess) return cuda_status(r, "reset work queues");
+    ci = 0;
+    step(0);
+    step(1);
+    return SWF_OK;
+  };
+  if ((s = run_step_pairs(ctx, st, n_steps / 2, clk, pair)) != SWF_OK) return s;
+  if (n_steps % 2) {
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * 64, st)) != cudaSuccess) return cuda_status(e, "reset work queues");
+    ci = 0;
+    step(0);
+  }
+  for (int gi = 0; gi < ng; ++gi) {
+    const size_t state = (size_t)G[gi].F * 4 * G[gi].g.N * esz;
+    if (bw) {
+      ProfScope ps(ctx, "k_mdot_final", st);
+      k_mdot_final<<<G[gi].F / 2, 96, 0, st>>>((const cpx<double>*)ppart[gi], nb[gi], (cpx<double>*)G[gi].macc);
+    }
+    if ((e = cudaMemcpyAsync(G[gi].psi_out, base[gi].y, state, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return cuda_status(e, "copy psi(t_in)");
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "multi-grid march kernels");
+  // the host tables above are the sources of asynchronous uploads
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(e, "multi-grid march");
+  ctx->multi_marches += 1;
+  return SWF_OK;
+}
+
+bool multi_compatible(const GridDesc& a, const GridDesc& b) {
+  return (a.n[1] > 1) == (b.n[1] > 1) && (a.n[2] > 1) == (b.n[2] > 1);
+}
+
+swf_status march_multi(swf_ctx* ctx, const std::vector<MultiGroup>& groups, double t_in, double t_out, int n_steps,
+                       swf_precision prec, int bw, cudaStream_t st) {
+  if (groups.empty() || (int)groups.size() > kMaxMultiGroups) {
+    set_error("multi-grid march: 1 to 8 groups");
+    return SWF_EINVAL;
+  }
+  for (const MultiGroup& M : groups) {
+    if (!multi_compatible(M.g, groups[0].g) || M.F < 1 || (bw && (M.F % 2 || !M.photon || !M.macc))) {
+      set_error("multi-grid march: groups must share the non-trivial axes (and carry U, V pairs and photons)");
+      return SWF_EINVAL;
+    }
+  }
+  if (prec == SWF_C64) return march_multi_impl<float>(ctx, groups, t_in, t_out, n_steps, bw, st);
+  return march_multi_impl<double>(ctx, groups, t_in, t_out, n_steps, bw, st);
+}
+
+// Plain marches of several groups (the spin reuse of march_fields within each group).
+swf_status march_fields_multi(swf_ctx* ctx, const std::vector<MultiGroup>& groups, double t_in, double t_out,
+                              int n_steps, swf_precision prec, cudaStream_t st) {
+  const int ng = (int)groups.size();
+  std::vector<MultiGroup> todo(groups);
+  std::vector<std::vector<int>> rep(ng), sgn(ng);
+  std::vector<std::vector<FieldDesc>> uniq(ng);
+  const size_t elem = prec == SWF_C64 ? 8 : 16;
+  swf_status s;
+  for (int gi = 0; gi < ng; ++gi) {
+    const MultiGroup& M = groups[gi];
+    const int n_u = ctx->dedupe ? dedupe_fields(M.g, M.F, M.fd, rep[gi], sgn[gi], uniq[gi]) : M.F;
+    ctx->fields_marched += n_u;
+    if (n_u == M.F) {
+      rep[gi].clear();
+      continue;
+    }
+    void* pu = nullptr;
+    if ((s = ws_get(ctx, "mg.unique" + std::to_string(gi), (size_t)n_u * 4 * M.g.N * elem, &pu)) != SWF_OK) return s;
+    todo[gi].F = n_u;
+    todo[gi].fd = uniq[gi].data();
+    todo[gi].psi_out = pu;
+  }
+  if ((s = march_multi(ctx, todo, t_in, t_out, n_steps, prec, 0, st)) != SWF_OK) return s;
+  for (int gi = 0; gi < ng; ++gi) {
+    if (rep[gi].empty()) continue;
+    const MultiGroup& M = groups[gi];
+    void* ptab = nullptr;
+    if ((s = ws_get(ctx, "mg.unique_map" + std::to_string(gi), sizeof(int) * 2 * (size_t)M.F, &ptab)) != SWF_OK)
+      return s;
+    std::vector<int> tabv(rep[gi]);
+    tabv.insert(tabv.end(), sgn[gi].begin(), sgn[gi].end());
+    cudaError_t e = cudaMemcpyAsync(ptab, tabv.data(), sizeof(int) * 2 * (size_t)M.F, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "upload field map");
+    const dim3 grid((unsigned)std::min<size_t>((M.g.N + 255) / 256, 1024), M.F, 4);
+    ProfScope ps(ctx, "k_expand_fields", st);
+    if (prec == SWF_C64)
+      k_expand_fields<float><<<grid, 256, 0, st>>>((const cpx<float>*)todo[gi].psi_out, (const int*)ptab,
+                                                   (const int*)ptab + M.F, (size_t)M.g.N, (cpx<float>*)M.psi_out);
+    else
+      k_expand_fields<double><<<grid, 256, 0, st>>>((const cpx<double>*)todo[gi].psi_out, (const int*)ptab,
+                                                    (const int*)ptab + M.F, (size_t)M.g.N, (cpx<double>*)M.psi_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "expand fields");
+    e = cudaStreamSynchronize(st);  // the host table must outlive its upload
+    if (e != cudaSuccess) return cuda_status(e, "expand fields");
+  }
+  return SWF_OK;
 }
 
 }  // namespace swf

@@ -49,7 +49,7 @@ EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_sw
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_set_dedupe", "swf_fields_marched",
            "swf_fields_fused", "swf_plan_split",
-           "swf_set_tolerances", "swf_march_stats",
+           "swf_set_tolerances", "swf_march_stats", "swf_set_multi_grid",
            "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
            "swf_mlp_get_params"]
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_set_march_path.argtypes = [vp, ip]
     lib.swf_set_autotune.argtypes = [vp, ip]
     lib.swf_set_dedupe.argtypes = [vp, ip]
+    lib.swf_set_multi_grid.argtypes = [vp, ip]
     lib.swf_set_tolerances.argtypes = [vp, dp, dp]
     lib.swf_march_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     lib.swf_fields_marched.argtypes = [vp, C.POINTER(C.c_longlong)]
@@ -221,6 +222,11 @@ class Context:
     def set_dedupe(self, on: bool):
         """March repeated fields (the other spin of a z-spin-conserving field) once (True, default)."""
         _check(_lib.swf_set_dedupe(self._h, 1 if on else 0))
+
+    def set_multi_grid(self, mode: int):
+        """Instance groups on different grids sharing a time grid: 0 one after another, 1 together
+        when they are small enough (default), 2 always together."""
+        _check(_lib.swf_set_multi_grid(self._h, int(mode)))
 
     def fields_marched(self):
         n = C.c_longlong()

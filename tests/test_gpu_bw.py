@@ -326,3 +326,41 @@ def test_bw_step_size_controlled_march_matches_oracle(env):
     with pytest.raises(swf.SwfError) as ei:
         ctx.solve([bad], swf.BREIT_WHEELER, swf.C64)
     assert ei.value.status == swf.SWF_EUNSUPPORTED
+
+
+def test_uneven_grids_share_one_multi_grid_march(env):
+    """Breit-Wheeler instances on three grids with one time grid (the uneven-grid workload's
+    pattern): one launch per pass and one integrand launch per stage for all of them, bitwise the
+    amplitudes of marching each grid group alone, in both precisions; one instance against the
+    oracle."""
+    swf, _ = env
+    c = CASE2D
+    perp, par = O.polarisation_basis((1, 0, 0), c["k"])
+    L = c["L"]
+    insts, cases = [], []
+    for n in (24, 16, 20):
+        for P in (-0.3, 0.25):
+            d = dict(n=(n, n, 1), p=(P, -1.0, 0.0), q=(-P, -1.0, 0.0))
+            cases.append(d)
+            insts.append(_bw_inst(swf, *c["fld"], d["n"], L, c["t_in"], c["t_out"], 150, d["p"], 1, d["q"], 1, c["k"],
+                                  par))
+    for prec in (swf.C64, swf.C128):
+        out = {}
+        for multi in (True, False):
+            ctx = swf.Context(0)
+            ctx.set_multi_grid(2 if multi else 0)
+            ctx.profile_enable(True)
+            ctx.profile_read()
+            res, _ = ctx.solve(insts, swf.BREIT_WHEELER, prec)
+            prof, _ = ctx.profile_read()
+            ctx.close()
+            out[multi] = ([list(r.amp) + list(r.prob) for r in res], prof)
+        assert "k_mdot_multi" in out[True][1] and "k_mdot_multi" not in out[False][1]
+        assert out[True][0] == out[False][0], prec
+    # the second instance of the 16^2 group (not the first group in the call) against the oracle
+    d = cases[3]
+    ph = O.Photon(c["k"], tuple(par))
+    ref = O.bw_amplitude(O.Field(*c["fld"]), O.Grid(d["n"], L), d["p"], 1, d["q"], 1, ph, c["t_in"], c["t_out"], 150)
+    M = ref["M"]
+    got = complex(out[True][0][3][6], out[True][0][3][7])  # last precision run: complex128
+    assert abs(got - M) <= 1e-10 * abs(M), (got, M)

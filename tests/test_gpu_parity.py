@@ -608,3 +608,47 @@ def test_step_size_controlled_march_matches_oracle(env):
     got = to_complex(out64).reshape(ref_fixed.shape)
     assert rel_state(got, ref_fixed) < 20 * 1e-7 and ctx.march_stats()[0] > stats[0]
     ctx.close()
+
+
+def _multi_solve(swf, ds, process, prec, mode):
+    ctx = swf.Context(0)
+    ctx.set_multi_grid(mode)
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    res, spec = ctx.solve([swf.from_workload(d) for d in ds], process, prec)
+    prof, _ = ctx.profile_read()
+    ctx.close()
+    return [list(r.amp) + list(r.prob) + list(r.diag) for r in res], spec, prof
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_uneven_grids_share_one_multi_grid_march(env, dims):
+    """Batching of uneven grids (Sec. II.A): instance groups on different grids with one time grid
+    are marched by one launch per pass (persistent blocks on a device work queue) and give bitwise
+    the results of marching each group alone; a 256^2 complex64 group still takes the fused
+    kernel beside them.  Spectra and the full pair number, both precisions, 2D and 3D grids."""
+    torch, swf, _ = env
+    base = dict(field=("sauter_gauss", (0.8, 0.6, 2.5)), t_in=-3.0, t_out=3.0, n_steps=24, k=(0, 0, 0),
+                eps=(0, 0, 0), flags=("spectrum", "full_n"))
+    if dims == 2:
+        grids = [((32, 24, 1), (16.0, 12.0, 1.0)), ((40, 30, 1), (20.0, 15.0, 1.0)), ((20, 20, 1), (10.0, 10.0, 1.0))]
+    else:
+        grids = [((12, 10, 8), (8.0, 7.0, 6.0)), ((16, 8, 6), (9.0, 6.0, 5.0))]
+    ds = []
+    for j, (n, L) in enumerate(grids):
+        for i in range(3):
+            p = (0.1 * i - 0.1, 0.2 - 0.1 * j, 0.0 if dims == 2 else 0.05)
+            ds.append(dict(base, n=n, L=L, p=p, s=1 if i % 2 else -1, q=(-0.2, 0.1 * j, 0.0), r=1 if i else -1))
+    if dims == 2:  # a group for the fused kernel (complex64) in the same call (|kappa|_max h = 1.6)
+        ds.append(dict(base, n=(256, 256, 1), L=(128.0, 128.0, 1.0), p=(0.3, 0.1, 0.0), s=1, q=(-0.3, 0.0, 0.0),
+                       r=1, flags=("spectrum",)))
+    for prec in (swf.C64, swf.C128):
+        r1, s1, prof1 = _multi_solve(swf, ds, swf.SCHWINGER, prec, 2)   # always together
+        r0, s0, prof0 = _multi_solve(swf, ds, swf.SCHWINGER, prec, 0)   # one group after another
+        ra, sa, profa = _multi_solve(swf, ds, swf.SCHWINGER, prec, 1)   # automatic: small groups go together
+        assert "k_first_multi" in prof1 and "k_first_multi" not in prof0, (prof1, prof0)
+        assert "k_first_multi" in profa
+        assert np.all(np.isfinite(r1)) and np.all(np.isfinite(s1))
+        assert r1 == r0 == ra, prec
+        assert np.array_equal(s1, s0) and np.array_equal(s1, sa), prec
+        assert max(abs(x) for r in r1 for x in r) > 0
