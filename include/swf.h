@@ -230,6 +230,13 @@ swf_status swf_set_tolerances(swf_ctx* ctx, double rtol, double atol);
 /* Accepted and rejected steps of the context's last step-size-controlled march. */
 swf_status swf_march_stats(swf_ctx* ctx, long long* accepted, long long* rejected);
 
+/* Step-size-controlled marches of this context that ran as one graph launch with the attempt
+ * loop on the device (a while node of a CUDA graph: every attempt, its acceptance or rejection
+ * and the stop decided by the controller kernel; Sec. II.A's Dopri5 control with no host round
+ * trip per attempt).  Where that graph form is unavailable, or kernel timing is on, the march
+ * replays attempts from the host in growing chunks instead (the same attempts and results). */
+swf_status swf_device_loop_marches(swf_ctx* ctx, long long* count);
+
 /* Repeated marches.  on = 1 (default): within one call, a field whose march repeats another's
  * is marched once: the same field, window and background wave, or (with the z axis trivial,
  * p_z = 0 and A_3 = 0, where the spin along z is conserved) the other spin s = -1 vs +1 (or r),

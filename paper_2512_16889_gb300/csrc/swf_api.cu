@@ -903,6 +903,12 @@ swf_status swf_set_multi_grid(swf_ctx* ctx, int mode) {
   return SWF_OK;
 }
 
+swf_status swf_device_loop_marches(swf_ctx* ctx, long long* count) {
+  if (!ctx || !count) { set_error("swf_device_loop_marches: NULL argument"); return SWF_EINVAL; }
+  *count = ctx->device_loop_marches;
+  return SWF_OK;
+}
+
 swf_status swf_fields_marched(swf_ctx* ctx, long long* count) {
   if (!ctx || !count) { set_error("swf_fields_marched: NULL argument"); return SWF_EINVAL; }
   *count = ctx->fields_marched;

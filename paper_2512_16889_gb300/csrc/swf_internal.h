@@ -129,6 +129,7 @@ struct swf_ctx {
   long long fields_fused = 0;    // of those, fields marched by the fused cluster kernel
   int multi_grid = 1;            // grid groups sharing a time grid in one launch sequence: 0 never, 1 auto, 2 always
   long long multi_marches = 0;   // multi-grid marches run since the context's creation
+  long long device_loop_marches = 0;  // step-size-controlled marches decided entirely on the device
   int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
   bool sm_split = true;   // automatic path: pass kernels on the SMs the fused clusters leave free
   cudaStream_t aux = nullptr;            // stream of that concurrent pass-kernel march (lazy)

@@ -61,7 +61,21 @@ struct StageArgs {
   cpx<R>* ynew;         // with ctl: the last stage writes the step's result here, not into y
   cpx<R>* yspec;        // optional: receives the grid transform of the stage value (written by the
                         // y or z pass that applies H0, before it does)
+  cpx<R>* ylo;          // optional (complex64 fixed-step marches): the rounding error of y, so that
+                        // y + ylo carries the state in float-float (Knuth's two-sum per step)
 };
+
+// (hi, lo) += s in float-float arithmetic (Knuth's two-sum, then a fast renormalisation): on
+// return s holds the new rounded state and lo its rounding error.
+__device__ __forceinline__ void ff_accumulate(float hi, float& lo, float& s) {
+  const float t = __fadd_rn(hi, s);
+  const float bp = __fsub_rn(t, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(s, bp));
+  const float l = __fadd_rn(lo, e);
+  const float nh = __fadd_rn(t, l);
+  lo = __fsub_rn(l, __fsub_rn(nh, t));
+  s = nh;
+}
 
 // State of a step-size-controlled march, in device memory: the accepted time t and the step h
 // of the current attempt (the stage times are t + c_i h and the stage coefficients h a_ij), the
@@ -480,15 +494,39 @@ __device__ __forceinline__ void first_body(const StageArgs<R>& A, int bx, int f,
     cpx<R> v[4];
     if (row < A.nrows) {
       const size_t gi = fo + (size_t)row * nx + x;
+      if (sizeof(R) == 4 && A.ylo && A.write_y) {
+        // the new state: the step's increment h sum_j b_j k_j apart, then (y, ylo) += it in
+        // float-float, so that the single-precision rounding of y does not accumulate over steps
 #pragma unroll
-      for (int c = 0; c < 4; ++c) v[c] = A.y[gi + c * cs];
+        for (int c = 0; c < 4; ++c) v[c] = mk<R>(0, 0);
 #pragma unroll
-      for (int q = 0; q < 6; ++q)
-        if (q < A.nterm) {
-          const R co = (R)(A.coef[q] * hscale);
+        for (int q = 0; q < 6; ++q)
+          if (q < A.nterm) {
+            const R co = (R)(A.coef[q] * hscale);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) v[c] = v[c] + co * A.kin[q][gi + c * cs];
+            for (int c = 0; c < 4; ++c) v[c] = v[c] + co * A.kin[q][gi + c * cs];
+          }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const cpx<R> yh = A.y[gi + c * cs];
+          cpx<R> lo = A.ylo[gi + c * cs];
+          float sx = (float)v[c].x, sy = (float)v[c].y, lx = (float)lo.x, ly = (float)lo.y;
+          ff_accumulate((float)yh.x, lx, sx);
+          ff_accumulate((float)yh.y, ly, sy);
+          v[c] = mk<R>((R)sx, (R)sy);
+          A.ylo[gi + c * cs] = mk<R>((R)lx, (R)ly);
         }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = A.y[gi + c * cs];
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          if (q < A.nterm) {
+            const R co = (R)(A.coef[q] * hscale);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = v[c] + co * A.kin[q][gi + c * cs];
+          }
+      }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         if (A.write_y) yout[gi + c * cs] = v[c];
@@ -1036,6 +1074,21 @@ static swf_status run_step_pairs(swf_ctx* ctx, cudaStream_t st, int pairs, March
   return SWF_OK;
 }
 
+// complex64 fixed-step marches carry the state in float-float: a zeroed low part beside y.
+template <typename R>
+static swf_status state_low_part(swf_ctx* ctx, const std::string& name, size_t bytes, StageArgs<R>* A,
+                                 cudaStream_t st) {
+  A->ylo = nullptr;
+  if (sizeof(R) != 4) return SWF_OK;
+  void* p = nullptr;
+  swf_status s = ws_get(ctx, name, bytes, &p);
+  if (s != SWF_OK) return s;
+  const cudaError_t e = cudaMemsetAsync(p, 0, bytes, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset state low part");
+  A->ylo = (cpx<R>*)p;
+  return SWF_OK;
+}
+
 template <typename R>
 static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps,
                              int F, const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
@@ -1055,6 +1108,7 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
   if (e != cudaSuccess) return cuda_status(e, "memset state");
   A.y = (cpx<R>*)py;
   A.T = (cpx<R>*)pT;
+  if ((s = state_low_part<R>(ctx, "march.ylo", state, &A, st)) != SWF_OK) return s;
   {
     // shapes by timing, on the slots before they hold anything (the heaviest stage: six inputs)
     StageArgs<R> B = A;
@@ -1229,6 +1283,77 @@ __global__ void k_step_accept(const StepControl* ctl, cpx<R>* y, const cpx<R>* y
 // Runs step attempts recorded by `attempt` (launches only, on st) until the controller in ctl
 // reports t_in reached or a failure: chunks of 8, 16, .. 64 attempts as CUDA-graph replays
 // (kernel by kernel when timing is on), the controller's state read once per chunk into *out.
+// Condition of the device-side attempt loop: another attempt while the controller is not done
+// (the controller itself stops at max_attempts; the bound is repeated here so that the loop ends
+// whatever the state).
+__global__ void k_attempt_condition(cudaGraphConditionalHandle h, const StepControl* ctl) {
+  const bool more = !ctl->done && ctl->accepted + ctl->rejected < ctl->max_attempts;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// The whole controlled march as one graph launch: a while node whose body is one attempt and
+// k_attempt_condition, so that accepting, rejecting and stopping are decided on the device and
+// the host reads the controller's state once, at the end.  *built = false (nothing launched) when
+// the graph cannot be built here; the caller then runs its host loop.
+template <typename Att>
+static swf_status attempts_on_device(swf_ctx* ctx, cudaStream_t st, const StepControl* ctl, Att&& attempt,
+                                     StepControl* out, bool* built) {
+  *built = false;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return SWF_OK;
+  }
+  swf_status s = SWF_OK;
+  long long per_attempt = 0;
+  cudaGraphConditionalHandle h;
+  // the parameter union has no default constructor: zeroed storage
+  alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)];
+  std::memset(np_raw, 0, sizeof(np_raw));
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+  cudaGraphNode_t node;
+  bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  if (ok) ok = cudaStreamBeginCaptureToGraph(st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const long long l0 = ctx->prof.launches;
+    s = attempt();
+    k_attempt_condition<<<1, 1, 0, st>>>(h, ctl);
+    cudaGraph_t body = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &body);
+    per_attempt = ctx->prof.launches - l0 + 1;
+    ctx->prof.launches = l0;
+    ok = s == SWF_OK && ec == cudaSuccess && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  }
+  cudaGraphDestroy(g);
+  if (s != SWF_OK) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return s;
+  }
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();  // an unsupported graph form is not an error of the march
+    return SWF_OK;
+  }
+  *built = true;
+  cudaError_t e = cudaGraphLaunch(exec, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, ctl, sizeof(StepControl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return cuda_status(e, "step-size-controlled march (device loop)");
+  ctx->prof.launches += per_attempt * (out->accepted + out->rejected);
+  ctx->device_loop_marches += 1;
+  return SWF_OK;
+}
+
 template <typename Att>
 static swf_status run_attempts(swf_ctx* ctx, cudaStream_t st, int max_attempts, const StepControl* ctl,
                                Att&& attempt, StepControl* out) {
@@ -1237,6 +1362,11 @@ static swf_status run_attempts(swf_ctx* ctx, cudaStream_t st, int max_attempts, 
   bool graph = !ctx->prof.on && st != 0 && ctx->use_graphs;
   cudaGraphExec_t exec = nullptr;
   long long per_attempt = 0;
+  if (graph) {
+    bool built = false;
+    s = attempts_on_device(ctx, st, ctl, attempt, out, &built);
+    if (s != SWF_OK || built) return s;
+  }
   if (graph) {
     const long long l0 = ctx->prof.launches;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -1477,6 +1607,7 @@ static swf_status reserve_march(swf_ctx* ctx, const GridDesc& g, int F) {
   if ((s = ws_get(ctx, "march.gcplx", sizeof(cpx<R>) * F * (nt + 4), &p)) != SWF_OK) return s;
   if ((s = ws_get(ctx, "march.y", state, &p)) != SWF_OK) return s;
   if ((s = ws_get(ctx, "march.T", state, &p)) != SWF_OK) return s;
+  if (sizeof(R) == 4 && (s = ws_get(ctx, "march.ylo", state, &p)) != SWF_OK) return s;
   for (int i = 0; i < 7; ++i) {
     char nm[32];
     std::snprintf(nm, sizeof nm, "march.k%d", i);
@@ -2416,6 +2547,7 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
     return cuda_status(e, "memset M accumulators");
   A.y = (cpx<R>*)py;
   A.T = (cpx<R>*)pT;
+  if ((s = state_low_part<R>(ctx, "march.ylo", state, &A, st)) != SWF_OK) return s;
   {
     StageArgs<R> B = A;  // shapes by timing, as in the plain march
     B.nterm = 6;
@@ -2928,6 +3060,7 @@ static swf_status march_multi_impl(swf_ctx* ctx, const std::vector<MultiGroup>& 
     if ((e = cudaMemsetAsync(py, 0, state, st)) != cudaSuccess) return cuda_status(e, "memset state");
     base[gi].y = (cpx<R>*)py;
     base[gi].T = (cpx<R>*)pT;
+    if ((s = state_low_part<R>(ctx, tag + ".ylo", state, &base[gi], st)) != SWF_OK) return s;
     if (bw) {
       const int n_inst = F / 2;
       const int nt = g.n[0] + g.n[1] + g.n[2];

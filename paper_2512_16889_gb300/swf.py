@@ -49,7 +49,7 @@ EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_sw
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_set_dedupe", "swf_fields_marched",
            "swf_fields_fused", "swf_plan_split",
-           "swf_set_tolerances", "swf_march_stats", "swf_set_multi_grid",
+           "swf_set_tolerances", "swf_march_stats", "swf_set_multi_grid", "swf_device_loop_marches",
            "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
            "swf_mlp_get_params"]
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_set_tolerances.argtypes = [vp, dp, dp]
     lib.swf_march_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     lib.swf_fields_marched.argtypes = [vp, C.POINTER(C.c_longlong)]
+    lib.swf_device_loop_marches.argtypes = [vp, C.POINTER(C.c_longlong)]
     lib.swf_fields_fused.argtypes = [vp, C.POINTER(C.c_longlong)]
     lib.swf_plan_split.argtypes = [ip, ip, ip, C.POINTER(C.c_int)]
     lib.swf_rhs_noalloc.argtypes = [inst_p, ip, ip, dp, vp, vp, vp]
@@ -227,6 +228,12 @@ class Context:
         """Instance groups on different grids sharing a time grid: 0 one after another, 1 together
         when they are small enough (default), 2 always together."""
         _check(_lib.swf_set_multi_grid(self._h, int(mode)))
+
+    def device_loop_marches(self):
+        """Step-size-controlled marches that ran as one graph launch with the attempt loop on the device."""
+        n = C.c_longlong()
+        _check(_lib.swf_device_loop_marches(self._h, C.byref(n)))
+        return n.value
 
     def fields_marched(self):
         n = C.c_longlong()

@@ -317,6 +317,7 @@ def test_bw_step_size_controlled_march_matches_oracle(env):
         got = _amps(res[0])
         if prec == swf.C128:
             assert ctx.march_stats() == (ref["accepted"], ref["rejected"])
+            assert ctx.device_loop_marches() > 0  # decided on the device, one graph launch
         assert abs(got[3] - M) <= tol * abs(M), (prec, got[3], M)
         _check_prob(res[0].prob[0], M, tol)
         for j in range(3):

@@ -587,6 +587,8 @@ def test_step_size_controlled_march_matches_oracle(env):
             torch.cuda.synchronize()
             outs.append(out.cpu().numpy())
             stats = ctx.march_stats()
+            # untimed: the attempt loop runs on the device (one graph launch); timed: host chunks
+            assert ctx.device_loop_marches() == (0 if timed else 1), timed
             ctx.close()
         assert np.array_equal(outs[0], outs[1])
         assert stats == (na, nr), (stats, na, nr)
