@@ -885,11 +885,13 @@ def run_workload(args):
         res, _ = ctx.solve(insts, process, prec)
         times.append(time.perf_counter() - t0)
     t = min(times)
-    ctx.profile_read()  # per-kernel device times of one more solve
-    ctx.profile_enable(True)
-    ctx.solve(insts, process, prec)
-    ctx.profile_enable(False)
-    prof, _ = ctx.profile_read()
+    prof = {}
+    if not args.no_profile:
+        ctx.profile_read()  # per-kernel device times of one more solve
+        ctx.profile_enable(True)
+        ctx.solve(insts, process, prec)
+        ctx.profile_enable(False)
+        prof, _ = ctx.profile_read()
     if args.adaptive:  # site-updates of the accepted steps (the last march's count for every field)
         su = sum(int(np.prod(d["n"])) * ctx.march_stats()[0] * fields for d in ds)
     forms = None
@@ -945,6 +947,8 @@ def main():
     ap.add_argument("--max-steps", type=int, default=0, help="at most this many steps (--workload)")
     ap.add_argument("--adaptive", action="store_true", help="step-size-controlled marches (--workload)")
     ap.add_argument("--epochs", type=int, default=0, help="training epochs (--workload surrogate_spec)")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="skip the extra solve with per-kernel timing (--workload; for long workloads)")
     ap.add_argument("--no-multi-grid", action="store_true",
                     help="march the grid groups one after another (--workload)")
     ap.add_argument("--multi-grid", action="store_true",
