@@ -317,6 +317,45 @@ def accuracy_vs_fp64(ctx, swf, ds, spec32_dev, stream, n_sample=16):
     return {"frac_within_1e-4": float(within.mean()), "table": table, "fp64": fp64}
 
 
+# ------------------------------------------------------------------ the other configurations (bounded samples)
+def other_configs(swf, W):
+    """One timed solve (CUDA events, after a two-step warm-up that sizes the workspace and tunes
+    the launch shapes) of each other workload of the family, each in a fresh context: the single
+    FP64 Schwinger workload in full (128^2, 1000 steps, both marches of the full pair number), the
+    uneven-grid Breit-Wheeler workload on its first 32 instances for 300 of its 2605 steps, and the
+    (3+1)D workload on its 16 instances for 10 of its 2000 steps.  Site-updates/s of each."""
+    import numpy as np
+    import torch
+    out = {}
+    cases = (
+        ("c0_fp64_single_full", [dict(d, flags=("spectrum", "full_n")) for d in W.schwinger_fp64_single()],
+         swf.SCHWINGER, swf.C128, 2, None),
+        ("c2_bw_uneven_32x300", W.bw_uneven()[:32], swf.BREIT_WHEELER, swf.C64, 2, 300),
+        ("c3_3d_16x10", W.schwinger_3d(), swf.SCHWINGER, swf.C64, 1, 10),
+    )
+    for name, ds, process, prec, fields, cap in cases:
+        ds = [dict(d) for d in ds]
+        if cap:
+            for d in ds:
+                frac = cap / d["n_steps"]
+                d["t_in"] = d["t_out"] - frac * (d["t_out"] - d["t_in"])
+                d["n_steps"] = cap
+        insts = [swf.from_workload(d) for d in ds]
+        ctx = swf.Context(0)
+        ctx.solve([swf.from_workload(dict(d, n_steps=2)) for d in ds], process, prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve(insts, process, prec)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        ctx.close()
+        su = sum(int(np.prod(d["n"])) * d["n_steps"] * fields for d in ds)
+        out[name] = {"instances": len(ds), "n_steps": ds[0]["n_steps"], "grids": sorted({d["n"] for d in ds}),
+                     "precision": "complex128" if prec == swf.C128 else "complex64", "s": t,
+                     "site_updates_per_s": su / t}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -393,6 +432,8 @@ def run_gpu(args):
     # accuracy of the complex64 probabilities against it (untimed for the headline value)
     acc = accuracy_vs_fp64(ctx, swf, ds, spec_dev, stream)
 
+    others = other_configs(swf, W) if rank == 0 and not args.no_other_configs else None
+
     # end to end through the host-pointer API (copies of inputs and outputs included)
     e2e_steps = max(1, min(args.steps, 2))
     ctx.solve(insts, swf.SCHWINGER, prec)  # warm the host path once
@@ -462,7 +503,7 @@ def run_gpu(args):
                            "l2": "inputs larger than L2 (2.3 GB working set per GPU)"},
                 "probabilities_per_s": world * probs * args.steps / (ms_max / 1e3),
                 "probabilities_per_s_at_1e-4": world * probs * args.steps / (ms_max / 1e3) * acc["frac_within_1e-4"],
-                "accuracy": acc["table"], "fp64_comparator": acc["fp64"],
+                "accuracy": acc["table"], "fp64_comparator": acc["fp64"], "other_configs": others,
                 "roofline": roof, "fft_flops": alu, "kernels": kernels, "dominant_kernel": dominant,
                 "gpu_launches": int(launches),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_inst * swf.C.sizeof(swf.Instance),
@@ -941,6 +982,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true", help="skip the other workloads' samples")
     ap.add_argument("--small-march", action="store_true", help="one small march for profiler captures")
     ap.add_argument("--workload", default=None, help="time another workload (see run_workload)")
     ap.add_argument("--limit", type=int, default=0, help="at most this many instances (--workload)")
