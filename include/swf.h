@@ -331,6 +331,10 @@ swf_status swf_mlp_gradients(swf_mlp* m, const float* x_dev, const float* y_dev,
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on one batch with learning rate lr. */
 swf_status swf_mlp_train_step(swf_mlp* m, const float* x_dev, const float* y_dev, int B, float lr,
                               float* loss_dev, void* stream);
+/* The network's activation GELU(x) = x Phi(x) and its derivative Phi(x) + x phi(x),
+ * elementwise on n device floats, as the network's kernels evaluate them (erf by Abramowitz and
+ * Stegun's formula 7.1.26, |error| <= 1.5e-7); asynchronous on `stream`. */
+swf_status swf_mlp_activation(const float* x_dev, int n, float* gelu_dev, float* grad_dev, void* stream);
 swf_status swf_mlp_get_params(swf_mlp* m, float* params_host);
 
 #ifdef __cplusplus

@@ -44,9 +44,38 @@ struct EpiArgs {
   const float* zprev;         // DX: pre-activation of the previous layer [M][N]
 };
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// The normal distribution function Phi(x) = (1 + erf(x / sqrt 2)) / 2 and the density phi(x),
+// with erf from Abramowitz and Stegun's formula 7.1.26 (Hastings' rational approximation):
+// erf(z) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) e^{-z^2}, t = 1/(1 + p z), z >= 0,
+// |error| <= 1.5e-7.  One reciprocal, one exponential and five fused multiply-adds; the GELU
+// values it gives are rounded to bfloat16 (8 significand bits) before use, far coarser than it.
+__device__ __forceinline__ void normal_cdf_pdf(float x, float& cdf, float& pdf) {
+  const float z = fabsf(x) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+  const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
+                                      -0.284496736f), 0.254829592f);
+  const float e = __expf(-0.5f * x * x);  // e^{-z^2}
+  const float tail = 0.5f * poly * e;     // (1 - erf(z)) / 2
+  cdf = x >= 0.0f ? 1.0f - tail : tail;
+  pdf = 0.39894228040143268f * e;
+}
+__device__ __forceinline__ float gelu(float x) {
+  float c, d;
+  normal_cdf_pdf(x, c, d);
+  return x * c;
+}
 __device__ __forceinline__ float gelu_grad(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+  float c, d;
+  normal_cdf_pdf(x, c, d);
+  return fmaf(x, d, c);
+}
+
+// The activation and its derivative elementwise (the network's own GELU, for checks).
+__global__ void k_gelu_eval(const float* __restrict__ x, int n, float* __restrict__ g, float* __restrict__ dg) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    g[i] = gelu(x[i]);
+    dg[i] = gelu_grad(x[i]);
+  }
 }
 
 constexpr int TM = 64, TN = 64, TK = 16, SP = 24;  // tile, k step, padded smem row (bf16)
@@ -779,6 +808,16 @@ swf_status swf_mlp_train_step(swf_mlp* m, const float* x_dev, const float* y_dev
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "surrogate update");
+  return SWF_OK;
+}
+
+swf_status swf_mlp_activation(const float* x_dev, int n, float* gelu_dev, float* grad_dev, void* stream) {
+  if (!x_dev || !gelu_dev || !grad_dev || n < 0) { set_error("swf_mlp_activation: invalid arguments"); return SWF_EINVAL; }
+  if (n == 0) return SWF_OK;
+  const int nb = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  k_gelu_eval<<<nb, 256, 0, (cudaStream_t)stream>>>(x_dev, n, gelu_dev, grad_dev);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "swf_mlp_activation");
   return SWF_OK;
 }
 

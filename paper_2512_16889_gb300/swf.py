@@ -51,7 +51,7 @@ EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_sw
            "swf_fields_fused", "swf_plan_split",
            "swf_set_tolerances", "swf_march_stats", "swf_set_multi_grid", "swf_device_loop_marches",
            "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
-           "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
+           "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_activation", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
            "swf_mlp_get_params"]
 
 
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH):
     lib.swf_mlp_gradients.argtypes = [vp, vp, vp, ip, vp, vp, vp]
     lib.swf_mlp_train_step.argtypes = [vp, vp, vp, ip, C.c_float, vp, vp]
     lib.swf_mlp_get_params.argtypes = [vp, fp]
+    lib.swf_mlp_activation.argtypes = [vp, ip, vp, vp, vp]
     lib.swf_profile_read.argtypes = [vp, ip, C.c_char_p, dbl_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
                                      C.POINTER(C.c_longlong)]
     for name in EXPORTS:
@@ -380,6 +381,18 @@ class Surrogate:
         _check(_lib.swf_mlp_create(C.byref(self._h), int(device), p.ctypes.data_as(C.POINTER(C.c_float)),
                                    int(max_batch), n.ctypes.data_as(C.POINTER(C.c_float))))
         self.max_batch = max_batch
+
+    @staticmethod
+    def activation(x, gelu_out, grad_out, stream=None):
+        """swf_mlp_activation: the network's GELU and its derivative on device float tensors."""
+        load_library()
+        for t in (x, gelu_out, grad_out):
+            if t.dtype.itemsize != 4 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("activation: contiguous float32 CUDA tensors")
+        if gelu_out.numel() < x.numel() or grad_out.numel() < x.numel():
+            raise ValueError("activation: outputs shorter than the input")
+        _check(_lib.swf_mlp_activation(C.c_void_p(x.data_ptr()), int(x.numel()), C.c_void_p(gelu_out.data_ptr()),
+                                       C.c_void_p(grad_out.data_ptr()), _stream_ptr(stream)))
 
     @staticmethod
     def param_count():
