@@ -406,8 +406,12 @@ static swf_status premarch_schwinger(swf_ctx* ctx, const swf_instance* inst,
         mg.push_back(MultiGroup{g, (int)fd.size(), fd.data(), out, nullptr, nullptr});
         premarched[k] = out;
       }
-      if ((s = march_fields_multi(ctx, mg, kv.first.t_in, kv.first.t_out, kv.first.n_steps, prec, st)) != SWF_OK)
-        return s;
+      s = march_fields_multi(ctx, mg, kv.first.t_in, kv.first.t_out, kv.first.n_steps, prec, st);
+      if (s == SWF_EUNSUPPORTED) {  // not a form the grouped launch takes: these groups march alone
+        for (size_t i = b; i < e; ++i) premarched.erase(list[i]);
+        continue;
+      }
+      if (s != SWF_OK) return s;
     }
   }
   return SWF_OK;
@@ -607,8 +611,12 @@ static swf_status premarch_bw(swf_ctx* ctx, const swf_instance* inst, const std:
         mg.push_back(MultiGroup{g, 2 * G, fd.data(), psi, ph.data(), (double2*)macc});
         premarched[list[i]] = {psi, macc};
       }
-      if ((s = march_multi(ctx, mg, kv.first.t_in, kv.first.t_out, kv.first.n_steps, prec, 1, st)) != SWF_OK)
-        return s;
+      s = march_multi(ctx, mg, kv.first.t_in, kv.first.t_out, kv.first.n_steps, prec, 1, st);
+      if (s == SWF_EUNSUPPORTED) {  // not a form the grouped launch takes: these groups march alone
+        for (size_t i = b; i < e; ++i) premarched.erase(list[i]);
+        continue;
+      }
+      if (s != SWF_OK) return s;
     }
   }
   return SWF_OK;

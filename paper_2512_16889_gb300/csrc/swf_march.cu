@@ -2885,6 +2885,7 @@ swf_status march_bw_adaptive(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
 // tables, uploaded once before the graph is captured (the slots rotate with period two).
 
 constexpr int kMaxMultiGroups = 8;
+constexpr int kMultiCounters = 128;  // work counters of one step pair (one per grouped launch)
 
 struct MultiPlan {
   int items;                       // work items of the launch
@@ -3224,7 +3225,7 @@ static swf_status march_multi_impl(swf_ctx* ctx, const std::vector<MultiGroup>& 
   }
   void *ptabs = nullptr, *pmd = nullptr, *pcnt = nullptr;
   if ((s = ws_get(ctx, "mg.tables", sizeof(StageArgs<R>) * tab.size(), &ptabs)) != SWF_OK) return s;
-  if ((s = ws_get(ctx, "mg.counters", sizeof(int) * 64, &pcnt)) != SWF_OK) return s;
+  if ((s = ws_get(ctx, "mg.counters", sizeof(int) * kMultiCounters, &pcnt)) != SWF_OK) return s;
   if ((e = cudaMemcpyAsync(ptabs, tab.data(), sizeof(StageArgs<R>) * tab.size(), cudaMemcpyHostToDevice, st)) !=
       cudaSuccess)
     return cuda_status(e, "upload multi-grid tables");
@@ -3259,17 +3260,19 @@ static swf_status march_multi_impl(swf_ctx* ctx, const std::vector<MultiGroup>& 
       }
     }
   };
-  const int per_pair = 2 * 6 * (2 + (int)mids.size() + (bw ? 1 : 0));
-  if (per_pair > 64) {
+  // work counters used per step pair: every stage's passes, and the integrand at stages 2..6
+  const int per_eval = only_x ? 1 : 2 + (int)mids.size();
+  const int per_pair = 2 * (6 * per_eval + (bw ? 5 : 0));
+  if (per_pair > kMultiCounters) {
     set_error("multi-grid march: too many launches per step pair");
     return SWF_EUNSUPPORTED;
   }
   k_clock_set<<<1, 1, 0, st>>>(clk, t_out, h);
-  if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * 64, st)) != cudaSuccess) return cuda_status(e, "reset work queues");
+  if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * kMultiCounters, st)) != cudaSuccess) return cuda_status(e, "reset work queues");
   ci = 0;
   eval(0);  // k_1 = f(t_out, 0) (the integrand of Eq. 17 vanishes at psi_s(t_out) = 0)
   auto pair = [&]() -> swf_status {
-    cudaError_t r = cudaMemsetAsync(cnt, 0, sizeof(int) * 64, st);
+    cudaError_t r = cudaMemsetAsync(cnt, 0, sizeof(int) * kMultiCounters, st);
     if (r != cudaSuccess) return cuda_status(r, "reset work queues");
     ci = 0;
     step(0);
@@ -3278,7 +3281,7 @@ static swf_status march_multi_impl(swf_ctx* ctx, const std::vector<MultiGroup>& 
   };
   if ((s = run_step_pairs(ctx, st, n_steps / 2, clk, pair)) != SWF_OK) return s;
   if (n_steps % 2) {
-    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * 64, st)) != cudaSuccess) return cuda_status(e, "reset work queues");
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * kMultiCounters, st)) != cudaSuccess) return cuda_status(e, "reset work queues");
     ci = 0;
     step(0);
   }

@@ -365,3 +365,31 @@ def test_uneven_grids_share_one_multi_grid_march(env):
     M = ref["M"]
     got = complex(out[True][0][3][6], out[True][0][3][7])  # last precision run: complex128
     assert abs(got - M) <= 1e-10 * abs(M), (got, M)
+
+
+def test_multi_grid_march_on_3d_grids(env):
+    """(3+1)D Breit-Wheeler instances on two grids with one time grid (3 y/z passes and the
+    integrand per stage: the longest launch sequence of a grouped step pair) give bitwise the
+    amplitudes of marching each grid alone, in both precisions."""
+    swf, _ = env
+    c = EDGE_CASES["3d"]
+    perp, par = O.polarisation_basis((0, 0, 1), c["k"])
+    insts = []
+    for n in ((8, 6, 6), (10, 8, 6)):
+        for P in (0.3, -0.2):
+            insts.append(_bw_inst(swf, *c["fld"], n, c["L"], c["t_in"], c["t_out"], 40, (P, 0.2, -0.1), 1,
+                                  (-0.2, 0.1, 0.3), -1, c["k"], par))
+    for prec in (swf.C64, swf.C128):
+        out = {}
+        for mode in (2, 0):
+            ctx = swf.Context(0)
+            ctx.set_multi_grid(mode)
+            ctx.profile_enable(True)
+            ctx.profile_read()
+            res, _ = ctx.solve(insts, swf.BREIT_WHEELER, prec)
+            prof, _ = ctx.profile_read()
+            ctx.close()
+            out[mode] = ([list(r.amp) + list(r.prob) for r in res], prof)
+        assert "k_mid_multi" in out[2][1] and "k_mdot_multi" in out[2][1]
+        assert out[2][0] == out[0][0], prec
+        assert np.all(np.isfinite(out[2][0]))
