@@ -172,6 +172,25 @@ def _check_state_tensors(instance, psi, out, prec):
     return psi.device
 
 
+def _check_device_buffer(name, t, dtype, need, device=None):
+    """A contiguous CUDA tensor of `dtype` holding at least `need` elements (on `device` if given)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} has dtype {t.dtype}; {dtype} is needed")
+    if t.numel() < need:
+        raise ValueError(f"{name} holds {t.numel()} values; {need} are needed")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on {t.device}; this context runs on cuda:{device}")
+
+
+def _grid_points(inst):
+    return int(inst.grid.n[0]) * int(inst.grid.n[1]) * int(inst.grid.n[2])
+
+
 def rhs_noalloc(instance, t, psi, out, bg=0, prec=C64, stream=None):
     """swf_rhs_noalloc: one right-hand-side evaluation without any device allocation (see swf.h),
     on the tensors' device."""
@@ -316,13 +335,23 @@ class Context:
     # -- device buffers (torch tensors), asynchronous on `stream`
     def solve_dev(self, instances, results_dev, spectrum_dev=None, process=SCHWINGER, prec=C64, stream=None,
                   arr=None):
+        import torch
         arr = arr if arr is not None else instance_array(instances)
+        _check_device_buffer("results_dev", results_dev, results_dev.dtype, 0, self.device)
+        if results_dev.numel() * results_dev.element_size() < len(arr) * C.sizeof(Result):
+            raise ValueError(f"results_dev holds fewer than {len(arr)} results")
+        if spectrum_dev is not None:
+            nspec = sum(2 * _grid_points(x) for x in arr if process == SCHWINGER and (x.flags & WANT_SPECTRUM))
+            _check_device_buffer("spectrum_dev", spectrum_dev, torch.float64, nspec, self.device)
         _check(_lib.solve_swf_dev(self._h, len(arr), arr, process, prec, C.c_void_p(results_dev.data_ptr()),
                                   C.c_void_p(spectrum_dev.data_ptr()) if spectrum_dev is not None else None,
                                   _stream_ptr(stream)))
 
     def march_dev(self, instances, psi_out, bg=0, prec=C64, stream=None):
+        import torch
         arr = instance_array(instances)
+        need = sum(8 * _grid_points(x) for x in arr)
+        _check_device_buffer("psi_out", psi_out, torch.float64 if prec == C128 else torch.float32, need, self.device)
         _check(_lib.swf_march_dev(self._h, len(instances), arr, bg, prec, C.c_void_p(psi_out.data_ptr()),
                                   _stream_ptr(stream)))
 
@@ -335,7 +364,14 @@ class Context:
                                 C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
 
     def spectrum_dev(self, instances, psi, c_out=None, prob_out=None, prec=C64, stream=None):
+        import torch
         arr = instance_array(instances)
+        npts = sum(_grid_points(x) for x in arr)
+        _check_device_buffer("psi", psi, torch.float64 if prec == C128 else torch.float32, 8 * npts, self.device)
+        if c_out is not None:
+            _check_device_buffer("c_out", c_out, torch.float64, 4 * npts, self.device)
+        if prob_out is not None:
+            _check_device_buffer("prob_out", prob_out, torch.float64, 2 * npts, self.device)
         _check(_lib.swf_spectrum_dev(self._h, len(instances), arr, prec, C.c_void_p(psi.data_ptr()),
                                      C.c_void_p(c_out.data_ptr()) if c_out is not None else None,
                                      C.c_void_p(prob_out.data_ptr()) if prob_out is not None else None,

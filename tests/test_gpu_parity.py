@@ -206,6 +206,18 @@ def test_validation_errors_are_reported(env):
     # empty input is a no-op
     res, spec = ctx.solve([], swf.SCHWINGER, swf.C64)
     assert len(res) == 0
+    # device buffers too short, of the wrong dtype or not contiguous are refused before any launch
+    inst = [swf.from_workload(d)]
+    N = int(np.prod(d["n"]))
+    with pytest.raises(ValueError, match="needed"):
+        ctx.march_dev(inst, torch.zeros(8 * N - 1, dtype=torch.float32, device="cuda"), prec=swf.C64)
+    with pytest.raises(ValueError, match="dtype"):
+        ctx.march_dev(inst, torch.zeros(8 * N, dtype=torch.float32, device="cuda"), prec=swf.C128)
+    with pytest.raises(ValueError, match="contiguous"):
+        ctx.march_dev(inst, torch.zeros(16 * N, dtype=torch.float32, device="cuda")[::2], prec=swf.C64)
+    with pytest.raises(ValueError, match="needed"):
+        ctx.spectrum_dev(inst, torch.zeros(8 * N, dtype=torch.float64, device="cuda"),
+                         torch.zeros(4 * N - 2, dtype=torch.float64, device="cuda"), prec=swf.C128)
 
 
 def test_workspace_limit_gives_enomem(env):
