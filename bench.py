@@ -172,12 +172,12 @@ def run_reference(args):
     return 0
 
 
-def measured_traffic():
+def measured_traffic(kernel):
     """DRAM bytes (read + write) of one full-size launch of the march kernel from the committed
     ncu counters, or None when the kernel source changed since they were taken."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "k_fused_counters.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", kernel + "_counters.json")) as fh:
             d = json.load(fh)
         with open(os.path.join(ROOT, d["source"]), "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest() != d["source_sha256"]:
@@ -452,15 +452,16 @@ def run_gpu(args):
     dominant = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     S = 32.0
     su_field = 256 * 256 * 1000
-    fused_ms = prof.get("k_fused", (0.0, 0))[0] / args.steps
+    fk = "k_fused3" if "k_fused3" in prof else "k_fused"  # the fused variant the library ran
+    fused_ms = prof.get(fk, (0.0, 0))[0] / args.steps
     fused_su = su_field * fused_fields
     alg_bytes = 14.0 * S * fused_su
     achieved = alg_bytes / (fused_ms / 1e3) / 1e9 if fused_ms > 0 else None
-    march = {k: v for k, v in prof.items() if k in ("k_first", "k_mid", "k_last", "k_fused")}
-    roof = {"bound": "hbm", "kernel": "k_fused (one launch per solve)",
+    march = {k: v for k, v in prof.items() if k in ("k_first", "k_mid", "k_last", fk)}
+    roof = {"bound": "hbm", "kernel": fk + " (one launch per solve)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm if achieved else None, "traffic": measured_traffic(),
-            "peak_kind": peak_kind + " (burst copy)", "launches_per_step": prof.get("k_fused", (0, 0))[1] / args.steps,
+            "frac": achieved / hbm if achieved else None, "traffic": measured_traffic(fk),
+            "peak_kind": peak_kind + " (burst copy)", "launches_per_step": prof.get(fk, (0, 0))[1] / args.steps,
             "algorithmic_bytes_per_launch": alg_bytes, "fields_per_launch": fused_fields,
             "fields_on_pass_kernels": n_inst - fused_fields,
             "whole_march_frac": 14.0 * S * site_updates / (ms_step / 1e3) / 1e9 / hbm}
@@ -959,14 +960,20 @@ def run_workload(args):
 
 
 def run_small_march(args):
-    """One small march for profiler captures: 14 instances (28 sectors) of the batched workload,
-    20 steps, complex64, through swf_march_dev."""
+    """One march for profiler captures, complex64, through swf_march_dev: 14 instances (28
+    sectors) of the batched workload for 20 steps (--small-march), or all 128 instances for the
+    full 1000 steps in one fused launch with no fields on the pass kernels (--fused-march)."""
     import torch
     from paper_2512_16889_gb300 import build, swf
     from paper_2512_16889_gb300 import workloads as W
     build.build()
     ctx = swf.Context(0)
-    ds = W.schwinger_batched(n_steps=20, t_window=0.4)[:14]
+    if args.fused_march:
+        ctx.set_dedupe(False)
+        ctx.set_march_path(2)
+        ds = W.schwinger_batched()
+    else:
+        ds = W.schwinger_batched(n_steps=20, t_window=0.4)[:14]
     out = torch.zeros(len(ds) * 8 * 256 * 256, dtype=torch.float32, device="cuda")
     ctx.march_dev([swf.from_workload(d) for d in ds], out, bg=0, prec=swf.C64)
     torch.cuda.synchronize()
@@ -984,6 +991,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true", help="skip the other workloads' samples")
     ap.add_argument("--small-march", action="store_true", help="one small march for profiler captures")
+    ap.add_argument("--fused-march", action="store_true",
+                    help="the benchmark's march as one fused launch, for profiler captures at full size")
     ap.add_argument("--workload", default=None, help="time another workload (see run_workload)")
     ap.add_argument("--limit", type=int, default=0, help="at most this many instances (--workload)")
     ap.add_argument("--max-steps", type=int, default=0, help="at most this many steps (--workload)")
@@ -998,7 +1007,7 @@ def main():
     ap.add_argument("--bw-partial", action="store_true",
                     help="partial-integration form of the Breit-Wheeler terms (--workload bw_uneven)")
     args = ap.parse_args()
-    if args.small_march:
+    if args.small_march or args.fused_march:
         return run_small_march(args)
     if args.workload == "surrogate":
         return run_surrogate(args)

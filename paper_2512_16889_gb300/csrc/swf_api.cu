@@ -875,10 +875,10 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
 }
 
 swf_status swf_set_march_path(swf_ctx* ctx, int path) {
-  if (!ctx || path < 0 || path > 3) { set_error("swf_set_march_path: ctx NULL or path not in 0..3"); return SWF_EINVAL; }
+  if (!ctx || path < 0 || path > 5) { set_error("swf_set_march_path: ctx NULL or path not in 0..5"); return SWF_EINVAL; }
   ctx->use_fused = path != 1;
   ctx->sm_split = path == 0;
-  ctx->fused_variant = path >= 2 ? path - 1 : 1;
+  ctx->fused_variant = path == 3 ? 2 : path == 4 ? 1 : path == 5 ? 3 : kDefaultFusedVariant;
   return SWF_OK;
 }
 

@@ -994,6 +994,532 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
   if (warp == 0) tmem_dealloc(tbase, 256);
 }
 
+// ------------------------------------------------------------------ asynchronous-transpose variant
+// The two transposes of an evaluation are pushed by the bulk-copy engine (cp.async.bulk from this
+// CTA's shared memory to a peer's, completing on the peer's mbarrier) instead of being pulled by
+// the threads, and the threads meanwhile do the work that needs no transposed data: the local
+// term of the stage while the forward transpose is in flight, and all but the newest term of the
+// next stage combine while the backward one is.  The arithmetic is that of `k_fused`, in the same
+// order; only the data movement differs.
+//
+// Both exchange buffers are 2 x 16 chunks of 16 x 16 values: chunk (c, a) of component c holds, in
+// the row buffer X1, the 16 rows of this CTA at x in [16 a, 16 a + 16), and in the column buffer
+// X2, the 16 columns of this CTA at y in [16 a, 16 a + 16).  Chunk (c, s) of one CTA is exactly
+// chunk (c, rank) of CTA s after the transpose, so each transpose is 32 contiguous 2 KB copies per
+// CTA.  Inside a chunk, row b keeps its 16 values at positions d ^ b (an XOR swizzle written by the
+// producer and kept by the copy), so that every FFT pass reads and writes without bank conflicts.
+//
+// Ordering.  Each CTA arms its receive barrier for a transpose before it arrives at the cluster
+// barrier that lets the senders start, and arrives only after its previous receive completed; a
+// sender waits at that cluster barrier before it copies.  So every copy finds its destination free
+// (all copies of the previous use, and the receiver's reads, are complete) and its barrier armed.
+// Every wait is bounded: a CTA whose copies do not arrive in about half a second stops copying
+// and waiting, keeps to the cluster barriers (so that no peer is left waiting there), and writes
+// NaN for its rows of the sector, so that the failure shows in the result.
+namespace v3 {
+constexpr int CHK = 256;                    // complex values in one chunk
+constexpr int NBUF = 2 * CL * CHK;          // complex values in one exchange buffer
+constexpr uint32_t XBYTES = NBUF * 8;       // bytes received per transpose
+constexpr int OFF_X1 = 0;                   // rows, chunk (c, x / 16), row, x % 16
+constexpr int OFF_X2 = OFF_X1 + NBUF * 8;   // columns, chunk (c, y / 16), y % 16, column
+constexpr int OFF_Y3 = OFF_X2 + NBUF * 8;   // state y [2][RB][NX]
+constexpr int OFF_TW3 = OFF_Y3 + NSL * 8;
+constexpr int OFF_EX3 = OFF_TW3 + 256 * 8;
+constexpr int OFF_GX3 = OFF_EX3 + NX * 8;
+constexpr int OFF_EY3 = OFF_GX3 + NX * 4;
+constexpr int OFF_GY3 = OFF_EY3 + RB * 8;
+constexpr int OFF_KX3 = OFF_GY3 + RB * 4;
+constexpr int OFF_KY3 = OFF_KX3 + NX * 4;
+constexpr int OFF_MISC3 = OFF_KY3 + NY * 4;
+constexpr int OFF_BAR3 = OFF_MISC3 + 7 * RB * 4 + 7 * 8 + 16 + 16;  // two mbarriers
+constexpr int SMEM3 = OFF_BAR3 + 16;
+constexpr long long WAIT3 = 1ll << 30;  // cycles before a receive wait gives up
+static_assert(OFF_BAR3 % 8 == 0, "mbarrier alignment");
+static_assert(OFF_X2 % 16 == 0 && OFF_X1 % 16 == 0, "bulk-copy alignment");
+static_assert(SMEM3 <= 227 * 1024, "shared memory");
+}  // namespace v3
+
+// position of value (c, a, b, d) in an exchange buffer: chunk (c, a), row b, column d ^ b
+__host__ __device__ __forceinline__ int q3(int c, int a, int b, int d) {
+  return ((((c << 4) + a) << 4) + b) * 16 + (d ^ b);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// the address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void bulk_push(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst),
+               "r"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init3(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arm3(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// waits for the phase of the given parity to complete; false after WAIT3 cycles
+__device__ __forceinline__ bool mbar_wait3(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > v3::WAIT3) return false;
+  }
+}
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+// generic-proxy writes of this thread become visible to the bulk-copy engine
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 256-point FFTs of the 32 rows (both components) of X1 along x, in place, the same two radix-16
+// passes as fft256_lines.  Pass 1: thread (c, row, j) transforms x = 16 n1 + j; pass 2: thread
+// (c, jj, row) transforms x = 16 jj + n2 and writes x = jj + 16 k2.  The caller synchronises after.
+template <bool INV>
+__device__ __forceinline__ void fft_rows3(float2* X, const float2* tw) {
+  const int t = threadIdx.x, c = t >> 8;
+  float2 a[16];
+  {
+    const int row = (t >> 4) & 15, j = t & 15;
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) a[n1] = X[q3(c, n1, row, j)];
+    dft16<INV>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+      const float2 w = tw[(j * k1) & 255];
+      a[k1] = INV ? cmulc(a[k1], w) : cmul(a[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, row, j)] = a[k1];
+  }
+  __syncthreads();
+  const int jj = (t >> 4) & 15, row = t & 15;
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, jj, row, n2)];
+  dft16<INV>(a);
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) X[q3(c, k2, row, jj)] = a[k2];
+}
+
+// The same along y for the 32 columns of X2: thread (c, j, col), y = 16 n1 + j, then y = 16 j + n2
+// written to y = j + 16 k2.  The caller synchronises after.
+template <bool INV>
+__device__ __forceinline__ void fft_cols3(float2* X, const float2* tw) {
+  const int t = threadIdx.x, c = t >> 8, j = (t >> 4) & 15, col = t & 15;
+  float2 a[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) a[n1] = X[q3(c, n1, j, col)];
+  dft16<INV>(a);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) {
+    const float2 w = tw[(j * k1) & 255];
+    a[k1] = INV ? cmulc(a[k1], w) : cmul(a[k1], w);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, j, col)] = a[k1];
+  __syncthreads();
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, j, n2, col)];
+  dft16<INV>(a);
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) X[q3(c, k2, j, col)] = a[k2];
+}
+
+// the two sites (x, x + 1) of row r, component c (x even): one aligned float4 of X1, in site
+// order for even r and swapped for odd r (the swizzle exchanges neighbours)
+__device__ __forceinline__ float4 row_pair_ld(const float2* X1, int c, int r, int x) {
+  const float4 v = *reinterpret_cast<const float4*>(X1 + (q3(c, x >> 4, r, x & 15) & ~1));
+  return (r & 1) ? make_float4(v.z, v.w, v.x, v.y) : v;
+}
+__device__ __forceinline__ void row_pair_st(float2* X1, int c, int r, int x, float4 v) {
+  if (r & 1) v = make_float4(v.z, v.w, v.x, v.y);
+  *reinterpret_cast<float4*>(X1 + (q3(c, x >> 4, r, x & 15) & ~1)) = v;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
+  using namespace v3;
+  extern __shared__ __align__(16) unsigned char sm[];
+  float2* X1 = reinterpret_cast<float2*>(sm + OFF_X1);
+  float2* X2 = reinterpret_cast<float2*>(sm + OFF_X2);
+  float2* Ys = reinterpret_cast<float2*>(sm + OFF_Y3);
+  float2* tw = reinterpret_cast<float2*>(sm + OFF_TW3);
+  float2* ex = reinterpret_cast<float2*>(sm + OFF_EX3);
+  float* gx = reinterpret_cast<float*>(sm + OFF_GX3);
+  float2* ey = reinterpret_cast<float2*>(sm + OFF_EY3);
+  float* gy = reinterpret_cast<float*>(sm + OFF_GY3);
+  float* kxt = reinterpret_cast<float*>(sm + OFF_KX3);
+  float* kyt = reinterpret_cast<float*>(sm + OFF_KY3);
+  float* s_ft = reinterpret_cast<float*>(sm + OFF_MISC3);
+  float2* s_tf = reinterpret_cast<float2*>(sm + OFF_MISC3 + 7 * RB * 4);
+  float2* s_w = reinterpret_cast<float2*>(sm + OFF_MISC3 + 7 * RB * 4 + 56);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + OFF_MISC3 + 7 * RB * 4 + 72);
+  const uint32_t bar_f = smem_u32(sm + OFF_BAR3), bar_b = bar_f + 8;
+  const uint32_t x1a = smem_u32(X1), x2a = smem_u32(X2);
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int cid = blockIdx.x / CL;
+  const int ncl = gridDim.x / CL;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int row0 = rank * RB;
+  const size_t plane = (size_t)NX * NY;
+  float2* slot = A.slots + (size_t)cid * 4 * 2 * plane;
+  float2* ylo = slot + (size_t)3 * 2 * plane;
+  if (warp == 0) {
+    tmem_alloc(s_tmem, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init3(bar_f, 1);
+    mbar_init3(bar_b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int m = tid; m < 256; m += NT) {
+    double s, c;
+    sincospi(-2.0 * m / 256.0, &s, &c);
+    tw[m] = make_float2((float)c, (float)s);
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *s_tmem;
+  const uint32_t tme = tbase + (((uint32_t)(32 * (warp & 3))) << 16) + 32 * (warp >> 2);
+  const uint32_t tstash = tme + 128 * 3;
+  if (tid == 0) mbar_arm3(bar_f, XBYTES);  // the first forward transpose
+  cl_arrive();                             // barriers initialised and armed
+  uint32_t par_f = 0, par_b = 0;
+  bool err = false;
+  // lane L of warp 0 copies chunk (L / 16, peer) to peer (rank + L) % 16
+  const int cc = lane >> 4, peer = (rank + (lane & 15)) & (CL - 1);
+
+  const double dxx = A.Lx / NX, dyy = A.Ly / NY;
+  const float inv_n = 1.0f / (float)(NX * NY);
+  const double DPc[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
+  const double DPa[7][6] = {{0, 0, 0, 0, 0, 0},
+                            {0.2, 0, 0, 0, 0, 0},
+                            {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+                            {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+                            {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+                            {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+                            {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+
+  for (int si = cid; si < A.n_sec; si += ncl) {
+    const Sector S = A.sec[si];
+    const FieldDesc& F = A.fd[S.inst];
+    for (int i = tid; i < NX; i += NT) {
+      const double xc = -0.5 * A.Lx + i * dxx;
+      gx[i] = (float)axis_factor(F, 0, xc);
+      double s, c;
+      sincos(F.pmom[0] * xc, &s, &c);
+      ex[i] = make_float2((float)c, (float)s);
+    }
+    if (tid < RB) {
+      const double yc = -0.5 * A.Ly + (row0 + tid) * dyy;
+      gy[tid] = (float)axis_factor(F, 1, yc);
+      double s, c;
+      sincos(F.pmom[1] * yc, &s, &c);
+      ey[tid] = make_float2((float)c, (float)s);
+    }
+    for (int i = tid; i < NX; i += NT) kxt[i] = (float)(6.283185307179586476925286766559 * (i < NX / 2 ? i : i - NX) / A.Lx);
+    for (int i = tid; i < NY; i += NT)
+      kyt[i] = (float)(S.sigma * 6.283185307179586476925286766559 * (i < NY / 2 ? i : i - NY) / A.Ly);
+    if (tid < 2) {
+      const int c = tid == 0 ? S.c0 : S.c1;
+      s_w[tid] = make_float2((float)F.w[2 * c], (float)F.w[2 * c + 1]);
+    }
+    // y = 0, its low part 0, and the first stage value Y = y = 0 in X1 and in the stash
+    for (int i = tid; i < NSL; i += NT) Ys[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < NBUF; i += NT) X1[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < NSL; i += NT) {
+      const int comp = i / (RB * NX), rem = i % (RB * NX);
+      __stcg(ylo + comp * plane + (size_t)row0 * NX + rem, make_float2(0.f, 0.f));
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) tmem_st8(tstash + 8 * m, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f));
+    tmem_wait_st();
+    __syncthreads();
+
+    const int n_eval = 1 + 6 * A.n_steps;
+    for (int ev = 0; ev < n_eval; ++ev) {
+      const int step = ev == 0 ? 0 : (ev - 1) / 6;
+      const int stage = ev == 0 ? 0 : 1 + (ev - 1) % 6;
+      if (ev == 0 || stage == 1) {
+        const int st0 = ev == 0 ? 0 : 1, nst = ev == 0 ? 1 : 6;
+        if (F.kind == SWF_FIELD_PULSE_GAUSS) {
+          if (tid < nst * RB) {
+            const int si2 = st0 + tid / RB, r = tid % RB;
+            const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+            const double yc = -0.5 * A.Ly + (row0 + r) * dyy;
+            s_ft[si2 * RB + r] = (float)time_factor(F, ts, yc);
+          } else if (tid >= 128 && tid < 128 + nst) {
+            const int si2 = st0 + tid - 128;
+            const double ts = A.t_out + step * A.h + DPc[si2] * A.h;
+            double s, c;
+            sincos(F.tsign * F.e0 * ts, &s, &c);
+            s_tf[si2] = make_float2((float)c, (float)s);
+          }
+        } else if (tid < nst * RB) {
+          const int si2 = st0 + tid / RB, r = tid % RB;
+          const float4 e = __ldg(A.ttab + ((size_t)S.inst * A.n_steps + step) * 7 + si2);
+          s_ft[si2 * RB + r] = e.x;
+          if (r == 0) s_tf[si2] = make_float2(e.y, e.z);
+        }
+        __syncthreads();
+      }
+
+      // ---- forward x-FFT of the stage value Y (in X1), then push chunk (c, s) to CTA s
+      fft_rows3<false>(X1, tw);
+      fence_async_smem();
+      __syncthreads();
+      cl_wait();  // every CTA's X2 is free and its receive barrier armed
+      if (warp == 0 && !err)
+        bulk_push(peer_addr(x2a + (uint32_t)((cc * CL + rank) * CHK * 8), peer),
+                  x1a + (uint32_t)((cc * CL + peer) * CHK * 8), CHK * 8, peer_addr(bar_f, peer));
+
+      // ---- meanwhile: local term Z = -i V (Y + psi_b) of this stage, from the stash (Y) to the stash
+      {
+        const float2 tf = s_tf[stage];
+        const float* ftr = s_ft + stage * RB;
+        const float2 w0 = s_w[0], w1 = s_w[1];
+#pragma unroll 2
+        for (int m = 0; m < 4; ++m) {
+          const int sp = tid + NT * m;
+          const int r = sp >> 7;
+          const int x = (sp & 127) * 2;
+          float4 y0, y1;
+          tmem_ld8(tstash + 8 * m, y0, y1);
+          const float ft = ftr[r];
+          const float2 phy = cmul(tf, ey[r]);
+          float4 z0, z1;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float2 ph = cmul(phy, ex[x + e]);
+            const float a = ft * gy[r] * gx[x + e];
+            const float2 p0 = (e ? make_float2(y0.z, y0.w) : make_float2(y0.x, y0.y)) + cmul(w0, ph);
+            const float2 p1 = (e ? make_float2(y1.z, y1.w) : make_float2(y1.x, y1.y)) + cmul(w1, ph);
+            float2 v0, v1;
+            sector_v(F.acomp, S.sigma, a, p0, p1, v0, v1);
+            v0 = rot<false>(v0);
+            v1 = rot<false>(v1);
+            if (e) { z0.z = v0.x; z0.w = v0.y; z1.z = v1.x; z1.w = v1.y; }
+            else { z0.x = v0.x; z0.y = v0.y; z1.x = v1.x; z1.y = v1.y; }
+          }
+          tmem_st8(tstash + 8 * m, z0, z1);
+        }
+        tmem_wait_st();
+      }
+      {
+        int bad = 0;
+        if (tid == 0 && !err) {
+          bad = !mbar_wait3(bar_f, par_f);
+          if (!bad) mbar_arm3(bar_b, XBYTES);  // for the backward transpose of this evaluation
+        }
+        err = __syncthreads_or(bad) || err;
+        par_f ^= 1u;
+      }
+      cl_arrive();  // the forward copies into this CTA are complete
+
+      // ---- columns: forward y-FFT, -i H0(kappa)/N per mode, inverse y-FFT; push chunk (c, s) back
+      fft_cols3<false>(X2, tw);
+      __syncthreads();
+      {
+#pragma unroll 2
+        for (int m = tid; m < CB * NY; m += NT) {
+          const int col = m & 15, iy = m >> 4;
+          const float kx = kxt[rank * CB + col];
+          const float ky = kyt[iy];
+          float2* pa = X2 + q3(0, iy >> 4, iy & 15, col);
+          float2* pb = X2 + q3(1, iy >> 4, iy & 15, col);
+          const float2 a = *pa, b = *pb;
+          const float2 h0 = make_float2(a.x + kx * b.x + ky * b.y, a.y + kx * b.y - ky * b.x);
+          const float2 h1 = make_float2(kx * a.x - ky * a.y - b.x, kx * a.y + ky * a.x - b.y);
+          *pa = scl(inv_n, rot<false>(h0));
+          *pb = scl(inv_n, rot<false>(h1));
+        }
+      }
+      __syncthreads();
+      fft_cols3<true>(X2, tw);
+      fence_async_smem();
+      __syncthreads();
+      cl_wait();  // every CTA's X1 is free and its receive barrier armed
+      if (warp == 0 && !err)
+        bulk_push(peer_addr(x1a + (uint32_t)((cc * CL + rank) * CHK * 8), peer),
+                  x2a + (uint32_t)((cc * CL + peer) * CHK * 8), CHK * 8, peer_addr(bar_b, peer));
+
+      // ---- meanwhile: the next stage combine without its newest term, P = y + h sum_{j < new} a_j k_j
+      // (h sum b_j k_j without y before the last stage), in the order of k_fused
+      const bool has_next = ev + 1 < n_eval;
+      const int nxt = stage == 6 ? 1 : stage + 1;  // the next stage (stage 0 is followed by 1)
+      const int jn = nxt - 1;                      // index of the newest k (the one computed now)
+      const bool nlast = nxt == 6;
+      float4 P0[4], P1[4];
+      if (has_next) {
+        const int ntp = jn < 3 ? jn : 3;  // tensor-memory terms before the newest
+        float ct[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) ct[j] = (j < ntp) ? (float)(A.h * DPa[nxt][j]) : 0.f;
+        float coef[3];
+        const float2* kin[3];
+        int nterm = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          coef[j] = 0.f;
+          kin[j] = slot;
+        }
+#pragma unroll
+        for (int j = 3; j < 5; ++j) {
+          if (j < jn && DPa[nxt][j] != 0.0) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q == nterm) {
+                coef[q] = (float)(A.h * DPa[nxt][j]);
+                kin[q] = slot + (size_t)(j - 3) * 2 * plane;
+              }
+            ++nterm;
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int sp = tid + NT * m;
+          const int r = sp >> 7;
+          const int x = (sp & 127) * 2;
+          const size_t g0 = (size_t)(row0 + r) * NX + x;
+          float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = y0;
+          if (!nlast) {
+            y0 = *reinterpret_cast<const float4*>(Ys + r * NX + x);
+            y1 = *reinterpret_cast<const float4*>(Ys + RB * NX + r * NX + x);
+          }
+          if (ntp > 0) {
+            uint32_t tr[3][8];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+              if (j < ntp) tmem_ld8_nowait(tme + 128 * j + 8 * m, tr[j]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              if (j < ntp) {
+                const float2 c = make_float2(ct[j], ct[j]);
+                fma4(c, make_float4(__uint_as_float(tr[j][0]), __uint_as_float(tr[j][1]), __uint_as_float(tr[j][2]),
+                                    __uint_as_float(tr[j][3])), y0);
+                fma4(c, make_float4(__uint_as_float(tr[j][4]), __uint_as_float(tr[j][5]), __uint_as_float(tr[j][6]),
+                                    __uint_as_float(tr[j][7])), y1);
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            if (q < nterm) {
+              const float4 k0 = __ldcg(reinterpret_cast<const float4*>(kin[q] + g0));
+              const float4 k1 = __ldcg(reinterpret_cast<const float4*>(kin[q] + plane + g0));
+              const float2 c = make_float2(coef[q], coef[q]);
+              fma4(c, k0, y0);
+              fma4(c, k1, y1);
+            }
+          }
+          P0[m] = y0;
+          P1[m] = y1;
+        }
+      }
+      {
+        int bad = 0;
+        if (tid == 0 && !err) {
+          bad = !mbar_wait3(bar_b, par_b);
+          if (!bad) mbar_arm3(bar_f, XBYTES);  // for the next forward transpose
+        }
+        err = __syncthreads_or(bad) || err;
+        par_b ^= 1u;
+      }
+      cl_arrive();  // the backward copies into this CTA are complete
+
+      // ---- inverse x-FFT; k = (that) + Z; the next stage value Y' = P + h a_new k
+      fft_rows3<true>(X1, tw);
+      __syncthreads();
+      {
+        const int oslab = stage == 0 || stage == 6 ? 0 : (stage <= 2 ? stage : -1);
+        float2* kout = slot + (size_t)(stage >= 3 && stage <= 5 ? stage - 3 : 0) * 2 * plane;
+        const bool use_new = jn < 3 || DPa[nxt][jn] != 0.0;
+        const float cnv = (float)(A.h * DPa[nxt][jn]);
+        const float2 cn = make_float2(cnv, cnv);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int sp = tid + NT * m;
+          const int r = sp >> 7;
+          const int x = (sp & 127) * 2;
+          const size_t g0 = (size_t)(row0 + r) * NX + x;
+          float4 z0, z1;
+          tmem_ld8(tstash + 8 * m, z0, z1);
+          const float4 wa0 = row_pair_ld(X1, 0, r, x);
+          const float4 wa1 = row_pair_ld(X1, 1, r, x);
+          const float4 o0 = make_float4(wa0.x + z0.x, wa0.y + z0.y, wa0.z + z0.z, wa0.w + z0.w);
+          const float4 o1 = make_float4(wa1.x + z1.x, wa1.y + z1.y, wa1.z + z1.z, wa1.w + z1.w);
+          if (oslab >= 0) {
+            tmem_st8(tme + 128 * oslab + 8 * m, o0, o1);
+          } else {
+            __stcg(reinterpret_cast<float4*>(kout + g0), o0);
+            __stcg(reinterpret_cast<float4*>(kout + plane + g0), o1);
+          }
+          if (has_next) {
+            float4 y0 = P0[m], y1 = P1[m];
+            if (use_new) {
+              fma4(cn, o0, y0);
+              fma4(cn, o1, y1);
+            }
+            if (nlast) {
+              // y_new = y + h sum_j b_j k_j in float-float
+              const float4 yh0 = *reinterpret_cast<const float4*>(Ys + r * NX + x);
+              const float4 yh1 = *reinterpret_cast<const float4*>(Ys + RB * NX + r * NX + x);
+              float4 l0 = __ldcg(reinterpret_cast<const float4*>(ylo + g0));
+              float4 l1 = __ldcg(reinterpret_cast<const float4*>(ylo + plane + g0));
+              ff_add(yh0.x, l0.x, y0.x); ff_add(yh0.y, l0.y, y0.y); ff_add(yh0.z, l0.z, y0.z); ff_add(yh0.w, l0.w, y0.w);
+              ff_add(yh1.x, l1.x, y1.x); ff_add(yh1.y, l1.y, y1.y); ff_add(yh1.z, l1.z, y1.z); ff_add(yh1.w, l1.w, y1.w);
+              __stcg(reinterpret_cast<float4*>(ylo + g0), l0);
+              __stcg(reinterpret_cast<float4*>(ylo + plane + g0), l1);
+              *reinterpret_cast<float4*>(Ys + r * NX + x) = y0;
+              *reinterpret_cast<float4*>(Ys + RB * NX + r * NX + x) = y1;
+            }
+            row_pair_st(X1, 0, r, x, y0);
+            row_pair_st(X1, 1, r, x, y1);
+            tmem_st8(tstash + 8 * m, y0, y1);
+          }
+        }
+        tmem_wait_st();
+      }
+      __syncthreads();
+    }
+    // psi(t_in) of the sector into the 4-component output (NaN if a transpose failed)
+    float2* out0 = A.psi_out + ((size_t)S.inst * 4 + S.c0) * plane + (size_t)row0 * NX;
+    float2* out1 = A.psi_out + ((size_t)S.inst * 4 + S.c1) * plane + (size_t)row0 * NX;
+    const float2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+    for (int i = tid; i < RB * NX; i += NT) {
+      out0[i] = err ? nan2 : Ys[i];
+      out1[i] = err ? nan2 : Ys[RB * NX + i];
+    }
+    __syncthreads();
+  }
+  if (err) {  // let copies that were still under way land before the cluster lets this CTA go
+    const long long t0 = clock64();
+    while (clock64() - t0 < 20000000ll) {
+    }
+  }
+  cl_wait();  // every copy of the last transposes is complete
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 512);
+}
+
 }  // namespace fused
 
 // True when the fused kernel covers this march: (2+1)D 256 x 256 grid, complex64, no
@@ -1008,14 +1534,14 @@ bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_preci
   return true;
 }
 
-static int g_fused_clusters[64][2];  // per device and variant: resident clusters + 1 (0: not set up)
+static int g_fused_clusters[64][3];  // per device and variant: resident clusters + 1 (0: not set up)
 
 // Kernel attributes and the number of clusters that can be resident at once (cached per device).
 static swf_status fused_setup(int var, cudaStream_t st) {
   using namespace fused;
-  void (*kern)(Args) = var ? k_fused2 : k_fused;
-  const int nthr = var ? v2::NT2 : NT;
-  const int smem = var ? v2::SMEM2 : SMEM;
+  void (*kern)(Args) = var == 2 ? k_fused3 : var == 1 ? k_fused2 : k_fused;
+  const int nthr = var == 1 ? v2::NT2 : NT;
+  const int smem = var == 2 ? v3::SMEM3 : var == 1 ? v2::SMEM2 : SMEM;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return cuda_status(e, "cluster size attribute");
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1040,7 +1566,7 @@ static swf_status fused_setup(int var, cudaStream_t st) {
 }
 
 int fused_resident_clusters(swf_ctx* ctx) {
-  const int var = ctx->fused_variant == 2 ? 1 : 0;
+  const int var = ctx->fused_variant - 1;
   if (g_fused_clusters[dev_slot()][var] == 0 && fused_setup(var, ctx->stream) != SWF_OK) return 0;
   return g_fused_clusters[dev_slot()][var] - 1;
 }
@@ -1050,13 +1576,15 @@ int fused_resident_clusters(swf_ctx* ctx) {
 // concurrently on those SMs, shortens the march when they finish within the fused kernel's
 // time.  With R = ceil(2 n_f / ncl) rounds of sectors per cluster, removing r rounds leaves
 // n_1 = floor((R - r) ncl / 2) fields to the clusters and n_2 = n_f - n_1 to the pass kernels,
-// which take about alpha n_2 rounds' time on the free SMs: alpha = 2.0 measured with 40 free SMs
-// on (2+1)D 256^2 complex64 marches (16 fields on the free SMs took as long as 32 fused rounds),
-// scaled by 40 / (free SMs).  The largest r with alpha n_2 <= R - r is taken.
-int fused_split_count(int n_f, int ncl, int n_sm) {
+// which take about alpha n_2 rounds' time on the free SMs.  alpha was measured with 40 free SMs
+// on (2+1)D 256^2 complex64 marches: 16 fields on the free SMs took as long as 32 rounds of the
+// kernel with pulled transposes (alpha = 2.0); a round of the kernel with pushed transposes is
+// 1.31 times shorter (alpha = 2.62).  alpha scales with 40 / (free SMs).  The largest r with
+// alpha n_2 <= R - r is taken.
+int fused_split_count(int n_f, int ncl, int n_sm, int variant) {
   const int free_sm = n_sm - fused::CL * ncl;
   if (ncl < 1 || free_sm < 16 || n_f < 16) return 0;
-  const double alpha = 2.0 * 40.0 / free_sm;
+  const double alpha = (variant == 3 ? 2.62 : 2.0) * 40.0 / free_sm;
   const int R = (2 * n_f + ncl - 1) / ncl;
   int best = 0;
   for (int r = 1; r < R; ++r) {
@@ -1072,11 +1600,11 @@ int fused_split_count(int n_f, int ncl, int n_sm) {
 swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
                        const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
   using namespace fused;
-  const int var = ctx->fused_variant == 2 ? 1 : 0;
-  void (*kern)(Args) = var ? k_fused2 : k_fused;
-  const int nthr = var ? v2::NT2 : NT;
-  const int smem = var ? v2::SMEM2 : SMEM;
-  const int narr = var ? 7 : 4;
+  const int var = ctx->fused_variant - 1;
+  void (*kern)(Args) = var == 2 ? k_fused3 : var == 1 ? k_fused2 : k_fused;
+  const int nthr = var == 1 ? v2::NT2 : NT;
+  const int smem = var == 2 ? v3::SMEM3 : var == 1 ? v2::SMEM2 : SMEM;
+  const int narr = var == 1 ? 7 : 4;
   cudaError_t e;
   auto config = [&](int ncl, cudaLaunchAttribute* at) {
     cudaLaunchConfig_t cfg = {};
@@ -1144,7 +1672,7 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
   cudaLaunchAttribute at;
   cudaLaunchConfig_t cfg = config(ncl, &at);
   {
-    ProfScope ps(ctx, "k_fused", st);
+    ProfScope ps(ctx, var == 2 ? "k_fused3" : var == 1 ? "k_fused2" : "k_fused", st);
     e = cudaLaunchKernelEx(&cfg, kern, A);
   }
   if (e != cudaSuccess) return cuda_status(e, "launch fused march");
@@ -1152,6 +1680,5 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
   return SWF_OK;
 }
 
-int fused_clusters() { return g_fused_clusters[dev_slot()][0] - 1; }
 
 }  // namespace swf

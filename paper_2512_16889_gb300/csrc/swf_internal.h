@@ -113,6 +113,10 @@ struct TuneCache {
 };
 }  // namespace swf
 
+// Fused kernel of march paths 0 and 2: 1 = threads pull the transposes through distributed
+// shared memory (k_fused), 3 = the bulk-copy engine pushes them while the threads compute (k_fused3).
+constexpr int kDefaultFusedVariant = 3;
+
 struct swf_ctx {
   int device;
   cudaStream_t stream;
@@ -130,7 +134,7 @@ struct swf_ctx {
   int multi_grid = 1;            // grid groups sharing a time grid in one launch sequence: 0 never, 1 auto, 2 always
   long long multi_marches = 0;   // multi-grid marches run since the context's creation
   long long device_loop_marches = 0;  // step-size-controlled marches decided entirely on the device
-  int fused_variant = 1;  // 1: one CTA per SM, 2: two CTAs per SM
+  int fused_variant = kDefaultFusedVariant;  // 1: pulled transposes, 2: two CTAs per SM, 3: pushed
   bool sm_split = true;   // automatic path: pass kernels on the SMs the fused clusters leave free
   cudaStream_t aux = nullptr;            // stream of that concurrent pass-kernel march (lazy)
   cudaEvent_t aux_ev[2] = {nullptr, nullptr};
@@ -225,13 +229,12 @@ swf_status march_fields_multi(swf_ctx* ctx, const std::vector<MultiGroup>& group
 bool fused_applicable(const GridDesc& g, int n_f, const FieldDesc* fd, swf_precision prec);
 swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
                        const FieldDesc* fd_host, void* psi_out, cudaStream_t st);
-int fused_clusters();
 // Clusters of the fused kernel resident at once on this device (sets the kernel up on first use);
 // 0 if it cannot be resident.
 int fused_resident_clusters(swf_ctx* ctx);
 // Fields of an n_f-field fused march to give to the pass kernels running concurrently on the SMs
 // that the 16-CTA clusters leave free (0: no split).
-int fused_split_count(int n_f, int ncl, int n_sm);
+int fused_split_count(int n_f, int ncl, int n_sm, int variant = kDefaultFusedVariant);
 swf_status rhs_eval(swf_ctx* ctx, const GridDesc& g, const FieldDesc& fd, swf_precision prec,
                     double t, const void* psi, void* out, cudaStream_t st);
 // The same evaluation with all workspace taken from caller-provided device scratch.

@@ -1659,8 +1659,8 @@ static swf_status march_unique(swf_ctx* ctx, const GridDesc& g, double t_in, dou
     return march_adaptive(ctx, g, t_in, t_out, (t_in - t_out) / n_steps, 100 * n_steps + 100, n_f, fd_host, prec,
                           psi_out, st);
   if (ctx->use_fused && fused_applicable(g, n_f, fd_host, prec)) {
-    const int n2 = (ctx->sm_split && ctx->fused_variant == 1)
-                       ? fused_split_count(n_f, fused_resident_clusters(ctx), sm_count())
+    const int n2 = (ctx->sm_split && ctx->fused_variant != 2)
+                       ? fused_split_count(n_f, fused_resident_clusters(ctx), sm_count(), ctx->fused_variant)
                        : 0;
     if (n2 > 0) return march_split(ctx, g, t_in, t_out, n_steps, n_f, n2, fd_host, psi_out, st);
     swf_status s = march_fused(ctx, g, t_in, t_out, n_steps, n_f, fd_host, psi_out, st);

@@ -227,7 +227,9 @@ class Context:
         _check(_lib.swf_set_workspace_limit(self._h, int(nbytes)))
 
     def set_march_path(self, path: int):
-        """0 = automatic (fused cluster kernel where it applies), 1 = pass kernels only."""
+        """0 = automatic (fused cluster kernel where it applies, the pass kernels on the free SMs),
+        1 = pass kernels only, 2 = the automatic fused kernel for every field, 3 = two CTAs per SM,
+        4 = transposes pulled by the threads, 5 = transposes pushed by the bulk-copy engine."""
         _check(_lib.swf_set_march_path(self._h, int(path)))
 
     def set_tolerances(self, rtol, atol):
