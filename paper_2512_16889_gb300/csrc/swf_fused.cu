@@ -303,6 +303,17 @@ __global__ void k_time_table(const FieldDesc* fd, int n_inst, int n_steps, doubl
   }
 }
 
+// -i H0(kappa)/N of one mode of a sector, (a, b) -> (o0, o1): [[1, kx - i ky], [kx + i ky, -1]]
+// (a, b), times -i/N, with every fused multiply-add rounded once in this order, so that every
+// fused kernel gives the same bits.
+__device__ __forceinline__ void h0_pair(float2 a, float2 b, float kx, float ky, float inv_n, float2& o0,
+                                        float2& o1) {
+  const float2 h0 = make_float2(__fmaf_rn(ky, b.y, __fmaf_rn(kx, b.x, a.x)), __fmaf_rn(-ky, b.x, __fmaf_rn(kx, b.y, a.y)));
+  const float2 h1 = make_float2(__fmaf_rn(-ky, a.y, __fmaf_rn(kx, a.x, -b.x)), __fmaf_rn(ky, a.x, __fmaf_rn(kx, a.y, -b.y)));
+  o0 = scl(inv_n, rot<false>(h0));
+  o1 = scl(inv_n, rot<false>(h1));
+}
+
 // V (phi0, phi1) for the sector (components c0, c1) with the one non-zero A_mu = a.
 __device__ __forceinline__ void sector_v(int acomp, int sigma, float a, float2 p0, float2 p1, float2& o0, float2& o1) {
   if (acomp == 0) {
@@ -572,12 +583,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused(Args A) {
           const float ky = kyt[iy];
           float2* pa = WB + col * LD + pidx(iy);
           float2* pb = WB + (CB + col) * LD + pidx(iy);
-          const float2 a = *pa, b = *pb;
-          // [[1, kx - i ky], [kx + i ky, -1]] (a, b), then times -i/N
-          const float2 h0 = make_float2(a.x + kx * b.x + ky * b.y, a.y + kx * b.y - ky * b.x);
-          const float2 h1 = make_float2(kx * a.x - ky * a.y - b.x, kx * a.y + ky * a.x - b.y);
-          *pa = scl(inv_n, rot<false>(h0));
-          *pb = scl(inv_n, rot<false>(h1));
+          h0_pair(*pa, *pb, kx, ky, inv_n, *pa, *pb);
         }
       }
       __syncthreads();
@@ -927,11 +933,7 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
         const float ky = kyt[iy];
         float2* pa = W + col * LD + pidx(iy);
         float2* pb = W + (CB + col) * LD + pidx(iy);
-        const float2 a = *pa, b = *pb;
-        const float2 h0 = make_float2(a.x + kx * b.x + ky * b.y, a.y + kx * b.y - ky * b.x);
-        const float2 h1 = make_float2(kx * a.x - ky * a.y - b.x, kx * a.y + ky * a.x - b.y);
-        *pa = scl(inv_n, rot<false>(h0));
-        *pb = scl(inv_n, rot<false>(h1));
+        h0_pair(*pa, *pb, kx, ky, inv_n, *pa, *pb);
       }
       __syncthreads();
       fft256_lines2<true>(W, tw);
@@ -1085,9 +1087,11 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 
 // 256-point FFTs of the 32 rows (both components) of X1 along x, in place, the same two radix-16
 // passes as fft256_lines.  Pass 1: thread (c, row, j) transforms x = 16 n1 + j; pass 2: thread
-// (c, jj, row) transforms x = 16 jj + n2 and writes x = jj + 16 k2.  The caller synchronises after.
+// (c, jj, row) transforms x = 16 jj + n2 and writes x = jj + 16 k2.  twp[16 k1 + j] holds the
+// twiddle W256^(j k1) of pass 1 (consecutive for the 16 values of j that a half-warp reads).  The
+// caller synchronises after.
 template <bool INV>
-__device__ __forceinline__ void fft_rows3(float2* X, const float2* tw) {
+__device__ __forceinline__ void fft_rows3(float2* X, const float2* twp) {
   const int t = threadIdx.x, c = t >> 8;
   float2 a[16];
   {
@@ -1097,7 +1101,7 @@ __device__ __forceinline__ void fft_rows3(float2* X, const float2* tw) {
     dft16<INV>(a);
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) {
-      const float2 w = tw[(j * k1) & 255];
+      const float2 w = twp[k1 * 16 + j];
       a[k1] = INV ? cmulc(a[k1], w) : cmul(a[k1], w);
     }
 #pragma unroll
@@ -1114,19 +1118,34 @@ __device__ __forceinline__ void fft_rows3(float2* X, const float2* tw) {
 }
 
 // The same along y for the 32 columns of X2: thread (c, j, col), y = 16 n1 + j, then y = 16 j + n2
-// written to y = j + 16 k2.  The caller synchronises after.
-template <bool INV>
-__device__ __forceinline__ void fft_cols3(float2* X, const float2* tw) {
+// written to y = j + 16 k2.  With H0, pass 1 first applies -i H0(kappa)/N to each mode it reads,
+// from both components (kxc: kappa_x of this CTA's columns, kyt: sigma kappa_y per mode).  The
+// caller synchronises after.
+template <bool INV, bool H0>
+__device__ __forceinline__ void fft_cols3(float2* X, const float2* twp, const float* kxc, const float* kyt,
+                                          float inv_n) {
   const int t = threadIdx.x, c = t >> 8, j = (t >> 4) & 15, col = t & 15;
   float2 a[16];
+  if (H0) {
+    const float kx = kxc[col];
 #pragma unroll
-  for (int n1 = 0; n1 < 16; ++n1) a[n1] = X[q3(c, n1, j, col)];
+    for (int n1 = 0; n1 < 16; ++n1) {
+      const float2 m0 = X[q3(0, n1, j, col)], m1 = X[q3(1, n1, j, col)];
+      float2 o0, o1;
+      h0_pair(m0, m1, kx, kyt[16 * n1 + j], inv_n, o0, o1);
+      a[n1] = c ? o1 : o0;
+    }
+  } else {
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) a[n1] = X[q3(c, n1, j, col)];
+  }
   dft16<INV>(a);
 #pragma unroll
   for (int k1 = 1; k1 < 16; ++k1) {
-    const float2 w = tw[(j * k1) & 255];
+    const float2 w = twp[k1 * 16 + j];
     a[k1] = INV ? cmulc(a[k1], w) : cmul(a[k1], w);
   }
+  if (H0) __syncthreads();  // every thread has read both components before any overwrites one
 #pragma unroll
   for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, j, col)] = a[k1];
   __syncthreads();
@@ -1155,7 +1174,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
   float2* X1 = reinterpret_cast<float2*>(sm + OFF_X1);
   float2* X2 = reinterpret_cast<float2*>(sm + OFF_X2);
   float2* Ys = reinterpret_cast<float2*>(sm + OFF_Y3);
-  float2* tw = reinterpret_cast<float2*>(sm + OFF_TW3);
+  float2* twp = reinterpret_cast<float2*>(sm + OFF_TW3);  // [k1][j]: W256^(j k1)
   float2* ex = reinterpret_cast<float2*>(sm + OFF_EX3);
   float* gx = reinterpret_cast<float*>(sm + OFF_GX3);
   float2* ey = reinterpret_cast<float2*>(sm + OFF_EY3);
@@ -1189,9 +1208,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int m = tid; m < 256; m += NT) {
+    const int k1 = m >> 4, j = m & 15;
     double s, c;
-    sincospi(-2.0 * m / 256.0, &s, &c);
-    tw[m] = make_float2((float)c, (float)s);
+    sincospi(-2.0 * ((j * k1) & 255) / 256.0, &s, &c);
+    twp[m] = make_float2((float)c, (float)s);
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1281,7 +1301,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       }
 
       // ---- forward x-FFT of the stage value Y (in X1), then push chunk (c, s) to CTA s
-      fft_rows3<false>(X1, tw);
+      fft_rows3<false>(X1, twp);
       fence_async_smem();
       __syncthreads();
       cl_wait();  // every CTA's X2 is free and its receive barrier armed
@@ -1332,26 +1352,11 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       }
       cl_arrive();  // the forward copies into this CTA are complete
 
-      // ---- columns: forward y-FFT, -i H0(kappa)/N per mode, inverse y-FFT; push chunk (c, s) back
-      fft_cols3<false>(X2, tw);
+      // ---- columns: forward y-FFT; -i H0(kappa)/N per mode, folded into the first pass of the
+      // inverse y-FFT; push chunk (c, s) back
+      fft_cols3<false, false>(X2, twp, nullptr, nullptr, 0.f);
       __syncthreads();
-      {
-#pragma unroll 2
-        for (int m = tid; m < CB * NY; m += NT) {
-          const int col = m & 15, iy = m >> 4;
-          const float kx = kxt[rank * CB + col];
-          const float ky = kyt[iy];
-          float2* pa = X2 + q3(0, iy >> 4, iy & 15, col);
-          float2* pb = X2 + q3(1, iy >> 4, iy & 15, col);
-          const float2 a = *pa, b = *pb;
-          const float2 h0 = make_float2(a.x + kx * b.x + ky * b.y, a.y + kx * b.y - ky * b.x);
-          const float2 h1 = make_float2(kx * a.x - ky * a.y - b.x, kx * a.y + ky * a.x - b.y);
-          *pa = scl(inv_n, rot<false>(h0));
-          *pb = scl(inv_n, rot<false>(h1));
-        }
-      }
-      __syncthreads();
-      fft_cols3<true>(X2, tw);
+      fft_cols3<true, true>(X2, twp, kxt + rank * CB, kyt, inv_n);
       fence_async_smem();
       __syncthreads();
       cl_wait();  // every CTA's X1 is free and its receive barrier armed
@@ -1445,7 +1450,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       cl_arrive();  // the backward copies into this CTA are complete
 
       // ---- inverse x-FFT; k = (that) + Z; the next stage value Y' = P + h a_new k
-      fft_rows3<true>(X1, tw);
+      fft_rows3<true>(X1, twp);
       __syncthreads();
       {
         const int oslab = stage == 0 || stage == 6 ? 0 : (stage <= 2 ? stage : -1);
@@ -1579,12 +1584,12 @@ int fused_resident_clusters(swf_ctx* ctx) {
 // which take about alpha n_2 rounds' time on the free SMs.  alpha was measured with 40 free SMs
 // on (2+1)D 256^2 complex64 marches: 16 fields on the free SMs took as long as 32 rounds of the
 // kernel with pulled transposes (alpha = 2.0); a round of the kernel with pushed transposes is
-// 1.31 times shorter (alpha = 2.62).  alpha scales with 40 / (free SMs).  The largest r with
+// 1.37 times shorter (alpha = 2.74).  alpha scales with 40 / (free SMs).  The largest r with
 // alpha n_2 <= R - r is taken.
 int fused_split_count(int n_f, int ncl, int n_sm, int variant) {
   const int free_sm = n_sm - fused::CL * ncl;
   if (ncl < 1 || free_sm < 16 || n_f < 16) return 0;
-  const double alpha = (variant == 3 ? 2.62 : 2.0) * 40.0 / free_sm;
+  const double alpha = (variant == 3 ? 2.74 : 2.0) * 40.0 / free_sm;
   const int R = (2 * n_f + ncl - 1) / ncl;
   int best = 0;
   for (int r = 1; r < R; ++r) {
