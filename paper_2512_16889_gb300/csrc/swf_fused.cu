@@ -72,11 +72,13 @@ constexpr int SMEM = OFF_MISC + 7 * RB * 4 + 7 * 8 + 16 + 64 + 16;
 
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex products with every rounding fixed (one product, then one fused multiply-add per
+// part), so that the fused kernels, however the compiler schedules them, give the same bits.
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
-  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+  return make_float2(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), __fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)));
 }
 __device__ __forceinline__ float2 scl(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
 __device__ __forceinline__ float2 fma2(float s, float2 a, float2 c) {
@@ -1157,15 +1159,64 @@ __device__ __forceinline__ void fft_cols3(float2* X, const float2* twp, const fl
   for (int k2 = 0; k2 < 16; ++k2) X[q3(c, k2, j, col)] = a[k2];
 }
 
-// the two sites (x, x + 1) of row r, component c (x even): one aligned float4 of X1, in site
-// order for even r and swapped for odd r (the swizzle exchanges neighbours)
-__device__ __forceinline__ float4 row_pair_ld(const float2* X1, int c, int r, int x) {
-  const float4 v = *reinterpret_cast<const float4*>(X1 + (q3(c, x >> 4, r, x & 15) & ~1));
-  return (r & 1) ? make_float4(v.z, v.w, v.x, v.y) : v;
+// Row lines kept in registers between the inverse x-FFT of one evaluation and the forward x-FFT
+// of the next.  Thread t owns the 16 sites (c, row, x = jj + 16 k2), k2 = 0..15, of
+// c = (t >> 4) & 1, row = t & 15, jj = t >> 5: the outputs of its last inverse pass and the
+// inputs of its next forward first pass.  Its tensor-memory columns 2 k2, 2 k2 + 1 hold site k2
+// of each slab; the state y (shared memory) and the cluster's global slots keep two sites per
+// float4 at [k2 / 2][t], so every access of a warp is contiguous.  The partner component of a
+// site is lane ^ 16 of the same warp.
+__device__ __forceinline__ int own_c() { return (threadIdx.x >> 4) & 1; }
+__device__ __forceinline__ int own_row() { return threadIdx.x & 15; }
+__device__ __forceinline__ int own_jj() { return threadIdx.x >> 5; }
+
+// forward x-FFT of the rows, pass 1 from the registers a[k2] (x = jj + 16 k2 = 16 n1 + j with
+// j = jj), pass 2 as fft_rows3; the caller synchronises after
+__device__ __forceinline__ void fft_rows3_from_regs(float2* X, const float2* twp, float2 (&a)[16]) {
+  const int t = threadIdx.x;
+  {
+    const int c = own_c(), row = own_row(), j = own_jj();
+    dft16<false>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) a[k1] = cmul(a[k1], twp[k1 * 16 + j]);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, row, j)] = a[k1];
+  }
+  __syncthreads();
+  const int c = t >> 8, jj = (t >> 4) & 15, row = t & 15;
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, jj, row, n2)];
+  dft16<false>(a);
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) X[q3(c, k2, row, jj)] = a[k2];
 }
-__device__ __forceinline__ void row_pair_st(float2* X1, int c, int r, int x, float4 v) {
-  if (r & 1) v = make_float4(v.z, v.w, v.x, v.y);
-  *reinterpret_cast<float4*>(X1 + (q3(c, x >> 4, r, x & 15) & ~1)) = v;
+
+// inverse x-FFT of the rows, pass 1 as fft_rows3, pass 2 into the registers a[k2] of the owning
+// thread; ends with a barrier (every thread has read X before anyone writes it again)
+__device__ __forceinline__ void fft_rows3_to_regs(float2* X, const float2* twp, float2 (&a)[16]) {
+  const int t = threadIdx.x;
+  {
+    const int c = t >> 8, row = (t >> 4) & 15, j = t & 15;
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) a[n1] = X[q3(c, n1, row, j)];
+    dft16<true>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) a[k1] = cmulc(a[k1], twp[k1 * 16 + j]);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, row, j)] = a[k1];
+  }
+  __syncthreads();
+  const int c = own_c(), row = own_row(), jj = own_jj();
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, jj, row, n2)];
+  dft16<true>(a);
+  __syncthreads();
+}
+
+__device__ __forceinline__ float4 shfl16(float4 v) {
+  return make_float4(__shfl_xor_sync(0xffffffffu, v.x, 16), __shfl_xor_sync(0xffffffffu, v.y, 16),
+                     __shfl_xor_sync(0xffffffffu, v.z, 16), __shfl_xor_sync(0xffffffffu, v.w, 16));
 }
 
 __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
@@ -1173,7 +1224,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
   extern __shared__ __align__(16) unsigned char sm[];
   float2* X1 = reinterpret_cast<float2*>(sm + OFF_X1);
   float2* X2 = reinterpret_cast<float2*>(sm + OFF_X2);
-  float2* Ys = reinterpret_cast<float2*>(sm + OFF_Y3);
+  float4* Ys4 = reinterpret_cast<float4*>(sm + OFF_Y3);  // [k2 / 2][t]: the sites this thread owns
   float2* twp = reinterpret_cast<float2*>(sm + OFF_TW3);  // [k1][j]: W256^(j k1)
   float2* ex = reinterpret_cast<float2*>(sm + OFF_EX3);
   float* gx = reinterpret_cast<float*>(sm + OFF_GX3);
@@ -1196,8 +1247,11 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
   const int warp = tid >> 5, lane = tid & 31;
   const int row0 = rank * RB;
   const size_t plane = (size_t)NX * NY;
-  float2* slot = A.slots + (size_t)cid * 4 * 2 * plane;
-  float2* ylo = slot + (size_t)3 * 2 * plane;
+  // the cluster's global slots k_4, k_5, k_6 and the low part of y; this CTA's part of each,
+  // two of this thread's sites per float4 at [k2 / 2][t]
+  float4* slot4 = reinterpret_cast<float4*>(A.slots + (size_t)cid * 4 * 2 * plane) + (size_t)rank * (NSL / 2);
+  const size_t sstride = plane;  // float4 per slot (2 plane complex values)
+  float4* ylo4 = slot4 + 3 * sstride;
   if (warp == 0) {
     tmem_alloc(s_tmem, 512);
     tmem_relinquish();
@@ -1224,6 +1278,8 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
   bool err = false;
   // lane L of warp 0 copies chunk (L / 16, peer) to peer (rank + L) % 16
   const int cc = lane >> 4, peer = (rank + (lane & 15)) & (CL - 1);
+  // the sites this thread owns
+  const int oc = own_c(), orow = own_row(), ojj = own_jj();
 
   const double dxx = A.Lx / NX, dyy = A.Ly / NY;
   const float inv_n = 1.0f / (float)(NX * NY);
@@ -1260,16 +1316,19 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       const int c = tid == 0 ? S.c0 : S.c1;
       s_w[tid] = make_float2((float)F.w[2 * c], (float)F.w[2 * c + 1]);
     }
-    // y = 0, its low part 0, and the first stage value Y = y = 0 in X1 and in the stash
-    for (int i = tid; i < NSL; i += NT) Ys[i] = make_float2(0.f, 0.f);
-    for (int i = tid; i < NBUF; i += NT) X1[i] = make_float2(0.f, 0.f);
-    for (int i = tid; i < NSL; i += NT) {
-      const int comp = i / (RB * NX), rem = i % (RB * NX);
-      __stcg(ylo + comp * plane + (size_t)row0 * NX + rem, make_float2(0.f, 0.f));
+    // y = 0, its low part 0, and the first stage value Y = y = 0 in registers and in the stash
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      Ys4[h * NT + tid] = z4;
+      __stcg(ylo4 + h * NT + tid, z4);
     }
 #pragma unroll
-    for (int m = 0; m < 4; ++m) tmem_st8(tstash + 8 * m, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int q = 0; q < 4; ++q) tmem_st8(tstash + 8 * q, z4, z4);
     tmem_wait_st();
+    float2 a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = make_float2(0.f, 0.f);
     __syncthreads();
 
     const int n_eval = 1 + 6 * A.n_steps;
@@ -1300,8 +1359,8 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
         __syncthreads();
       }
 
-      // ---- forward x-FFT of the stage value Y (in X1), then push chunk (c, s) to CTA s
-      fft_rows3<false>(X1, twp);
+      // ---- forward x-FFT of the stage value Y (registers), then push chunk (c, s) to CTA s
+      fft_rows3_from_regs(X1, twp, a);
       fence_async_smem();
       __syncthreads();
       cl_wait();  // every CTA's X2 is free and its receive barrier armed
@@ -1309,35 +1368,37 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
         bulk_push(peer_addr(x2a + (uint32_t)((cc * CL + rank) * CHK * 8), peer),
                   x1a + (uint32_t)((cc * CL + peer) * CHK * 8), CHK * 8, peer_addr(bar_f, peer));
 
-      // ---- meanwhile: local term Z = -i V (Y + psi_b) of this stage, from the stash (Y) to the stash
+      // ---- meanwhile: local term Z = -i V (Y + psi_b) of this stage, from the stash (Y, both
+      // components through the partner lane) to the stash
       {
         const float2 tf = s_tf[stage];
-        const float* ftr = s_ft + stage * RB;
+        const float ft = s_ft[stage * RB + orow];
         const float2 w0 = s_w[0], w1 = s_w[1];
-#pragma unroll 2
-        for (int m = 0; m < 4; ++m) {
-          const int sp = tid + NT * m;
-          const int r = sp >> 7;
-          const int x = (sp & 127) * 2;
-          float4 y0, y1;
-          tmem_ld8(tstash + 8 * m, y0, y1);
-          const float ft = ftr[r];
-          const float2 phy = cmul(tf, ey[r]);
-          float4 z0, z1;
+        const float2 phy = cmul(tf, ey[orow]);
+        const float fg = ft * gy[orow];
 #pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const float2 ph = cmul(phy, ex[x + e]);
-            const float a = ft * gy[r] * gx[x + e];
-            const float2 p0 = (e ? make_float2(y0.z, y0.w) : make_float2(y0.x, y0.y)) + cmul(w0, ph);
-            const float2 p1 = (e ? make_float2(y1.z, y1.w) : make_float2(y1.x, y1.y)) + cmul(w1, ph);
+        for (int q = 0; q < 4; ++q) {
+          float4 ya, yb;
+          tmem_ld8(tstash + 8 * q, ya, yb);
+          const float4 pa = shfl16(ya), pb = shfl16(yb);
+          float2 z[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int x = ojj + 16 * (4 * q + e);
+            const float4& yo = e < 2 ? ya : yb;
+            const float4& yp = e < 2 ? pa : pb;
+            const float2 own = (e & 1) ? make_float2(yo.z, yo.w) : make_float2(yo.x, yo.y);
+            const float2 oth = (e & 1) ? make_float2(yp.z, yp.w) : make_float2(yp.x, yp.y);
+            const float2 y0 = oc ? oth : own, y1 = oc ? own : oth;
+            const float2 ph = cmul(phy, ex[x]);
+            const float av = fg * gx[x];
+            const float2 p0 = y0 + cmul(w0, ph);
+            const float2 p1 = y1 + cmul(w1, ph);
             float2 v0, v1;
-            sector_v(F.acomp, S.sigma, a, p0, p1, v0, v1);
-            v0 = rot<false>(v0);
-            v1 = rot<false>(v1);
-            if (e) { z0.z = v0.x; z0.w = v0.y; z1.z = v1.x; z1.w = v1.y; }
-            else { z0.x = v0.x; z0.y = v0.y; z1.x = v1.x; z1.y = v1.y; }
+            sector_v(F.acomp, S.sigma, av, p0, p1, v0, v1);
+            z[e] = rot<false>(oc ? v1 : v0);
           }
-          tmem_st8(tstash + 8 * m, z0, z1);
+          tmem_st8(tstash + 8 * q, make_float4(z[0].x, z[0].y, z[1].x, z[1].y), make_float4(z[2].x, z[2].y, z[3].x, z[3].y));
         }
         tmem_wait_st();
       }
@@ -1370,48 +1431,44 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       const int nxt = stage == 6 ? 1 : stage + 1;  // the next stage (stage 0 is followed by 1)
       const int jn = nxt - 1;                      // index of the newest k (the one computed now)
       const bool nlast = nxt == 6;
-      float4 P0[4], P1[4];
+      float4 P[8];
       if (has_next) {
         const int ntp = jn < 3 ? jn : 3;  // tensor-memory terms before the newest
         float ct[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) ct[j] = (j < ntp) ? (float)(A.h * DPa[nxt][j]) : 0.f;
-        float coef[3];
-        const float2* kin[3];
+        float coef[2];
+        const float4* kin[2];
         int nterm = 0;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < 2; ++j) {
           coef[j] = 0.f;
-          kin[j] = slot;
+          kin[j] = slot4;
         }
 #pragma unroll
         for (int j = 3; j < 5; ++j) {
           if (j < jn && DPa[nxt][j] != 0.0) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
+            for (int q = 0; q < 2; ++q)
               if (q == nterm) {
                 coef[q] = (float)(A.h * DPa[nxt][j]);
-                kin[q] = slot + (size_t)(j - 3) * 2 * plane;
+                kin[q] = slot4 + (size_t)(j - 3) * sstride;
               }
             ++nterm;
           }
         }
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int sp = tid + NT * m;
-          const int r = sp >> 7;
-          const int x = (sp & 127) * 2;
-          const size_t g0 = (size_t)(row0 + r) * NX + x;
+        for (int q = 0; q < 4; ++q) {
           float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = y0;
           if (!nlast) {
-            y0 = *reinterpret_cast<const float4*>(Ys + r * NX + x);
-            y1 = *reinterpret_cast<const float4*>(Ys + RB * NX + r * NX + x);
+            y0 = Ys4[(2 * q) * NT + tid];
+            y1 = Ys4[(2 * q + 1) * NT + tid];
           }
           if (ntp > 0) {
             uint32_t tr[3][8];
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-              if (j < ntp) tmem_ld8_nowait(tme + 128 * j + 8 * m, tr[j]);
+              if (j < ntp) tmem_ld8_nowait(tme + 128 * j + 8 * q, tr[j]);
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -1425,17 +1482,17 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
             }
           }
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            if (q < nterm) {
-              const float4 k0 = __ldcg(reinterpret_cast<const float4*>(kin[q] + g0));
-              const float4 k1 = __ldcg(reinterpret_cast<const float4*>(kin[q] + plane + g0));
-              const float2 c = make_float2(coef[q], coef[q]);
+          for (int qq = 0; qq < 2; ++qq) {
+            if (qq < nterm) {
+              const float4 k0 = __ldcg(kin[qq] + (2 * q) * NT + tid);
+              const float4 k1 = __ldcg(kin[qq] + (2 * q + 1) * NT + tid);
+              const float2 c = make_float2(coef[qq], coef[qq]);
               fma4(c, k0, y0);
               fma4(c, k1, y1);
             }
           }
-          P0[m] = y0;
-          P1[m] = y1;
+          P[2 * q] = y0;
+          P[2 * q + 1] = y1;
         }
       }
       {
@@ -1449,68 +1506,65 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       }
       cl_arrive();  // the backward copies into this CTA are complete
 
-      // ---- inverse x-FFT; k = (that) + Z; the next stage value Y' = P + h a_new k
-      fft_rows3<true>(X1, twp);
-      __syncthreads();
+      // ---- inverse x-FFT into registers; k = (that) + Z; the next stage value Y' = P + h a_new k
+      fft_rows3_to_regs(X1, twp, a);
       {
         const int oslab = stage == 0 || stage == 6 ? 0 : (stage <= 2 ? stage : -1);
-        float2* kout = slot + (size_t)(stage >= 3 && stage <= 5 ? stage - 3 : 0) * 2 * plane;
+        float4* kout = slot4 + (size_t)(stage >= 3 && stage <= 5 ? stage - 3 : 0) * sstride;
         const bool use_new = jn < 3 || DPa[nxt][jn] != 0.0;
         const float cnv = (float)(A.h * DPa[nxt][jn]);
         const float2 cn = make_float2(cnv, cnv);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int sp = tid + NT * m;
-          const int r = sp >> 7;
-          const int x = (sp & 127) * 2;
-          const size_t g0 = (size_t)(row0 + r) * NX + x;
-          float4 z0, z1;
-          tmem_ld8(tstash + 8 * m, z0, z1);
-          const float4 wa0 = row_pair_ld(X1, 0, r, x);
-          const float4 wa1 = row_pair_ld(X1, 1, r, x);
-          const float4 o0 = make_float4(wa0.x + z0.x, wa0.y + z0.y, wa0.z + z0.z, wa0.w + z0.w);
-          const float4 o1 = make_float4(wa1.x + z1.x, wa1.y + z1.y, wa1.z + z1.z, wa1.w + z1.w);
+        for (int q = 0; q < 4; ++q) {
+          float4 za, zb;
+          tmem_ld8(tstash + 8 * q, za, zb);
+          const float4 o0 = make_float4(a[4 * q].x + za.x, a[4 * q].y + za.y, a[4 * q + 1].x + za.z, a[4 * q + 1].y + za.w);
+          const float4 o1 = make_float4(a[4 * q + 2].x + zb.x, a[4 * q + 2].y + zb.y, a[4 * q + 3].x + zb.z, a[4 * q + 3].y + zb.w);
           if (oslab >= 0) {
-            tmem_st8(tme + 128 * oslab + 8 * m, o0, o1);
+            tmem_st8(tme + 128 * oslab + 8 * q, o0, o1);
           } else {
-            __stcg(reinterpret_cast<float4*>(kout + g0), o0);
-            __stcg(reinterpret_cast<float4*>(kout + plane + g0), o1);
+            __stcg(kout + (2 * q) * NT + tid, o0);
+            __stcg(kout + (2 * q + 1) * NT + tid, o1);
           }
           if (has_next) {
-            float4 y0 = P0[m], y1 = P1[m];
+            float4 y0 = P[2 * q], y1 = P[2 * q + 1];
             if (use_new) {
               fma4(cn, o0, y0);
               fma4(cn, o1, y1);
             }
             if (nlast) {
               // y_new = y + h sum_j b_j k_j in float-float
-              const float4 yh0 = *reinterpret_cast<const float4*>(Ys + r * NX + x);
-              const float4 yh1 = *reinterpret_cast<const float4*>(Ys + RB * NX + r * NX + x);
-              float4 l0 = __ldcg(reinterpret_cast<const float4*>(ylo + g0));
-              float4 l1 = __ldcg(reinterpret_cast<const float4*>(ylo + plane + g0));
+              const float4 yh0 = Ys4[(2 * q) * NT + tid];
+              const float4 yh1 = Ys4[(2 * q + 1) * NT + tid];
+              float4 l0 = __ldcg(ylo4 + (2 * q) * NT + tid);
+              float4 l1 = __ldcg(ylo4 + (2 * q + 1) * NT + tid);
               ff_add(yh0.x, l0.x, y0.x); ff_add(yh0.y, l0.y, y0.y); ff_add(yh0.z, l0.z, y0.z); ff_add(yh0.w, l0.w, y0.w);
               ff_add(yh1.x, l1.x, y1.x); ff_add(yh1.y, l1.y, y1.y); ff_add(yh1.z, l1.z, y1.z); ff_add(yh1.w, l1.w, y1.w);
-              __stcg(reinterpret_cast<float4*>(ylo + g0), l0);
-              __stcg(reinterpret_cast<float4*>(ylo + plane + g0), l1);
-              *reinterpret_cast<float4*>(Ys + r * NX + x) = y0;
-              *reinterpret_cast<float4*>(Ys + RB * NX + r * NX + x) = y1;
+              __stcg(ylo4 + (2 * q) * NT + tid, l0);
+              __stcg(ylo4 + (2 * q + 1) * NT + tid, l1);
+              Ys4[(2 * q) * NT + tid] = y0;
+              Ys4[(2 * q + 1) * NT + tid] = y1;
             }
-            row_pair_st(X1, 0, r, x, y0);
-            row_pair_st(X1, 1, r, x, y1);
-            tmem_st8(tstash + 8 * m, y0, y1);
+            tmem_st8(tstash + 8 * q, y0, y1);
+            a[4 * q] = make_float2(y0.x, y0.y);
+            a[4 * q + 1] = make_float2(y0.z, y0.w);
+            a[4 * q + 2] = make_float2(y1.x, y1.y);
+            a[4 * q + 3] = make_float2(y1.z, y1.w);
           }
         }
         tmem_wait_st();
       }
-      __syncthreads();
     }
     // psi(t_in) of the sector into the 4-component output (NaN if a transpose failed)
-    float2* out0 = A.psi_out + ((size_t)S.inst * 4 + S.c0) * plane + (size_t)row0 * NX;
-    float2* out1 = A.psi_out + ((size_t)S.inst * 4 + S.c1) * plane + (size_t)row0 * NX;
-    const float2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
-    for (int i = tid; i < RB * NX; i += NT) {
-      out0[i] = err ? nan2 : Ys[i];
-      out1[i] = err ? nan2 : Ys[RB * NX + i];
+    {
+      const float2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+      float2* out = A.psi_out + ((size_t)S.inst * 4 + (oc ? S.c1 : S.c0)) * plane + (size_t)(row0 + orow) * NX + ojj;
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const float4 v = Ys4[h * NT + tid];
+        out[16 * (2 * h)] = err ? nan2 : make_float2(v.x, v.y);
+        out[16 * (2 * h + 1)] = err ? nan2 : make_float2(v.z, v.w);
+      }
     }
     __syncthreads();
   }
@@ -1584,12 +1638,12 @@ int fused_resident_clusters(swf_ctx* ctx) {
 // which take about alpha n_2 rounds' time on the free SMs.  alpha was measured with 40 free SMs
 // on (2+1)D 256^2 complex64 marches: 16 fields on the free SMs took as long as 32 rounds of the
 // kernel with pulled transposes (alpha = 2.0); a round of the kernel with pushed transposes is
-// 1.37 times shorter (alpha = 2.74).  alpha scales with 40 / (free SMs).  The largest r with
+// 1.44 times shorter (alpha = 2.87).  alpha scales with 40 / (free SMs).  The largest r with
 // alpha n_2 <= R - r is taken.
 int fused_split_count(int n_f, int ncl, int n_sm, int variant) {
   const int free_sm = n_sm - fused::CL * ncl;
   if (ncl < 1 || free_sm < 16 || n_f < 16) return 0;
-  const double alpha = (variant == 3 ? 2.74 : 2.0) * 40.0 / free_sm;
+  const double alpha = (variant == 3 ? 2.87 : 2.0) * 40.0 / free_sm;
   const int R = (2 * n_f + ncl - 1) / ncl;
   int best = 0;
   for (int r = 1; r < R; ++r) {
