@@ -1087,78 +1087,11 @@ __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.a
 // generic-proxy writes of this thread become visible to the bulk-copy engine
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 256-point FFTs of the 32 rows (both components) of X1 along x, in place, the same two radix-16
-// passes as fft256_lines.  Pass 1: thread (c, row, j) transforms x = 16 n1 + j; pass 2: thread
-// (c, jj, row) transforms x = 16 jj + n2 and writes x = jj + 16 k2.  twp[16 k1 + j] holds the
-// twiddle W256^(j k1) of pass 1 (consecutive for the 16 values of j that a half-warp reads).  The
-// caller synchronises after.
-template <bool INV>
-__device__ __forceinline__ void fft_rows3(float2* X, const float2* twp) {
-  const int t = threadIdx.x, c = t >> 8;
-  float2 a[16];
-  {
-    const int row = (t >> 4) & 15, j = t & 15;
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) a[n1] = X[q3(c, n1, row, j)];
-    dft16<INV>(a);
-#pragma unroll
-    for (int k1 = 1; k1 < 16; ++k1) {
-      const float2 w = twp[k1 * 16 + j];
-      a[k1] = INV ? cmulc(a[k1], w) : cmul(a[k1], w);
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, row, j)] = a[k1];
-  }
-  __syncthreads();
-  const int jj = (t >> 4) & 15, row = t & 15;
-#pragma unroll
-  for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, jj, row, n2)];
-  dft16<INV>(a);
-  __syncthreads();
-#pragma unroll
-  for (int k2 = 0; k2 < 16; ++k2) X[q3(c, k2, row, jj)] = a[k2];
-}
-
-// The same along y for the 32 columns of X2: thread (c, j, col), y = 16 n1 + j, then y = 16 j + n2
-// written to y = j + 16 k2.  With H0, pass 1 first applies -i H0(kappa)/N to each mode it reads,
-// from both components (kxc: kappa_x of this CTA's columns, kyt: sigma kappa_y per mode).  The
-// caller synchronises after.
-template <bool INV, bool H0>
-__device__ __forceinline__ void fft_cols3(float2* X, const float2* twp, const float* kxc, const float* kyt,
-                                          float inv_n) {
-  const int t = threadIdx.x, c = t >> 8, j = (t >> 4) & 15, col = t & 15;
-  float2 a[16];
-  if (H0) {
-    const float kx = kxc[col];
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) {
-      const float2 m0 = X[q3(0, n1, j, col)], m1 = X[q3(1, n1, j, col)];
-      float2 o0, o1;
-      h0_pair(m0, m1, kx, kyt[16 * n1 + j], inv_n, o0, o1);
-      a[n1] = c ? o1 : o0;
-    }
-  } else {
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) a[n1] = X[q3(c, n1, j, col)];
-  }
-  dft16<INV>(a);
-#pragma unroll
-  for (int k1 = 1; k1 < 16; ++k1) {
-    const float2 w = twp[k1 * 16 + j];
-    a[k1] = INV ? cmulc(a[k1], w) : cmul(a[k1], w);
-  }
-  if (H0) __syncthreads();  // every thread has read both components before any overwrites one
-#pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, j, col)] = a[k1];
-  __syncthreads();
-#pragma unroll
-  for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, j, n2, col)];
-  dft16<INV>(a);
-  __syncthreads();
-#pragma unroll
-  for (int k2 = 0; k2 < 16; ++k2) X[q3(c, k2, j, col)] = a[k2];
-}
-
+// 256-point FFTs of the 32 rows (both components) of X1 along x, in place, are the same two
+// radix-16 passes as fft256_lines.  Pass 1: thread (c, row, j) transforms x = 16 n1 + j; pass 2:
+// thread (c, jj, row) transforms x = 16 jj + n2 and writes x = jj + 16 k2.  twp[16 k1 + j] holds
+// the twiddle W256^(j k1) of pass 1 (consecutive for the 16 values of j that a half-warp reads).
+//
 // Row lines kept in registers between the inverse x-FFT of one evaluation and the forward x-FFT
 // of the next.  Thread t owns the 16 sites (c, row, x = jj + 16 k2), k2 = 0..15, of
 // c = (t >> 4) & 1, row = t & 15, jj = t >> 5: the outputs of its last inverse pass and the
@@ -1171,7 +1104,8 @@ __device__ __forceinline__ int own_row() { return threadIdx.x & 15; }
 __device__ __forceinline__ int own_jj() { return threadIdx.x >> 5; }
 
 // forward x-FFT of the rows, pass 1 from the registers a[k2] (x = jj + 16 k2 = 16 n1 + j with
-// j = jj), pass 2 as fft_rows3; the caller synchronises after
+// j = jj), pass 2 with thread (c, jj, row) = (t >> 8, (t >> 4) & 15, t & 15); the caller
+// synchronises after
 __device__ __forceinline__ void fft_rows3_from_regs(float2* X, const float2* twp, float2 (&a)[16]) {
   const int t = threadIdx.x;
   {
@@ -1192,8 +1126,9 @@ __device__ __forceinline__ void fft_rows3_from_regs(float2* X, const float2* twp
   for (int k2 = 0; k2 < 16; ++k2) X[q3(c, k2, row, jj)] = a[k2];
 }
 
-// inverse x-FFT of the rows, pass 1 as fft_rows3, pass 2 into the registers a[k2] of the owning
-// thread; ends with a barrier (every thread has read X before anyone writes it again)
+// inverse x-FFT of the rows, pass 1 with thread (c, row, j) = (t >> 8, (t >> 4) & 15, t & 15),
+// pass 2 into the registers a[k2] of the owning thread; ends with a barrier (every thread has
+// read X before anyone writes it again)
 __device__ __forceinline__ void fft_rows3_to_regs(float2* X, const float2* twp, float2 (&a)[16]) {
   const int t = threadIdx.x;
   {
@@ -1212,6 +1147,51 @@ __device__ __forceinline__ void fft_rows3_to_regs(float2* X, const float2* twp, 
   for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, jj, row, n2)];
   dft16<true>(a);
   __syncthreads();
+}
+
+// The column side of an evaluation in one pass over X2: forward 256-point y-FFT of the 32 columns
+// (two radix-16 passes as fft256_lines, y = 16 n1 + j then y = 16 j + n2), -i H0(kappa)/N per
+// mode (kxc: kappa_x of this CTA's columns, kyt: sigma kappa_y per mode), inverse y-FFT.
+// Thread t = (j = t >> 5, c = (t >> 4) & 1, col = t & 15): the outputs y = j + 16 k2 of its forward
+// pass 2 are the inputs y = 16 n1 + j of its inverse pass 1, and the other component of each mode
+// is lane ^ 16, so H0 is applied in registers.  The caller synchronises after.
+__device__ __forceinline__ void fft_cols3_h0(float2* X, const float2* twp, const float* kxc, const float* kyt,
+                                             float inv_n) {
+  const int t = threadIdx.x, col = t & 15, c = (t >> 4) & 1, j = t >> 5;
+  float2 a[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) a[n1] = X[q3(c, n1, j, col)];
+  dft16<false>(a);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) a[k1] = cmul(a[k1], twp[k1 * 16 + j]);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, j, col)] = a[k1];
+  __syncthreads();
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, j, n2, col)];
+  dft16<false>(a);
+  const float kx = kxc[col];
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    const float2 own = a[k2];
+    const float2 oth = make_float2(__shfl_xor_sync(0xffffffffu, own.x, 16), __shfl_xor_sync(0xffffffffu, own.y, 16));
+    float2 o0, o1;
+    h0_pair(c ? oth : own, c ? own : oth, kx, kyt[j + 16 * k2], inv_n, o0, o1);
+    a[k2] = c ? o1 : o0;
+  }
+  dft16<true>(a);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) a[k1] = cmulc(a[k1], twp[k1 * 16 + j]);
+  __syncthreads();  // every thread has read its forward pass-2 inputs
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) X[q3(c, k1, j, col)] = a[k1];
+  __syncthreads();
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) a[n2] = X[q3(c, j, n2, col)];
+  dft16<true>(a);
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) X[q3(c, k2, j, col)] = a[k2];
 }
 
 __device__ __forceinline__ float4 shfl16(float4 v) {
@@ -1413,11 +1393,9 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       }
       cl_arrive();  // the forward copies into this CTA are complete
 
-      // ---- columns: forward y-FFT; -i H0(kappa)/N per mode, folded into the first pass of the
-      // inverse y-FFT; push chunk (c, s) back
-      fft_cols3<false, false>(X2, twp, nullptr, nullptr, 0.f);
-      __syncthreads();
-      fft_cols3<true, true>(X2, twp, kxt + rank * CB, kyt, inv_n);
+      // ---- columns: forward y-FFT, -i H0(kappa)/N per mode in registers, inverse y-FFT; push
+      // chunk (c, s) back
+      fft_cols3_h0(X2, twp, kxt + rank * CB, kyt, inv_n);
       fence_async_smem();
       __syncthreads();
       cl_wait();  // every CTA's X1 is free and its receive barrier armed
@@ -1638,12 +1616,12 @@ int fused_resident_clusters(swf_ctx* ctx) {
 // which take about alpha n_2 rounds' time on the free SMs.  alpha was measured with 40 free SMs
 // on (2+1)D 256^2 complex64 marches: 16 fields on the free SMs took as long as 32 rounds of the
 // kernel with pulled transposes (alpha = 2.0); a round of the kernel with pushed transposes is
-// 1.44 times shorter (alpha = 2.87).  alpha scales with 40 / (free SMs).  The largest r with
+// 1.46 times shorter (alpha = 2.91).  alpha scales with 40 / (free SMs).  The largest r with
 // alpha n_2 <= R - r is taken.
 int fused_split_count(int n_f, int ncl, int n_sm, int variant) {
   const int free_sm = n_sm - fused::CL * ncl;
   if (ncl < 1 || free_sm < 16 || n_f < 16) return 0;
-  const double alpha = (variant == 3 ? 2.87 : 2.0) * 40.0 / free_sm;
+  const double alpha = (variant == 3 ? 2.91 : 2.0) * 40.0 / free_sm;
   const int R = (2 * n_f + ncl - 1) / ncl;
   int best = 0;
   for (int r = 1; r < R; ++r) {
