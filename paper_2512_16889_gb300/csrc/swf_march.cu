@@ -49,6 +49,8 @@ struct StageArgs {
   const R* greal;       // per field: gx[nx] gy[ny] gz[nz]
   const cpx<R>* gcplx;  // per field: ex[nx] ey[ny] ez[nz] w[4]
   const cpx<R>* tw[3];
+  const R* kap;         // mode momenta kappa_j = 2 pi j'/L_a of the axes with n_a > 1, rounded once
+                        // from FP64, at offsets 0, nx, nx + ny (FP64 is scarce on this GPU)
   RadixPlan plan[3];
   GridDesc g;
   int nrows;            // ny * nz
@@ -183,6 +185,18 @@ __global__ void k_tables(const FieldDesc* fd, GridDesc g, R* greal, cpx<R>* gcpl
       const int c = i - nt;
       gcplx[(size_t)f * (nt + 4) + i] = mk<R>((R)F.w[2 * c], (R)F.w[2 * c + 1]);
     }
+  }
+}
+
+// The mode momenta of every axis, kap[off_a + j] = (R) mode_kappa(j, n_a, L_a) (0 on trivial axes):
+// the values the H0 step used to compute per element in FP64.
+template <typename R>
+__global__ void k_kappa_table(GridDesc g, R* kap) {
+  const int nt = g.n[0] + g.n[1] + g.n[2];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
+    int axis = 0, j = i;
+    while (j >= g.n[axis]) { j -= g.n[axis]; ++axis; }
+    kap[i] = g.n[axis] > 1 ? (R)mode_kappa(j, g.n[axis], g.L[axis]) : (R)0;
   }
 }
 
@@ -572,7 +586,7 @@ __device__ __forceinline__ void first_body(const StageArgs<R>& A, int bx, int f,
     cpx<R> v[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) v[c] = res[(c * rows + j) * ld + pad32(x)];
-    h0_mi<R>(v, (R)kappa_of(x, nx, A.g.L[0], F->K[0]), ky, kz, sc);
+    h0_mi<R>(v, nx > 1 ? A.kap[x] : (R)F->K[0], ky, kz, sc);
 #pragma unroll
     for (int c = 0; c < 4; ++c) res[(c * rows + j) * ld + pad32(x)] = v[c];
   }
@@ -654,8 +668,8 @@ __device__ __forceinline__ void mid_body(const StageArgs<R>& A, int bx, int f, i
       cpx<R> v[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) v[c] = res[(c * TX + t) * ld + pad32(m)];
-      h0_mi<R>(v, (R)kappa_of(x, nx, A.g.L[0], F->K[0]), (R)kappa_of(iy, ny, A.g.L[1], F->K[1]),
-               (R)kappa_of(iz, nz, A.g.L[2], F->K[2]), sc);
+      h0_mi<R>(v, nx > 1 ? A.kap[x] : (R)F->K[0], ny > 1 ? A.kap[nx + iy] : (R)F->K[1],
+               nz > 1 ? A.kap[nx + ny + iz] : (R)F->K[2], sc);
 #pragma unroll
       for (int c = 0; c < 4; ++c) res[(c * TX + t) * ld + pad32(m)] = v[c];
     }
@@ -1008,14 +1022,18 @@ static swf_status prepare_args(swf_ctx* ctx, const GridDesc& g, int F, const Fie
   if ((s = ws_get(ctx, t + ".fd", sizeof(FieldDesc) * F, &pfd)) != SWF_OK) return s;
   if ((s = ws_get(ctx, t + ".greal", sizeof(R) * F * nt, &pgr)) != SWF_OK) return s;
   if ((s = ws_get(ctx, t + ".gcplx", sizeof(cpx<R>) * F * (nt + 4), &pgc)) != SWF_OK) return s;
+  void* pkap = nullptr;
+  if ((s = ws_get(ctx, t + ".kap", sizeof(R) * nt, &pkap)) != SWF_OK) return s;
   cudaError_t e = cudaMemcpyAsync(pfd, fd_host, sizeof(FieldDesc) * F, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "upload field descriptors");
   A->fd = (const FieldDesc*)pfd;
   A->greal = (const R*)pgr;
   A->gcplx = (const cpx<R>*)pgc;
+  A->kap = (const R*)pkap;
   dim3 tg((nt + 4 + 127) / 128, F);
   ProfScope ps(ctx, "k_tables", st);
   k_tables<R><<<tg, 128, 0, st>>>(A->fd, g, (R*)pgr, (cpx<R>*)pgc);
+  k_kappa_table<R><<<(nt + 127) / 128, 128, 0, st>>>(g, (R*)pkap);
   return SWF_OK;
 }
 
@@ -1754,7 +1772,7 @@ __global__ void k_store_field_desc(FieldDesc fd, FieldDesc* dst) { *dst = fd; }
 size_t rhs_scratch_bytes(const GridDesc& g, swf_precision prec) {
   const size_t e = prec == SWF_C64 ? 8 : 16, r = prec == SWF_C64 ? 4 : 8;
   const size_t nt = g.n[0] + g.n[1] + g.n[2];
-  return align256(4 * (size_t)g.N * e) + align256(sizeof(FieldDesc)) + align256(nt * r) +
+  return align256(4 * (size_t)g.N * e) + align256(sizeof(FieldDesc)) + 2 * align256(nt * r) +
          align256((nt + 4) * e) + 3 * align256(512 * e);
 }
 
@@ -1776,6 +1794,8 @@ static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, doubl
   p += align256((size_t)nt * sizeof(R));
   cpx<R>* gcplx = (cpx<R>*)p;
   p += align256((size_t)(nt + 4) * sizeof(cpx<R>));
+  R* kap = (R*)p;
+  p += align256((size_t)nt * sizeof(R));
   StageArgs<R> A;
   std::memset(&A, 0, sizeof(A));
   A.g = g;
@@ -1792,6 +1812,8 @@ static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, doubl
   }
   k_store_field_desc<<<1, 1, 0, st>>>(fd, dfd);
   k_tables<R><<<dim3((nt + 4 + 127) / 128, 1), 128, 0, st>>>(dfd, g, greal, gcplx);
+  k_kappa_table<R><<<(nt + 127) / 128, 128, 0, st>>>(g, kap);
+  A.kap = kap;
   A.fd = dfd;
   A.greal = greal;
   A.gcplx = gcplx;
