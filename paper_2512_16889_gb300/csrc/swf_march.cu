@@ -51,6 +51,7 @@ struct StageArgs {
   const cpx<R>* tw[3];
   const R* kap;         // mode momenta kappa_j = 2 pi j'/L_a of the axes with n_a > 1, rounded once
                         // from FP64, at offsets 0, nx, nx + ny (FP64 is scarce on this GPU)
+  R inv_n;              // 1/N rounded once
   RadixPlan plan[3];
   GridDesc g;
   int nrows;            // ny * nz
@@ -471,7 +472,7 @@ __device__ __forceinline__ void first_body(const StageArgs<R>& A, int bx, int f,
   cpx<R>* buf2 = buf + 4 * rows * ld;
   const double hscale = A.ctl ? A.ctl->h : 1.0;  // stage coefficients are a_ij (times h here) under control
   cpx<R>* const yout = A.ynew ? A.ynew : A.y;
-  __shared__ double s_ft[64];
+  __shared__ R s_ft[64];  // field time factor per row, computed in FP64 and rounded once
   __shared__ cpx<R> s_tf;
   const int row0 = bx * rows;
   const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
@@ -482,7 +483,7 @@ __device__ __forceinline__ void first_body(const StageArgs<R>& A, int bx, int f,
   for (int j = threadIdx.x; j < rows; j += blockDim.x) {
     const int iy = (row0 + j) % ny;
     const double yc = ny > 1 ? A.g.x0[1] + iy * A.g.dx[1] : 0.0;
-    s_ft[j] = field_time_factor(*F, tst, yc);
+    s_ft[j] = (R)field_time_factor(*F, tst, yc);
   }
   if (threadIdx.x == 0) {
     double sn, cs;
@@ -548,7 +549,7 @@ __device__ __forceinline__ void first_body(const StageArgs<R>& A, int bx, int f,
       }
       // local term Z = -i V (Y + psi_b), kept in the output slot until the last pass
       const int iy = row % ny, iz = row / ny;
-      const R a = (R)s_ft[j] * gx[x] * gy[iy] * gz[iz];
+      const R a = s_ft[j] * gx[x] * gy[iy] * gz[iz];
       const cpx<R> ph = s_tf * ex[x] * ey[iy] * ez[iz];
       cpx<R> phi[4], vz[4];
 #pragma unroll
@@ -579,14 +580,14 @@ __device__ __forceinline__ void first_body(const StageArgs<R>& A, int bx, int f,
     return;
   }
   // one non-trivial axis: the whole derivative in this block
-  const R sc = (R)(1.0 / (double)N);
-  const R ky = (R)F->K[1], kz = (R)F->K[2];
+  const R sc = A.inv_n;
+  const R kx0 = (R)F->K[0], ky = (R)F->K[1], kz = (R)F->K[2];
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / nx, x = e - j * nx;
     cpx<R> v[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) v[c] = res[(c * rows + j) * ld + pad32(x)];
-    h0_mi<R>(v, nx > 1 ? A.kap[x] : (R)F->K[0], ky, kz, sc);
+    h0_mi<R>(v, nx > 1 ? A.kap[x] : kx0, ky, kz, sc);
 #pragma unroll
     for (int c = 0; c < 4; ++c) res[(c * rows + j) * ld + pad32(x)] = v[c];
   }
@@ -658,7 +659,8 @@ __device__ __forceinline__ void mid_body(const StageArgs<R>& A, int bx, int f, i
   }
   if (do_h0) {
     const FieldDesc* F = A.fd + f;
-    const R sc = (R)(1.0 / (double)N);
+    const R sc = A.inv_n;
+    const R K0 = (R)F->K[0], K1 = (R)F->K[1], K2 = (R)F->K[2];  // momenta along trivial axes
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int t = e / na, m = e - t * na;
       const int x = xt * TX + t;
@@ -668,8 +670,7 @@ __device__ __forceinline__ void mid_body(const StageArgs<R>& A, int bx, int f, i
       cpx<R> v[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) v[c] = res[(c * TX + t) * ld + pad32(m)];
-      h0_mi<R>(v, nx > 1 ? A.kap[x] : (R)F->K[0], ny > 1 ? A.kap[nx + iy] : (R)F->K[1],
-               nz > 1 ? A.kap[nx + ny + iz] : (R)F->K[2], sc);
+      h0_mi<R>(v, nx > 1 ? A.kap[x] : K0, ny > 1 ? A.kap[nx + iy] : K1, nz > 1 ? A.kap[nx + ny + iz] : K2, sc);
 #pragma unroll
       for (int c = 0; c < 4; ++c) res[(c * TX + t) * ld + pad32(m)] = v[c];
     }
@@ -1030,6 +1031,7 @@ static swf_status prepare_args(swf_ctx* ctx, const GridDesc& g, int F, const Fie
   A->greal = (const R*)pgr;
   A->gcplx = (const cpx<R>*)pgc;
   A->kap = (const R*)pkap;
+  A->inv_n = (R)(1.0 / (double)g.N);
   dim3 tg((nt + 4 + 127) / 128, F);
   ProfScope ps(ctx, "k_tables", st);
   k_tables<R><<<tg, 128, 0, st>>>(A->fd, g, (R*)pgr, (cpx<R>*)pgc);
@@ -1814,6 +1816,7 @@ static swf_status rhs_scratch_impl(const GridDesc& g, const FieldDesc& fd, doubl
   k_tables<R><<<dim3((nt + 4 + 127) / 128, 1), 128, 0, st>>>(dfd, g, greal, gcplx);
   k_kappa_table<R><<<(nt + 127) / 128, 128, 0, st>>>(g, kap);
   A.kap = kap;
+  A.inv_n = (R)(1.0 / (double)g.N);
   A.fd = dfd;
   A.greal = greal;
   A.gcplx = gcplx;
@@ -2115,7 +2118,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_f2_x(StageArgs<
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* buf2 = buf + 4 * rows * ld;
-  __shared__ double s_ft[64];
+  __shared__ R s_ft[64];  // field time factor per row, computed in FP64 and rounded once
   __shared__ cpx<R> s_tf;
   __shared__ cpx<double> red[8][4];
   const int f = blockIdx.y;
@@ -2130,7 +2133,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_f2_x(StageArgs<
   for (int j = threadIdx.x; j < rows; j += blockDim.x) {
     const int iy = (row0 + j) % ny;
     const double yc = ny > 1 ? A.g.x0[1] + iy * A.g.dx[1] : 0.0;
-    s_ft[j] = field_time_factor(*F, tst, yc);
+    s_ft[j] = (R)field_time_factor(*F, tst, yc);
   }
   if (threadIdx.x == 0) {
     double sn, c;
@@ -2166,7 +2169,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_f2_x(StageArgs<
         for (int c = 0; c < 4; ++c) v[c] = ys[gi + c * cs];
         if (part == 1) {
           const int iy = row % ny, iz = row / ny;
-          const R a = (R)s_ft[j] * gx[x] * gy[iy] * gz[iz];
+          const R a = s_ft[j] * gx[x] * gy[iy] * gz[iz];
           const cpx<R> ph = s_tf * ex[x] * ey[iy] * ez[iz];
           cpx<R> phi[4], vz[4];
 #pragma unroll
