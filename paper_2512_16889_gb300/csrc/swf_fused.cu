@@ -1615,13 +1615,14 @@ int fused_resident_clusters(swf_ctx* ctx) {
 // n_1 = floor((R - r) ncl / 2) fields to the clusters and n_2 = n_f - n_1 to the pass kernels,
 // which take about alpha n_2 rounds' time on the free SMs.  alpha was measured with 40 free SMs
 // on (2+1)D 256^2 complex64 marches: 16 fields on the free SMs took as long as 32 rounds of the
-// kernel with pulled transposes (alpha = 2.0); a round of the kernel with pushed transposes is
-// 1.46 times shorter (alpha = 2.91).  alpha scales with 40 / (free SMs).  The largest r with
+// kernel with pulled transposes (alpha = 2.0).  With the kernel with pushed transposes and the
+// pass kernels' tables of mode momenta, 9 fields took 1.88 s on the free SMs while a fused round
+// took 84.9 ms (alpha = 2.45).  alpha scales with 40 / (free SMs).  The largest r with
 // alpha n_2 <= R - r is taken.
 int fused_split_count(int n_f, int ncl, int n_sm, int variant) {
   const int free_sm = n_sm - fused::CL * ncl;
   if (ncl < 1 || free_sm < 16 || n_f < 16) return 0;
-  const double alpha = (variant == 3 ? 2.91 : 2.0) * 40.0 / free_sm;
+  const double alpha = (variant == 3 ? 2.45 : 2.0) * 40.0 / free_sm;
   const int R = (2 * n_f + ncl - 1) / ncl;
   int best = 0;
   for (int r = 1; r < R; ++r) {

@@ -1033,8 +1033,11 @@ static swf_status prepare_args(swf_ctx* ctx, const GridDesc& g, int F, const Fie
   A->kap = (const R*)pkap;
   A->inv_n = (R)(1.0 / (double)g.N);
   dim3 tg((nt + 4 + 127) / 128, F);
-  ProfScope ps(ctx, "k_tables", st);
-  k_tables<R><<<tg, 128, 0, st>>>(A->fd, g, (R*)pgr, (cpx<R>*)pgc);
+  {
+    ProfScope ps(ctx, "k_tables", st);
+    k_tables<R><<<tg, 128, 0, st>>>(A->fd, g, (R*)pgr, (cpx<R>*)pgc);
+  }
+  ProfScope pk(ctx, "k_kappa_table", st);
   k_kappa_table<R><<<(nt + 127) / 128, 128, 0, st>>>(g, (R*)pkap);
   return SWF_OK;
 }

@@ -82,14 +82,14 @@ def test_errors_without_device(lib):
 
 
 def test_split_plan_of_fused_marches(lib):
-    """Host logic of the fused/pass split (default fused kernel, pushed transposes, alpha = 2.91
+    """Host logic of the fused/pass split (default fused kernel, pushed transposes, alpha = 2.45
     sector rounds per pass-kernel field with 40 free SMs): the benchmark's 128 fields on GB300's
-    152 SMs and 7 resident 16-CTA clusters give 9 fields to the pass kernels (R = 37 rounds; 34
-    rounds leave 9 fields, 9 x 2.91 <= 34, while 33 rounds would leave 13, 13 x 2.91 > 33); the
+    152 SMs and 7 resident 16-CTA clusters give 13 fields to the pass kernels (R = 37 rounds; 33
+    rounds leave 13 fields, 13 x 2.45 <= 33, while 32 rounds would leave 16, 16 x 2.45 > 32); the
     fused part always ends in fewer sector rounds than the whole, and the pass part stays within
     the time model."""
     from paper_2512_16889_gb300 import swf
-    assert swf.plan_split(128, 7, 152) == 9
+    assert swf.plan_split(128, 7, 152) == 13
     assert swf.plan_split(14, 7, 152) == 0      # too few fields
     assert swf.plan_split(128, 9, 152) == 0     # too few free SMs
     assert swf.plan_split(128, 0, 152) == 0
@@ -101,7 +101,7 @@ def test_split_plan_of_fused_marches(lib):
         rounds_all = -(-2 * n // 7)
         rounds_fused = -(-2 * n1 // 7)
         assert 0 < n2 < n and rounds_fused < rounds_all, n
-        assert 2.91 * n2 <= rounds_fused + 1e-12, n
+        assert 2.45 * n2 <= rounds_fused + 1e-12, n
     with pytest.raises(swf.SwfError) as ei:
         swf.plan_split(-1, 7, 152)
     assert ei.value.status == swf.SWF_EINVAL
