@@ -736,6 +736,17 @@ __global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) 
   last_body<R>(A, blockIdx.x, blockIdx.y, rows, ld);
 }
 
+// The x lines of one evaluation's end and the next one's start in one launch: k_i = inverse
+// x-FFT of T + Z for stage P, then the stage combine, local term and forward x-FFT of stage Nx on
+// the same rows.  Each thread reads back the k_i entries it has just written (the two bodies map
+// the rows' entries to threads alike), so the arithmetic is that of k_last then k_first.
+template <typename R>
+__global__ void __launch_bounds__(256) k_last_first(StageArgs<R> P, StageArgs<R> Nx, int rows, int ld) {
+  last_body<R>(P, blockIdx.x, blockIdx.y, rows, ld);
+  __syncthreads();
+  first_body<R>(Nx, blockIdx.x, blockIdx.y, rows, ld, 0);
+}
+
 // ---------------------------------------------------------------- host side
 template <typename R> struct Prec;
 template <> struct Prec<float> { static constexpr int is_double = 0; };
@@ -857,29 +868,40 @@ static swf_status set_smem_attrs() {
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_mid)");
   e = cudaFuncSetAttribute(k_last<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last)");
+  e = cudaFuncSetAttribute(k_last_first<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemTune);
+  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_last_first)");
   done[dv].store(true, std::memory_order_release);
   return SWF_OK;
 }
 
-// Launches one right-hand-side evaluation for F fields (ctx may be null: no profiling).
+// Launch shape of the x passes (k_first, k_last, k_last_first): rows per block, threads, padded
+// line length, shared memory, grid.
+struct XLaunch {
+  int rows, thr, ld;
+  size_t smem;
+  dim3 grid;
+};
+
 template <typename R>
-static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaStream_t st) {
-  const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
+static XLaunch x_launch(swf_ctx* ctx, const StageArgs<R>& A, int F) {
   constexpr int esz = (int)sizeof(cpx<R>);
+  const int nx = A.g.n[0];
   // tuned values: rows (x passes) or log2 TX (y, z passes) times 4, plus 1 for 128-thread blocks
   const int xv = tune_lookup(ctx, tune_key('x', esz, nx, A.nrows, 0, F), 4 * x_rows<R>(nx, A.nrows, F));
-  const int rows = xv >> 2;
-  const int xthr = (xv & 3) ? kThreads / 2 : kThreads;
-  if (rows < 1) return SWF_EUNSUPPORTED;
-  const int ld = padded_len(nx);
-  const bool only_x = (ny == 1 && nz == 1);
-  const size_t smem = (size_t)2 * 4 * rows * ld * sizeof(cpx<R>);
-  dim3 grid_rows((A.nrows + rows - 1) / rows, F);
-  {
-    ProfScope ps(ctx, "k_first", st);
-    k_first<R><<<grid_rows, xthr, smem, st>>>(A, rows, ld, only_x ? 1 : 0);
-  }
-  if (only_x) return SWF_OK;
+  XLaunch L;
+  L.rows = xv >> 2;
+  L.thr = (xv & 3) ? kThreads / 2 : kThreads;
+  L.ld = padded_len(nx);
+  L.smem = (size_t)2 * 4 * (L.rows > 0 ? L.rows : 1) * L.ld * sizeof(cpx<R>);
+  L.grid = dim3(L.rows > 0 ? (A.nrows + L.rows - 1) / L.rows : 1, F);
+  return L;
+}
+
+// The y and z passes of one evaluation.
+template <typename R>
+static void launch_mids(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaStream_t st) {
+  const int nx = A.g.n[0], ny = A.g.n[1], nz = A.g.n[2];
+  constexpr int esz = (int)sizeof(cpx<R>);
   int axes[2], na = 0;
   if (ny > 1) axes[na++] = 1;
   if (nz > 1) axes[na++] = 2;
@@ -896,15 +918,67 @@ static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaSt
   };
   if (na == 1) {
     mid(axes[0], 1, 1, 1);
-  } else {
+  } else if (na == 2) {
     mid(1, 1, 0, 0);
     mid(2, 1, 1, 1);
     mid(1, 0, 0, 1);
   }
+}
+
+// Launches one right-hand-side evaluation for F fields (ctx may be null: no profiling).
+template <typename R>
+static swf_status launch_eval(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaStream_t st) {
+  const bool only_x = (A.g.n[1] == 1 && A.g.n[2] == 1);
+  const XLaunch L = x_launch<R>(ctx, A, F);
+  if (L.rows < 1) return SWF_EUNSUPPORTED;
+  {
+    ProfScope ps(ctx, "k_first", st);
+    k_first<R><<<L.grid, L.thr, L.smem, st>>>(A, L.rows, L.ld, only_x ? 1 : 0);
+  }
+  if (only_x) return SWF_OK;
+  launch_mids<R>(ctx, A, F, st);
   {
     ProfScope ps(ctx, "k_last", st);
-    k_last<R><<<grid_rows, xthr, smem, st>>>(A, rows, ld);
+    k_last<R><<<L.grid, L.thr, L.smem, st>>>(A, L.rows, L.ld);
   }
+  return SWF_OK;
+}
+
+// An evaluation whose inverse x pass is left for the next launch (march chains with at least one
+// non-trivial axis besides x): k_first and the y/z passes of A.
+template <typename R>
+static swf_status launch_eval_open(swf_ctx* ctx, const StageArgs<R>& A, int F, cudaStream_t st) {
+  const XLaunch L = x_launch<R>(ctx, A, F);
+  if (L.rows < 1) return SWF_EUNSUPPORTED;
+  {
+    ProfScope ps(ctx, "k_first", st);
+    k_first<R><<<L.grid, L.thr, L.smem, st>>>(A, L.rows, L.ld, 0);
+  }
+  launch_mids<R>(ctx, A, F, st);
+  return SWF_OK;
+}
+
+// Closes the open evaluation P and runs evaluation Nx with it: k_last_first, then Nx's y/z passes.
+template <typename R>
+static swf_status launch_eval_chain(swf_ctx* ctx, const StageArgs<R>& P, const StageArgs<R>& Nx, int F,
+                                    cudaStream_t st) {
+  const XLaunch L = x_launch<R>(ctx, Nx, F);
+  if (L.rows < 1) return SWF_EUNSUPPORTED;
+  {
+    ProfScope ps(ctx, "k_last_first", st);
+    k_last_first<R><<<L.grid, L.thr, L.smem, st>>>(P, Nx, L.rows, L.ld);
+  }
+  launch_mids<R>(ctx, Nx, F, st);
+  return SWF_OK;
+}
+
+// Closes the open evaluation P (its inverse x pass).
+template <typename R>
+static swf_status launch_eval_close(swf_ctx* ctx, const StageArgs<R>& P, int F, cudaStream_t st) {
+  const XLaunch L = x_launch<R>(ctx, P, F);
+  if (L.rows < 1) return SWF_EUNSUPPORTED;
+  ProfScope ps(ctx, "k_last", st);
+  k_last<R><<<L.grid, L.thr, L.smem, st>>>(P, L.rows, L.ld);
   return SWF_OK;
 }
 
@@ -1153,13 +1227,20 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
   MarchClock* clk = (MarchClock*)pclk;
   k_clock_set<<<1, 1, 0, st>>>(clk, t_out, h);
   A.clk = clk;
+  // Evaluations chain: each one's inverse x pass runs in one launch with the next one's forward x
+  // pass (k_last_first), except on grids with x as the only non-trivial axis (one pass per
+  // evaluation).  The open evaluation after every second step writes slot 0, as the first
+  // evaluation does, so a recorded pair of steps replays unchanged.
+  const bool chain = !(g.n[1] == 1 && g.n[2] == 1);
+  StageArgs<R> open = A;
   // k_1 = f(t_out, 0)
   A.nterm = 0;
   A.write_y = 0;
   A.kout = (cpx<R>*)pk[slot[0]];
   A.ls = 0;
   A.c = 0.0;
-  if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  if ((s = chain ? launch_eval_open<R>(ctx, A, F, st) : launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  open = A;
   // one step at clock offset ls (stage times from the clock: the same arithmetic as
   // tn = t_out + n h, t = tn + c_i h)
   auto step = [&](int ls) -> swf_status {
@@ -1176,8 +1257,9 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
       A.kout = (cpx<R>*)pk[slot[i]];
       A.ls = ls;
       A.c = DP_C[i];
-      swf_status r = launch_eval<R>(ctx, A, F, st);
+      swf_status r = chain ? launch_eval_chain<R>(ctx, open, A, F, st) : launch_eval<R>(ctx, A, F, st);
       if (r != SWF_OK) return r;
+      open = A;
     }
     std::swap(slot[0], slot[6]);
     return SWF_OK;
@@ -1188,6 +1270,7 @@ static swf_status march_impl(swf_ctx* ctx, const GridDesc& g, double t_in, doubl
   });
   if (s != SWF_OK) return s;
   if (n_steps % 2 && (s = step(0)) != SWF_OK) return s;
+  if (chain && (s = launch_eval_close<R>(ctx, open, F, st)) != SWF_OK) return s;
   e = cudaMemcpyAsync(psi_out, py, state, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_status(e, "copy psi(t_in)");
   e = cudaGetLastError();
@@ -2605,7 +2688,11 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   A.ls = 0;
   A.c = 0.0;
   A.ystage = nullptr;  // the integrand of Eq. 17 vanishes at psi_s(t_out) = 0
-  if ((s = launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  // evaluations chain through k_last_first as in march_impl (the integrands read only the stage
+  // value and the transforms written by the forward passes, never T or the k slots)
+  const bool chain = !(g.n[1] == 1 && g.n[2] == 1);
+  if ((s = chain ? launch_eval_open<R>(ctx, A, F, st) : launch_eval<R>(ctx, A, F, st)) != SWF_OK) return s;
+  StageArgs<R> open = A;
   // the partial-integration integrand does not (its source term is V psi_b): stage value y = 0
   if (form == 2 && (s = f2_integrand<R>(ctx, A, p2, (const cpx<R>*)py, (const double*)pph, (const cpx<double>*)ptab,
                                         7 * n_steps, 0, 0, st)) != SWF_OK)
@@ -2630,8 +2717,9 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
       const bool weighted = i >= 2;
       A.ystage = weighted ? (cpx<R>*)pys : nullptr;
       A.yspec = (weighted && form == 2) ? p2.Yspec : nullptr;  // the y or z pass writes F[Y] (if there is one)
-      swf_status r = launch_eval<R>(ctx, A, F, st);
+      swf_status r = chain ? launch_eval_chain<R>(ctx, open, A, F, st) : launch_eval<R>(ctx, A, F, st);
       if (r != SWF_OK) return r;
+      open = A;
       if (weighted && form == 2) {
         if ((r = f2_integrand<R>(ctx, A, p2, (const cpx<R>*)pys, (const double*)pph, (const cpx<double>*)ptab,
                                  7 * n_steps, ls, i, st)) != SWF_OK)
@@ -2663,6 +2751,7 @@ static swf_status march_bw_impl(swf_ctx* ctx, const GridDesc& g, double t_in, do
   });
   if (s != SWF_OK) return s;
   if (n_steps % 2 && (s = step(0)) != SWF_OK) return s;
+  if (chain && (s = launch_eval_close<R>(ctx, open, F, st)) != SWF_OK) return s;
   if (form == 2) {
     ProfScope ps(ctx, "k_f2_final", st);
     k_f2_final<<<n_inst, 288, 0, st>>>(p2.sspart, p2.nbs, p2.dpart, p2.nbx, (cpx<double>*)macc);
