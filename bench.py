@@ -961,8 +961,10 @@ def run_workload(args):
 
 def run_small_march(args):
     """One march for profiler captures, complex64, through swf_march_dev: 14 instances (28
-    sectors) of the batched workload for 20 steps (--small-march), or all 128 instances for the
-    full 1000 steps in one fused launch with no fields on the pass kernels (--fused-march)."""
+    sectors) of the batched workload for 20 steps (--small-march), all 128 instances for the
+    full 1000 steps in one fused launch with no fields on the pass kernels (--fused-march), or 16
+    instances for 4 steps on the pass kernels alone with their default launch shapes
+    (--small-pass)."""
     import torch
     from paper_2512_16889_gb300 import build, swf
     from paper_2512_16889_gb300 import workloads as W
@@ -972,6 +974,11 @@ def run_small_march(args):
         ctx.set_dedupe(False)
         ctx.set_march_path(2)
         ds = W.schwinger_batched()
+    elif args.small_pass:
+        ctx.set_dedupe(False)
+        ctx.set_march_path(1)
+        ctx.set_autotune(False)
+        ds = W.schwinger_batched(n_steps=4)[:16]
     else:
         ds = W.schwinger_batched(n_steps=20, t_window=0.4)[:14]
     out = torch.zeros(len(ds) * 8 * 256 * 256, dtype=torch.float32, device="cuda")
@@ -993,6 +1000,8 @@ def main():
     ap.add_argument("--small-march", action="store_true", help="one small march for profiler captures")
     ap.add_argument("--fused-march", action="store_true",
                     help="the benchmark's march as one fused launch, for profiler captures at full size")
+    ap.add_argument("--small-pass", action="store_true",
+                    help="a small march on the pass kernels alone, for profiler captures")
     ap.add_argument("--workload", default=None, help="time another workload (see run_workload)")
     ap.add_argument("--limit", type=int, default=0, help="at most this many instances (--workload)")
     ap.add_argument("--max-steps", type=int, default=0, help="at most this many steps (--workload)")
@@ -1007,7 +1016,7 @@ def main():
     ap.add_argument("--bw-partial", action="store_true",
                     help="partial-integration form of the Breit-Wheeler terms (--workload bw_uneven)")
     args = ap.parse_args()
-    if args.small_march or args.fused_march:
+    if args.small_march or args.fused_march or args.small_pass:
         return run_small_march(args)
     if args.workload == "surrogate":
         return run_surrogate(args)

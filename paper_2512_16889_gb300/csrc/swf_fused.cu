@@ -1608,33 +1608,6 @@ int fused_resident_clusters(swf_ctx* ctx) {
   return g_fused_clusters[dev_slot()][var] - 1;
 }
 
-// The fused kernel's 16-CTA clusters (one CTA per SM) fit once per GPC, so some SMs stay idle
-// (on GB300: 7 clusters on 112 of 152 SMs).  Moving some fields to the pass kernels, run
-// concurrently on those SMs, shortens the march when they finish within the fused kernel's
-// time.  With R = ceil(2 n_f / ncl) rounds of sectors per cluster, removing r rounds leaves
-// n_1 = floor((R - r) ncl / 2) fields to the clusters and n_2 = n_f - n_1 to the pass kernels,
-// which take about alpha n_2 rounds' time on the free SMs.  alpha was measured with 40 free SMs
-// on (2+1)D 256^2 complex64 marches: 16 fields on the free SMs took as long as 32 rounds of the
-// kernel with pulled transposes (alpha = 2.0).  With the kernel with pushed transposes and the
-// pass kernels' tables of mode momenta, 9 fields took 1.88 s on the free SMs while a fused round
-// took 84.9 ms (alpha = 2.45).  alpha scales with 40 / (free SMs).  The largest r with
-// alpha n_2 <= R - r is taken.
-int fused_split_count(int n_f, int ncl, int n_sm, int variant) {
-  const int free_sm = n_sm - fused::CL * ncl;
-  if (ncl < 1 || free_sm < 16 || n_f < 16) return 0;
-  const double alpha = (variant == 3 ? 2.45 : 2.0) * 40.0 / free_sm;
-  const int R = (2 * n_f + ncl - 1) / ncl;
-  int best = 0;
-  for (int r = 1; r < R; ++r) {
-    const int n1 = ((R - r) * ncl) / 2;
-    const int n2 = n_f - n1;
-    if (n2 <= 0) continue;
-    if (alpha * n2 > (double)(R - r)) break;
-    best = n2;
-  }
-  return best;
-}
-
 swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_out, int n_steps, int n_f,
                        const FieldDesc* fd_host, void* psi_out, cudaStream_t st) {
   using namespace fused;

@@ -116,6 +116,8 @@ struct TuneCache {
 // Fused kernel of march paths 0 and 2: 1 = threads pull the transposes through distributed
 // shared memory (k_fused), 3 = the bulk-copy engine pushes them while the threads compute (k_fused3).
 constexpr int kDefaultFusedVariant = 3;
+// CTAs per cluster of the fused kernels (one CTA per SM).
+constexpr int kFusedClusterCtas = 16;
 
 struct swf_ctx {
   int device;

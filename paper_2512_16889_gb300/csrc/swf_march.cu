@@ -1727,6 +1727,32 @@ static swf_status reserve_march(swf_ctx* ctx, const GridDesc& g, int F) {
   return SWF_OK;
 }
 
+// The fused kernel's 16-CTA clusters (one CTA per SM) fit once per GPC, so some SMs stay idle
+// (on GB300: 7 clusters on 112 of 152 SMs).  Moving some fields to the pass kernels, run
+// concurrently on those SMs, shortens the march when they finish within the fused kernel's
+// time.  With R = ceil(2 n_f / ncl) rounds of sectors per cluster, removing r rounds leaves
+// n_1 = floor((R - r) ncl / 2) fields to the clusters and n_2 = n_f - n_1 to the pass kernels,
+// which take about alpha n_2 rounds' time on the free SMs.  alpha was measured with 40 free SMs
+// on (2+1)D 256^2 complex64 marches: with the pushed-transpose kernel and the chained x passes,
+// 16 fields took 2.75 s on the free SMs while the fused launch took 32 rounds in 2.78 s
+// (alpha = 2.0); rounds of the pulled-transpose kernel are 1.46 times longer (alpha = 1.37).
+// alpha scales with 40 / (free SMs).  The largest r with alpha n_2 <= R - r is taken.
+int fused_split_count(int n_f, int ncl, int n_sm, int variant) {
+  const int free_sm = n_sm - kFusedClusterCtas * ncl;
+  if (ncl < 1 || free_sm < 16 || n_f < 16) return 0;
+  const double alpha = (variant == 3 ? 2.0 : 1.37) * 40.0 / free_sm;
+  const int R = (2 * n_f + ncl - 1) / ncl;
+  int best = 0;
+  for (int r = 1; r < R; ++r) {
+    const int n1 = ((R - r) * ncl) / 2;
+    const int n2 = n_f - n1;
+    if (n2 <= 0) continue;
+    if (alpha * n2 > (double)(R - r)) break;
+    best = n2;
+  }
+  return best;
+}
+
 // The fused kernel on the first n_f - n2 fields (stream st) and, concurrently, the pass kernels
 // on the last n2 fields (the context's auxiliary stream), which take the SMs that the fused
 // kernel's clusters leave free.  The auxiliary stream starts after the work already queued on

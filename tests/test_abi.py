@@ -82,14 +82,14 @@ def test_errors_without_device(lib):
 
 
 def test_split_plan_of_fused_marches(lib):
-    """Host logic of the fused/pass split (default fused kernel, pushed transposes, alpha = 2.45
+    """Host logic of the fused/pass split (default fused kernel, pushed transposes, alpha = 2.0
     sector rounds per pass-kernel field with 40 free SMs): the benchmark's 128 fields on GB300's
-    152 SMs and 7 resident 16-CTA clusters give 13 fields to the pass kernels (R = 37 rounds; 33
-    rounds leave 13 fields, 13 x 2.45 <= 33, while 32 rounds would leave 16, 16 x 2.45 > 32); the
+    152 SMs and 7 resident 16-CTA clusters give 16 fields to the pass kernels (R = 37 rounds; 32
+    rounds leave 16 fields, 16 x 2.0 <= 32, while 31 rounds would leave 20, 20 x 2.0 > 31); the
     fused part always ends in fewer sector rounds than the whole, and the pass part stays within
     the time model."""
     from paper_2512_16889_gb300 import swf
-    assert swf.plan_split(128, 7, 152) == 13
+    assert swf.plan_split(128, 7, 152) == 16
     assert swf.plan_split(14, 7, 152) == 0      # too few fields
     assert swf.plan_split(128, 9, 152) == 0     # too few free SMs
     assert swf.plan_split(128, 0, 152) == 0
@@ -101,7 +101,7 @@ def test_split_plan_of_fused_marches(lib):
         rounds_all = -(-2 * n // 7)
         rounds_fused = -(-2 * n1 // 7)
         assert 0 < n2 < n and rounds_fused < rounds_all, n
-        assert 2.45 * n2 <= rounds_fused + 1e-12, n
+        assert 2.0 * n2 <= rounds_fused + 1e-12, n
     with pytest.raises(swf.SwfError) as ei:
         swf.plan_split(-1, 7, 152)
     assert ei.value.status == swf.SWF_EINVAL
