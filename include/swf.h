@@ -224,6 +224,16 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
  * arithmetic in the same order. */
 swf_status swf_set_march_path(swf_ctx* ctx, int path);
 
+/* Status of the context's last march on the pushed-transpose fused kernel (march paths 0, 2
+ * and 5): *status = 0 when every transpose arrived, 1 when a CTA's receive wait ran out (after
+ * about half a second), in which case that CTA stopped copying and wrote NaN for its rows while
+ * keeping to the cluster's barriers, so the kernel still ended.  Synchronises the context's
+ * stream.  0 if no such march has run. */
+swf_status swf_fused_status(swf_ctx* ctx, int* status);
+/* Diagnostic for the bounded waits above: on = 1 makes the pushed-transpose kernel issue none of
+ * its transposes, so that every receive wait runs out (tests only; default 0). */
+swf_status swf_set_fused_drop(swf_ctx* ctx, int on);
+
 /* Tolerances of step-size-controlled marches (SWF_ADAPTIVE): a Dormand-Prince 5(4) step is
  * accepted when the RMS over the field's complex entries of |e|/(atol + rtol max(|y_n|, |y_n+1|))
  * is at most 1 (the largest over the fields of one call), e the difference of the fifth- and

@@ -882,6 +882,22 @@ swf_status swf_set_march_path(swf_ctx* ctx, int path) {
   return SWF_OK;
 }
 
+swf_status swf_fused_status(swf_ctx* ctx, int* status) {
+  if (!ctx || !status) { set_error("swf_fused_status: NULL argument"); return SWF_EINVAL; }
+  *status = 0;
+  if (!ctx->fused_status_dev) return SWF_OK;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(status, ctx->fused_status_dev, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e, "read the fused kernel's status");
+  return SWF_OK;
+}
+
+swf_status swf_set_fused_drop(swf_ctx* ctx, int on) {
+  if (!ctx) { set_error("swf_set_fused_drop: ctx is NULL"); return SWF_EINVAL; }
+  ctx->fused_drop = on ? 1 : 0;
+  return SWF_OK;
+}
+
 swf_status swf_set_tolerances(swf_ctx* ctx, double rtol, double atol) {
   if (!ctx || !(rtol > 0.0) || !(atol > 0.0) || !std::isfinite(rtol) || !std::isfinite(atol)) {
     set_error("swf_set_tolerances: need ctx and positive finite rtol, atol");

@@ -54,6 +54,8 @@ struct Args {
   double Lx, Ly, t_out, h;
   int n_steps;
   const float4* ttab;      // per instance [n_steps][7]: field time factor, background time phase (re, im)
+  int* status;             // k_fused3: set to 1 when a receive wait ran out (may be null)
+  int drop;                // k_fused3 diagnostic: nonzero = no CTA copies, so every receive wait runs out
 };
 
 // shared-memory map (bytes)
@@ -1344,7 +1346,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       fence_async_smem();
       __syncthreads();
       cl_wait();  // every CTA's X2 is free and its receive barrier armed
-      if (warp == 0 && !err)
+      if (warp == 0 && !err && !A.drop)
         bulk_push(peer_addr(x2a + (uint32_t)((cc * CL + rank) * CHK * 8), peer),
                   x1a + (uint32_t)((cc * CL + peer) * CHK * 8), CHK * 8, peer_addr(bar_f, peer));
 
@@ -1387,6 +1389,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
         if (tid == 0 && !err) {
           bad = !mbar_wait3(bar_f, par_f);
           if (!bad) mbar_arm3(bar_b, XBYTES);  // for the backward transpose of this evaluation
+          else if (A.status) atomicOr(A.status, 1);
         }
         err = __syncthreads_or(bad) || err;
         par_f ^= 1u;
@@ -1399,7 +1402,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       fence_async_smem();
       __syncthreads();
       cl_wait();  // every CTA's X1 is free and its receive barrier armed
-      if (warp == 0 && !err)
+      if (warp == 0 && !err && !A.drop)
         bulk_push(peer_addr(x1a + (uint32_t)((cc * CL + rank) * CHK * 8), peer),
                   x2a + (uint32_t)((cc * CL + peer) * CHK * 8), CHK * 8, peer_addr(bar_b, peer));
 
@@ -1478,6 +1481,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
         if (tid == 0 && !err) {
           bad = !mbar_wait3(bar_b, par_b);
           if (!bad) mbar_arm3(bar_f, XBYTES);  // for the next forward transpose
+          else if (A.status) atomicOr(A.status, 1);
         }
         err = __syncthreads_or(bad) || err;
         par_b ^= 1u;
@@ -1668,7 +1672,14 @@ swf_status march_fused(swf_ctx* ctx, const GridDesc& g, double t_in, double t_ou
     k_time_table<<<nb, 256, 0, st>>>((const FieldDesc*)pfd, n_f, n_steps, t_out, (t_in - t_out) / n_steps,
                                      (float4*)ptab);
   }
+  void* pstatus;
+  if ((s = ws_get(ctx, "fused.status", sizeof(int), &pstatus)) != SWF_OK) return s;
+  e = cudaMemsetAsync(pstatus, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_status(e, "clear the fused kernel's status");
+  ctx->fused_status_dev = (int*)pstatus;
   Args A;
+  A.status = (int*)pstatus;
+  A.drop = var == 2 ? ctx->fused_drop : 0;
   A.ttab = (const float4*)ptab;
   A.fd = (const FieldDesc*)pfd;
   A.sec = (const Sector*)psec;

@@ -137,6 +137,8 @@ struct swf_ctx {
   long long multi_marches = 0;   // multi-grid marches run since the context's creation
   long long device_loop_marches = 0;  // step-size-controlled marches decided entirely on the device
   int fused_variant = kDefaultFusedVariant;  // 1: pulled transposes, 2: two CTAs per SM, 3: pushed
+  int fused_drop = 0;                // diagnostic: the pushed-transpose kernel issues no copies
+  int* fused_status_dev = nullptr;   // status word of the last fused launch (workspace)
   bool sm_split = true;   // automatic path: pass kernels on the SMs the fused clusters leave free
   cudaStream_t aux = nullptr;            // stream of that concurrent pass-kernel march (lazy)
   cudaEvent_t aux_ev[2] = {nullptr, nullptr};

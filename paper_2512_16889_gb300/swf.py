@@ -48,7 +48,7 @@ EXPORTS = ["swf_create", "swf_destroy", "swf_last_error", "solve_swf", "solve_sw
            "swf_bw_photons", "swf_march_dev",
            "swf_rhs_dev", "swf_spectrum_dev", "swf_set_workspace_limit", "swf_profile_enable",
            "swf_profile_read", "swf_set_march_path", "swf_set_autotune", "swf_set_dedupe", "swf_fields_marched",
-           "swf_fields_fused", "swf_plan_split",
+           "swf_fields_fused", "swf_plan_split", "swf_fused_status", "swf_set_fused_drop",
            "swf_set_tolerances", "swf_march_stats", "swf_set_multi_grid", "swf_device_loop_marches",
            "swf_rhs_noalloc", "swf_mlp_param_count", "swf_mlp_create",
            "swf_mlp_destroy", "swf_mlp_forward", "swf_mlp_activation", "swf_mlp_status", "swf_mlp_gradients", "swf_mlp_train_step",
@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH):
     lib.swf_set_workspace_limit.argtypes = [vp, C.c_size_t]
     lib.swf_profile_enable.argtypes = [vp, ip]
     lib.swf_set_march_path.argtypes = [vp, ip]
+    lib.swf_fused_status.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.swf_set_fused_drop.argtypes = [vp, ip]
     lib.swf_set_autotune.argtypes = [vp, ip]
     lib.swf_set_dedupe.argtypes = [vp, ip]
     lib.swf_set_multi_grid.argtypes = [vp, ip]
@@ -231,6 +233,16 @@ class Context:
         1 = pass kernels only, 2 = the automatic fused kernel for every field, 3 = two CTAs per SM,
         4 = transposes pulled by the threads, 5 = transposes pushed by the bulk-copy engine."""
         _check(_lib.swf_set_march_path(self._h, int(path)))
+
+    def fused_status(self) -> int:
+        """swf_fused_status: 1 if a receive wait of the last pushed-transpose fused march ran out."""
+        s = C.c_int(0)
+        _check(_lib.swf_fused_status(self._h, C.byref(s)))
+        return s.value
+
+    def set_fused_drop(self, on: bool):
+        """swf_set_fused_drop (diagnostic): the pushed-transpose fused kernel issues no copies."""
+        _check(_lib.swf_set_fused_drop(self._h, 1 if on else 0))
 
     def set_tolerances(self, rtol, atol):
         """Tolerances of step-size-controlled marches (flag "adaptive")."""

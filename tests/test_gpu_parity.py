@@ -311,6 +311,39 @@ def test_pushed_transposes_match_pulled_transposes(env):
         assert rel_state(got[i], ref) < 2e-5, (i, rel_state(got[i], ref))
 
 
+def test_fused_receive_waits_are_bounded(env):
+    """The pushed-transpose fused kernel's receive waits end by themselves.  With its copies
+    switched off (swf_set_fused_drop), every CTA's first receive wait runs out after about half
+    a second.  The kernel still ends, reports status 1 and writes NaN for every sector.  The same
+    context marches normally again afterwards, with status 0."""
+    import time
+    torch, swf, _ = env
+    ds = _fused_cases(n_steps=2)[:4]
+    insts = [swf.from_workload(d) for d in ds]
+    N = 256 * 256
+    ctx = swf.Context(0)
+    try:
+        ctx.set_dedupe(False)
+        ctx.set_march_path(5)
+        out = torch.zeros(len(ds) * 8 * N, dtype=torch.float32, device="cuda")
+        ctx.set_fused_drop(True)
+        t0 = time.perf_counter()
+        ctx.march_dev(insts, out, bg=0, prec=swf.C64)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        assert ctx.fused_status() == 1
+        assert torch.isnan(out).all().item(), "every sector of a march whose waits ran out is NaN"
+        assert dt < 60.0, dt
+        ctx.set_fused_drop(False)
+        out.zero_()
+        ctx.march_dev(insts, out, bg=0, prec=swf.C64)
+        torch.cuda.synchronize()
+        assert ctx.fused_status() == 0
+        assert torch.isfinite(out).all().item()
+    finally:
+        ctx.close()
+
+
 def test_split_march_is_fused_plus_pass_kernels(env):
     """A large fused march gives its last fields to the pass kernels, run concurrently on the SMs
     the 16-CTA clusters leave free: the result is bit for bit the fused-only march on the first
