@@ -79,6 +79,10 @@ def test_errors_without_device(lib):
     assert lib.solve_swf(None, 1, arr, 0, 1, res, None) == swf.SWF_EINVAL
     assert b"ctx is NULL" in lib.swf_last_error()
     assert lib.swf_destroy(None) == swf.SWF_OK
+    # the fused kernel's status and its diagnostic switch reject a NULL context or output
+    status = C.c_int(7)
+    assert lib.swf_fused_status(None, C.byref(status)) == swf.SWF_EINVAL
+    assert lib.swf_set_fused_drop(None, 1) == swf.SWF_EINVAL
 
 
 def test_split_plan_of_fused_marches(lib):
