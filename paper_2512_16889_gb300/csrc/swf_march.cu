@@ -605,8 +605,10 @@ __device__ __forceinline__ void first_body(const StageArgs<R>& A, int bx, int f,
   }
 }
 
+// The x-pass kernels are held to 64 registers in complex64 (no spills), so that four 256-thread
+// blocks fit an SM when the tuner picks a shape of at most 56 KB of shared memory.
 template <typename R>
-__global__ void __launch_bounds__(256) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_first(StageArgs<R> A, int rows, int ld, int only_x) {
   first_body<R>(A, blockIdx.x, blockIdx.y, rows, ld, only_x);
 }
 
@@ -732,7 +734,7 @@ __device__ __forceinline__ void last_body(const StageArgs<R>& A, int bx, int f, 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_last(StageArgs<R> A, int rows, int ld) {
   last_body<R>(A, blockIdx.x, blockIdx.y, rows, ld);
 }
 
@@ -741,7 +743,7 @@ __global__ void __launch_bounds__(256) k_last(StageArgs<R> A, int rows, int ld) 
 // the same rows.  Each thread reads back the k_i entries it has just written (the two bodies map
 // the rows' entries to threads alike), so the arithmetic is that of k_last then k_first.
 template <typename R>
-__global__ void __launch_bounds__(256) k_last_first(StageArgs<R> P, StageArgs<R> Nx, int rows, int ld) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_last_first(StageArgs<R> P, StageArgs<R> Nx, int rows, int ld) {
   last_body<R>(P, blockIdx.x, blockIdx.y, rows, ld);
   __syncthreads();
   first_body<R>(Nx, blockIdx.x, blockIdx.y, rows, ld, 0);
