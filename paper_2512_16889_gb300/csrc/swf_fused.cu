@@ -15,6 +15,9 @@
 // Two shared buffers (rows, columns) make each transpose a single pull after one barrier.
 // The 256-point FFTs are two radix-16 passes over lines padded by one element per 16 (and one
 // more per line) so that the passes and the transposes are free of bank conflicts.
+// That is `k_fused`.  The default kernel, `k_fused3` (further below), does the same arithmetic but
+// has the bulk-copy engine push the transposes while its threads compute, and `k_fused2` runs two
+// smaller CTAs per SM.
 #include <cooperative_groups.h>
 
 #include <cstdio>
@@ -49,7 +52,8 @@ struct Args {
   const FieldDesc* fd;     // per instance
   const Sector* sec;       // per sector
   int n_sec;
-  float2* slots;           // per cluster: 9 arrays (k1..k7, stash, y low part) of 2 * NX * NY complex
+  float2* slots;           // per cluster, arrays of 2 NX NY complex: k_4..k_6 and the low part of y
+                           // (k_fused, k_fused3), or k_2..k_6, y and its low part (k_fused2)
   float2* psi_out;         // [inst][4][NY][NX] complex64
   double Lx, Ly, t_out, h;
   int n_steps;
@@ -1005,8 +1009,11 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
 // CTA's shared memory to a peer's, completing on the peer's mbarrier) instead of being pulled by
 // the threads, and the threads meanwhile do the work that needs no transposed data: the local
 // term of the stage while the forward transpose is in flight, and all but the newest term of the
-// next stage combine while the backward one is.  The arithmetic is that of `k_fused`, in the same
-// order; only the data movement differs.
+// next stage combine while the backward one is.  Lines stay in registers where one pass's outputs
+// are the next pass's inputs in the same thread: from the inverse x-FFT through k_i and the next
+// stage value into the next forward x-FFT, and from the forward y-FFT through H0 (the components
+// paired through lane ^ 16) into the inverse y-FFT.  The arithmetic is that of `k_fused`, in the
+// same order; only the data movement differs.
 //
 // Both exchange buffers are 2 x 16 chunks of 16 x 16 values: chunk (c, a) of component c holds, in
 // the row buffer X1, the 16 rows of this CTA at x in [16 a, 16 a + 16), and in the column buffer
@@ -1019,16 +1026,17 @@ __global__ void __launch_bounds__(v2::NT2, 2) k_fused2(Args A) {
 // barrier that lets the senders start, and arrives only after its previous receive completed; a
 // sender waits at that cluster barrier before it copies.  So every copy finds its destination free
 // (all copies of the previous use, and the receiver's reads, are complete) and its barrier armed.
-// Every wait is bounded: a CTA whose copies do not arrive in about half a second stops copying
-// and waiting, keeps to the cluster barriers (so that no peer is left waiting there), and writes
-// NaN for its rows of the sector, so that the failure shows in the result.
+// Every wait is bounded: a CTA whose copies do not arrive in about half a second sets the
+// launch's status word, stops copying and waiting, keeps to the cluster barriers (so that no peer
+// is left waiting there), and writes NaN for its rows of the sector, so that the failure shows in
+// the result as well.
 namespace v3 {
 constexpr int CHK = 256;                    // complex values in one chunk
 constexpr int NBUF = 2 * CL * CHK;          // complex values in one exchange buffer
 constexpr uint32_t XBYTES = NBUF * 8;       // bytes received per transpose
 constexpr int OFF_X1 = 0;                   // rows, chunk (c, x / 16), row, x % 16
 constexpr int OFF_X2 = OFF_X1 + NBUF * 8;   // columns, chunk (c, y / 16), y % 16, column
-constexpr int OFF_Y3 = OFF_X2 + NBUF * 8;   // state y [2][RB][NX]
+constexpr int OFF_Y3 = OFF_X2 + NBUF * 8;   // state y, two sites per float4 at [k2 / 2][thread]
 constexpr int OFF_TW3 = OFF_Y3 + NSL * 8;
 constexpr int OFF_EX3 = OFF_TW3 + 256 * 8;
 constexpr int OFF_GX3 = OFF_EX3 + NX * 8;
