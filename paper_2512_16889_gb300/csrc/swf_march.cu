@@ -1585,7 +1585,11 @@ static swf_status march_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double t_
   A.ynew = (cpx<R>*)pyn;
   ErrWeights W;
   for (int j = 0; j < 7; ++j) W.db[j] = DP_DB[j];
+  // the evaluations of an attempt chain through k_last_first; the attempt's last one is closed
+  // before the error estimate reads k_7
+  const bool chain = !(g.n[1] == 1 && g.n[2] == 1);
   auto attempt = [&]() -> swf_status {
+    StageArgs<R> open = A;
     for (int i = 1; i < 7; ++i) {
       int nt = 0;
       for (int j = 0; j < i; ++j) {
@@ -1598,7 +1602,13 @@ static swf_status march_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double t_
       A.write_y = (i == 6);
       A.kout = (cpx<R>*)pk[i];
       A.c = DP_C[i];
-      swf_status r = launch_eval<R>(ctx, A, F, st);
+      swf_status r = !chain ? launch_eval<R>(ctx, A, F, st)
+                            : (i == 1 ? launch_eval_open<R>(ctx, A, F, st) : launch_eval_chain<R>(ctx, open, A, F, st));
+      if (r != SWF_OK) return r;
+      open = A;
+    }
+    if (chain) {
+      swf_status r = launch_eval_close<R>(ctx, open, F, st);
       if (r != SWF_OK) return r;
     }
     {
@@ -2940,6 +2950,9 @@ static swf_status march_bw_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double
                                                    (const double*)pph, g, (const cpx<double>*)prow, clk, 0, stage,
                                                    7, 1, (cpx<double>*)ptry);
   };
+  // the evaluations of an attempt chain through k_last_first (the integrand reads only the stage
+  // values); the attempt's last one is closed before the error estimate reads k_7
+  const bool chain = !(g.n[1] == 1 && g.n[2] == 1);
   auto attempt = [&]() -> swf_status {
     cudaError_t e1 = cudaMemsetAsync(ptry, 0, sizeof(cpx<double>) * nacc, st);
     if (e1 != cudaSuccess) return cuda_status(e1, "memset attempt sums");
@@ -2948,6 +2961,7 @@ static swf_status march_bw_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double
       k_bw_attempt_rows<<<n_inst, 32, 0, st>>>(A.fd, (const double*)pph, ctl, cell, (cpx<double>*)prow);
     }
     mdot(py, 0);  // stage 1 of the step: the accepted state
+    StageArgs<R> open = A;
     for (int i = 1; i < 7; ++i) {
       int ntm = 0;
       for (int j = 0; j < i; ++j) {
@@ -2962,9 +2976,15 @@ static swf_status march_bw_adaptive_impl(swf_ctx* ctx, const GridDesc& g, double
       A.c = DP_C[i];
       const bool weighted = i >= 2 && i <= 5;  // b_2 = b_7 = 0
       A.ystage = weighted ? (cpx<R>*)pys : nullptr;
-      swf_status r = launch_eval<R>(ctx, A, F, st);
+      swf_status r = !chain ? launch_eval<R>(ctx, A, F, st)
+                            : (i == 1 ? launch_eval_open<R>(ctx, A, F, st) : launch_eval_chain<R>(ctx, open, A, F, st));
       if (r != SWF_OK) return r;
+      open = A;
       if (weighted) mdot(pys, i);
+    }
+    if (chain) {
+      swf_status r = launch_eval_close<R>(ctx, open, F, st);
+      if (r != SWF_OK) return r;
     }
     {
       ProfScope ps(ctx, "k_step_error", st);
