@@ -1354,7 +1354,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       fence_async_smem();
       __syncthreads();
       cl_wait();  // every CTA's X2 is free and its receive barrier armed
-      if (warp == 0 && !err && !A.drop)
+      if (warp == 0 && !__any_sync(0xffffffffu, err) && !A.drop)
         bulk_push(peer_addr(x2a + (uint32_t)((cc * CL + rank) * CHK * 8), peer),
                   x1a + (uint32_t)((cc * CL + peer) * CHK * 8), CHK * 8, peer_addr(bar_f, peer));
 
@@ -1393,13 +1393,13 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
         tmem_wait_st();
       }
       {
-        int bad = 0;
+        // every thread waits for the forward copies itself (no block barrier after the wait)
+        const bool bad = !err && !mbar_wait3(bar_f, par_f);
         if (tid == 0 && !err) {
-          bad = !mbar_wait3(bar_f, par_f);
           if (!bad) mbar_arm3(bar_b, XBYTES);  // for the backward transpose of this evaluation
           else if (A.status) atomicOr(A.status, 1);
         }
-        err = __syncthreads_or(bad) || err;
+        err = err || bad;
         par_f ^= 1u;
       }
       cl_arrive();  // the forward copies into this CTA are complete
@@ -1410,7 +1410,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       fence_async_smem();
       __syncthreads();
       cl_wait();  // every CTA's X1 is free and its receive barrier armed
-      if (warp == 0 && !err && !A.drop)
+      if (warp == 0 && !__any_sync(0xffffffffu, err) && !A.drop)
         bulk_push(peer_addr(x1a + (uint32_t)((cc * CL + rank) * CHK * 8), peer),
                   x2a + (uint32_t)((cc * CL + peer) * CHK * 8), CHK * 8, peer_addr(bar_b, peer));
 
@@ -1485,13 +1485,12 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
         }
       }
       {
-        int bad = 0;
+        const bool bad = !err && !mbar_wait3(bar_b, par_b);
         if (tid == 0 && !err) {
-          bad = !mbar_wait3(bar_b, par_b);
           if (!bad) mbar_arm3(bar_f, XBYTES);  // for the next forward transpose
           else if (A.status) atomicOr(A.status, 1);
         }
-        err = __syncthreads_or(bad) || err;
+        err = err || bad;
         par_b ^= 1u;
       }
       cl_arrive();  // the backward copies into this CTA are complete
@@ -1546,6 +1545,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused3(Args A) {
       }
     }
     // psi(t_in) of the sector into the 4-component output (NaN if a transpose failed)
+    err = __syncthreads_or(err);
     {
       const float2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
       float2* out = A.psi_out + ((size_t)S.inst * 4 + (oc ? S.c1 : S.c0)) * plane + (size_t)(row0 + orow) * NX + ojj;
