@@ -467,21 +467,24 @@ def run_gpu(args):
             "whole_march_frac": 14.0 * S * site_updates / (ms_step / 1e3) / 1e9 / hbm}
     # What binds the fused kernel instead of HBM: its two transposes per evaluation through the
     # cluster network (distributed shared memory).  Per evaluation of a z-spin sector every CTA of
-    # the 16-CTA cluster pulls 15 remote 16 x 16 blocks of both components (8 B each) per
+    # the 16-CTA cluster sends 15 remote 16 x 16 blocks of both components (8 B each) per
     # transpose: 2 x 15 x 16 x 16 x 2 x 8 B = 120 KiB per CTA, 16 CTAs per sector; 2 sectors per
-    # field, 1 + 6 n_steps evaluations.  Peak: the 13 B per cycle per SM that a pull probe
-    # measured in 16-CTA clusters, on the SMs the clusters occupy, at the sampled SM clock.
+    # field, 1 + 6 n_steps evaluations.  Peak: the 13 B per cycle per SM that probes of pulls and of
+    # bulk-copy pushes measured in 16-CTA clusters, on the SMs the clusters occupy, at the sampled
+    # SM clock.
     dsm_bytes = 2 * fused_fields * (1 + 6 * 1000) * 16 * (2 * 15 * 16 * 16 * 2 * 8)
     clk_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
     dsm_peak = 13.0 * 16 * 7 * clk_hz
     roof["limiter"] = {
-        "what": "cluster network (distributed shared memory) during the two transposes per evaluation; "
-                "latency (L2 loads of the stage combine, barriers) elsewhere",
+        "what": "cluster network (distributed shared memory) during the two transposes per evaluation, "
+                "pushed by the bulk-copy engine and partly hidden behind the local term and the next stage "
+                "combine; FFT passes and block and cluster barriers elsewhere",
         "dsmem_bytes_per_launch": dsm_bytes,
         "dsmem_achieved_GBps": dsm_bytes / (fused_ms / 1e3) / 1e9 if fused_ms > 0 else None,
         "dsmem_peak_GBps": dsm_peak / 1e9,
         "dsmem_frac": dsm_bytes / (fused_ms / 1e3) / dsm_peak if fused_ms > 0 else None,
-        "peak_kind": "measured probe: 13 B/clk/SM pulled within a 16-CTA cluster, x 112 SMs x sampled SM clock"}
+        "peak_kind": "measured probe: 13 B/clk/SM within a 16-CTA cluster (pulls and bulk-copy pushes alike), "
+                     "x 112 SMs x sampled SM clock"}
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     # FFT flops alongside: 5 N log2 N per complex transform, 8 transforms (4 components forward
     # and back) per evaluation, 6 evaluations per FSAL step; FP32 lane peak = SMs x 128 lanes x
