@@ -216,8 +216,8 @@ swf_status swf_profile_read(swf_ctx* ctx, int max_entries, char* names, double* 
 /* March path selection: 0 = automatic (the fused cluster kernel for (2+1)D 256 x 256
  * complex64 marches that keep the z-spin sectors apart, the pass kernels otherwise; a large
  * fused march gives some of its fields to the pass kernels, run concurrently on the SMs that the
- * 16-CTA clusters leave free), 1 = pass kernels only, 2 = the fused kernel of path 0 for every
- * field, 3 = fused kernel with two CTAs per SM, 4 = fused kernel whose threads pull the two
+ * 16-CTA clusters leave free), 1 = pass kernels only, 2 = the fused kernel of path 0 (the
+ * pushed-transpose kernel of path 5) for every field, 3 = fused kernel with two CTAs per SM, 4 = fused kernel whose threads pull the two
  * transposes of an evaluation through distributed shared memory, 5 = fused kernel whose
  * transposes are pushed by the bulk-copy engine while the threads compute (2 to 5 still fall back
  * to the pass kernels where the fused kernel does not apply).  All fused variants give the same
