@@ -228,7 +228,7 @@ swf_status swf_set_march_path(swf_ctx* ctx, int path);
  * and 5): *status = 0 when every transpose arrived, 1 when a CTA's receive wait ran out (after
  * about half a second), in which case that CTA stopped copying and wrote NaN for its rows while
  * keeping to the cluster's barriers, so the kernel still ended.  Synchronises the context's
- * stream.  0 if no such march has run. */
+ * device (the march may have run on a caller's stream).  0 if no such march has run. */
 swf_status swf_fused_status(swf_ctx* ctx, int* status);
 /* Diagnostic for the bounded waits above: on = 1 makes the pushed-transpose kernel issue none of
  * its transposes, so that every receive wait runs out (tests only; default 0). */

@@ -886,7 +886,9 @@ swf_status swf_fused_status(swf_ctx* ctx, int* status) {
   if (!ctx || !status) { set_error("swf_fused_status: NULL argument"); return SWF_EINVAL; }
   *status = 0;
   if (!ctx->fused_status_dev) return SWF_OK;
-  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  // the march may have run on a caller's stream (swf_march_dev, solve_swf_dev): wait for the device
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(status, ctx->fused_status_dev, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_status(e, "read the fused kernel's status");
   return SWF_OK;
